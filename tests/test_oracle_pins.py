@@ -1,0 +1,485 @@
+"""Pins of the FP64 oracle against things other than itself.
+
+Each test ties one part of the oracle to a fact fixed by the paper or by
+mathematics: a dense KKT solve of the tree QP (an independent
+formulation), exact constraint satisfaction, brute-force minimisation of
+the prox objectives, the Moreau identity, the theta identity of §4.3,
+symmetry/sign of the dual Hessian, a dense eigen-solve for the step size,
+scipy's SLSQP on the input-box-only problem, a vanishing duality gap
+(weak duality, eq. fenchel-dual), special cases and invariances.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from synthetic import make_problem, make_tree
+from tests.dense_kkt import kkt_dual_gradient
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+def synth(name="tiny", **cost_kw):
+    Pb = make_problem(name, **cost_kw)
+    P = O.OracleProblem.from_parts(Pb.net, Pb.cost, Pb.tree)
+    return P, Pb.data
+
+
+def random_problem(nx=3, nu=5, nd=2, ne=2, branching=(3, 1, 2, 1), seed=0,
+                   general_A=True, dense_W=True):
+    """A problem with a non-symmetric A, dense W_u, dense B/E and unequal
+    probabilities, so that a transposed or dropped operand shows up."""
+    rng = np.random.default_rng(seed)
+    tree = make_tree(list(branching), seed=seed + 1)
+    A = np.eye(nx) + (0.2 * rng.standard_normal((nx, nx)) if general_A else 0.0)
+    M = rng.standard_normal((nu, nu))
+    Wu = (M @ M.T / nu + np.eye(nu)) if dense_W else 3.0 * np.eye(nu)
+    P = O.OracleProblem(
+        A=A, B=rng.standard_normal((nx, nu)), Gd=rng.standard_normal((nx, nd)),
+        E=rng.standard_normal((ne, nu)), Ed=rng.standard_normal((ne, nd)),
+        xmin=-np.ones(nx), xmax=np.ones(nx) * 2, xs=np.zeros(nx) + 0.5,
+        umin=-np.ones(nu), umax=np.ones(nu) * 3, W_alpha=1.3,
+        alpha0=rng.uniform(0, 0.1, nu), Wu=Wu, Ws=0.7, Wx=5.0, N=tree.N,
+        stage_ptr=tree.stage_ptr, anc=tree.anc, prob=tree.prob)
+    n = P.n_nodes
+    data = dict(x0=rng.standard_normal(nx), q=rng.standard_normal(nu),
+                demand=rng.standard_normal((n, nd)), alpha=rng.uniform(0, 1, (n, nu)))
+    return P, data
+
+
+def consts(P, F, data):
+    if isinstance(data, dict):
+        return O.solve_consts(P, F, data["x0"], data["q"], data["demand"], data["alpha"])
+    return O.solve_consts(P, F, data.x0, data.q, data.demand, data.alpha)
+
+
+def raw(data):
+    if isinstance(data, dict):
+        return data["x0"], data["q"], data["demand"], data["alpha"]
+    return data.x0, data.q, data.demand, data.alpha
+
+
+# ---------------------------------------------------------------------------
+# theta / beta (§4.3)
+# ---------------------------------------------------------------------------
+def test_theta_meets_requirement_with_equality():
+    beta, theta = O.theta_beta(3000)
+    assert beta[0] == 0.0 and beta[1] == 0.0      # theta_0 = theta_{-1} = 1
+    lhs = 1.0 - theta[1:]
+    rhs = theta[1:] ** 2 / theta[:-1] ** 2
+    assert np.max(np.abs(lhs - rhs)) < 1e-15
+    # the rule behaves like 2/(nu+2) for large nu and beta -> 1
+    assert abs(theta[3000] * 3000 / 2.0 - 1.0) < 0.01
+    assert 0.99 < beta[-1] < 1.0
+    assert np.all(np.diff(beta[1:]) > 0)
+
+
+# ---------------------------------------------------------------------------
+# proximal operators (§4.2-§4.3)
+# ---------------------------------------------------------------------------
+def _grid_min(fun, center, half=3.0, h=0.004):
+    g = np.arange(-half, half + h / 2, h)
+    X, Y = np.meshgrid(center[0] + g, center[1] + g, indexing="ij")
+    pts = np.stack([X.ravel(), Y.ravel()], axis=1)
+    vals = fun(pts)
+    return pts[np.argmin(vals)]
+
+
+@pytest.mark.parametrize("kind", ["box", "halfline"])
+def test_prox_dist_matches_bruteforce_2d(kind):
+    rng = np.random.default_rng(11 if kind == "box" else 12)
+    lo, hi = np.array([-0.5, 0.2]), np.array([0.7, 1.1])
+    if kind == "box":
+        proj = lambda z: O.smpc.proj_box(z, lo, hi)
+    else:
+        proj = lambda z: np.maximum(z, lo)
+    for _ in range(12):
+        v = rng.uniform(-2.5, 2.5, 2)
+        lam = rng.uniform(0.0, 2.0)
+        fun = lambda X: lam * np.linalg.norm(X - proj(X), axis=1) + 0.5 * np.sum((X - v) ** 2, axis=1)
+        best = _grid_min(fun, v)
+        got = O.prox_dist(v[None, :], lam, proj)[0]
+        assert np.linalg.norm(got - best) < 0.012, (v, lam, got, best)
+        # the closed form is a minimiser: its value is not above the grid's
+        assert fun(got[None])[0] <= fun(best[None])[0] + 1e-12
+
+
+def test_prox_dist_special_cases():
+    rng = np.random.default_rng(3)
+    lo, hi = -np.ones(4), np.ones(4)
+    proj = lambda z: O.smpc.proj_box(z, lo, hi)
+    v = rng.uniform(-3, 3, (50, 4))
+    # lam = 0: the prox of the zero function is the identity
+    assert np.array_equal(O.prox_dist(v, 0.0, proj), v)
+    # points of C are fixed points
+    inside = rng.uniform(-1, 1, (50, 4))
+    assert np.allclose(O.prox_dist(inside, 0.8, proj), inside, atol=0, rtol=0)
+    # lam >= dist: the prox lands on C (projection)
+    assert np.allclose(O.prox_dist(v, 100.0, proj), proj(v))
+    # lam < dist: moves exactly lam towards C along v - proj(v)
+    far = v[np.linalg.norm(v - proj(v), axis=1) > 0.5]
+    t = O.prox_dist(far, 0.3, proj)
+    assert np.allclose(np.linalg.norm(far - t, axis=1), 0.3)
+
+
+def _single_node_problem(nx=2, nu=1, Wx=1.3, Ws=0.6):
+    tree = make_tree([1], seed=0)
+    return O.OracleProblem(
+        A=np.eye(nx), B=np.zeros((nx, nu)), Gd=np.zeros((nx, 1)), E=np.zeros((0, nu)),
+        Ed=np.zeros((0, 1)), xmin=np.array([-0.5, 0.2])[:nx], xmax=np.array([0.7, 1.1])[:nx],
+        xs=np.array([0.1, -0.3])[:nx], umin=-np.ones(nu) * 0.4, umax=np.ones(nu) * 0.9,
+        W_alpha=1.0, alpha0=np.zeros(nu), Wu=np.eye(nu), Ws=Ws, Wx=Wx, N=1,
+        stage_ptr=tree.stage_ptr, anc=tree.anc, prob=tree.prob)
+
+
+def _check_strongly_convex_min(fun, y, best):
+    """fun is 1-strongly convex: fun(b) - fun(y*) >= |b - y*|^2 / 2, so the
+    true minimiser y* must beat the grid's best point b and lie within
+    sqrt(2 (fun(b) - fun(y*))) of it."""
+    fy, fb = fun(y[None])[0], fun(best[None])[0]
+    assert np.isfinite(fy)
+    assert fy <= fb + 1e-10
+    assert np.linalg.norm(y - best) <= np.sqrt(2.0 * max(fb - fy, 0.0)) + 1e-6
+
+
+def test_dual_update_is_prox_of_conjugate_bruteforce():
+    """prox_{gamma g*} evaluated through the Moreau decomposition equals a
+    brute-force minimisation of gamma g*(y) + 1/2 |y - z|^2 with the
+    conjugates written out: g1* = sigma_[xmin,xmax] + indicator(|y| <= W_x),
+    g2* = <., x_s> + indicator(y <= 0, |y| <= W_s), g3* = sigma_U."""
+    P = _single_node_problem()
+    rng = np.random.default_rng(5)
+    slack = 1 + 1e-12
+    for _ in range(8):
+        gamma = rng.uniform(0.3, 2.0)
+        z = np.zeros((2, P.ny))
+        z[1] = rng.uniform(-3, 3, P.ny)
+        y, _ = O.prox_gstar(P, z, gamma)
+        # block 1
+        def f1(Y):
+            sig = np.sum(np.maximum(Y * P.xmax, Y * P.xmin), axis=1)
+            pen = np.where(np.linalg.norm(Y, axis=1) <= P.Wx * slack, 0.0, np.inf)
+            return gamma * sig + pen + 0.5 * np.sum((Y - z[1, :2]) ** 2, axis=1)
+        _check_strongly_convex_min(f1, y[1, :2], _grid_min(f1, np.zeros(2), half=P.Wx + 0.01, h=0.003))
+        # block 2
+        def f2(Y):
+            ok = (np.linalg.norm(Y, axis=1) <= P.Ws * slack) & np.all(Y <= 0, axis=1)
+            return np.where(ok, gamma * (Y @ P.xs), np.inf) + 0.5 * np.sum((Y - z[1, 2:4]) ** 2, axis=1)
+        _check_strongly_convex_min(f2, y[1, 2:4], _grid_min(f2, np.zeros(2), half=P.Ws + 0.01, h=0.002))
+        # block 3 (1-D)
+        g = np.linspace(-6, 6, 240001)
+        f3 = gamma * np.maximum(g * P.umax[0], g * P.umin[0]) + 0.5 * (g - z[1, 4]) ** 2
+        assert abs(y[1, 4] - g[np.argmin(f3)]) < 1e-4
+
+
+def test_moreau_identity_numerically():
+    """prox_{gamma g}(v) + gamma prox_{g*/gamma}(v/gamma) = v with both
+    proxes evaluated by brute force on a grid, compared with the oracle's
+    distance prox (block 1, 2-D)."""
+    P = _single_node_problem()
+    rng = np.random.default_rng(9)
+    proj = lambda z: O.smpc.proj_box(z, P.xmin, P.xmax)
+    for _ in range(6):
+        gamma = rng.uniform(0.4, 1.5)
+        v = rng.uniform(-2.5, 2.5, 2)
+        p1 = O.prox_dist(v[None], gamma * P.Wx, proj)[0]
+        def fc(Y):  # (1/gamma) g1*(Y) + 1/2 |Y - v/gamma|^2
+            sig = np.sum(np.maximum(Y * P.xmax, Y * P.xmin), axis=1)
+            pen = np.where(np.linalg.norm(Y, axis=1) <= P.Wx * (1 + 1e-12), 0.0, np.inf)
+            return sig / gamma + pen + 0.5 * np.sum((Y - v / gamma) ** 2, axis=1)
+        # the identity fixes prox_{g*/gamma}(v/gamma) = (v - p1)/gamma; that
+        # point must minimise the conjugate's prox objective
+        p2 = (v - p1) / gamma
+        _check_strongly_convex_min(fc, p2, _grid_min(fc, np.zeros(2), half=P.Wx + 0.01, h=0.003))
+
+
+# ---------------------------------------------------------------------------
+# dual gradient (§4.4) against a dense KKT solve
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("case", ["tiny", "random_general", "random_single_scenario",
+                                  "random_no_coupling"])
+@pytest.mark.parametrize("constants", [True, False])
+def test_dual_gradient_matches_dense_kkt(case, constants):
+    if case == "tiny":
+        P, data = synth("tiny")
+    elif case == "random_general":
+        P, data = random_problem(seed=1)
+    elif case == "random_single_scenario":
+        P, data = random_problem(branching=(1, 1, 1, 1, 1), seed=2)
+    else:
+        P, data = random_problem(ne=0, branching=(2, 3, 1), seed=3)
+    F = O.factor(P)
+    S = consts(P, F, data)
+    rng = np.random.default_rng(7)
+    w = rng.standard_normal((P.n_nodes, P.ny))
+    w[0] = 0
+    u, x = O.dual_gradient(P, F, S, w, constants=constants)
+    uk, xk = kkt_dual_gradient(P, w, *raw(data), constants=constants)
+    scale = max(np.abs(uk).max(), np.abs(xk).max())
+    assert np.abs(u - uk).max() <= 1e-9 * scale
+    assert np.abs(x - xk).max() <= 1e-9 * scale
+
+
+def test_dual_gradient_satisfies_dynamics_and_coupling_exactly():
+    P, data = synth("barcelona32")
+    F = O.factor(P)
+    S = consts(P, F, data)
+    rng = np.random.default_rng(1)
+    w = 10.0 * rng.standard_normal((P.n_nodes, P.ny))
+    u, x = O.dual_gradient(P, F, S, w)
+    a = P.anc[1:]
+    dyn = x[1:] - x[a] @ P.A.T - u[1:] @ P.B.T - S.d[1:] @ P.Gd.T
+    cpl = u[1:] @ P.E.T + S.d[1:] @ P.Ed.T
+    sx = np.abs(x).max() + np.abs(u).max()
+    assert np.abs(dyn).max() <= 1e-12 * sx
+    assert np.abs(cpl).max() <= 1e-12 * (np.abs(u).max() + np.abs(S.d).max())
+    assert np.array_equal(u[0], data.q) and np.array_equal(x[0], data.x0)
+
+
+def test_dual_hessian_is_symmetric_positive_semidefinite():
+    """M v = -H x_lin(v) is the Hessian of f*(-H' .): symmetric, PSD."""
+    P, data = random_problem(seed=4)
+    F = O.factor(P)
+    rng = np.random.default_rng(2)
+    def M(v):
+        u, x = O.dual_gradient(P, F, None, v, constants=False)
+        return -O.apply_H(P, u, x)
+    for _ in range(5):
+        a = rng.standard_normal((P.n_nodes, P.ny)); a[0] = 0
+        b = rng.standard_normal((P.n_nodes, P.ny)); b[0] = 0
+        Ma, Mb = M(a), M(b)
+        assert abs(np.sum(Ma * b) - np.sum(a * Mb)) <= 1e-11 * (np.abs(Ma).sum() + np.abs(Mb).sum())
+        assert np.sum(Ma * a) >= -1e-12 * np.abs(Ma).sum()
+
+
+# ---------------------------------------------------------------------------
+# the structure that the GPU path relies on, derived from the general recursion
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("general_A", [True, False])
+def test_general_recursion_collapses_to_shared_factor(general_A):
+    """With P_c L = 0 at the leaves, induction gives 2 p Phi_nu = F shared by
+    all nodes, F = L (L'W_u L)^{-1} L' = W^-1 - W^-1 E'(E W^-1 E')^-1 E W^-1,
+    K_nu = F W_u (a projector), and (I - Phi Q) ud = -W^-1 E' S^-1 Ed d."""
+    P, data = random_problem(seed=5, general_A=general_A, branching=(3, 2, 1, 2, 1))
+    F = O.factor(P, keep_P=True)
+    Wi = np.linalg.inv(P.Wu)
+    S_ = P.E @ Wi @ P.E.T
+    Fs = Wi - Wi @ P.E.T @ np.linalg.solve(S_, P.E @ Wi)
+    Fl = F.L @ np.linalg.solve(F.L.T @ P.Wu @ F.L, F.L.T)
+    assert np.abs(Fs - Fl).max() < 1e-12 * np.abs(Fs).max()
+    K = Fs @ P.Wu
+    assert np.abs(K @ K - K).max() < 1e-12
+    for k in range(1, P.n_nodes):
+        assert np.abs(2 * P.prob[k] * F.Phi[k] - Fs).max() < 1e-10 * np.abs(Fs).max()
+        assert np.abs(F.K[k] - K).max() < 1e-10
+        assert np.abs(F.Pm[k] @ F.L).max() < 1e-10 * np.abs(F.Pm[k]).max()
+    S = consts(P, F, data)
+    ubar = -(S.d @ P.Ed.T) @ np.linalg.solve(S_, P.E @ Wi)
+    assert np.abs(S.mc[1:] - ubar[1:]).max() < 1e-10 * np.abs(ubar).max()
+
+
+# ---------------------------------------------------------------------------
+# step size
+# ---------------------------------------------------------------------------
+def test_power_iteration_matches_dense_eigensolve():
+    P, _ = synth("tiny")
+    F = O.factor(P)
+    n, ny = P.n_nodes, P.ny
+    cols = []
+    for k in range(1, n):
+        for j in range(ny):
+            v = np.zeros((n, ny)); v[k, j] = 1.0
+            u, x = O.dual_gradient(P, F, None, v, constants=False)
+            cols.append(-O.apply_H(P, u, x)[1:].ravel())
+    M = np.array(cols).T
+    assert np.abs(M - M.T).max() < 1e-10 * np.abs(M).max()
+    lmax = np.linalg.eigvalsh(0.5 * (M + M.T)).max()
+    L200 = O.power_iteration(P, F, 200)
+    L2000 = O.power_iteration(P, F, 2000)
+    assert L200 <= lmax * (1 + 1e-12)
+    assert L200 >= 0.999 * lmax
+    assert abs(L2000 - lmax) <= 1e-9 * lmax
+
+
+def test_splitmix64_reference_values():
+    """First outputs of SplitMix64 seeded with 0 (published test vector)."""
+    ref = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    got = O.splitmix64_unit(np.arange(3), 0)
+    assert np.array_equal(got, np.array([(r >> 11) * 2.0 ** -53 for r in ref]))
+
+
+# ---------------------------------------------------------------------------
+# full APG: optimality certificates and special cases
+# ---------------------------------------------------------------------------
+def _run(P, data, iters, **kw):
+    F = O.factor(P)
+    S = consts(P, F, data)
+    gamma = O.step_size(O.power_iteration(P, F, 200))
+    R = O.apg(P, F, S, iters, gamma, **kw)
+    return F, S, R
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("Ws", [0.1, 20.0])
+def test_duality_gap_vanishes(Ws):
+    P, data = synth("tiny", Ws=Ws)
+    if Ws > 1:
+        P.xs = 0.75 * P.xmax  # tanks start below the safety level
+    F, S, R = _run(P, data, 6000)
+    pc = O.primal_cost(P, S, R.u, R.x)
+    dv = O.dual_value(P, F, S, R.y)
+    assert np.isfinite(dv)
+    assert abs(pc - dv) <= 2e-5 * abs(pc)
+    assert R.residual < (1e-4 if Ws < 1 else 1e-3)
+    # weak duality holds for every dual point: D(y) <= P at the optimum
+    nx = P.nx
+    y1, y2 = R.y[1:, :nx], R.y[1:, nx:2 * nx]
+    assert np.all(np.linalg.norm(y1, axis=1) <= P.Wx * (1 + 1e-12))
+    assert np.all(y2 <= 0.0)
+    assert np.all(np.linalg.norm(y2, axis=1) <= P.Ws * (1 + 1e-12))
+    if Ws > 1:
+        assert np.abs(y2).max() > 0  # the safety prox is active in this variant
+
+
+def test_g_zero_gives_unconstrained_tree_qp():
+    P, data = synth("tiny")
+    P.Wx = 0.0
+    P.Ws = 0.0
+    P.umin = np.full(P.nu, -np.inf)
+    P.umax = np.full(P.nu, np.inf)
+    F, S, R = _run(P, data, 3)
+    assert np.all(R.y == 0.0)
+    uk, xk = kkt_dual_gradient(P, np.zeros((P.n_nodes, P.ny)), *raw(data))
+    assert np.abs(R.u - uk).max() <= 1e-10 * np.abs(uk).max()
+    assert np.abs(R.x - xk).max() <= 1e-10 * np.abs(xk).max()
+
+
+@pytest.mark.slow
+def test_input_box_only_matches_scipy_qp():
+    """W_x = W_s = 0 leaves a convex QP in u: probability-weighted linear
+    and smoothing cost, couplings per node and the box U; solved by SLSQP
+    on the stacked inputs (no tree recursion, no duality)."""
+    from scipy.optimize import minimize
+    P, data = synth("tiny")
+    P.Wx = 0.0
+    P.Ws = 0.0
+    F, S, R = _run(P, data, 20000)
+    n, nu, m = P.n_nodes, P.nu, P.n_nodes - 1
+
+    def obj(z):
+        u = np.vstack([S.q, z.reshape(m, nu)])
+        du = u[1:] - u[P.anc[1:]]
+        f = np.sum(S.c0[1:] * u[1:]) + np.sum(P.prob[1:] * np.einsum("ni,ij,nj->n", du, P.Wu, du))
+        gd = 2 * P.prob[1:, None] * (du @ P.Wu)
+        G = np.zeros((n, nu))
+        G[1:] += gd
+        np.add.at(G, P.anc[1:], -gd)
+        return f, (S.c0[1:] + G[1:]).ravel()
+
+    Aeq = np.zeros((m * P.ne, m * nu))
+    beq = np.zeros(m * P.ne)
+    for k in range(1, n):
+        Aeq[(k - 1) * P.ne:k * P.ne, (k - 1) * nu:k * nu] = P.E
+        beq[(k - 1) * P.ne:k * P.ne] = -P.Ed @ S.d[k]
+    bounds = [(P.umin[j % nu], P.umax[j % nu]) for j in range(m * nu)]
+    res = minimize(obj, np.tile(np.clip(S.q, P.umin, P.umax), m), jac=True, method="SLSQP",
+                   bounds=bounds, constraints=[dict(type="eq", fun=lambda z: Aeq @ z - beq,
+                                                    jac=lambda z: Aeq)],
+                   options=dict(ftol=1e-15, maxiter=2000))
+    assert res.success
+    us = res.x.reshape(m, nu)
+    assert np.abs(R.u[1:] - us).max() <= 1e-6 * np.abs(us).max()
+    assert abs(O.primal_cost(P, S, R.u, R.x) - res.fun) <= 1e-7 * abs(res.fun)
+
+
+def test_single_scenario_is_deterministic_mpc():
+    P, data = random_problem(branching=(1,) * 6, seed=6, general_A=False)
+    F, S, R = _run(P, data, 4000)
+    assert np.allclose(P.prob, 1.0)
+    pc = O.primal_cost(P, S, R.u, R.x)
+    dv = O.dual_value(P, F, S, R.y)
+    assert abs(pc - dv) <= 1e-4 * abs(pc)
+
+
+def _swap_subtrees(P, data):
+    """Relabel the tiny tree so that the two stage-1 subtrees trade places
+    (breadth-first numbering kept)."""
+    t = P.stage
+    order = []
+    for s in range(P.N + 1):
+        sl = t(s)
+        idx = list(range(sl.start, sl.stop))
+        if s >= 1:
+            half = len(idx) // 2
+            idx = idx[half:] + idx[:half]
+        order += idx
+    order = np.array(order)
+    inv = np.empty_like(order)
+    inv[order] = np.arange(len(order))
+    Q = O.OracleProblem(**{k: getattr(P, k) for k in P.__dataclass_fields__})
+    Q.anc = np.where(P.anc[order] >= 0, inv[np.maximum(P.anc[order], 0)], -1)
+    Q.prob = P.prob[order]
+    d2 = dict(x0=data.x0, q=data.q, demand=data.demand[order], alpha=data.alpha[order])
+    return Q, d2, order
+
+
+def test_sibling_permutation_permutes_results():
+    P, data = synth("tiny")
+    Q, d2, order = _swap_subtrees(P, data)
+    assert np.all(Q.anc[1:] >= 0) and np.all(np.diff(Q.anc[1:]) >= 0)
+    F1 = O.factor(P)
+    F2 = O.factor(Q)
+    gamma = O.step_size(O.power_iteration(P, F1, 200))
+    R1 = O.apg(P, F1, consts(P, F1, data), 300, gamma)
+    R2 = O.apg(Q, F2, consts(Q, F2, d2), 300, gamma)
+    assert np.allclose(R2.u, R1.u[order], rtol=1e-12, atol=1e-12 * np.abs(R1.u).max())
+    assert np.allclose(R2.y, R1.y[order], rtol=1e-10, atol=1e-10 * np.abs(R1.y).max())
+
+
+def test_cost_scaling_invariance():
+    """All weights times kappa: the Lipschitz constant drops by kappa, the
+    step grows by kappa, the primal iterates are unchanged and the duals
+    scale by kappa."""
+    kappa = 7.25
+    P, data = synth("tiny", Ws=3.0)
+    Q = O.OracleProblem(**{k: getattr(P, k) for k in P.__dataclass_fields__})
+    Q.W_alpha *= kappa
+    Q.Wu = P.Wu * kappa
+    Q.Ws *= kappa
+    Q.Wx *= kappa
+    F1, F2 = O.factor(P), O.factor(Q)
+    L1, L2 = O.power_iteration(P, F1, 200), O.power_iteration(Q, F2, 200)
+    assert abs(L1 / L2 - kappa) <= 1e-10 * kappa
+    g1 = O.step_size(L1)
+    R1 = O.apg(P, F1, consts(P, F1, data), 400, g1)
+    R2 = O.apg(Q, F2, consts(Q, F2, data), 400, g1 * kappa)
+    assert np.abs(R2.x - R1.x).max() <= 1e-9 * np.abs(R1.x).max()
+    assert np.abs(R2.u - R1.u).max() <= 1e-9 * np.abs(R1.u).max()
+    assert np.abs(R2.y - kappa * R1.y).max() <= 1e-9 * kappa * np.abs(R1.y).max()
+
+
+def test_paper_variable_counts_fix_the_node_layout():
+    """§6.3: at 631 scenarios the problem has 2,306,133 primal and
+    3,126,960 dual variables.  Both are whole multiples of the per-node
+    sizes n_x + n_u = 177 and 2 n_x + n_u = 240 for one and the same node
+    count: every non-root node carries (u, x) and one dual block."""
+    with open(os.path.join(GOLDEN, "paper_counts.json")) as f:
+        g = json.load(f)
+    nx, nu = g["nx"], g["nu"]
+    assert g["primal_variables"] % (nx + nu) == 0
+    assert g["dual_variables"] % (2 * nx + nu) == 0
+    nodes = g["primal_variables"] // (nx + nu)
+    assert nodes == g["dual_variables"] // (2 * nx + nu)
+    assert nodes > g["scenarios"] * 1  # more nodes than leaves
+    # the oracle's layout has exactly these per-node sizes
+    P, data = synth("barcelona32")
+    assert (P.nx, P.nu) == (nx, nu)
+    F = O.factor(P)
+    u, x = O.dual_gradient(P, F, consts(P, F, data), np.zeros((P.n_nodes, P.ny)))
+    assert u.shape[1] + x.shape[1] == nx + nu
+    assert O.apply_H(P, u, x).shape[1] == 2 * nx + nu
