@@ -1,0 +1,193 @@
+/*
+ * rapidnet.h -- C ABI of a GB300 (sm_103a) solver for scenario-based
+ * stochastic MPC of drinking-water networks by the accelerated proximal
+ * gradient method on the Fenchel dual (Sopasakis, Sampathirao, Bemporad,
+ * Patrinos, "Uncertainty-aware demand management of water distribution
+ * networks in deregulated energy markets", arXiv 1904.10548).
+ *
+ * Problem (paper §3.2, eq. SMPC): on a scenario tree with stages 0..N,
+ * every non-root node nu carries an input u_nu (n_u) and a state x_nu
+ * (n_x) with
+ *     x_nu = A x_a(nu) + B u_nu + Gd d_nu      (eq. dynamics:tree)
+ *     E u_nu + Ed d_nu = 0                     (eq. input-disturbance-coupling)
+ *     umin <= u_nu <= umax                     (eq. input-constraints)
+ * and the cost
+ *     sum_nu p_nu [ W_alpha (alpha0 + alpha_nu)' u_nu + du' W_u du ]
+ *   + sum_nu W_x dist(x_nu | [xmin, xmax]) + W_s dist(x_nu | [x_s, inf)),
+ * du = u_nu - u_a(nu), with the root fixed at x_0 = p and u_{-1} = q.
+ * The dual is solved by eqs. apg:1 / apg:2 (§4.3); the dual gradient is
+ * a backward/forward recursion over the tree (§4.4).
+ *
+ * Conventions for every call:
+ *   - matrices are dense, row-major, double precision, on the HOST;
+ *   - nodes are numbered breadth first (node 0 = root, the nodes of stage
+ *     t are [stage_ptr[t], stage_ptr[t+1]), children of a node contiguous);
+ *   - per-node arrays are node-major: row nu holds node nu's vector;
+ *   - the library never keeps a caller pointer past the call; what it
+ *     needs is copied;
+ *   - every call returns an rn_status; no call aborts, exits or throws;
+ *     rapidnet_last_error() describes the last failure of this thread.
+ */
+#ifndef RAPIDNET_H
+#define RAPIDNET_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RN_OK = 0,
+  RN_NOT_CONVERGED = 1,   /* max_iters reached; outputs are valid */
+  RN_ERR_INVAL = -1,      /* an argument is malformed (see last error) */
+  RN_ERR_RANK = -2,       /* E does not have full row rank */
+  RN_ERR_CUDA = -3,       /* a CUDA call failed */
+  RN_ERR_TIMEOUT = -4,    /* a device-side wait gave up (bounded spin) */
+  RN_ERR_NOMEM = -5,      /* device memory could not be obtained */
+  RN_ERR_UNSUPPORTED = -6,/* valid input outside what this build handles */
+  RN_ERR_DIVERGED = -7    /* the residual became NaN or infinite */
+} rn_status;
+
+typedef enum {
+  RN_PREC_FP64 = 0,       /* every step of the iteration in FP64 */
+  RN_PREC_MIXED = 1       /* FP32 iteration around an FP64 reference point */
+} rn_precision;
+
+/* Water network, paper §2.1 (eqs. dynamics, input-disturbance-coupling,
+ * state-constraints, input-constraints).  Shapes: A nx*nx, B nx*nu,
+ * Gd nx*nd, E ne*nu, Ed ne*nd; xmin, xmax, xs: nx; umin, umax: nu.
+ * ne may be 0 (then E, Ed may be NULL).  This build requires A = I (the
+ * exact discretisation of the tank mass balance, eq. tank-dynamics);
+ * other A give RN_ERR_UNSUPPORTED. */
+typedef struct {
+  int nx, nu, nd, ne;
+  const double *A, *B, *Gd, *E, *Ed;
+  const double *xmin, *xmax, *xs, *umin, *umax;
+} rn_network;
+
+/* Scenario tree, paper §2.3 (Fig. "tree"): N stages after the root,
+ * stage_ptr has N+2 entries, anc[0] = -1, anc[nu] < nu is the ancestor,
+ * prob[nu] the probability of reaching nu (prob[0] = 1).  Validated: the
+ * children of every node are contiguous and in parent order, their
+ * probabilities sum to the parent's (relative 1e-9), every node before
+ * stage N has a child, all leaves are at stage N. */
+typedef struct {
+  int N, n_nodes;
+  const int *stage_ptr;
+  const int *anc;
+  const double *prob;
+} rn_tree;
+
+/* Cost weights, paper §3.1 (eqs. cost:linear, cost:smooth,
+ * cost:non-smooth): W_alpha > 0, alpha0 (nu), W_u (nu*nu, symmetric
+ * positive definite), W_s >= 0, W_x >= 0.  This build requires a
+ * diagonal W_u (the paper's choice W_u = w I); a dense W_u gives
+ * RN_ERR_UNSUPPORTED.  W_u not positive definite gives RN_ERR_INVAL. */
+typedef struct {
+  double W_alpha;
+  const double *alpha0;
+  const double *Wu;
+  double Ws, Wx;
+} rn_cost;
+
+/* Options of the factor step.  Zero-initialise for the defaults. */
+typedef struct {
+  int device;          /* CUDA device ordinal */
+  void *stream;        /* cudaStream_t for all work of this handle; NULL =
+                          a stream owned by the handle */
+  int precision;       /* rn_precision */
+  double gamma;        /* APG step; 0 = 1 / (1.01 L) with L from power
+                          iteration on the dual Hessian */
+  int power_iters;     /* 0 = 200 */
+  int check_every;     /* residual test every k iterations; 0 = 10 */
+  int refresh_every;   /* RN_PREC_MIXED: FP64 reference refresh period;
+                          0 = 20 */
+  int max_ctas;        /* cap on the persistent grid; 0 = device maximum */
+} rn_opts;
+
+/* Output of a solve.  The caller allocates u (n_nodes*nu), x (n_nodes*nx)
+ * and y (n_nodes*(2 nx + nu)) in the memory space of the call (host for
+ * rapidnet_solve, device for rapidnet_solve_device); res_hist (may be
+ * NULL) receives one residual per check, at most res_hist_len.  Root
+ * rows: u = q, x = x0, y = 0. */
+typedef struct {
+  double *u, *x, *y;
+  double *res_hist;
+  int res_hist_len;
+  int compute_gap;     /* nonzero: also evaluate the duality gap (one more
+                          dual-gradient evaluation) */
+  /* filled by the call */
+  int iters;           /* APG iterations performed */
+  int n_checks;        /* residual checks performed */
+  double primal_res;   /* |H x*(w) - t|_inf of the last iteration */
+  double ubox_viol;    /* max violation of umin <= u <= umax by u* */
+  double cost;         /* objective of eq. SMPC at (u*, x*) without the
+                          indicator of the input box */
+  double gap;          /* cost(x*(y)) - dual value at y (NaN unless
+                          compute_gap) */
+  double gamma;        /* step size used */
+} rn_result;
+
+typedef struct rn_factor rn_factor;
+
+/* Sizes and derived quantities of a factor handle. */
+typedef struct {
+  int nx, nu, nd, ne, N, n_nodes;
+  int n_chains;        /* leaves = scenarios */
+  int n_top;           /* nodes whose subtree holds more than one leaf */
+  int grid_ctas, block_threads;
+  double L;            /* power-iteration estimate of the dual Lipschitz
+                          constant (0 if gamma was given) */
+  double gamma;
+  int precision;
+  long long device_bytes;  /* device memory held by the handle */
+} rn_factor_info;
+
+/* Factor step (paper Table 2 Engine::factorStep, §4.4): validates the
+ * inputs, builds the tree schedule, the Schur complement E W_u^-1 E' and
+ * its inverse (FP64), uploads everything to the device, and, unless
+ * opts->gamma > 0, estimates the Lipschitz constant of the dual gradient
+ * by FP64 power iteration.  On success *out owns device memory until
+ * rapidnet_factor_free.  opts may be NULL (defaults). */
+int rapidnet_factor(const rn_network *net, const rn_tree *tree,
+                    const rn_cost *cost, const rn_opts *opts,
+                    rn_factor **out);
+void rapidnet_factor_free(rn_factor *f);
+int rapidnet_factor_info(const rn_factor *f, rn_factor_info *info);
+
+/* One solve (paper Table 2 SmpcController::controlAction): APG from
+ * y_warm (NULL = 0; n_nodes*(2nx+nu), also used as y^{-1}) for at most
+ * max_iters iterations, stopping at the first check with residual <= tol
+ * (tol <= 0: run exactly max_iters).  Host pointers: x0 (nx), q (nu),
+ * demand (n_nodes*nd, row 0 ignored), alpha (n_nodes*nu, row 0 ignored).
+ * Copies in and out on the handle's stream and synchronises it.
+ * Returns RN_OK (converged), RN_NOT_CONVERGED, or an error. */
+int rapidnet_solve(rn_factor *f, const double *x0, const double *q,
+                   const double *demand, const double *alpha, int max_iters,
+                   double tol, const double *y_warm, rn_result *out);
+
+/* Same as rapidnet_solve with every array argument (inputs, y_warm, and
+ * out->u, x, y, res_hist) a DEVICE pointer on the handle's device.
+ * Synchronises the handle's stream before returning (the scalars of *out
+ * are read back). */
+int rapidnet_solve_device(rn_factor *f, const double *x0, const double *q,
+                          const double *demand, const double *alpha,
+                          int max_iters, double tol, const double *y_warm,
+                          rn_result *out);
+
+/* Dual gradient x*(w) = grad f*(-H'w) (eq. dual-gradient, §4.4) for the
+ * data of the last solve, or of (x0, q, demand, alpha) when given (all
+ * device pointers, NULL = keep the last solve's data): w (n_nodes*(2nx+nu),
+ * row 0 ignored) in, u (n_nodes*nu) and x (n_nodes*nx) out, device
+ * pointers, FP64.  Synchronises the handle's stream. */
+int rapidnet_dual_gradient_device(rn_factor *f, const double *x0,
+                                  const double *q, const double *demand,
+                                  const double *alpha, const double *w,
+                                  double *u, double *x);
+
+/* Description of the last failure on the calling thread ("" if none). */
+const char *rapidnet_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RAPIDNET_H */

@@ -1,0 +1,265 @@
+"""ctypes binding of librapidnet.so (include/rapidnet.h).
+
+Argument marshalling only: every computation runs in the CUDA library.
+The module-level functions carry the C names; ``Factor`` bundles them for
+numpy (host) and torch (device) arrays.  Importing this module does not
+need a GPU; loading the library does need it to be built
+(``__graft_entry__.build()``), and a missing library is an error, never
+a fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_int, c_longlong, c_void_p
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librapidnet.so")
+
+RN_OK = 0
+RN_NOT_CONVERGED = 1
+RN_ERR_INVAL = -1
+RN_ERR_RANK = -2
+RN_ERR_CUDA = -3
+RN_ERR_TIMEOUT = -4
+RN_ERR_NOMEM = -5
+RN_ERR_UNSUPPORTED = -6
+RN_ERR_DIVERGED = -7
+RN_PREC_FP64 = 0
+RN_PREC_MIXED = 1
+
+STATUS_NAMES = {0: "RN_OK", 1: "RN_NOT_CONVERGED", -1: "RN_ERR_INVAL", -2: "RN_ERR_RANK",
+                -3: "RN_ERR_CUDA", -4: "RN_ERR_TIMEOUT", -5: "RN_ERR_NOMEM",
+                -6: "RN_ERR_UNSUPPORTED", -7: "RN_ERR_DIVERGED"}
+
+PD = POINTER(c_double)
+PI = POINTER(c_int)
+
+
+class rn_network(ctypes.Structure):
+    _fields_ = [("nx", c_int), ("nu", c_int), ("nd", c_int), ("ne", c_int),
+                ("A", PD), ("B", PD), ("Gd", PD), ("E", PD), ("Ed", PD),
+                ("xmin", PD), ("xmax", PD), ("xs", PD), ("umin", PD), ("umax", PD)]
+
+
+class rn_tree(ctypes.Structure):
+    _fields_ = [("N", c_int), ("n_nodes", c_int), ("stage_ptr", PI), ("anc", PI), ("prob", PD)]
+
+
+class rn_cost(ctypes.Structure):
+    _fields_ = [("W_alpha", c_double), ("alpha0", PD), ("Wu", PD), ("Ws", c_double),
+                ("Wx", c_double)]
+
+
+class rn_opts(ctypes.Structure):
+    _fields_ = [("device", c_int), ("stream", c_void_p), ("precision", c_int),
+                ("gamma", c_double), ("power_iters", c_int), ("check_every", c_int),
+                ("refresh_every", c_int), ("max_ctas", c_int)]
+
+
+class rn_result(ctypes.Structure):
+    _fields_ = [("u", PD), ("x", PD), ("y", PD), ("res_hist", PD), ("res_hist_len", c_int),
+                ("compute_gap", c_int), ("iters", c_int), ("n_checks", c_int),
+                ("primal_res", c_double), ("ubox_viol", c_double), ("cost", c_double),
+                ("gap", c_double), ("gamma", c_double)]
+
+
+class rn_factor_info(ctypes.Structure):
+    _fields_ = [("nx", c_int), ("nu", c_int), ("nd", c_int), ("ne", c_int), ("N", c_int),
+                ("n_nodes", c_int), ("n_chains", c_int), ("n_top", c_int),
+                ("grid_ctas", c_int), ("block_threads", c_int), ("L", c_double),
+                ("gamma", c_double), ("precision", c_int), ("device_bytes", c_longlong)]
+
+
+EXPORTS = {
+    "rapidnet_factor": (c_int, [POINTER(rn_network), POINTER(rn_tree), POINTER(rn_cost),
+                                POINTER(rn_opts), POINTER(c_void_p)]),
+    "rapidnet_factor_free": (None, [c_void_p]),
+    "rapidnet_factor_info": (c_int, [c_void_p, POINTER(rn_factor_info)]),
+    "rapidnet_solve": (c_int, [c_void_p, PD, PD, PD, PD, c_int, c_double, PD,
+                               POINTER(rn_result)]),
+    "rapidnet_solve_device": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int,
+                                      c_double, c_void_p, POINTER(rn_result)]),
+    "rapidnet_dual_gradient_device": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                              c_void_p, c_void_p, c_void_p]),
+    "rapidnet_last_error": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load librapidnet.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in EXPORTS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class RapidNetError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def rapidnet_last_error() -> str:
+    return load().rapidnet_last_error().decode()
+
+
+def _check(rc: int) -> int:
+    if rc < 0:
+        raise RapidNetError(rc, rapidnet_last_error())
+    return rc
+
+
+def rapidnet_factor(net, tree, cost, opts):
+    h = c_void_p()
+    _check(load().rapidnet_factor(ctypes.byref(net), ctypes.byref(tree), ctypes.byref(cost),
+                                  ctypes.byref(opts), ctypes.byref(h)))
+    return h
+
+
+def rapidnet_factor_free(h) -> None:
+    load().rapidnet_factor_free(h)
+
+
+def rapidnet_factor_info(h) -> rn_factor_info:
+    info = rn_factor_info()
+    _check(load().rapidnet_factor_info(h, ctypes.byref(info)))
+    return info
+
+
+def rapidnet_solve(h, x0, q, demand, alpha, max_iters, tol, y_warm, res) -> int:
+    return _check(load().rapidnet_solve(h, x0, q, demand, alpha, int(max_iters), float(tol),
+                                        y_warm, ctypes.byref(res)))
+
+
+def rapidnet_solve_device(h, x0, q, demand, alpha, max_iters, tol, y_warm, res) -> int:
+    return _check(load().rapidnet_solve_device(h, x0, q, demand, alpha, int(max_iters),
+                                               float(tol), y_warm, ctypes.byref(res)))
+
+
+def rapidnet_dual_gradient_device(h, x0, q, demand, alpha, w, u, x) -> int:
+    return _check(load().rapidnet_dual_gradient_device(h, x0, q, demand, alpha, w, u, x))
+
+
+# ---------------------------------------------------------------------------
+# convenience wrapper
+# ---------------------------------------------------------------------------
+def _f64(a, shape=None) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def _pd(a: np.ndarray):
+    return a.ctypes.data_as(PD)
+
+
+def _dev_ptr(t):
+    """Device address of a contiguous float64 CUDA tensor (or None)."""
+    if t is None:
+        return None
+    if not (t.is_cuda and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor")
+    import torch
+    if t.dtype != torch.float64:
+        raise ValueError("expected float64")
+    return c_void_p(t.data_ptr())
+
+
+class Factor:
+    """A factor handle (paper Table 2: Engine::factorStep) with solve calls."""
+
+    def __init__(self, net, cost, tree, precision: int = RN_PREC_FP64, gamma: float = 0.0,
+                 device: int = 0, stream=None, power_iters: int = 0, check_every: int = 0,
+                 refresh_every: int = 0, max_ctas: int = 0):
+        nx, nu, nd, ne = net.nx, net.nu, net.nd, net.ne
+        self._keep = [
+            _f64(net.A, (nx, nx)), _f64(net.B, (nx, nu)), _f64(net.Gd, (nx, nd)),
+            _f64(net.E, (ne, nu)) if ne else np.zeros((1, nu)),
+            _f64(net.Ed, (ne, nd)) if ne else np.zeros((1, nd)),
+            _f64(net.xmin), _f64(net.xmax), _f64(net.xs), _f64(net.umin), _f64(net.umax),
+            np.ascontiguousarray(tree.stage_ptr, dtype=np.int32),
+            np.ascontiguousarray(tree.anc, dtype=np.int32), _f64(tree.prob),
+            _f64(cost.alpha0), _f64(cost.Wu, (nu, nu)),
+        ]
+        k = self._keep
+        self.net_c = rn_network(nx, nu, nd, ne, *[_pd(a) for a in k[:10]])
+        self.tree_c = rn_tree(int(tree.N), int(tree.stage_ptr[-1]), k[10].ctypes.data_as(PI),
+                              k[11].ctypes.data_as(PI), _pd(k[12]))
+        self.cost_c = rn_cost(float(cost.W_alpha), _pd(k[13]), _pd(k[14]), float(cost.Ws),
+                              float(cost.Wx))
+        st = None if stream is None else c_void_p(getattr(stream, "cuda_stream", stream))
+        self.opts_c = rn_opts(device, st, precision, gamma, power_iters, check_every,
+                              refresh_every, max_ctas)
+        self.nx, self.nu, self.nd, self.ne = nx, nu, nd, ne
+        self.n_nodes = int(tree.stage_ptr[-1])
+        self.ny = 2 * nx + nu
+        self.h = rapidnet_factor(self.net_c, self.tree_c, self.cost_c, self.opts_c)
+
+    def info(self) -> dict:
+        i = rapidnet_factor_info(self.h)
+        return {f: getattr(i, f) for f, _ in rn_factor_info._fields_}
+
+    def solve(self, x0, q, demand, alpha, max_iters: int, tol: float = 0.0, y_warm=None,
+              compute_gap: bool = False, res_hist_len: int = 0) -> dict:
+        """Host arrays in and out (rapidnet_solve)."""
+        n = self.n_nodes
+        x0 = _f64(x0, (self.nx,))
+        q = _f64(q, (self.nu,))
+        demand = _f64(demand, (n, self.nd))
+        alpha = _f64(alpha, (n, self.nu))
+        yw = None if y_warm is None else _f64(y_warm, (n, self.ny))
+        u = np.empty((n, self.nu))
+        x = np.empty((n, self.nx))
+        y = np.empty((n, self.ny))
+        hist = np.zeros(max(res_hist_len, 1))
+        res = rn_result(_pd(u), _pd(x), _pd(y), _pd(hist) if res_hist_len else None,
+                        res_hist_len, int(compute_gap))
+        rc = rapidnet_solve(self.h, _pd(x0), _pd(q), _pd(demand), _pd(alpha), max_iters, tol,
+                            None if yw is None else _pd(yw), res)
+        out = {f: getattr(res, f) for f in ("iters", "n_checks", "primal_res", "ubox_viol",
+                                            "cost", "gap", "gamma")}
+        out.update(status=rc, u=u, x=x, y=y,
+                   res_hist=hist[:min(res_hist_len, res.n_checks)] if res_hist_len else None)
+        return out
+
+    def solve_device(self, x0, q, demand, alpha, max_iters: int, tol: float, u, x, y,
+                     y_warm=None, compute_gap: bool = False, res_hist=None) -> dict:
+        """torch CUDA float64 tensors in and out (rapidnet_solve_device)."""
+        res = rn_result(ctypes.cast(_dev_ptr(u), PD), ctypes.cast(_dev_ptr(x), PD),
+                        ctypes.cast(_dev_ptr(y), PD),
+                        ctypes.cast(_dev_ptr(res_hist), PD) if res_hist is not None else None,
+                        0 if res_hist is None else res_hist.numel(), int(compute_gap))
+        rc = rapidnet_solve_device(self.h, _dev_ptr(x0), _dev_ptr(q), _dev_ptr(demand),
+                                   _dev_ptr(alpha), max_iters, tol, _dev_ptr(y_warm), res)
+        out = {f: getattr(res, f) for f in ("iters", "n_checks", "primal_res", "ubox_viol",
+                                            "cost", "gap", "gamma")}
+        out["status"] = rc
+        return out
+
+    def dual_gradient_device(self, w, u, x, x0=None, q=None, demand=None, alpha=None) -> None:
+        rapidnet_dual_gradient_device(self.h, _dev_ptr(x0), _dev_ptr(q), _dev_ptr(demand),
+                                      _dev_ptr(alpha), _dev_ptr(w), _dev_ptr(u), _dev_ptr(x))
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            rapidnet_factor_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

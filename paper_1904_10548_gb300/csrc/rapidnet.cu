@@ -1,0 +1,1160 @@
+// C ABI of the solver: factor step, solve, dual gradient (include/rapidnet.h).
+//
+// Host orchestration around the persistent kernel of solve_kernels.cu:
+//   factor:  validation, tree schedule, Schur complement S = E W^-1 E' and
+//            S^-1 in FP64 (Cholesky), uploads, step size by power iteration
+//   solve:   per-solve constants -> x*(0) (one dual-gradient evaluation
+//            with the data terms) -> APG iterations -> outputs, cost,
+//            input-box violation, optional duality gap.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <vector>
+
+#include "kernels.cuh"
+#include "rn_internal.h"
+
+using namespace rn;
+
+// ---------------------------------------------------------------------------
+// helper kernels (FP64)
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kRedBlocks = 304;  // partial sums of the node reductions
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// kq = q - W^-1 E' S^-1 E q: the input q projected on ker E in the W metric
+__global__ void k_kq(NetDev<double> nt, const double *q, double *kq) {
+  extern __shared__ double sh[];
+  double *e = sh, *f = sh + nt.NEP;
+  const int tid = threadIdx.x;
+  for (int r = tid; r < nt.ne; r += blockDim.x) {
+    double acc = 0.0;
+    for (int k = nt.Er_ptr[r]; k < nt.Er_ptr[r + 1]; ++k) acc += nt.Er_val[k] * q[nt.Er_idx[k]];
+    e[r] = acc;
+  }
+  __syncthreads();
+  for (int r = tid; r < nt.ne; r += blockDim.x) {
+    double acc = 0.0;
+    for (int c = 0; c < nt.ne; ++c) acc += nt.Sinv[(size_t)r * nt.ne + c] * e[c];
+    f[r] = acc;
+  }
+  __syncthreads();
+  for (int j = tid; j < nt.nu; j += blockDim.x) {
+    double acc = 0.0;
+    for (int k = nt.Ec_ptr[j]; k < nt.Ec_ptr[j + 1]; ++k) acc += nt.Ec_val[k] * f[nt.Ec_idx[k]];
+    kq[j] = q[j] - nt.winv[j] * acc;
+  }
+}
+
+struct PrepArgs {
+  const int *perm;
+  const double *prob;
+  const double *demand, *alpha, *alpha0, *kq;
+  const int *Gd_ptr, *Gd_idx;
+  const double *Gd_val;
+  const int *Ed_ptr, *Ed_idx;
+  const double *Ed_val;
+  double W_alpha;
+  int nd;
+};
+
+// per node: s = (0 | c0), ub = ubar + kq, gb = Gd d, with
+// c0 = p W_alpha (alpha0 + alpha_nu) and ubar = -W^-1 E' S^-1 Ed d
+__global__ void k_prep(NetDev<double> nt, PrepArgs a, int n, double *s, double *ub, double *gb) {
+  extern __shared__ double sh[];
+  double *e = sh, *f = sh + nt.NEP;
+  const int tid = threadIdx.x;
+  for (int v = blockIdx.x + 1; v < n; v += gridDim.x) {
+    const int b = a.perm[v];
+    const double *d = a.demand + (size_t)b * a.nd;
+    const double *al = a.alpha + (size_t)b * nt.nu;
+    const double p = a.prob[v];
+    for (int r = tid; r < nt.ne; r += blockDim.x) {
+      double acc = 0.0;
+      for (int k = a.Ed_ptr[r]; k < a.Ed_ptr[r + 1]; ++k) acc += a.Ed_val[k] * d[a.Ed_idx[k]];
+      e[r] = acc;
+    }
+    __syncthreads();
+    for (int r = tid; r < nt.ne; r += blockDim.x) {
+      double acc = 0.0;
+      for (int c = 0; c < nt.ne; ++c) acc += nt.Sinv[(size_t)r * nt.ne + c] * e[c];
+      f[r] = acc;
+    }
+    __syncthreads();
+    for (int j = tid; j < nt.NUP; j += blockDim.x) {
+      double c0 = 0.0, u = 0.0;
+      if (j < nt.nu) {
+        c0 = p * a.W_alpha * (a.alpha0[j] + al[j]);
+        double acc = 0.0;
+        for (int k = nt.Ec_ptr[j]; k < nt.Ec_ptr[j + 1]; ++k) acc += nt.Ec_val[k] * f[nt.Ec_idx[k]];
+        u = a.kq[j] - nt.winv[j] * acc;
+      }
+      s[(size_t)v * nt.SP + nt.NXP + j] = c0;
+      ub[(size_t)v * nt.NUP + j] = u;
+    }
+    for (int i = tid; i < nt.NXP; i += blockDim.x) {
+      double g = 0.0;
+      if (i < nt.nx)
+        for (int k = a.Gd_ptr[i]; k < a.Gd_ptr[i + 1]; ++k) g += a.Gd_val[k] * d[a.Gd_idx[k]];
+      gb[(size_t)v * nt.NXP + i] = g;
+      s[(size_t)v * nt.SP + i] = 0.0;
+    }
+    __syncthreads();
+  }
+}
+
+// y^0 = y^{-1} = y_warm (or 0) in the internal layout, s = (y1 + y2 | y3)
+__global__ void k_init_apg(NetDev<double> nt, const int *perm, int n, const double *y_warm,
+                           double *ya, double *yb, double *s) {
+  const int ny = 2 * nt.nx + nt.nu;
+  for (int v = blockIdx.x + 1; v < n; v += gridDim.x) {
+    const double *src = y_warm ? y_warm + (size_t)perm[v] * ny : nullptr;
+    for (int e = threadIdx.x; e < nt.YP; e += blockDim.x) {
+      double val = 0.0;
+      if (src) {
+        if (e < nt.nx) val = src[e];
+        else if (e >= nt.NXP && e < nt.NXP + nt.nx) val = src[nt.nx + e - nt.NXP];
+        else if (e >= 2 * nt.NXP && e < 2 * nt.NXP + nt.nu) val = src[2 * nt.nx + e - 2 * nt.NXP];
+      }
+      ya[(size_t)v * nt.YP + e] = val;
+      yb[(size_t)v * nt.YP + e] = val;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nt.SP; e += blockDim.x) {
+      const double *y = ya + (size_t)v * nt.YP;
+      double val = 0.0;
+      if (e < nt.nx) val = y[e] + y[nt.NXP + e];
+      else if (e >= nt.NXP && e < nt.NXP + nt.nu) val = y[2 * nt.NXP + (e - nt.NXP)];
+      s[(size_t)v * nt.SP + e] = val;
+    }
+  }
+}
+
+// s = (y1 + y2 | y3) from a dual vector given in breadth-first rows
+__global__ void k_s_from_w(NetDev<double> nt, const int *perm, int n, const double *w, double *s) {
+  const int ny = 2 * nt.nx + nt.nu;
+  for (int v = blockIdx.x + 1; v < n; v += gridDim.x) {
+    const double *src = w + (size_t)perm[v] * ny;
+    for (int e = threadIdx.x; e < nt.SP; e += blockDim.x) {
+      double val = 0.0;
+      if (e < nt.nx) val = src[e] + src[nt.nx + e];
+      else if (e >= nt.NXP && e < nt.NXP + nt.nu) val = src[2 * nt.nx + (e - nt.NXP)];
+      s[(size_t)v * nt.SP + e] = val;
+    }
+  }
+}
+
+// internal rows -> breadth-first rows of u, x (and y if given); root rows q, x0, 0
+__global__ void k_gather(NetDev<double> nt, const int *perm, int n, const double *uo,
+                         const double *xo, const double *yin, const double *q, const double *x0,
+                         double *u, double *x, double *y) {
+  const int ny = 2 * nt.nx + nt.nu;
+  for (int v = blockIdx.x; v < n; v += gridDim.x) {
+    const int b = perm[v];
+    for (int j = threadIdx.x; j < nt.nu; j += blockDim.x)
+      u[(size_t)b * nt.nu + j] = v == 0 ? q[j] : uo[(size_t)v * nt.NUP + j];
+    for (int i = threadIdx.x; i < nt.nx; i += blockDim.x)
+      x[(size_t)b * nt.nx + i] = v == 0 ? x0[i] : xo[(size_t)v * nt.NXP + i];
+    if (y) {
+      for (int e = threadIdx.x; e < ny; e += blockDim.x) {
+        double val = 0.0;
+        if (v != 0) {
+          const double *r = yin + (size_t)v * nt.YP;
+          if (e < nt.nx) val = r[e];
+          else if (e < 2 * nt.nx) val = r[nt.NXP + e - nt.nx];
+          else val = r[2 * nt.NXP + e - 2 * nt.nx];
+        }
+        y[(size_t)b * ny + e] = val;
+      }
+    }
+  }
+}
+
+struct ReduceArgs {
+  const int *parent, *perm;
+  const double *prob, *alpha, *alpha0, *wdiag, *q;
+  const double *uo, *xo;   // internal rows
+  const double *y;         // internal rows (gap) or null
+  double W_alpha;
+  int mode;                // 0: cost + ubox, 1: gap terms
+};
+
+// Per-node terms reduced over the tree, one warp per node.
+// mode 0: [smooth cost, soft cost, u-box violation (max)]
+// mode 1: [gap terms, domain violation count]
+__global__ void k_node_reduce(NetDev<double> nt, ReduceArgs a, int n, double *partial) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __shared__ double sh[3][32];
+  double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
+  for (int v = 1 + blockIdx.x * nw + warp; v < n; v += gridDim.x * nw) {
+    const double *u = a.uo + (size_t)v * nt.NUP;
+    const double *x = a.xo + (size_t)v * nt.NXP;
+    double d1 = 0.0, d2 = 0.0, t = 0.0, m = 0.0;
+    if (a.mode == 0) {
+      const int pa = a.parent[v];
+      const double *ua = pa == 0 ? a.q : a.uo + (size_t)pa * nt.NUP;
+      const double *al = a.alpha + (size_t)a.perm[v] * nt.nu;
+      const double p = a.prob[v];
+      for (int j = lane; j < nt.nu; j += 32) {
+        const double du = u[j] - ua[j];
+        t += p * (a.W_alpha * (a.alpha0[j] + al[j]) * u[j] + a.wdiag[j] * du * du);
+        m = fmax(m, fmax(nt.umin[j] - u[j], u[j] - nt.umax[j]));
+      }
+      for (int i = lane; i < nt.nx; i += 32) {
+        const double e1 = x[i] - fmin(fmax(x[i], nt.xmin[i]), nt.xmax[i]);
+        const double e2 = fmin(x[i] - nt.xs[i], 0.0);
+        d1 += e1 * e1;
+        d2 += e2 * e2;
+      }
+      t = warp_sum(t);
+      d1 = warp_sum(d1);
+      d2 = warp_sum(d2);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if (lane == 0) {
+        acc0 += t;
+        acc1 += nt.Wx * sqrt(d1) + nt.Ws * sqrt(d2);
+        acc2 = fmax(acc2, m);
+      }
+    } else {
+      // soft(x) - <y1 + y2, x> - <y3, u> + sigma_X(y1) + <y2, xs> + sigma_U(y3)
+      const double *y = a.y + (size_t)v * nt.YP;
+      double n1 = 0.0, n2 = 0.0, pos = 0.0;
+      for (int i = lane; i < nt.nx; i += 32) {
+        const double e1 = x[i] - fmin(fmax(x[i], nt.xmin[i]), nt.xmax[i]);
+        const double e2 = fmin(x[i] - nt.xs[i], 0.0);
+        d1 += e1 * e1;
+        d2 += e2 * e2;
+        const double y1 = y[i], y2 = y[nt.NXP + i];
+        n1 += y1 * y1;
+        n2 += y2 * y2;
+        pos = fmax(pos, y2);
+        t += -(y1 + y2) * x[i] + fmax(y1 * nt.xmax[i], y1 * nt.xmin[i]) + y2 * nt.xs[i];
+      }
+      for (int j = lane; j < nt.nu; j += 32) {
+        const double y3 = y[2 * nt.NXP + j];
+        t += -y3 * u[j] + fmax(y3 * nt.umax[j], y3 * nt.umin[j]);
+      }
+      t = warp_sum(t);
+      d1 = warp_sum(d1);
+      d2 = warp_sum(d2);
+      n1 = warp_sum(n1);
+      n2 = warp_sum(n2);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) pos = fmax(pos, __shfl_xor_sync(0xffffffffu, pos, o));
+      if (lane == 0) {
+        acc0 += t + nt.Wx * sqrt(d1) + nt.Ws * sqrt(d2);
+        const bool bad = sqrt(n1) > nt.Wx * (1.0 + 1e-9) + 1e-300 ||
+                         sqrt(n2) > nt.Ws * (1.0 + 1e-9) + 1e-300 ||
+                         pos > 1e-9 * fmax(nt.Ws, 1e-300);
+        acc1 += bad ? 1.0 : 0.0;
+      }
+    }
+  }
+  if (lane == 0) {
+    sh[0][warp] = acc0;
+    sh[1][warp] = acc1;
+    sh[2][warp] = acc2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int w = 0; w < nw; ++w) {
+      s0 += sh[0][w];
+      s1 += sh[1][w];
+      s2 = fmax(s2, sh[2][w]);
+    }
+    partial[3 * blockIdx.x + 0] = s0;
+    partial[3 * blockIdx.x + 1] = s1;
+    partial[3 * blockIdx.x + 2] = s2;
+  }
+}
+
+__global__ void k_final_reduce(const double *partial, int nb, double *out) {
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int b = 0; b < nb; ++b) {
+      s0 += partial[3 * b];
+      s1 += partial[3 * b + 1];
+      s2 = fmax(s2, partial[3 * b + 2]);
+    }
+    out[0] = s0;
+    out[1] = s1;
+    out[2] = s2;
+  }
+}
+
+// Power iteration on M v = -H x_lin(v).  The iterate v is never stored:
+// only s = (v1 + v2 | v3) enters the dual gradient.
+//   start: v = 1 + SplitMix64 over (breadth-first node, component), not
+//          normalised (the estimate after one step does not depend on it)
+//   step:  v <- M v / |M v| with M v = -(x, x, u), |M v|^2 = sum 2|x|^2 + |u|^2
+__device__ __forceinline__ double splitmix_unit(unsigned long long i) {
+  unsigned long long z = (i + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z = z ^ (z >> 31);
+  return (double)(z >> 11) * 0x1.0p-53;
+}
+
+__global__ void k_power_start(NetDev<double> nt, const int *perm, int n, double *s) {
+  const int ny = 2 * nt.nx + nt.nu;
+  for (int v = blockIdx.x + 1; v < n; v += gridDim.x) {
+    const unsigned long long base = (unsigned long long)(perm[v] - 1) * ny;
+    for (int e = threadIdx.x; e < nt.SP; e += blockDim.x) {
+      double val = 0.0;
+      if (e < nt.nx)
+        val = (1.0 + splitmix_unit(base + e)) + (1.0 + splitmix_unit(base + nt.nx + e));
+      else if (e >= nt.NXP && e < nt.NXP + nt.nu)
+        val = 1.0 + splitmix_unit(base + 2 * nt.nx + (e - nt.NXP));
+      s[(size_t)v * nt.SP + e] = val;
+    }
+  }
+}
+
+// per-block partial sums of sum_nu 2 |x_nu|^2 + |u_nu|^2
+__global__ void k_norm2(NetDev<double> nt, int n, const double *uo, const double *xo,
+                        double *partial) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (int v = blockIdx.x + 1; v < n; v += gridDim.x) {
+    for (int j = threadIdx.x; j < nt.nu; j += blockDim.x) {
+      const double a = uo[(size_t)v * nt.NUP + j];
+      acc += a * a;
+    }
+    for (int i = threadIdx.x; i < nt.nx; i += blockDim.x) {
+      const double a = xo[(size_t)v * nt.NXP + i];
+      acc += 2.0 * a * a;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    partial[3 * blockIdx.x] = t;
+    partial[3 * blockIdx.x + 1] = 0.0;
+    partial[3 * blockIdx.x + 2] = 0.0;
+  }
+}
+
+// s = (-2x | -u) / sqrt(norm2)
+__global__ void k_power_scale(NetDev<double> nt, int n, const double *uo, const double *xo,
+                              const double *norm2, double *s) {
+  const double inv = 1.0 / sqrt(norm2[0]);
+  for (int v = blockIdx.x + 1; v < n; v += gridDim.x) {
+    for (int e = threadIdx.x; e < nt.SP; e += blockDim.x) {
+      double val = 0.0;
+      if (e < nt.nx) val = -2.0 * xo[(size_t)v * nt.NXP + e] * inv;
+      else if (e >= nt.NXP && e < nt.NXP + nt.nu) val = -uo[(size_t)v * nt.NUP + (e - nt.NXP)] * inv;
+      s[(size_t)v * nt.SP + e] = val;
+    }
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// factor handle
+// ---------------------------------------------------------------------------
+struct rn_factor {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  rn_opts opts{};
+  Plan plan;
+  int nx = 0, nu = 0, nd = 0, ne = 0, NXP = 0, NUP = 0, SP = 0, YP = 0, NEP = 0;
+  double W_alpha = 0.0, Ws = 0.0, Wx = 0.0;
+  double gamma = 0.0, L = 0.0;
+  int grid = 0, block = 0;
+  size_t smem = 0;
+  std::vector<void *> allocs;
+  long long bytes = 0;
+  NetDev<double> net{};
+  PlanDev pd{};
+  StateDev<double> st{};
+  // device copies of host data
+  int *perm = nullptr;
+  double *prob = nullptr, *inv2p = nullptr, *alpha0 = nullptr, *wdiag = nullptr;
+  int *Gd_ptr = nullptr, *Gd_idx = nullptr, *Ed_ptr = nullptr, *Ed_idx = nullptr;
+  double *Gd_val = nullptr, *Ed_val = nullptr;
+  // per-solve data owned by the handle
+  double *x0 = nullptr, *q = nullptr, *kq = nullptr, *demand = nullptr, *alpha = nullptr;
+  double *partial = nullptr, *scal = nullptr;
+  double *beta = nullptr;
+  int beta_cap = 0;
+  unsigned long long *res = nullptr;
+  int res_cap = 0;
+  unsigned *sync = nullptr;  // counts | flags | barrier
+  size_t sync_words = 0;
+  int *err = nullptr, *info = nullptr;
+  bool have_data = false;
+  // host staging for rapidnet_solve (host pointers)
+  double *io_y = nullptr, *io_u = nullptr, *io_x = nullptr, *io_hist = nullptr;
+  int io_hist_cap = 0;
+
+  ~rn_factor() {
+    if (device >= 0) cudaSetDevice(device);
+    for (void *p : allocs) cudaFree(p);
+    if (own_stream && stream) cudaStreamDestroy(stream);
+  }
+};
+
+namespace {
+
+#define RN_CUDA(call)                                                              \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      set_error("CUDA error %s at %s:%d: %s", #call, __FILE__, __LINE__,           \
+                cudaGetErrorString(e_));                                           \
+      return e_ == cudaErrorMemoryAllocation ? RN_ERR_NOMEM : RN_ERR_CUDA;         \
+    }                                                                              \
+  } while (0)
+
+template <typename T>
+int dalloc(rn_factor *f, T **p, size_t count) {
+  if (count == 0) count = 1;
+  void *ptr = nullptr;
+  cudaError_t e = cudaMalloc(&ptr, count * sizeof(T));
+  if (e != cudaSuccess) {
+    set_error("cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? RN_ERR_NOMEM : RN_ERR_CUDA;
+  }
+  f->allocs.push_back(ptr);
+  f->bytes += (long long)(count * sizeof(T));
+  *p = static_cast<T *>(ptr);
+  return RN_OK;
+}
+
+template <typename T>
+int upload(rn_factor *f, T **p, const std::vector<T> &h) {
+  int rc = dalloc(f, p, h.size());
+  if (rc) return rc;
+  if (!h.empty()) RN_CUDA(cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return RN_OK;
+}
+
+void release(rn_factor *f, void *p) {
+  if (!p) return;
+  auto it = std::find(f->allocs.begin(), f->allocs.end(), p);
+  if (it != f->allocs.end()) f->allocs.erase(it);
+  cudaFree(p);
+}
+
+inline int ceil4(int v) { return (v + 3) & ~3; }
+
+bool finite_all(const double *p, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+// Cholesky A = R R' of an SPD m x m matrix in place (lower).  Returns false
+// if a pivot is not positive relative to the diagonal scale.
+bool cholesky(std::vector<double> &A, int m) {
+  double scale = 0.0;
+  for (int i = 0; i < m; ++i) scale = std::max(scale, std::fabs(A[(size_t)i * m + i]));
+  for (int j = 0; j < m; ++j) {
+    double d = A[(size_t)j * m + j];
+    for (int k = 0; k < j; ++k) d -= A[(size_t)j * m + k] * A[(size_t)j * m + k];
+    if (!(d > 1e-13 * scale)) return false;
+    d = std::sqrt(d);
+    A[(size_t)j * m + j] = d;
+    for (int i = j + 1; i < m; ++i) {
+      double v = A[(size_t)i * m + j];
+      for (int k = 0; k < j; ++k) v -= A[(size_t)i * m + k] * A[(size_t)j * m + k];
+      A[(size_t)i * m + j] = v / d;
+    }
+  }
+  return true;
+}
+
+// inverse of an SPD matrix from its Cholesky factor (columns of R^-T R^-1)
+std::vector<double> chol_inverse(const std::vector<double> &R, int m) {
+  std::vector<double> inv((size_t)m * m, 0.0), col(m);
+  for (int c = 0; c < m; ++c) {
+    for (int i = 0; i < m; ++i) {
+      double v = (i == c) ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) v -= R[(size_t)i * m + k] * col[k];
+      col[i] = v / R[(size_t)i * m + i];
+    }
+    for (int i = m - 1; i >= 0; --i) {
+      double v = col[i];
+      for (int k = i + 1; k < m; ++k) v -= R[(size_t)k * m + i] * col[k];
+      col[i] = v / R[(size_t)i * m + i];
+    }
+    for (int i = 0; i < m; ++i) inv[(size_t)i * m + c] = col[i];
+  }
+  return inv;
+}
+
+KParams<double> base_params(rn_factor *f) {
+  KParams<double> P{};
+  P.net = f->net;
+  P.plan = f->pd;
+  P.st = f->st;
+  P.iters = 1;
+  P.check_every = 1;
+  P.linear = 0;
+  P.step_base = 0;
+  P.gamma = f->gamma;
+  P.invgamma = f->gamma > 0 ? 1.0 / f->gamma : 0.0;
+  P.tol = 0.0;
+  return P;
+}
+
+int reset_sync(rn_factor *f) {
+  RN_CUDA(cudaMemsetAsync(f->sync, 0, f->sync_words * sizeof(unsigned), f->stream));
+  RN_CUDA(cudaMemsetAsync(f->err, 0, sizeof(int), f->stream));
+  return RN_OK;
+}
+
+int check_err(rn_factor *f) {
+  int e = 0;
+  RN_CUDA(cudaMemcpyAsync(&e, f->err, sizeof(int), cudaMemcpyDeviceToHost, f->stream));
+  RN_CUDA(cudaStreamSynchronize(f->stream));
+  if (e) {
+    set_error("a device-side wait gave up after %.1f s", kWaitNs * 1e-9);
+    return RN_ERR_TIMEOUT;
+  }
+  return RN_OK;
+}
+
+// one evaluation of the dual gradient from f->st.s into uo / xo
+int solve_step(rn_factor *f, int linear) {
+  int rc = reset_sync(f);
+  if (rc) return rc;
+  KParams<double> P = base_params(f);
+  P.linear = linear;
+  RN_CUDA((launch_solve<double, false>(P, f->grid, f->block, f->smem, f->stream)));
+  return RN_OK;
+}
+
+int node_blocks(int n) { return std::max(1, std::min(n - 1, 4096)); }
+
+int power_iteration(rn_factor *f, int iters, double *L_out) {
+  const int n = f->plan.n;
+  k_power_start<<<node_blocks(n), 128, 0, f->stream>>>(f->net, f->perm, n, f->st.s);
+  RN_CUDA(cudaGetLastError());
+  for (int k = 0; k < iters; ++k) {
+    int rc = solve_step(f, 1);
+    if (rc) return rc;
+    k_norm2<<<kRedBlocks, 256, 0, f->stream>>>(f->net, n, f->st.uo, f->st.xo, f->partial);
+    k_final_reduce<<<1, 32, 0, f->stream>>>(f->partial, kRedBlocks, f->scal);
+    k_power_scale<<<node_blocks(n), 128, 0, f->stream>>>(f->net, n, f->st.uo, f->st.xo, f->scal,
+                                                         f->st.s);
+    RN_CUDA(cudaGetLastError());
+  }
+  double nrm2 = 0.0;
+  RN_CUDA(cudaMemcpyAsync(&nrm2, f->scal, sizeof(double), cudaMemcpyDeviceToHost, f->stream));
+  int rc = check_err(f);
+  if (rc) return rc;
+  *L_out = std::sqrt(nrm2);
+  return RN_OK;
+}
+
+int validate_network(const rn_network *net, const rn_cost *cost) {
+  if (!net || !cost) {
+    set_error("network or cost is NULL");
+    return RN_ERR_INVAL;
+  }
+  const int nx = net->nx, nu = net->nu, nd = net->nd, ne = net->ne;
+  if (nx < 1 || nu < 1 || nd < 1 || ne < 0) {
+    set_error("network: need nx, nu, nd >= 1 and ne >= 0");
+    return RN_ERR_INVAL;
+  }
+  if (!net->A || !net->B || !net->Gd || !net->xmin || !net->xmax || !net->xs || !net->umin ||
+      !net->umax || (ne > 0 && (!net->E || !net->Ed))) {
+    set_error("network: NULL matrix or bound");
+    return RN_ERR_INVAL;
+  }
+  if (!cost->alpha0 || !cost->Wu) {
+    set_error("cost: NULL alpha0 or Wu");
+    return RN_ERR_INVAL;
+  }
+  if (!finite_all(net->A, (size_t)nx * nx) || !finite_all(net->B, (size_t)nx * nu) ||
+      !finite_all(net->Gd, (size_t)nx * nd) || (ne > 0 && !finite_all(net->E, (size_t)ne * nu)) ||
+      (ne > 0 && !finite_all(net->Ed, (size_t)ne * nd)) || !finite_all(cost->alpha0, nu) ||
+      !finite_all(cost->Wu, (size_t)nu * nu) || !finite_all(net->xs, nx)) {
+    set_error("network/cost: non-finite entry");
+    return RN_ERR_INVAL;
+  }
+  for (int i = 0; i < nx; ++i)
+    if (!(net->xmin[i] <= net->xmax[i])) {
+      set_error("network: xmin[%d] > xmax[%d]", i, i);
+      return RN_ERR_INVAL;
+    }
+  for (int j = 0; j < nu; ++j)
+    if (!(net->umin[j] <= net->umax[j])) {
+      set_error("network: umin[%d] > umax[%d]", j, j);
+      return RN_ERR_INVAL;
+    }
+  if (!(cost->W_alpha >= 0.0) || !(cost->Ws >= 0.0) || !(cost->Wx >= 0.0) ||
+      !std::isfinite(cost->W_alpha) || !std::isfinite(cost->Ws) || !std::isfinite(cost->Wx)) {
+    set_error("cost: weights must be finite and non-negative");
+    return RN_ERR_INVAL;
+  }
+  for (int i = 0; i < nu; ++i)
+    for (int j = 0; j < nu; ++j)
+      if (cost->Wu[(size_t)i * nu + j] != cost->Wu[(size_t)j * nu + i]) {
+        set_error("cost: Wu is not symmetric");
+        return RN_ERR_INVAL;
+      }
+  for (int i = 0; i < nu; ++i)
+    if (!(cost->Wu[(size_t)i * nu + i] > 0.0)) {
+      set_error("cost: Wu is not positive definite (diagonal entry %d)", i);
+      return RN_ERR_INVAL;
+    }
+  for (int i = 0; i < nu; ++i)
+    for (int j = 0; j < nu; ++j)
+      if (i != j && cost->Wu[(size_t)i * nu + j] != 0.0) {
+        set_error("cost: this build handles a diagonal Wu only");
+        return RN_ERR_UNSUPPORTED;
+      }
+  for (int i = 0; i < nx; ++i)
+    for (int j = 0; j < nx; ++j)
+      if (net->A[(size_t)i * nx + j] != (i == j ? 1.0 : 0.0)) {
+        set_error("network: this build handles A = I only (tank mass balance)");
+        return RN_ERR_UNSUPPORTED;
+      }
+  if (std::max(nx, nu) > 256) {
+    set_error("network: this build handles nx, nu <= 256");
+    return RN_ERR_UNSUPPORTED;
+  }
+  return RN_OK;
+}
+
+int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
+                const rn_opts *opts, rn_factor *f) {
+  int rc = validate_network(net, cost);
+  if (rc) return rc;
+  rc = build_plan(tree, f->plan);
+  if (rc) return rc;
+  f->opts = opts ? *opts : rn_opts{};
+  if (f->opts.precision != RN_PREC_FP64) {
+    set_error("this build implements RN_PREC_FP64 only");
+    return RN_ERR_UNSUPPORTED;
+  }
+  if (f->opts.power_iters <= 0) f->opts.power_iters = 200;
+  if (f->opts.check_every <= 0) f->opts.check_every = 10;
+  if (f->opts.refresh_every <= 0) f->opts.refresh_every = 20;
+  f->device = f->opts.device;
+  RN_CUDA(cudaSetDevice(f->device));
+  if (f->opts.stream) {
+    f->stream = static_cast<cudaStream_t>(f->opts.stream);
+  } else {
+    RN_CUDA(cudaStreamCreateWithFlags(&f->stream, cudaStreamNonBlocking));
+    f->own_stream = true;
+  }
+  const int nx = net->nx, nu = net->nu, nd = net->nd, ne = net->ne;
+  f->nx = nx;
+  f->nu = nu;
+  f->nd = nd;
+  f->ne = ne;
+  f->NXP = ceil4(nx);
+  f->NUP = ceil4(nu);
+  f->SP = f->NXP + f->NUP;
+  f->YP = 2 * f->NXP + f->NUP;
+  f->NEP = std::max(1, ne);
+  f->W_alpha = cost->W_alpha;
+  f->Ws = cost->Ws;
+  f->Wx = cost->Wx;
+
+  // Schur complement of the coupling: S = E W^-1 E', its Cholesky factor
+  // (full row rank of E) and inverse, in FP64
+  std::vector<double> winv(nu), wdiag(nu);
+  for (int j = 0; j < nu; ++j) {
+    wdiag[j] = cost->Wu[(size_t)j * nu + j];
+    winv[j] = 1.0 / wdiag[j];
+  }
+  std::vector<double> Sinv(std::max(1, ne * ne), 0.0);
+  if (ne > 0) {
+    std::vector<double> S((size_t)ne * ne, 0.0);
+    for (int r = 0; r < ne; ++r)
+      for (int c = 0; c < ne; ++c) {
+        double acc = 0.0;
+        for (int j = 0; j < nu; ++j)
+          acc += net->E[(size_t)r * nu + j] * winv[j] * net->E[(size_t)c * nu + j];
+        S[(size_t)r * ne + c] = acc;
+      }
+    std::vector<double> R = S;
+    if (!cholesky(R, ne)) {
+      set_error("E does not have full row rank (E W^-1 E' is singular)");
+      return RN_ERR_RANK;
+    }
+    Sinv = chol_inverse(R, ne);
+  }
+
+  const Plan &p = f->plan;
+  const int n = p.n;
+  // sparse operators
+  Csr Bc = dense_to_csc(net->B, nx, nu), Br = dense_to_csr(net->B, nx, nu);
+  Csr Er, Ec, Gdr = dense_to_csr(net->Gd, nx, nd), Edr;
+  if (ne > 0) {
+    Er = dense_to_csr(net->E, ne, nu);
+    Ec = dense_to_csc(net->E, ne, nu);
+    Edr = dense_to_csr(net->Ed, ne, nd);
+  } else {
+    Er.ptr.assign(1, 0);
+    Ec.ptr.assign(nu + 1, 0);
+    Edr.ptr.assign(1, 0);
+  }
+  NetDev<double> &nt = f->net;
+  nt.nx = nx;
+  nt.nu = nu;
+  nt.ne = ne;
+  nt.nd = nd;
+  nt.NXP = f->NXP;
+  nt.NUP = f->NUP;
+  nt.SP = f->SP;
+  nt.YP = f->YP;
+  nt.NEP = f->NEP;
+  nt.Wx = cost->Wx;
+  nt.Ws = cost->Ws;
+  int *ip;
+  double *dp;
+#define UP_I(field, vec) \
+  if ((rc = upload(f, &ip, vec))) return rc; \
+  field = ip;
+#define UP_D(field, vec) \
+  if ((rc = upload(f, &dp, vec))) return rc; \
+  field = dp;
+  UP_I(nt.Bc_ptr, Bc.ptr) UP_I(nt.Bc_idx, Bc.idx) UP_D(nt.Bc_val, Bc.val)
+  UP_I(nt.Br_ptr, Br.ptr) UP_I(nt.Br_idx, Br.idx) UP_D(nt.Br_val, Br.val)
+  UP_I(nt.Er_ptr, Er.ptr) UP_I(nt.Er_idx, Er.idx) UP_D(nt.Er_val, Er.val)
+  UP_I(nt.Ec_ptr, Ec.ptr) UP_I(nt.Ec_idx, Ec.idx) UP_D(nt.Ec_val, Ec.val)
+  UP_D(nt.winv, winv) UP_D(nt.Sinv, Sinv)
+  UP_D(nt.xmin, std::vector<double>(net->xmin, net->xmin + nx))
+  UP_D(nt.xmax, std::vector<double>(net->xmax, net->xmax + nx))
+  UP_D(nt.xs, std::vector<double>(net->xs, net->xs + nx))
+  UP_D(nt.umin, std::vector<double>(net->umin, net->umin + nu))
+  UP_D(nt.umax, std::vector<double>(net->umax, net->umax + nu))
+  UP_D(f->alpha0, std::vector<double>(cost->alpha0, cost->alpha0 + nu))
+  UP_D(f->wdiag, wdiag)
+  UP_I(f->Gd_ptr, Gdr.ptr) UP_I(f->Gd_idx, Gdr.idx) UP_D(f->Gd_val, Gdr.val)
+  UP_I(f->Ed_ptr, Edr.ptr) UP_I(f->Ed_idx, Edr.idx) UP_D(f->Ed_val, Edr.val)
+
+  PlanDev &pd = f->pd;
+  pd.n = n;
+  pd.n_top = p.n_top;
+  pd.n_chains = p.n_chains;
+  pd.n_flags = p.n_flags;
+  UP_I(pd.parent, p.parent) UP_I(pd.top_nchild, p.top_nchild) UP_I(pd.top_child_ptr, p.top_child_ptr)
+  UP_I(pd.top_child, p.top_child) UP_I(pd.top_flag, p.top_flag) UP_I(pd.ch_start, p.ch_start)
+  UP_I(pd.ch_len, p.ch_len) UP_I(pd.ch_parent, p.ch_parent) UP_I(pd.ch_path_ptr, p.ch_path_ptr)
+  UP_I(pd.ch_path, p.ch_path) UP_I(pd.ch_own_from, p.ch_own_from) UP_I(pd.ch_flag, p.ch_flag)
+  UP_I(f->perm, p.perm) UP_D(f->prob, p.prob)
+  std::vector<double> inv2p(n, 0.0);
+  for (int i = 1; i < n; ++i) inv2p[i] = 1.0 / (2.0 * p.prob[i]);
+  UP_D(f->inv2p, inv2p)
+#undef UP_I
+#undef UP_D
+
+  // state
+  StateDev<double> &st = f->st;
+  double *s, *ya, *yb, *ub, *gb, *z, *up, *uo, *xo;
+  if ((rc = dalloc(f, &s, (size_t)n * f->SP)) || (rc = dalloc(f, &ya, (size_t)n * f->YP)) ||
+      (rc = dalloc(f, &yb, (size_t)n * f->YP)) || (rc = dalloc(f, &ub, (size_t)n * f->NUP)) ||
+      (rc = dalloc(f, &gb, (size_t)n * f->NXP)) || (rc = dalloc(f, &z, (size_t)n * f->NUP)) ||
+      (rc = dalloc(f, &up, (size_t)n * f->SP)) || (rc = dalloc(f, &uo, (size_t)n * f->NUP)) ||
+      (rc = dalloc(f, &xo, (size_t)n * f->NXP)))
+    return rc;
+  RN_CUDA(cudaMemset(s, 0, (size_t)n * f->SP * sizeof(double)));
+  RN_CUDA(cudaMemset(ya, 0, (size_t)n * f->YP * sizeof(double)));
+  RN_CUDA(cudaMemset(yb, 0, (size_t)n * f->YP * sizeof(double)));
+  RN_CUDA(cudaMemset(ub, 0, (size_t)n * f->NUP * sizeof(double)));
+  RN_CUDA(cudaMemset(gb, 0, (size_t)n * f->NXP * sizeof(double)));
+  RN_CUDA(cudaMemset(z, 0, (size_t)n * f->NUP * sizeof(double)));
+  RN_CUDA(cudaMemset(up, 0, (size_t)n * f->SP * sizeof(double)));
+  RN_CUDA(cudaMemset(uo, 0, (size_t)n * f->NUP * sizeof(double)));
+  RN_CUDA(cudaMemset(xo, 0, (size_t)n * f->NXP * sizeof(double)));
+  st.s = s;
+  st.ya = ya;
+  st.yb = yb;
+  st.ub = ub;
+  st.gb = gb;
+  st.z = z;
+  st.up = up;
+  st.uo = uo;
+  st.xo = xo;
+  st.inv2p = f->inv2p;
+  if ((rc = dalloc(f, &f->x0, nx)) || (rc = dalloc(f, &f->q, nu)) || (rc = dalloc(f, &f->kq, nu)) ||
+      (rc = dalloc(f, &f->demand, (size_t)n * nd)) || (rc = dalloc(f, &f->alpha, (size_t)n * nu)) ||
+      (rc = dalloc(f, &f->partial, 3 * kRedBlocks)) || (rc = dalloc(f, &f->scal, 4)) ||
+      (rc = dalloc(f, &f->err, 1)) || (rc = dalloc(f, &f->info, 4)))
+    return rc;
+  RN_CUDA(cudaMemset(f->x0, 0, nx * sizeof(double)));
+  st.xroot = f->x0;
+  f->sync_words = (size_t)n + (size_t)std::max(1, p.n_flags) + 1;
+  if ((rc = dalloc(f, &f->sync, f->sync_words))) return rc;
+  st.count = f->sync;
+  st.flags = f->sync + n;
+  st.barrier = f->sync + n + std::max(1, p.n_flags);
+  st.err = f->err;
+  st.info = f->info;
+  st.res = nullptr;
+  st.beta = nullptr;
+
+  // launch configuration: one thread per input component; as many
+  // resident blocks as there are chains, up to what the device holds
+  f->block = std::max(64, ((std::max(nu, nx) + 31) / 32) * 32);
+  f->smem = smem_bytes<double>(f->SP, f->NEP, f->NUP);
+  int bps1 = 0, bps2 = 0, sms = 0;
+  RN_CUDA((solve_occupancy<double, true>(f->block, f->smem, &bps1)));
+  RN_CUDA((solve_occupancy<double, false>(f->block, f->smem, &bps2)));
+  RN_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, f->device));
+  const int resident = std::min(bps1, bps2) * sms;
+  if (resident < 1) {
+    set_error("the solve kernel does not fit on the device (block %d, smem %zu)", f->block, f->smem);
+    return RN_ERR_UNSUPPORTED;
+  }
+  f->grid = std::min(p.n_chains, resident);
+  if (f->opts.max_ctas > 0) f->grid = std::min(f->grid, f->opts.max_ctas);
+
+  if (f->opts.gamma > 0.0) {
+    f->gamma = f->opts.gamma;
+    f->L = 0.0;
+  } else {
+    double L = 0.0;
+    rc = power_iteration(f, f->opts.power_iters, &L);
+    if (rc) return rc;
+    if (!(L > 0.0) || !std::isfinite(L)) {
+      set_error("power iteration gave a non-positive Lipschitz estimate %g", L);
+      return RN_ERR_INVAL;
+    }
+    f->L = L;
+    f->gamma = 1.0 / (1.01 * L);
+  }
+  RN_CUDA(cudaStreamSynchronize(f->stream));
+  return RN_OK;
+}
+
+int ensure_beta(rn_factor *f, int iters) {
+  if (iters + 1 <= f->beta_cap) return RN_OK;
+  int cap = std::max(iters + 1, 2 * f->beta_cap);
+  // beta_nu = theta_nu (1 / theta_{nu-1} - 1), theta_{nu+1} = (sqrt(theta^4
+  // + 4 theta^2) - theta^2) / 2 from theta_0 = theta_{-1} = 1 (paper §4.3)
+  std::vector<double> b(cap);
+  double th = 1.0, prev = 1.0;
+  for (int k = 0; k < cap; ++k) {
+    b[k] = th * (1.0 / prev - 1.0);
+    const double t2 = th * th;
+    const double nt = 0.5 * (std::sqrt(t2 * t2 + 4.0 * t2) - t2);
+    prev = th;
+    th = nt;
+  }
+  release(f, f->beta);
+  f->beta = nullptr;
+  int rc = upload(f, &f->beta, b);
+  if (rc) return rc;
+  f->beta_cap = cap;
+  f->st.beta = f->beta;
+  return RN_OK;
+}
+
+int ensure_res(rn_factor *f, int checks) {
+  if (checks <= f->res_cap) return RN_OK;
+  int cap = std::max(checks, 2 * f->res_cap);
+  release(f, f->res);
+  f->res = nullptr;
+  int rc = dalloc(f, &f->res, cap);
+  if (rc) return rc;
+  f->res_cap = cap;
+  f->st.res = f->res;
+  return RN_OK;
+}
+
+// per-solve constants and the offset x*(0): s = (0 | c0), ub = ubar + Kq,
+// gb = Gd d, then one dual-gradient evaluation; its inputs become ub
+int prepare(rn_factor *f, const double *x0, const double *q, const double *demand,
+            const double *alpha) {
+  const int n = f->plan.n;
+  // the host entry point stages its inputs directly in the handle's buffers
+  if (x0 != f->x0)
+    RN_CUDA(cudaMemcpyAsync(f->x0, x0, f->nx * sizeof(double), cudaMemcpyDeviceToDevice, f->stream));
+  if (q != f->q)
+    RN_CUDA(cudaMemcpyAsync(f->q, q, f->nu * sizeof(double), cudaMemcpyDeviceToDevice, f->stream));
+  if (demand != f->demand)
+    RN_CUDA(cudaMemcpyAsync(f->demand, demand, (size_t)n * f->nd * sizeof(double),
+                            cudaMemcpyDeviceToDevice, f->stream));
+  if (alpha != f->alpha)
+    RN_CUDA(cudaMemcpyAsync(f->alpha, alpha, (size_t)n * f->nu * sizeof(double),
+                            cudaMemcpyDeviceToDevice, f->stream));
+  const size_t sh = 2 * f->NEP * sizeof(double);
+  k_kq<<<1, 128, sh, f->stream>>>(f->net, f->q, f->kq);
+  PrepArgs a{f->perm, f->prob, f->demand, f->alpha, f->alpha0, f->kq, f->Gd_ptr, f->Gd_idx,
+             f->Gd_val, f->Ed_ptr, f->Ed_idx, f->Ed_val, f->W_alpha, f->nd};
+  k_prep<<<node_blocks(n), 128, sh, f->stream>>>(f->net, a, n, f->st.s, f->st.ub, f->st.gb);
+  RN_CUDA(cudaGetLastError());
+  int rc = solve_step(f, 0);
+  if (rc) return rc;
+  RN_CUDA(cudaMemcpyAsync(f->st.ub, f->st.uo, (size_t)n * f->NUP * sizeof(double),
+                          cudaMemcpyDeviceToDevice, f->stream));
+  f->have_data = true;
+  return RN_OK;
+}
+
+int reduce_nodes(rn_factor *f, int mode, const double *y, double out[3]) {
+  ReduceArgs a{f->pd.parent, f->perm, f->prob, f->alpha, f->alpha0, f->wdiag, f->q,
+               f->st.uo, f->st.xo, y, f->W_alpha, mode};
+  k_node_reduce<<<kRedBlocks, 256, 0, f->stream>>>(f->net, a, f->plan.n, f->partial);
+  k_final_reduce<<<1, 32, 0, f->stream>>>(f->partial, kRedBlocks, f->scal);
+  RN_CUDA(cudaGetLastError());
+  RN_CUDA(cudaMemcpyAsync(out, f->scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, f->stream));
+  RN_CUDA(cudaStreamSynchronize(f->stream));
+  return RN_OK;
+}
+
+int solve_device_impl(rn_factor *f, const double *x0, const double *q, const double *demand,
+                      const double *alpha, int max_iters, double tol, const double *y_warm,
+                      rn_result *out) {
+  if (!f || !x0 || !q || !demand || !alpha || !out || !out->u || !out->x || !out->y) {
+    set_error("solve: NULL argument");
+    return RN_ERR_INVAL;
+  }
+  if (max_iters < 1) {
+    set_error("solve: max_iters must be >= 1");
+    return RN_ERR_INVAL;
+  }
+  if (!(tol >= 0.0) && !(tol < 0.0)) {
+    set_error("solve: tol is NaN");
+    return RN_ERR_INVAL;
+  }
+  RN_CUDA(cudaSetDevice(f->device));
+  const int n = f->plan.n;
+  const int checks = (max_iters + f->opts.check_every - 1) / f->opts.check_every + 1;
+  int rc;
+  if ((rc = ensure_beta(f, max_iters)) || (rc = ensure_res(f, checks))) return rc;
+  if ((rc = prepare(f, x0, q, demand, alpha))) return rc;
+  k_init_apg<<<node_blocks(n), 128, 0, f->stream>>>(f->net, f->perm, n, y_warm, f->st.ya,
+                                                    f->st.yb, f->st.s);
+  RN_CUDA(cudaGetLastError());
+  if ((rc = reset_sync(f))) return rc;
+  RN_CUDA(cudaMemsetAsync(f->res, 0, checks * sizeof(unsigned long long), f->stream));
+  KParams<double> P = base_params(f);
+  P.iters = max_iters;
+  P.check_every = f->opts.check_every;
+  P.tol = tol > 0.0 ? tol : 0.0;
+  RN_CUDA((launch_solve<double, true>(P, f->grid, f->block, f->smem, f->stream)));
+  int info[3] = {0, 0, 0};
+  RN_CUDA(cudaMemcpyAsync(info, f->info, 3 * sizeof(int), cudaMemcpyDeviceToHost, f->stream));
+  if ((rc = check_err(f))) return rc;
+  const int iters = info[0], nchk = info[1], reason = info[2];
+  // y^{iters} was written into the buffer that held y^{iters-2}
+  const double *yfin = ((iters - 1) & 1) ? f->st.ya : f->st.yb;
+  k_gather<<<node_blocks(n) + 1, 128, 0, f->stream>>>(f->net, f->perm, n, f->st.uo, f->st.xo, yfin,
+                                                      f->q, f->x0, out->u, out->x, out->y);
+  RN_CUDA(cudaGetLastError());
+  std::vector<unsigned long long> hist(std::max(1, nchk));
+  if (nchk > 0)
+    RN_CUDA(cudaMemcpyAsync(hist.data(), f->res, nchk * sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, f->stream));
+  double red[3];
+  if ((rc = reduce_nodes(f, 0, nullptr, red))) return rc;
+  out->cost = red[0] + red[1];
+  out->ubox_viol = red[2];
+  out->iters = iters;
+  out->n_checks = nchk;
+  out->gamma = f->gamma;
+  std::vector<double> rh(std::max(1, nchk));
+  for (int i = 0; i < nchk; ++i) {
+    double d;
+    std::memcpy(&d, &hist[i], sizeof d);
+    rh[i] = d * (1.0 / f->gamma);  // as the kernel's termination test
+  }
+  out->primal_res = nchk > 0 ? rh[nchk - 1] : NAN;
+  if (out->res_hist && out->res_hist_len > 0 && nchk > 0) {
+    const int m = std::min(out->res_hist_len, nchk);
+    RN_CUDA(cudaMemcpyAsync(out->res_hist, rh.data(), m * sizeof(double), cudaMemcpyHostToDevice,
+                            f->stream));
+  }
+  out->gap = NAN;
+  if (out->compute_gap) {
+    // x*(y) with s = (y1 + y2 | y3) of the final dual iterate
+    k_init_apg<<<node_blocks(n), 128, 0, f->stream>>>(f->net, f->perm, n, out->y, f->st.ya,
+                                                      f->st.yb, f->st.s);
+    RN_CUDA(cudaGetLastError());
+    if ((rc = solve_step(f, 0))) return rc;
+    double g[3];
+    if ((rc = reduce_nodes(f, 1, f->st.ya, g))) return rc;
+    if ((rc = check_err(f))) return rc;
+    out->gap = g[1] > 0.0 ? INFINITY : g[0];
+  }
+  RN_CUDA(cudaStreamSynchronize(f->stream));
+  if (reason == 2) {
+    set_error("the residual became non-finite after %d iterations", iters);
+    return RN_ERR_DIVERGED;
+  }
+  if (reason == 3) {
+    set_error("a device-side wait gave up");
+    return RN_ERR_TIMEOUT;
+  }
+  if (tol > 0.0 && reason != 1) return RN_NOT_CONVERGED;
+  return RN_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" int rapidnet_factor(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
+                               const rn_opts *opts, rn_factor **out) {
+  clear_error();
+  if (!out) {
+    set_error("factor: out is NULL");
+    return RN_ERR_INVAL;
+  }
+  *out = nullptr;
+  std::unique_ptr<rn_factor> f(new (std::nothrow) rn_factor());
+  if (!f) {
+    set_error("factor: host allocation failed");
+    return RN_ERR_NOMEM;
+  }
+  f->device = opts ? opts->device : 0;
+  int rc = factor_impl(net, tree, cost, opts, f.get());
+  if (rc) return rc;
+  *out = f.release();
+  return RN_OK;
+}
+
+extern "C" void rapidnet_factor_free(rn_factor *f) { delete f; }
+
+extern "C" int rapidnet_factor_info(const rn_factor *f, rn_factor_info *info) {
+  clear_error();
+  if (!f || !info) {
+    set_error("factor_info: NULL argument");
+    return RN_ERR_INVAL;
+  }
+  info->nx = f->nx;
+  info->nu = f->nu;
+  info->nd = f->nd;
+  info->ne = f->ne;
+  info->N = f->plan.N;
+  info->n_nodes = f->plan.n;
+  info->n_chains = f->plan.n_chains;
+  info->n_top = f->plan.n_top;
+  info->grid_ctas = f->grid;
+  info->block_threads = f->block;
+  info->L = f->L;
+  info->gamma = f->gamma;
+  info->precision = f->opts.precision;
+  info->device_bytes = f->bytes;
+  return RN_OK;
+}
+
+extern "C" int rapidnet_solve_device(rn_factor *f, const double *x0, const double *q,
+                                     const double *demand, const double *alpha, int max_iters,
+                                     double tol, const double *y_warm, rn_result *out) {
+  clear_error();
+  return solve_device_impl(f, x0, q, demand, alpha, max_iters, tol, y_warm, out);
+}
+
+extern "C" int rapidnet_solve(rn_factor *f, const double *x0, const double *q,
+                              const double *demand, const double *alpha, int max_iters, double tol,
+                              const double *y_warm, rn_result *out) {
+  clear_error();
+  if (!f || !x0 || !q || !demand || !alpha || !out || !out->u || !out->x || !out->y) {
+    set_error("solve: NULL argument");
+    return RN_ERR_INVAL;
+  }
+  RN_CUDA(cudaSetDevice(f->device));
+  const int n = f->plan.n, ny = 2 * f->nx + f->nu;
+  int rc;
+  // device staging of the caller's host arrays (kept by the handle)
+  if (!f->io_y) {
+    if ((rc = dalloc(f, &f->io_y, (size_t)n * ny)) || (rc = dalloc(f, &f->io_u, (size_t)n * f->nu)) ||
+        (rc = dalloc(f, &f->io_x, (size_t)n * f->nx)))
+      return rc;
+  }
+  // inputs: x0, q, demand, alpha land in the handle's own buffers
+  RN_CUDA(cudaMemcpyAsync(f->x0, x0, f->nx * sizeof(double), cudaMemcpyHostToDevice, f->stream));
+  RN_CUDA(cudaMemcpyAsync(f->q, q, f->nu * sizeof(double), cudaMemcpyHostToDevice, f->stream));
+  RN_CUDA(cudaMemcpyAsync(f->demand, demand, (size_t)n * f->nd * sizeof(double),
+                          cudaMemcpyHostToDevice, f->stream));
+  RN_CUDA(cudaMemcpyAsync(f->alpha, alpha, (size_t)n * f->nu * sizeof(double),
+                          cudaMemcpyHostToDevice, f->stream));
+  if (y_warm)
+    RN_CUDA(cudaMemcpyAsync(f->io_y, y_warm, (size_t)n * ny * sizeof(double),
+                            cudaMemcpyHostToDevice, f->stream));
+  rn_result dres = *out;
+  dres.u = f->io_u;
+  dres.x = f->io_x;
+  dres.y = f->io_y;
+  std::vector<double> hist;
+  if (out->res_hist && out->res_hist_len > 0) {
+    if (out->res_hist_len > f->io_hist_cap) {
+      release(f, f->io_hist);
+      f->io_hist = nullptr;
+      if ((rc = dalloc(f, &f->io_hist, out->res_hist_len))) return rc;
+      f->io_hist_cap = out->res_hist_len;
+    }
+    dres.res_hist = f->io_hist;
+  } else {
+    dres.res_hist = nullptr;
+  }
+  rc = solve_device_impl(f, f->x0, f->q, f->demand, f->alpha, max_iters, tol,
+                         y_warm ? f->io_y : nullptr, &dres);
+  if (rc < 0) return rc;
+  RN_CUDA(cudaMemcpyAsync(out->u, f->io_u, (size_t)n * f->nu * sizeof(double),
+                          cudaMemcpyDeviceToHost, f->stream));
+  RN_CUDA(cudaMemcpyAsync(out->x, f->io_x, (size_t)n * f->nx * sizeof(double),
+                          cudaMemcpyDeviceToHost, f->stream));
+  RN_CUDA(cudaMemcpyAsync(out->y, f->io_y, (size_t)n * ny * sizeof(double),
+                          cudaMemcpyDeviceToHost, f->stream));
+  if (dres.res_hist)
+    RN_CUDA(cudaMemcpyAsync(out->res_hist, f->io_hist,
+                            std::min(out->res_hist_len, std::max(dres.n_checks, 0)) * sizeof(double),
+                            cudaMemcpyDeviceToHost, f->stream));
+  RN_CUDA(cudaStreamSynchronize(f->stream));
+  double *hu = out->u, *hx = out->x, *hy = out->y, *hh = out->res_hist;
+  *out = dres;
+  out->u = hu;
+  out->x = hx;
+  out->y = hy;
+  out->res_hist = hh;
+  return rc;
+}
+
+extern "C" int rapidnet_dual_gradient_device(rn_factor *f, const double *x0, const double *q,
+                                             const double *demand, const double *alpha,
+                                             const double *w, double *u, double *x) {
+  clear_error();
+  if (!f || !w || !u || !x) {
+    set_error("dual_gradient: NULL argument");
+    return RN_ERR_INVAL;
+  }
+  RN_CUDA(cudaSetDevice(f->device));
+  int rc;
+  if (x0 || q || demand || alpha) {
+    if (!(x0 && q && demand && alpha)) {
+      set_error("dual_gradient: give all of x0, q, demand, alpha or none");
+      return RN_ERR_INVAL;
+    }
+    if ((rc = prepare(f, x0, q, demand, alpha))) return rc;
+  } else if (!f->have_data) {
+    set_error("dual_gradient: no data yet (give x0, q, demand, alpha)");
+    return RN_ERR_INVAL;
+  }
+  const int n = f->plan.n;
+  k_s_from_w<<<node_blocks(n), 128, 0, f->stream>>>(f->net, f->perm, n, w, f->st.s);
+  RN_CUDA(cudaGetLastError());
+  if ((rc = solve_step(f, 0))) return rc;
+  k_gather<<<node_blocks(n) + 1, 128, 0, f->stream>>>(f->net, f->perm, n, f->st.uo, f->st.xo,
+                                                      nullptr, f->q, f->x0, u, x, nullptr);
+  RN_CUDA(cudaGetLastError());
+  return check_err(f);
+}
