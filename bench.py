@@ -1,0 +1,403 @@
+#!/usr/bin/env python
+"""Benchmark of the dual APG on the 512-scenario Barcelona-sized tree.
+
+One step = one solve (rapidnet_solve_device) of ``--iters`` APG iterations
+on the synthetic 512-scenario tree (63 tanks, 114 flows, 88 demand
+sectors, 17 mixing nodes, N = 24, branching [8,4,4,2,2,1,...], 10,664
+decision nodes) with its inputs resident in HBM.  L2 is flushed (512 MB
+write) between steps, outside the timed events.  Prints one JSON line.
+
+  python bench.py [--gpus N --steps K --warmup W --precision fp64|mixed]
+  python bench.py --impl reference ...   # the FP64 CPU oracle, same metric
+
+Multi-GPU (torchrun, one rank per GPU): independent replicas of the same
+solve, no collective on the data path ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import platform
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "dual-APG iters/s & solve time to 1e-4 residual @512 scen; serving p50/p99"
+CONFIG_NAME = "barcelona512"
+WORKLOAD = ("barcelona512: synthetic Barcelona-sized network (63 tanks, 114 flows, 88 demand "
+            "sectors, 17 mixing nodes, A = I), N = 24, branching [8,4,4,2,2,1,...], "
+            "512 scenarios, 10,664 decision nodes, 2,559,360 duals")
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--iters", type=int, default=1000, help="APG iterations per step (solve)")
+    ap.add_argument("--tol-iters", type=int, default=100000,
+                    help="cap of the time-to-1e-4 solve (0 = skip)")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# per-node accounting of the persistent APG kernel (documented in the design doc)
+# ---------------------------------------------------------------------------
+def node_counts(net):
+    import numpy as np
+    nnzB = int(np.count_nonzero(net.B))
+    nnzE = int(np.count_nonzero(net.E))
+    nx, nu, ne = net.nx, net.nu, net.ne
+    # values moved per decision node per iteration in the fused two-sweep
+    # design: w read twice, y read, y+ and w+ written (5 (2nx+nu)), data
+    # terms c0, ubar, Gd d (2nu + nx)
+    values = 5 * (2 * nx + nu) + 2 * nu + nx
+    # FP64/FP32 flops per node per iteration of the sparse-Schur form
+    flops = 31 * nx + 18 * nu + 4 * nnzB + 5 * nnzE + 2 * ne * ne + 6
+    return values, flops
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6780.0), "measured"
+    return 6800.0, "fallback"
+
+
+# FP64 peak: the nominal 1.25 TFLOP/s of the GB300 (FMA = 2 flops); FP32
+# SIMT: 152 SMs x 128 lanes x 2 flops x 2.07 GHz = 80.5 TFLOP/s nominal.
+FP64_PEAK_TFLOPS = 1.25
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.device), "-lms", "200"], stdout=self.file,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [l.strip().split(", ") for l in self.file.read().splitlines() if l.strip()]
+        os.unlink(self.file.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if r[5 + k].strip().lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle: bounded sample, single thread, in a fresh process
+# ---------------------------------------------------------------------------
+ORACLE_SAMPLE = r"""
+import json, os, sys, time
+sys.path.insert(0, {root!r})
+import oracle as O
+from synthetic import make_problem
+pb = make_problem({cfg!r})
+P = O.OracleProblem.from_parts(pb.net, pb.cost, pb.tree)
+F = O.factor(P)
+S = O.solve_consts(P, F, pb.data.x0, pb.data.q, pb.data.demand, pb.data.alpha)
+gamma = O.step_size(O.power_iteration(P, F, 3))
+O.apg(P, F, S, 1, gamma)
+times = []
+t_end = time.perf_counter() + {seconds}
+while True:
+    t0 = time.perf_counter()
+    O.apg(P, F, S, {per}, gamma)
+    times.append(time.perf_counter() - t0)
+    if time.perf_counter() > t_end or len(times) >= {max_steps}:
+        break
+print(json.dumps(dict(times=times, per=int({per}))))
+"""
+
+
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def run_oracle_sample(seconds: float, per: int = 1, max_steps: int = 1000) -> dict:
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = ORACLE_SAMPLE.format(root=ROOT, cfg=CONFIG_NAME, seconds=seconds, per=per,
+                                max_steps=max_steps)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed:\n" + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle as it stands
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    total = args.warmup + args.steps
+    d = run_oracle_sample(seconds=1e9, per=1, max_steps=total)
+    times = d["times"][args.warmup:]
+    iters = d["per"] * len(times)
+    secs = sum(times)
+    value = iters / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * secs / len(times), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "step": "one APG iteration of the FP64 CPU oracle "
+                   "(general per-node Riccati recursion, numpy, one thread)"},
+        "cpu_baseline": {"value": value, "unit": "iters/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{len(times)} oracle APG iterations on {CONFIG_NAME} "
+                                   f"after {args.warmup} warm-up iterations; host {cpu_model()}"},
+        "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    # the oracle's CPU sample runs first, in a fresh process, before any GPU work
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = run_oracle_sample(args.cpu_seconds)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1904_10548_gb300 as rn
+    from synthetic import make_problem
+
+    pb = make_problem(CONFIG_NAME)
+    net, tree, data = pb.net, pb.tree, pb.data
+    n = tree.n_nodes
+    nx, nu, nd = net.nx, net.nu, net.nd
+    ny = 2 * nx + nu
+    prec = rn.RN_PREC_FP64 if args.precision == "fp64" else rn.RN_PREC_MIXED
+    stream = torch.cuda.Stream()
+    fac = rn.Factor(net, pb.cost, tree, precision=prec, device=local, stream=stream)
+    info = fac.info()
+
+    dev = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    x0, q, dem, alp = dev(data.x0), dev(data.q), dev(data.demand), dev(data.alpha)
+    u = torch.empty((n, nu), dtype=torch.float64, device="cuda")
+    x = torch.empty((n, nx), dtype=torch.float64, device="cuda")
+    y = torch.empty((n, ny), dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        return fac.solve_device(x0, q, dem, alp, args.iters, 0.0, u, x, y)
+
+    for _ in range(args.warmup):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = []
+    apg_ms = []
+    launches = 0
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = step()
+        e1.record(stream)
+        evs.append((e0, e1))
+        apg_ms.append(r["apg_ms"])
+        launches += 8  # kq, prep, x*(0) step, init, APG, gather, reduce, final reduce
+        assert r["iters"] == args.iters
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = sum(a.elapsed_time(b) for a, b in evs)
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = world * args.steps * args.iters / (total_ms / 1e3)
+
+    # end to end through the host entry point: pinned host inputs and outputs
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).pin_memory()
+    hx0, hq, hdem, halp = pin(data.x0), pin(data.q), pin(data.demand), pin(data.alpha)
+    hu = torch.empty((n, nu), dtype=torch.float64).pin_memory()
+    hx = torch.empty((n, nx), dtype=torch.float64).pin_memory()
+    hy = torch.empty((n, ny), dtype=torch.float64).pin_memory()
+    e2e_s = []
+    for k in range(args.e2e_steps + 1):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fac.solve(hx0.numpy(), hq.numpy(), hdem.numpy(), halp.numpy(), args.iters,
+                  out=(hu.numpy(), hx.numpy(), hy.numpy()))
+        if k > 0:
+            e2e_s.append(time.perf_counter() - t0)
+    e2e_val = args.iters / (sum(e2e_s) / len(e2e_s)) * world
+    h2d = 8 * (nx + nu + n * nd + n * nu)
+    d2h = 8 * n * (nu + nx + ny)
+
+    # time to 1e-4
+    tol_run = None
+    if args.tol_iters > 0:
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = fac.solve_device(x0, q, dem, alp, args.tol_iters, 1e-4, u, x, y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tol_run = {"tol": 1e-4, "converged": r["status"] == rn.RN_OK, "iters": r["iters"],
+                   "ms": e0.elapsed_time(e1), "residual": r["primal_res"],
+                   "ubox_viol": r["ubox_viol"], "check_every": 10}
+
+    # roofline of the dominant kernel (the persistent APG launch)
+    values, flops = node_counts(net)
+    nodes = n - 1
+    bpv = 8 if args.precision == "fp64" else 4
+    apg_avg_s = sum(apg_ms) / len(apg_ms) / 1e3
+    hbm_peak, hbm_src = load_peaks()
+    bytes_launch = values * bpv * nodes * args.iters
+    flops_launch = flops * nodes * args.iters
+    gbs = bytes_launch / apg_avg_s / 1e9
+    tfl = flops_launch / apg_avg_s / 1e12
+    if args.precision == "fp64":
+        roof = {"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": tfl / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "nominal GB300 FP64 (recipe table)",
+                "hbm_view": {"achieved_gbs": gbs, "peak_gbs": hbm_peak,
+                             "frac": gbs / hbm_peak, "peak_source": hbm_src}}
+    else:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": gbs / hbm_peak, "traffic": None, "peak_source": f"{hbm_src} copy bandwidth"}
+    roof.update(bytes_per_launch=bytes_launch, flops_per_launch=flops_launch,
+                kernel_ms=apg_avg_s * 1e3, us_per_iter=apg_avg_s * 1e6 / args.iters,
+                per_node={"values": values, "bytes": values * bpv, "flops": flops})
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "iters_per_step": args.iters,
+                   "precision": args.precision, "l2": "flushed between steps (512 MB write)",
+                   "grid_ctas": info["grid_ctas"], "block_threads": info["block_threads"],
+                   "gamma": info["gamma"], "parallelism": f"replicas x{world}"},
+        "e2e": {"value": e2e_val, "unit": "iters/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "roofline": roof,
+        "time_to_tol": tol_run,
+    }
+    if cpu is not None:
+        cv = cpu["per"] * len(cpu["times"]) / sum(cpu["times"])
+        line["cpu_baseline"] = {"value": cv, "unit": "iters/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{len(cpu['times'])} FP64 oracle APG iterations on "
+                                          f"{CONFIG_NAME}, one thread, host {cpu_model()} "
+                                          f"({os.cpu_count()} cores present)"}
+    if rank == 0:
+        print(json.dumps(line))
+    fac.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -125,6 +125,8 @@ typedef struct {
   double gap;          /* cost(x*(y)) - dual value at y (NaN unless
                           compute_gap) */
   double gamma;        /* step size used */
+  double apg_ms;       /* device time of the APG iterations (CUDA events on
+                          the handle's stream around the persistent launch) */
 } rn_result;
 
 typedef struct rn_factor rn_factor;

@@ -63,7 +63,7 @@ class rn_result(ctypes.Structure):
     _fields_ = [("u", PD), ("x", PD), ("y", PD), ("res_hist", PD), ("res_hist_len", c_int),
                 ("compute_gap", c_int), ("iters", c_int), ("n_checks", c_int),
                 ("primal_res", c_double), ("ubox_viol", c_double), ("cost", c_double),
-                ("gap", c_double), ("gamma", c_double)]
+                ("gap", c_double), ("gamma", c_double), ("apg_ms", c_double)]
 
 
 class rn_factor_info(ctypes.Structure):
@@ -213,24 +213,31 @@ class Factor:
         return {f: getattr(i, f) for f, _ in rn_factor_info._fields_}
 
     def solve(self, x0, q, demand, alpha, max_iters: int, tol: float = 0.0, y_warm=None,
-              compute_gap: bool = False, res_hist_len: int = 0) -> dict:
-        """Host arrays in and out (rapidnet_solve)."""
+              compute_gap: bool = False, res_hist_len: int = 0, out=None) -> dict:
+        """Host arrays in and out (rapidnet_solve).  ``out`` may supply
+        contiguous float64 arrays (u, x, y), e.g. views of pinned memory."""
         n = self.n_nodes
         x0 = _f64(x0, (self.nx,))
         q = _f64(q, (self.nu,))
         demand = _f64(demand, (n, self.nd))
         alpha = _f64(alpha, (n, self.nu))
         yw = None if y_warm is None else _f64(y_warm, (n, self.ny))
-        u = np.empty((n, self.nu))
-        x = np.empty((n, self.nx))
-        y = np.empty((n, self.ny))
+        if out is not None:
+            u, x, y = out
+            for a, shp in ((u, (n, self.nu)), (x, (n, self.nx)), (y, (n, self.ny))):
+                if a.dtype != np.float64 or a.shape != shp or not a.flags.c_contiguous:
+                    raise ValueError("out arrays must be C-contiguous float64 of the output shapes")
+        else:
+            u = np.empty((n, self.nu))
+            x = np.empty((n, self.nx))
+            y = np.empty((n, self.ny))
         hist = np.zeros(max(res_hist_len, 1))
         res = rn_result(_pd(u), _pd(x), _pd(y), _pd(hist) if res_hist_len else None,
                         res_hist_len, int(compute_gap))
         rc = rapidnet_solve(self.h, _pd(x0), _pd(q), _pd(demand), _pd(alpha), max_iters, tol,
                             None if yw is None else _pd(yw), res)
         out = {f: getattr(res, f) for f in ("iters", "n_checks", "primal_res", "ubox_viol",
-                                            "cost", "gap", "gamma")}
+                                            "cost", "gap", "gamma", "apg_ms")}
         out.update(status=rc, u=u, x=x, y=y,
                    res_hist=hist[:min(res_hist_len, res.n_checks)] if res_hist_len else None)
         return out
@@ -245,7 +252,7 @@ class Factor:
         rc = rapidnet_solve_device(self.h, _dev_ptr(x0), _dev_ptr(q), _dev_ptr(demand),
                                    _dev_ptr(alpha), max_iters, tol, _dev_ptr(y_warm), res)
         out = {f: getattr(res, f) for f in ("iters", "n_checks", "primal_res", "ubox_viol",
-                                            "cost", "gap", "gamma")}
+                                            "cost", "gap", "gamma", "apg_ms")}
         out["status"] = rc
         return out
 

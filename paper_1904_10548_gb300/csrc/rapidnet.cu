@@ -400,6 +400,7 @@ struct rn_factor {
   unsigned *sync = nullptr;  // counts | flags | barrier
   size_t sync_words = 0;
   int *err = nullptr, *info = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool have_data = false;
   // host staging for rapidnet_solve (host pointers)
   double *io_y = nullptr, *io_u = nullptr, *io_x = nullptr, *io_hist = nullptr;
@@ -407,6 +408,8 @@ struct rn_factor {
 
   ~rn_factor() {
     if (device >= 0) cudaSetDevice(device);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
     for (void *p : allocs) cudaFree(p);
     if (own_stream && stream) cudaStreamDestroy(stream);
   }
@@ -838,6 +841,8 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
     f->L = L;
     f->gamma = 1.0 / (1.01 * L);
   }
+  RN_CUDA(cudaEventCreate(&f->ev0));
+  RN_CUDA(cudaEventCreate(&f->ev1));
   RN_CUDA(cudaStreamSynchronize(f->stream));
   return RN_OK;
 }
@@ -948,11 +953,16 @@ int solve_device_impl(rn_factor *f, const double *x0, const double *q, const dou
   P.iters = max_iters;
   P.check_every = f->opts.check_every;
   P.tol = tol > 0.0 ? tol : 0.0;
+  RN_CUDA(cudaEventRecord(f->ev0, f->stream));
   RN_CUDA((launch_solve<double, true>(P, f->grid, f->block, f->smem, f->stream)));
+  RN_CUDA(cudaEventRecord(f->ev1, f->stream));
   int info[3] = {0, 0, 0};
   RN_CUDA(cudaMemcpyAsync(info, f->info, 3 * sizeof(int), cudaMemcpyDeviceToHost, f->stream));
   if ((rc = check_err(f))) return rc;
   const int iters = info[0], nchk = info[1], reason = info[2];
+  float apg_ms = 0.f;
+  RN_CUDA(cudaEventElapsedTime(&apg_ms, f->ev0, f->ev1));
+  out->apg_ms = apg_ms;
   // y^{iters} was written into the buffer that held y^{iters-2}
   const double *yfin = ((iters - 1) & 1) ? f->st.ya : f->st.yb;
   k_gather<<<node_blocks(n) + 1, 128, 0, f->stream>>>(f->net, f->perm, n, f->st.uo, f->st.xo, yfin,

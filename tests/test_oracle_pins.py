@@ -325,25 +325,36 @@ def _run(P, data, iters, **kw):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("Ws", [0.1, 20.0])
-def test_duality_gap_vanishes(Ws):
+@pytest.mark.parametrize("variant", ["base", "safety", "box"])
+def test_duality_gap_vanishes(variant):
+    """base: default weights; safety: tanks start below a raised safety
+    level with W_s = 20 (the y2 prox is active); box: the upper level is
+    lowered under the initial levels (the W_x penalty is active)."""
+    Ws = 20.0 if variant == "safety" else 0.1
     P, data = synth("tiny", Ws=Ws)
-    if Ws > 1:
-        P.xs = 0.75 * P.xmax  # tanks start below the safety level
-    F, S, R = _run(P, data, 6000)
+    iters, res_max, gap_max = 6000, 1e-4, 2e-5
+    if variant == "safety":
+        P.xs = 0.75 * P.xmax
+        res_max = 1e-3
+    if variant == "box":
+        P.xmax = 0.45 * P.xmax
+        iters, res_max, gap_max = 3000, 0.05, 1e-4
+    F, S, R = _run(P, data, iters)
     pc = O.primal_cost(P, S, R.u, R.x)
     dv = O.dual_value(P, F, S, R.y)
     assert np.isfinite(dv)
-    assert abs(pc - dv) <= 2e-5 * abs(pc)
-    assert R.residual < (1e-4 if Ws < 1 else 1e-3)
-    # weak duality holds for every dual point: D(y) <= P at the optimum
+    assert abs(pc - dv) <= gap_max * abs(pc)
+    assert R.residual < res_max
+    # the prox step leaves every dual block inside dom g*
     nx = P.nx
     y1, y2 = R.y[1:, :nx], R.y[1:, nx:2 * nx]
     assert np.all(np.linalg.norm(y1, axis=1) <= P.Wx * (1 + 1e-12))
     assert np.all(y2 <= 0.0)
     assert np.all(np.linalg.norm(y2, axis=1) <= P.Ws * (1 + 1e-12))
-    if Ws > 1:
-        assert np.abs(y2).max() > 0  # the safety prox is active in this variant
+    if variant == "safety":
+        assert np.abs(y2).max() > 0
+    if variant == "box":
+        assert np.abs(y1).max() > 0
 
 
 def test_g_zero_gives_unconstrained_tree_qp():
