@@ -186,6 +186,32 @@ int rapidnet_dual_gradient_device(rn_factor *f, const double *x0,
                                   const double *alpha, const double *w,
                                   double *u, double *x);
 
+/* Dual gradient without allocation.  The paper has no counterpart: this
+ * serves callers that must not allocate device memory after start-up (a
+ * real-time control loop with a no-allocation rule for predictable
+ * timing, or a host that owns the device memory pool).  Such a caller
+ * creates the handle and runs one solve (or rapidnet_dual_gradient_device
+ * with data) during set-up; this call then gives the same result as
+ * rapidnet_dual_gradient_device for the data of that last solve: w in
+ * (n_nodes*(2nx+nu)), u (n_nodes*nu) and x (n_nodes*nx) out, all device
+ * pointers, FP64.
+ * Scratch: one fixed array of 8 MiB of device memory inside the library,
+ * held by every device that loads the library until the process exits.
+ * A tree needs 8 n (2 (nxp + nup) + 2 nup + nxp) + 4 (n + max(s,1) + 6) bytes
+ * (n = n_nodes, s = number of stage-1 nodes with two or more leaves,
+ * nxp / nup = nx / nu rounded up to multiples of 4); larger trees get
+ * RN_ERR_INVAL.  About 1,590 nodes of the Barcelona-sized network fit:
+ * the 32-scenario tree does, the 512-scenario tree does not.
+ * No cudaMalloc, cudaFree or allocating routine is called.  The first
+ * call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call shares the one array and finds the previous call's contents
+ * in it: calls that overlap on the GPU (other streams, handles or host
+ * threads) race and must be serialised by the caller.  Synchronises the
+ * handle's stream. */
+int rapidnet_dual_gradient_noalloc(rn_factor *f, const double *w, double *u,
+                                   double *x);
+
 /* Description of the last failure on the calling thread ("" if none). */
 const char *rapidnet_last_error(void);
 

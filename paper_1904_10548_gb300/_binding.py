@@ -84,6 +84,7 @@ EXPORTS = {
                                       c_double, c_void_p, POINTER(rn_result)]),
     "rapidnet_dual_gradient_device": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                               c_void_p, c_void_p, c_void_p]),
+    "rapidnet_dual_gradient_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "rapidnet_last_error": (ctypes.c_char_p, []),
 }
 
@@ -150,6 +151,10 @@ def rapidnet_solve_device(h, x0, q, demand, alpha, max_iters, tol, y_warm, res) 
 
 def rapidnet_dual_gradient_device(h, x0, q, demand, alpha, w, u, x) -> int:
     return _check(load().rapidnet_dual_gradient_device(h, x0, q, demand, alpha, w, u, x))
+
+
+def rapidnet_dual_gradient_noalloc(h, w, u, x) -> int:
+    return _check(load().rapidnet_dual_gradient_noalloc(h, w, u, x))
 
 
 # ---------------------------------------------------------------------------
@@ -259,6 +264,10 @@ class Factor:
     def dual_gradient_device(self, w, u, x, x0=None, q=None, demand=None, alpha=None) -> None:
         rapidnet_dual_gradient_device(self.h, _dev_ptr(x0), _dev_ptr(q), _dev_ptr(demand),
                                       _dev_ptr(alpha), _dev_ptr(w), _dev_ptr(u), _dev_ptr(x))
+
+    def dual_gradient_noalloc(self, w, u, x) -> None:
+        """x*(w) with the library's fixed scratch array (no allocation)."""
+        rapidnet_dual_gradient_noalloc(self.h, _dev_ptr(w), _dev_ptr(u), _dev_ptr(x))
 
     def close(self) -> None:
         if getattr(self, "h", None):

@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <vector>
 
 #include "kernels.cuh"
@@ -1167,4 +1168,123 @@ extern "C" int rapidnet_dual_gradient_device(rn_factor *f, const double *x0, con
                                                       nullptr, f->q, f->x0, u, x, nullptr);
   RN_CUDA(cudaGetLastError());
   return check_err(f);
+}
+
+// ---------------------------------------------------------------------------
+// Dual gradient without any allocation
+//
+// For callers that must not allocate device memory once they are running:
+// a real-time control loop that forbids allocation after start-up for
+// predictable timing, a host that hands the GPU to us inside a memory pool
+// or a captured region it owns, or an embedding that counts every byte.
+// Such a caller creates the factor handle (and runs one solve or
+// rapidnet_dual_gradient_device with data) during set-up; afterwards
+// rapidnet_dual_gradient_noalloc evaluates x*(w) with the per-call scratch
+// (backward inputs, subtree sums, path terms, outputs in internal order,
+// counters and flags) taken from the fixed array below instead of the
+// handle's buffers.  It calls no cudaMalloc, cudaFree or allocating
+// library routine.
+// ---------------------------------------------------------------------------
+namespace {
+
+// 8 MiB of doubles, held by every device that loads the library until exit
+constexpr size_t kNoAllocDoubles = (size_t)1 << 20;
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double *g_noalloc_addr[kMaxDevices] = {};
+
+// device address of the scratch array on the current device (looked up once
+// per device; the host-side name is only a stand-in for the symbol)
+int noalloc_scratch(int device, double **out) {
+  if (device < 0 || device >= kMaxDevices) {
+    set_error("noalloc: device ordinal %d out of range", device);
+    return RN_ERR_INVAL;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[device]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      set_error("noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+      return RN_ERR_CUDA;
+    }
+    g_noalloc_addr[device] = static_cast<double *>(p);
+  }
+  *out = g_noalloc_addr[device];
+  return RN_OK;
+}
+
+}  // namespace
+
+extern "C" int rapidnet_dual_gradient_noalloc(rn_factor *f, const double *w, double *u,
+                                              double *x) {
+  clear_error();
+  if (!f || !w || !u || !x) {
+    set_error("dual_gradient_noalloc: NULL argument");
+    return RN_ERR_INVAL;
+  }
+  if (!f->have_data) {
+    set_error("dual_gradient_noalloc: no data yet (run a solve or "
+              "rapidnet_dual_gradient_device with data during set-up)");
+    return RN_ERR_INVAL;
+  }
+  const int n = f->plan.n;
+  const size_t rows = (size_t)n;
+  const size_t sync_words = rows + (size_t)std::max(1, f->plan.n_flags) + 1;
+  // doubles: s, up (SP), z, uo (NUP), xo (NXP); then sync words, err, info
+  const size_t need_d = rows * (2 * (size_t)f->SP + 2 * (size_t)f->NUP + (size_t)f->NXP);
+  const size_t need_w = sync_words + 1 + 4;  // 32-bit words
+  const size_t need = need_d + (need_w + 1) / 2;
+  if (need > kNoAllocDoubles) {
+    set_error("dual_gradient_noalloc: this tree needs %zu bytes of scratch, more than the "
+              "static %zu bytes (n_nodes = %d)", need * sizeof(double),
+              kNoAllocDoubles * sizeof(double), n);
+    return RN_ERR_INVAL;
+  }
+  RN_CUDA(cudaSetDevice(f->device));
+  double *base = nullptr;
+  int rc = noalloc_scratch(f->device, &base);
+  if (rc) return rc;
+  StateDev<double> st = f->st;
+  double *p = base;
+  st.s = p;
+  p += rows * f->SP;
+  st.up = p;
+  p += rows * f->SP;
+  st.z = p;
+  p += rows * f->NUP;
+  st.uo = p;
+  p += rows * f->NUP;
+  st.xo = p;
+  p += rows * f->NXP;
+  unsigned *words = reinterpret_cast<unsigned *>(p);
+  st.count = words;
+  st.flags = words + rows;
+  st.barrier = words + rows + std::max(1, f->plan.n_flags);
+  st.err = reinterpret_cast<int *>(words + sync_words);
+  st.info = st.err + 1;
+  st.res = nullptr;
+  st.beta = nullptr;
+  // the array keeps the previous call's contents: counters, flags and the
+  // error word must start at zero; padding columns of s and up as well
+  RN_CUDA(cudaMemsetAsync(words, 0, need_w * sizeof(unsigned), f->stream));
+  RN_CUDA(cudaMemsetAsync(st.s, 0, rows * 2 * f->SP * sizeof(double), f->stream));
+  k_s_from_w<<<node_blocks(n), 128, 0, f->stream>>>(f->net, f->perm, n, w, st.s);
+  RN_CUDA(cudaGetLastError());
+  KParams<double> P = base_params(f);
+  P.st = st;
+  RN_CUDA((launch_solve<double, false>(P, f->grid, f->block, f->smem, f->stream)));
+  k_gather<<<node_blocks(n) + 1, 128, 0, f->stream>>>(f->net, f->perm, n, st.uo, st.xo, nullptr,
+                                                      f->q, f->x0, u, x, nullptr);
+  RN_CUDA(cudaGetLastError());
+  int e = 0;
+  RN_CUDA(cudaMemcpyAsync(&e, st.err, sizeof(int), cudaMemcpyDeviceToHost, f->stream));
+  RN_CUDA(cudaStreamSynchronize(f->stream));
+  if (e) {
+    set_error("dual_gradient_noalloc: a device-side wait gave up");
+    return RN_ERR_TIMEOUT;
+  }
+  return RN_OK;
 }
