@@ -50,6 +50,7 @@ struct PlanDev {
 template <typename T>
 struct StateDev {
   T *s, *ya, *yb, *ub, *gb, *z, *up, *uo, *xo;
+  float *uo32, *xo32;  // optional FP32 copies of uo / xo (plain step)
   const T *inv2p;   // 1 / (2 p) per internal node
   const T *xroot;   // x0 (nx); unused when linear
   const double *beta;  // beta_0 .. beta_iters (APG)
@@ -67,16 +68,68 @@ struct KParams {
   int iters;        // APG iterations (1 for a plain solve step)
   int check_every;
   int linear;       // 1: constants of the dual gradient are zero
+  int maxc;         // state components per lane in the dual update: 2, 4 or 8
+  int buf_elems;    // shared-memory buffer size (elements of T), smem_buf_elems
+  int net_bytes;    // bytes of the block's shared-memory copy of the network
   unsigned step_base;
   double gamma, invgamma, tol;
 };
 
-// dynamic shared memory of the persistent kernel (layout in solve_kernels.cu)
+// Mixed precision (FP32 iteration around an FP64 reference): the dual is
+// y = yb + d with the FP64 base yb refreshed every R iterations and the
+// FP32 delta d; ybh = fl32(yb) serves the proximal decisions.  The
+// primal of the FP32 solve step is x = xref + x_lin(dw), dw = w - yb,
+// with xref = x*(yb) computed in FP64 at each refresh.
+struct MixedDev {
+  double *yb;         // n x YP  FP64 base of the dual
+  float *ybh;         // n x YP  fl32(yb)
+  float *da, *db;     // n x YP  FP32 deltas (swapped every iteration)
+  const float *uref;  // n x NUP inputs of x*(yb)
+  const float *xref;  // n x NXP states of x*(yb)
+  float *sw;          // n x SP  (dw1 + dw2 | dw3) of the last checked iteration
+  double *s64;        // n x SP  FP64 backward input of the refresh step
+  int refresh_every;
+};
+
+struct MixedParams {
+  KParams<float> f;   // FP32 iterations (linear dual gradient on dw)
+  KParams<double> d;  // FP64 refresh / final evaluations
+  MixedDev mx;
+};
+
+cudaError_t launch_mixed(const MixedParams &M, int maxc, int grid, int block, size_t smem,
+                         cudaStream_t st);
+cudaError_t mixed_occupancy(int maxc, int block, size_t smem, int *blocks_per_sm);
+
+// shared-memory buffer of the persistent kernels, in elements of T: the
+// backward segment (kSeg rows of s plus E/S^-1 work space) or one staged
+// forward segment (SEGF nodes, fwd_elems_per_node each), whichever is larger
+inline int smem_buf_elems(int elem_bytes, int NXP, int NUP, int YP, int SP, int NEP, int mode) {
+  const int segf = elem_bytes == 8 ? 4 : 8;
+  const int back = kSeg * SP + 2 * kSeg * NEP + kSeg;
+  const int fwd = segf * (3 * NUP + 2 * NXP + (mode == 1 ? 2 * YP : (mode == 2 ? 3 * YP : 0)));
+  return back > fwd ? back : fwd;
+}
+
+// dynamic shared memory in bytes for a buffer of buf_elems elements of T
+// (the block's copy of the network data comes on top: net_smem_bytes)
 template <typename T>
-inline size_t smem_bytes(int SP, int NEP, int NUP) {
-  size_t b = sizeof(T) * ((size_t)kSeg * SP + 2 * (size_t)kSeg * NEP + kSeg + NUP + 72);
+inline size_t smem_bytes(int buf_elems) {
+  size_t b = sizeof(T) * ((size_t)buf_elems + 72);
   b = (b + 15) & ~(size_t)15;
-  return b + 40 * sizeof(unsigned long long) + 4 * sizeof(int);
+  b += 40 * sizeof(unsigned long long) + (4 + 2 * kSeg) * sizeof(int);
+  return (b + 15) & ~(size_t)15;
+}
+
+__host__ __device__ inline size_t round16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+// bytes of a block's shared-memory copy of the network data: the NetDev
+// header, the sparse index arrays and the values in elements of elem bytes
+__host__ __device__ inline size_t net_smem_bytes(int nx, int nu, int ne, int nnzB, int nnzE,
+                                                 int elem) {
+  const size_t ints = (size_t)(nu + 1) + nnzB + (nx + 1) + nnzB + (ne + 1) + nnzE + (nu + 1) + nnzE;
+  const size_t vals = 2 * (size_t)nnzB + 2 * (size_t)nnzE + nu + (size_t)ne * ne + 3 * nx + 2 * nu;
+  return round16(sizeof(NetDev<double>)) + round16(ints * 4) + round16(vals * elem);
 }
 
 // host launchers of the persistent kernel (cooperative launch: every block
@@ -84,6 +137,6 @@ inline size_t smem_bytes(int SP, int NEP, int NUP) {
 template <typename T, bool APG>
 cudaError_t launch_solve(const KParams<T> &P, int grid, int block, size_t smem, cudaStream_t st);
 template <typename T, bool APG>
-cudaError_t solve_occupancy(int block, size_t smem, int *blocks_per_sm);
+cudaError_t solve_occupancy(int maxc, int block, size_t smem, int *blocks_per_sm);
 
 }  // namespace rn

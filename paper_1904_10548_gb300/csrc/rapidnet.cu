@@ -282,14 +282,20 @@ __global__ void k_node_reduce(NetDev<double> nt, ReduceArgs a, int n, double *pa
   }
 }
 
+// sum (max for the third entry) of the per-block partials, one warp, fixed order
 __global__ void k_final_reduce(const double *partial, int nb, double *out) {
-  if (threadIdx.x == 0) {
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-    for (int b = 0; b < nb; ++b) {
-      s0 += partial[3 * b];
-      s1 += partial[3 * b + 1];
-      s2 = fmax(s2, partial[3 * b + 2]);
-    }
+  const int lane = threadIdx.x;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  for (int b = lane; b < nb; b += 32) {
+    s0 += partial[3 * b];
+    s1 += partial[3 * b + 1];
+    s2 = fmax(s2, partial[3 * b + 2]);
+  }
+  s0 = warp_sum(s0);
+  s1 = warp_sum(s1);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s2 = fmax(s2, __shfl_xor_sync(0xffffffffu, s2, o));
+  if (lane == 0) {
     out[0] = s0;
     out[1] = s1;
     out[2] = s2;
@@ -365,6 +371,56 @@ __global__ void k_power_scale(NetDev<double> nt, int n, const double *uo, const 
   }
 }
 
+// mixed precision: base yb = y_warm (or 0), ybh = fl32(yb), deltas 0,
+// FP64 step input s64 = (yb1 + yb2 | yb3), FP32 step input 0
+__global__ void k_mixed_init(NetDev<double> nt, const int *perm, int n, const double *y_warm,
+                             double *yb, float *ybh, float *da, float *db, double *s64,
+                             float *s32) {
+  const int ny = 2 * nt.nx + nt.nu;
+  for (int v = blockIdx.x + 1; v < n; v += gridDim.x) {
+    const double *src = y_warm ? y_warm + (size_t)perm[v] * ny : nullptr;
+    for (int e = threadIdx.x; e < nt.YP; e += blockDim.x) {
+      double val = 0.0;
+      if (src) {
+        if (e < nt.nx) val = src[e];
+        else if (e >= nt.NXP && e < nt.NXP + nt.nx) val = src[nt.nx + e - nt.NXP];
+        else if (e >= 2 * nt.NXP && e < 2 * nt.NXP + nt.nu) val = src[2 * nt.nx + e - 2 * nt.NXP];
+      }
+      const size_t o = (size_t)v * nt.YP + e;
+      yb[o] = val;
+      ybh[o] = (float)val;
+      da[o] = 0.f;
+      db[o] = 0.f;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nt.SP; e += blockDim.x) {
+      const double *y = yb + (size_t)v * nt.YP;
+      double val = 0.0;
+      if (e < nt.nx) val = y[e] + y[nt.NXP + e];
+      else if (e >= nt.NXP && e < nt.NXP + nt.nu) val = y[2 * nt.NXP + (e - nt.NXP)];
+      s64[(size_t)v * nt.SP + e] = val;
+      s32[(size_t)v * nt.SP + e] = 0.f;
+    }
+  }
+}
+
+// final dual y = yb + d into breadth-first rows (FP64)
+__global__ void k_gather_mixed_y(NetDev<double> nt, const int *perm, int n, const double *yb,
+                                 const float *d, double *y) {
+  const int ny = 2 * nt.nx + nt.nu;
+  for (int v = blockIdx.x; v < n; v += gridDim.x) {
+    const int b = perm[v];
+    for (int e = threadIdx.x; e < ny; e += blockDim.x) {
+      double val = 0.0;
+      if (v != 0) {
+        const int c = e < nt.nx ? e : (e < 2 * nt.nx ? nt.NXP + e - nt.nx : 2 * nt.NXP + e - 2 * nt.nx);
+        val = yb[(size_t)v * nt.YP + c] + (double)d[(size_t)v * nt.YP + c];
+      }
+      y[(size_t)b * ny + e] = val;
+    }
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -379,13 +435,19 @@ struct rn_factor {
   int nx = 0, nu = 0, nd = 0, ne = 0, NXP = 0, NUP = 0, SP = 0, YP = 0, NEP = 0;
   double W_alpha = 0.0, Ws = 0.0, Wx = 0.0;
   double gamma = 0.0, L = 0.0;
-  int grid = 0, block = 0;
+  int grid = 0, block = 0, maxc = 2, buf_d = 0, buf_f = 0, net_bytes_d = 0, net_bytes_f = 0;
   size_t smem = 0;
   std::vector<void *> allocs;
   long long bytes = 0;
   NetDev<double> net{};
   PlanDev pd{};
   StateDev<double> st{};
+  // mixed precision: FP32 network data and state, delta form of the dual
+  NetDev<float> netf{};
+  StateDev<float> stf{};
+  MixedDev mx{};
+  int grid_mixed = 0;
+  size_t smem_mixed = 0;
   // device copies of host data
   int *perm = nullptr;
   double *prob = nullptr, *inv2p = nullptr, *alpha0 = nullptr, *wdiag = nullptr;
@@ -517,6 +579,29 @@ KParams<double> base_params(rn_factor *f) {
   P.gamma = f->gamma;
   P.invgamma = f->gamma > 0 ? 1.0 / f->gamma : 0.0;
   P.tol = 0.0;
+  P.maxc = f->maxc;
+  P.buf_elems = f->buf_d;
+  P.net_bytes = f->net_bytes_d;
+  return P;
+}
+
+KParams<float> base_params_f(rn_factor *f) {
+  KParams<float> P{};
+  P.net = f->netf;
+  P.plan = f->pd;
+  P.st = f->stf;
+  P.st.res = f->st.res;
+  P.st.beta = f->st.beta;
+  P.iters = 1;
+  P.check_every = 1;
+  P.linear = 1;
+  P.step_base = 0;
+  P.gamma = f->gamma;
+  P.invgamma = f->gamma > 0 ? 1.0 / f->gamma : 0.0;
+  P.tol = 0.0;
+  P.maxc = f->maxc;
+  P.buf_elems = f->buf_f;
+  P.net_bytes = f->net_bytes_f;
   return P;
 }
 
@@ -648,9 +733,9 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
   rc = build_plan(tree, f->plan);
   if (rc) return rc;
   f->opts = opts ? *opts : rn_opts{};
-  if (f->opts.precision != RN_PREC_FP64) {
-    set_error("this build implements RN_PREC_FP64 only");
-    return RN_ERR_UNSUPPORTED;
+  if (f->opts.precision != RN_PREC_FP64 && f->opts.precision != RN_PREC_MIXED) {
+    set_error("precision must be RN_PREC_FP64 or RN_PREC_MIXED");
+    return RN_ERR_INVAL;
   }
   if (f->opts.power_iters <= 0) f->opts.power_iters = 200;
   if (f->opts.check_every <= 0) f->opts.check_every = 10;
@@ -812,13 +897,88 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
   st.res = nullptr;
   st.beta = nullptr;
 
+  if (f->opts.precision == RN_PREC_MIXED) {
+    // FP32 copies of the network data (index arrays shared) and FP32 state
+    auto tof = [](const double *p, size_t m) { return std::vector<float>(p, p + m); };
+    auto tofv = [](const std::vector<double> &v) { return std::vector<float>(v.begin(), v.end()); };
+    NetDev<float> &nf = f->netf;
+    nf.nx = nx;
+    nf.nu = nu;
+    nf.ne = ne;
+    nf.nd = nd;
+    nf.NXP = f->NXP;
+    nf.NUP = f->NUP;
+    nf.SP = f->SP;
+    nf.YP = f->YP;
+    nf.NEP = f->NEP;
+    nf.Wx = (float)cost->Wx;
+    nf.Ws = (float)cost->Ws;
+    nf.Bc_ptr = nt.Bc_ptr;
+    nf.Bc_idx = nt.Bc_idx;
+    nf.Br_ptr = nt.Br_ptr;
+    nf.Br_idx = nt.Br_idx;
+    nf.Er_ptr = nt.Er_ptr;
+    nf.Er_idx = nt.Er_idx;
+    nf.Ec_ptr = nt.Ec_ptr;
+    nf.Ec_idx = nt.Ec_idx;
+    float *fp;
+#define UP_F(field, vec) \
+  if ((rc = upload(f, &fp, vec))) return rc; \
+  field = fp;
+    UP_F(nf.Bc_val, tofv(Bc.val)) UP_F(nf.Br_val, tofv(Br.val)) UP_F(nf.Er_val, tofv(Er.val))
+    UP_F(nf.Ec_val, tofv(Ec.val)) UP_F(nf.winv, tofv(winv)) UP_F(nf.Sinv, tofv(Sinv))
+    UP_F(nf.xmin, tof(net->xmin, nx)) UP_F(nf.xmax, tof(net->xmax, nx)) UP_F(nf.xs, tof(net->xs, nx))
+    UP_F(nf.umin, tof(net->umin, nu)) UP_F(nf.umax, tof(net->umax, nu))
+    UP_F(f->stf.inv2p, tofv(inv2p))
+#undef UP_F
+    float *s32, *z32, *up32, *da, *db, *ybh, *uref, *xref, *sw;
+    if ((rc = dalloc(f, &s32, (size_t)n * f->SP)) || (rc = dalloc(f, &z32, (size_t)n * f->NUP)) ||
+        (rc = dalloc(f, &up32, (size_t)n * f->SP)) || (rc = dalloc(f, &da, (size_t)n * f->YP)) ||
+        (rc = dalloc(f, &db, (size_t)n * f->YP)) || (rc = dalloc(f, &ybh, (size_t)n * f->YP)) ||
+        (rc = dalloc(f, &uref, (size_t)n * f->NUP)) || (rc = dalloc(f, &xref, (size_t)n * f->NXP)) ||
+        (rc = dalloc(f, &sw, (size_t)n * f->SP)))
+      return rc;
+    for (auto pr : {std::make_pair((void *)s32, (size_t)n * f->SP), {(void *)z32, (size_t)n * f->NUP},
+                    {(void *)up32, (size_t)n * f->SP}, {(void *)da, (size_t)n * f->YP},
+                    {(void *)db, (size_t)n * f->YP}, {(void *)ybh, (size_t)n * f->YP},
+                    {(void *)uref, (size_t)n * f->NUP}, {(void *)xref, (size_t)n * f->NXP},
+                    {(void *)sw, (size_t)n * f->SP}})
+      RN_CUDA(cudaMemset(pr.first, 0, pr.second * sizeof(float)));
+    StateDev<float> &sf = f->stf;
+    sf.s = s32;
+    sf.z = z32;
+    sf.up = up32;
+    sf.count = st.count;
+    sf.flags = st.flags;
+    sf.barrier = st.barrier;
+    sf.err = st.err;
+    sf.info = st.info;
+    f->mx.yb = st.ya;  // the FP64 iterate buffer holds the base
+    f->mx.ybh = ybh;
+    f->mx.da = da;
+    f->mx.db = db;
+    f->mx.uref = uref;
+    f->mx.xref = xref;
+    f->mx.sw = sw;
+    f->mx.s64 = st.s;
+    f->mx.refresh_every = f->opts.refresh_every;
+  }
+
   // launch configuration: one thread per input component; as many
   // resident blocks as there are chains, up to what the device holds
   f->block = std::max(64, ((std::max(nu, nx) + 31) / 32) * 32);
-  f->smem = smem_bytes<double>(f->SP, f->NEP, f->NUP);
+  f->buf_d = smem_buf_elems(8, f->NXP, f->NUP, f->YP, f->SP, f->NEP, 1);
+  f->buf_f = smem_buf_elems(4, f->NXP, f->NUP, f->YP, f->SP, f->NEP, 2);
+  {
+    const int nnzB = (int)Bc.idx.size(), nnzE = (int)Er.idx.size();
+    f->net_bytes_d = (int)net_smem_bytes(nx, nu, ne, nnzB, nnzE, 8);
+    f->net_bytes_f = (int)net_smem_bytes(nx, nu, ne, nnzB, nnzE, 4);
+  }
+  f->smem = smem_bytes<double>(f->buf_d) + f->net_bytes_d;
+  f->maxc = nx <= 64 ? 2 : (nx <= 128 ? 4 : 8);
   int bps1 = 0, bps2 = 0, sms = 0;
-  RN_CUDA((solve_occupancy<double, true>(f->block, f->smem, &bps1)));
-  RN_CUDA((solve_occupancy<double, false>(f->block, f->smem, &bps2)));
+  RN_CUDA((solve_occupancy<double, true>(f->maxc, f->block, f->smem, &bps1)));
+  RN_CUDA((solve_occupancy<double, false>(f->maxc, f->block, f->smem, &bps2)));
   RN_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, f->device));
   const int resident = std::min(bps1, bps2) * sms;
   if (resident < 1) {
@@ -827,6 +987,18 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
   }
   f->grid = std::min(p.n_chains, resident);
   if (f->opts.max_ctas > 0) f->grid = std::min(f->grid, f->opts.max_ctas);
+  if (f->opts.precision == RN_PREC_MIXED) {
+    f->smem_mixed = std::max(smem_bytes<double>(f->buf_d), smem_bytes<float>(f->buf_f)) +
+                    f->net_bytes_f + round16(sizeof(NetDev<double>));
+    int bpm = 0;
+    RN_CUDA(mixed_occupancy(f->maxc, f->block, f->smem_mixed, &bpm));
+    if (bpm < 1) {
+      set_error("the mixed kernel does not fit on the device");
+      return RN_ERR_UNSUPPORTED;
+    }
+    f->grid_mixed = std::min(p.n_chains, bpm * sms);
+    if (f->opts.max_ctas > 0) f->grid_mixed = std::min(f->grid_mixed, f->opts.max_ctas);
+  }
 
   if (f->opts.gamma > 0.0) {
     f->gamma = f->opts.gamma;
@@ -945,17 +1117,36 @@ int solve_device_impl(rn_factor *f, const double *x0, const double *q, const dou
   int rc;
   if ((rc = ensure_beta(f, max_iters)) || (rc = ensure_res(f, checks))) return rc;
   if ((rc = prepare(f, x0, q, demand, alpha))) return rc;
-  k_init_apg<<<node_blocks(n), 128, 0, f->stream>>>(f->net, f->perm, n, y_warm, f->st.ya,
-                                                    f->st.yb, f->st.s);
+  const bool mixed = f->opts.precision == RN_PREC_MIXED;
+  if (mixed)
+    k_mixed_init<<<node_blocks(n), 128, 0, f->stream>>>(f->net, f->perm, n, y_warm, f->mx.yb,
+                                                        f->mx.ybh, f->mx.da, f->mx.db, f->st.s,
+                                                        f->stf.s);
+  else
+    k_init_apg<<<node_blocks(n), 128, 0, f->stream>>>(f->net, f->perm, n, y_warm, f->st.ya,
+                                                      f->st.yb, f->st.s);
   RN_CUDA(cudaGetLastError());
   if ((rc = reset_sync(f))) return rc;
   RN_CUDA(cudaMemsetAsync(f->res, 0, checks * sizeof(unsigned long long), f->stream));
-  KParams<double> P = base_params(f);
-  P.iters = max_iters;
-  P.check_every = f->opts.check_every;
-  P.tol = tol > 0.0 ? tol : 0.0;
   RN_CUDA(cudaEventRecord(f->ev0, f->stream));
-  RN_CUDA((launch_solve<double, true>(P, f->grid, f->block, f->smem, f->stream)));
+  if (mixed) {
+    MixedParams M;
+    M.f = base_params_f(f);
+    M.f.iters = max_iters;
+    M.f.check_every = f->opts.check_every;
+    M.f.tol = tol > 0.0 ? tol : 0.0;
+    M.d = base_params(f);
+    M.d.st.uo32 = const_cast<float *>(f->mx.uref);
+    M.d.st.xo32 = const_cast<float *>(f->mx.xref);
+    M.mx = f->mx;
+    RN_CUDA(launch_mixed(M, f->maxc, f->grid_mixed, f->block, f->smem_mixed, f->stream));
+  } else {
+    KParams<double> P = base_params(f);
+    P.iters = max_iters;
+    P.check_every = f->opts.check_every;
+    P.tol = tol > 0.0 ? tol : 0.0;
+    RN_CUDA((launch_solve<double, true>(P, f->grid, f->block, f->smem, f->stream)));
+  }
   RN_CUDA(cudaEventRecord(f->ev1, f->stream));
   int info[3] = {0, 0, 0};
   RN_CUDA(cudaMemcpyAsync(info, f->info, 3 * sizeof(int), cudaMemcpyDeviceToHost, f->stream));
@@ -965,9 +1156,18 @@ int solve_device_impl(rn_factor *f, const double *x0, const double *q, const dou
   RN_CUDA(cudaEventElapsedTime(&apg_ms, f->ev0, f->ev1));
   out->apg_ms = apg_ms;
   // y^{iters} was written into the buffer that held y^{iters-2}
-  const double *yfin = ((iters - 1) & 1) ? f->st.ya : f->st.yb;
-  k_gather<<<node_blocks(n) + 1, 128, 0, f->stream>>>(f->net, f->perm, n, f->st.uo, f->st.xo, yfin,
-                                                      f->q, f->x0, out->u, out->x, out->y);
+  if (mixed) {
+    const float *dfin = ((iters - 1) & 1) ? f->mx.da : f->mx.db;
+    k_gather<<<node_blocks(n) + 1, 128, 0, f->stream>>>(f->net, f->perm, n, f->st.uo, f->st.xo,
+                                                        nullptr, f->q, f->x0, out->u, out->x,
+                                                        nullptr);
+    k_gather_mixed_y<<<node_blocks(n) + 1, 128, 0, f->stream>>>(f->net, f->perm, n, f->mx.yb,
+                                                                dfin, out->y);
+  } else {
+    const double *yfin = ((iters - 1) & 1) ? f->st.ya : f->st.yb;
+    k_gather<<<node_blocks(n) + 1, 128, 0, f->stream>>>(f->net, f->perm, n, f->st.uo, f->st.xo,
+                                                        yfin, f->q, f->x0, out->u, out->x, out->y);
+  }
   RN_CUDA(cudaGetLastError());
   std::vector<unsigned long long> hist(std::max(1, nchk));
   if (nchk > 0)
