@@ -176,6 +176,27 @@ int rapidnet_solve_device(rn_factor *f, const double *x0, const double *q,
                           int max_iters, double tol, const double *y_warm,
                           rn_result *out);
 
+/* One problem of a batch: device pointers as for rapidnet_solve_device;
+ * out->u, x, y (device) receive the outputs and out's scalars are filled. */
+typedef struct {
+  const double *x0, *q, *demand, *alpha;
+  const double *y_warm;  /* NULL = cold start */
+  rn_result *out;
+} rn_solve_req;
+
+/* Batched solve: n independent problems, each on its own factor handle
+ * (different networks and trees allowed, all created with
+ * RN_PREC_MIXED on one device), run together in one persistent
+ * cooperative launch on the stream of f[0] (the paper solves one problem
+ * at a time; this serves many MPC problems at once).  Every problem runs
+ * at most max_iters iterations and
+ * stops at its own first check with residual <= tol (tol <= 0: exactly
+ * max_iters).  Returns RN_OK when every problem converged (or tol <= 0),
+ * RN_NOT_CONVERGED when some did not, or an error; per-problem results in
+ * req[i].out.  Synchronises the streams of all handles. */
+int rapidnet_solve_batch(rn_factor *const *f, const rn_solve_req *req, int n,
+                         int max_iters, double tol);
+
 /* Dual gradient x*(w) = grad f*(-H'w) (eq. dual-gradient, §4.4) for the
  * data of the last solve, or of (x0, q, demand, alpha) when given (all
  * device pointers, NULL = keep the last solve's data): w (n_nodes*(2nx+nu),

@@ -66,6 +66,11 @@ class rn_result(ctypes.Structure):
                 ("gap", c_double), ("gamma", c_double), ("apg_ms", c_double)]
 
 
+class rn_solve_req(ctypes.Structure):
+    _fields_ = [("x0", c_void_p), ("q", c_void_p), ("demand", c_void_p), ("alpha", c_void_p),
+                ("y_warm", c_void_p), ("out", POINTER(rn_result))]
+
+
 class rn_factor_info(ctypes.Structure):
     _fields_ = [("nx", c_int), ("nu", c_int), ("nd", c_int), ("ne", c_int), ("N", c_int),
                 ("n_nodes", c_int), ("n_chains", c_int), ("n_top", c_int),
@@ -85,6 +90,8 @@ EXPORTS = {
     "rapidnet_dual_gradient_device": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                               c_void_p, c_void_p, c_void_p]),
     "rapidnet_dual_gradient_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "rapidnet_solve_batch": (c_int, [POINTER(c_void_p), POINTER(rn_solve_req), c_int, c_int,
+                                     c_double]),
     "rapidnet_last_error": (ctypes.c_char_p, []),
 }
 
@@ -151,6 +158,44 @@ def rapidnet_solve_device(h, x0, q, demand, alpha, max_iters, tol, y_warm, res) 
 
 def rapidnet_dual_gradient_device(h, x0, q, demand, alpha, w, u, x) -> int:
     return _check(load().rapidnet_dual_gradient_device(h, x0, q, demand, alpha, w, u, x))
+
+
+def rapidnet_solve_batch(handles, reqs, n, max_iters, tol) -> int:
+    return _check(load().rapidnet_solve_batch(handles, reqs, int(n), int(max_iters), float(tol)))
+
+
+def solve_batch(factors, data, max_iters: int, tol: float = 0.0, outs=None) -> list:
+    """Batched solve of several mixed-precision factors (rapidnet_solve_batch).
+    data[i] = (x0, q, demand, alpha[, y_warm]) as float64 CUDA tensors;
+    outs[i] = (u, x, y) CUDA tensors (allocated here when omitted)."""
+    import torch
+    n = len(factors)
+    handles = (c_void_p * n)(*[f.h.value if isinstance(f.h, c_void_p) else f.h for f in factors])
+    results = (rn_result * n)()
+    reqs = (rn_solve_req * n)()
+    keep = []
+    for i, (f, d) in enumerate(zip(factors, data)):
+        if outs is None:
+            u = torch.empty((f.n_nodes, f.nu), dtype=torch.float64, device="cuda")
+            x = torch.empty((f.n_nodes, f.nx), dtype=torch.float64, device="cuda")
+            y = torch.empty((f.n_nodes, f.ny), dtype=torch.float64, device="cuda")
+        else:
+            u, x, y = outs[i]
+        keep.append((u, x, y))
+        results[i].u = ctypes.cast(_dev_ptr(u), PD)
+        results[i].x = ctypes.cast(_dev_ptr(x), PD)
+        results[i].y = ctypes.cast(_dev_ptr(y), PD)
+        yw = d[4] if len(d) > 4 else None
+        reqs[i] = rn_solve_req(_dev_ptr(d[0]), _dev_ptr(d[1]), _dev_ptr(d[2]), _dev_ptr(d[3]),
+                               _dev_ptr(yw), ctypes.pointer(results[i]))
+    rc = rapidnet_solve_batch(handles, reqs, n, max_iters, tol)
+    out = []
+    for i in range(n):
+        r = results[i]
+        out.append(dict(status=rc, iters=r.iters, n_checks=r.n_checks, primal_res=r.primal_res,
+                        ubox_viol=r.ubox_viol, cost=r.cost, gamma=r.gamma, apg_ms=r.apg_ms,
+                        u=keep[i][0], x=keep[i][1], y=keep[i][2]))
+    return out
 
 
 def rapidnet_dual_gradient_noalloc(h, w, u, x) -> int:

@@ -99,6 +99,27 @@ struct MixedParams {
 
 cudaError_t launch_mixed(const MixedParams &M, int maxc, int grid, int block, size_t smem,
                          cudaStream_t st);
+
+// Batched mode: independent problems (each a factor handle in mixed
+// precision) in one cooperative launch.  Work items (problem, chain) are
+// sorted by problem; block b processes items [cta_begin[b], cta_begin[b+1]).
+constexpr int kBatchMaxDistinct = 32;  // problems one block may touch
+
+struct BatchDev {
+  int n_problems;
+  const MixedParams *probs;  // per problem (device copy)
+  const int *item_prob, *item_chain, *cta_begin;
+  unsigned *barrier;         // grid barrier of the batch
+  int *prob_info;            // per problem: iterations, checks, stop reason
+  int iters, check_every, refresh_every;
+  int buf_f, buf_d;          // shared buffer sizes (elements), max over problems
+  int net_bytes_f;           // bytes reserved for a problem's FP32 network copy
+  double tol;
+};
+
+cudaError_t launch_batch(const BatchDev &B, int maxc, int grid, int block, size_t smem,
+                         cudaStream_t st);
+cudaError_t batch_occupancy(int maxc, int block, size_t smem, int *blocks_per_sm);
 cudaError_t mixed_occupancy(int maxc, int block, size_t smem, int *blocks_per_sm);
 
 // shared-memory buffer of the persistent kernels, in elements of T: the

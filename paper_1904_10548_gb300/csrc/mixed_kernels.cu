@@ -15,56 +15,6 @@
 
 namespace rn {
 
-// apply fn to every node whose per-node work chain k owns
-template <typename F>
-__device__ void for_owned(const PlanDev &pl, int k, F fn) {
-  const int p0 = pl.ch_path_ptr[k], m = pl.ch_path_ptr[k + 1] - p0;
-  for (int q = pl.ch_own_from[k]; q < m; ++q) fn(pl.ch_path[p0 + q]);
-  const int start = pl.ch_start[k], L = pl.ch_len[k];
-  for (int q = 0; q < L; ++q) fn(start + q);
-}
-
-// Refresh of node v by one warp: yb += d_new, d_old -= d_new, d_new = 0,
-// ybh = fl32(yb); the FP64 step input s64 = (yb1 + yb2 | yb3) and the next
-// FP32 step input dw = -beta_next d_old.
-__device__ void refresh_node(const MixedParams &M, int v, float *dnew, float *dold,
-                             float beta_next) {
-  const NetDev<float> &nt = M.f.net;
-  const int lane = threadIdx.x & 31;
-  const size_t ro = (size_t)v * nt.YP;
-  for (int e = lane; e < nt.YP; e += 32) {
-    const double yb = M.mx.yb[ro + e] + (double)dnew[ro + e];
-    M.mx.yb[ro + e] = yb;
-    M.mx.ybh[ro + e] = (float)yb;
-    dold[ro + e] -= dnew[ro + e];
-    dnew[ro + e] = 0.f;
-  }
-  __syncwarp();
-  double *s64 = M.mx.s64 + (size_t)v * nt.SP;
-  float *s32 = M.f.st.s + (size_t)v * nt.SP;
-  for (int i = lane; i < nt.nx; i += 32) {
-    s64[i] = M.mx.yb[ro + i] + M.mx.yb[ro + nt.NXP + i];
-    s32[i] = -beta_next * (dold[ro + i] + dold[ro + nt.NXP + i]);
-  }
-  for (int j = lane; j < nt.nu; j += 32) {
-    s64[nt.NXP + j] = M.mx.yb[ro + 2 * nt.NXP + j];
-    s32[nt.NXP + j] = -beta_next * dold[ro + 2 * nt.NXP + j];
-  }
-}
-
-// input of the final FP64 evaluation at w = yb + dw of the last iteration
-__device__ void final_node(const MixedParams &M, int v) {
-  const NetDev<float> &nt = M.f.net;
-  const int lane = threadIdx.x & 31;
-  const size_t ro = (size_t)v * nt.YP;
-  double *s64 = M.mx.s64 + (size_t)v * nt.SP;
-  const float *sw = M.mx.sw + (size_t)v * nt.SP;
-  for (int i = lane; i < nt.nx; i += 32)
-    s64[i] = (M.mx.yb[ro + i] + M.mx.yb[ro + nt.NXP + i]) + (double)sw[i];
-  for (int j = lane; j < nt.nu; j += 32)
-    s64[nt.NXP + j] = M.mx.yb[ro + 2 * nt.NXP + j] + (double)sw[nt.NXP + j];
-}
-
 // one FP64 evaluation of the dual gradient from mx.s64 into d.st.uo / xo
 // (and the FP32 copies uref / xref); false on timeout
 __device__ bool fp64_step(const MixedParams &M, unsigned step, Smem<double> &sm) {

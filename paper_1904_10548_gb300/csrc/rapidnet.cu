@@ -1488,3 +1488,241 @@ extern "C" int rapidnet_dual_gradient_noalloc(rn_factor *f, const double *w, dou
   }
   return RN_OK;
 }
+
+// ---------------------------------------------------------------------------
+// batched solve (many handles, one cooperative launch)
+// ---------------------------------------------------------------------------
+namespace {
+
+struct BatchWorkspace {
+  unsigned char *dev = nullptr;
+  size_t cap = 0;
+  int device = -1;
+};
+std::mutex g_batch_mu;
+BatchWorkspace g_batch_ws[kMaxDevices];
+
+int batch_impl(rn_factor *const *fs, const rn_solve_req *req, int n, int max_iters, double tol) {
+  if (!fs || !req || n < 1) {
+    set_error("solve_batch: need n >= 1 handles and requests");
+    return RN_ERR_INVAL;
+  }
+  if (max_iters < 1) {
+    set_error("solve_batch: max_iters must be >= 1");
+    return RN_ERR_INVAL;
+  }
+  const int dev = fs[0] ? fs[0]->device : -1;
+  for (int i = 0; i < n; ++i) {
+    rn_factor *f = fs[i];
+    const rn_solve_req &r = req[i];
+    if (!f || !r.x0 || !r.q || !r.demand || !r.alpha || !r.out || !r.out->u || !r.out->x ||
+        !r.out->y) {
+      set_error("solve_batch: NULL handle or argument in request %d", i);
+      return RN_ERR_INVAL;
+    }
+    if (f->opts.precision != RN_PREC_MIXED) {
+      set_error("solve_batch: handle %d is not RN_PREC_MIXED", i);
+      return RN_ERR_INVAL;
+    }
+    if (f->device != dev) {
+      set_error("solve_batch: handles on different devices");
+      return RN_ERR_INVAL;
+    }
+    for (int j = 0; j < i; ++j)
+      if (fs[j] == f) {
+        set_error("solve_batch: handle %d appears twice", i);
+        return RN_ERR_INVAL;
+      }
+  }
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_error("solve_batch: device ordinal out of range");
+    return RN_ERR_INVAL;
+  }
+  RN_CUDA(cudaSetDevice(dev));
+  cudaStream_t bs = fs[0]->stream;
+  int rc;
+  // per-problem preparation on each handle's stream
+  int checks = 0, maxc = 2, block = 64, buf_f = 0, buf_d = 0, net_f = 0;
+  size_t smem = 0;
+  long long items = 0;
+  for (int i = 0; i < n; ++i) {
+    rn_factor *f = fs[i];
+    const int ck = (max_iters + f->opts.check_every - 1) / f->opts.check_every + 1;
+    checks = std::max(checks, ck);
+    if ((rc = ensure_beta(f, max_iters)) || (rc = ensure_res(f, ck))) return rc;
+    if ((rc = prepare(f, req[i].x0, req[i].q, req[i].demand, req[i].alpha))) return rc;
+    const int nn = f->plan.n;
+    k_mixed_init<<<node_blocks(nn), 128, 0, f->stream>>>(f->net, f->perm, nn, req[i].y_warm,
+                                                         f->mx.yb, f->mx.ybh, f->mx.da,
+                                                         f->mx.db, f->st.s, f->stf.s);
+    RN_CUDA(cudaGetLastError());
+    if ((rc = reset_sync(f))) return rc;
+    RN_CUDA(cudaMemsetAsync(f->res, 0, ck * sizeof(unsigned long long), f->stream));
+    maxc = std::max(maxc, f->maxc);
+    block = std::max(block, f->block);
+    buf_f = std::max(buf_f, f->buf_f);
+    buf_d = std::max(buf_d, f->buf_d);
+    net_f = std::max(net_f, f->net_bytes_f);
+    items += f->plan.n_chains;
+  }
+  for (int i = 0; i < n; ++i) RN_CUDA(cudaStreamSynchronize(fs[i]->stream));
+  smem = std::max(smem_bytes<double>(buf_d), smem_bytes<float>(buf_f)) + net_f +
+         round16(sizeof(NetDev<double>));
+  int bps = 0, sms = 0;
+  RN_CUDA(batch_occupancy(maxc, block, smem, &bps));
+  RN_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (bps < 1) {
+    set_error("solve_batch: the batched kernel does not fit on the device");
+    return RN_ERR_UNSUPPORTED;
+  }
+  int grid = (int)std::min<long long>(items, (long long)bps * sms);
+  if (fs[0]->opts.max_ctas > 0) grid = std::min(grid, fs[0]->opts.max_ctas);
+  // work items sorted by problem, contiguous ranges per block
+  std::vector<int> ip, ic, cb(grid + 1);
+  ip.reserve(items);
+  ic.reserve(items);
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < fs[i]->plan.n_chains; ++k) {
+      ip.push_back(i);
+      ic.push_back(k);
+    }
+  for (int b = 0; b <= grid; ++b) cb[b] = (int)((long long)b * items / grid);
+  for (int b = 0; b < grid; ++b) {
+    int distinct = 0;
+    for (int it = cb[b]; it < cb[b + 1]; ++it)
+      if (it == cb[b] || ip[it] != ip[it - 1]) ++distinct;
+    if (distinct > kBatchMaxDistinct) {
+      set_error("solve_batch: a block would touch %d problems (more than %d); "
+                "too many small problems for this batch size", distinct, kBatchMaxDistinct);
+      return RN_ERR_UNSUPPORTED;
+    }
+  }
+  std::vector<MixedParams> probs(n);
+  for (int i = 0; i < n; ++i) {
+    rn_factor *f = fs[i];
+    MixedParams &M = probs[i];
+    M.f = base_params_f(f);
+    M.f.iters = max_iters;
+    M.f.check_every = f->opts.check_every;
+    M.f.tol = tol > 0.0 ? tol : 0.0;
+    M.d = base_params(f);
+    M.d.st.uo32 = const_cast<float *>(f->mx.uref);
+    M.d.st.xo32 = const_cast<float *>(f->mx.xref);
+    M.mx = f->mx;
+  }
+  // device workspace (kept per device, grown on demand)
+  const size_t o_probs = 0;
+  const size_t o_ip = round16(o_probs + n * sizeof(MixedParams));
+  const size_t o_ic = round16(o_ip + items * sizeof(int));
+  const size_t o_cb = round16(o_ic + items * sizeof(int));
+  const size_t o_bar = round16(o_cb + (grid + 1) * sizeof(int));
+  const size_t o_info = round16(o_bar + sizeof(unsigned));
+  const size_t total = round16(o_info + 3 * n * sizeof(int));
+  std::lock_guard<std::mutex> lock(g_batch_mu);
+  BatchWorkspace &ws = g_batch_ws[dev];
+  if (ws.cap < total) {
+    if (ws.dev) cudaFree(ws.dev);
+    ws.dev = nullptr;
+    ws.cap = 0;
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, total);
+    if (e != cudaSuccess) {
+      set_error("solve_batch: cudaMalloc of %zu bytes failed: %s", total, cudaGetErrorString(e));
+      return e == cudaErrorMemoryAllocation ? RN_ERR_NOMEM : RN_ERR_CUDA;
+    }
+    ws.dev = static_cast<unsigned char *>(p);
+    ws.cap = total;
+  }
+  unsigned char *W = ws.dev;
+  RN_CUDA(cudaMemcpyAsync(W + o_probs, probs.data(), n * sizeof(MixedParams),
+                          cudaMemcpyHostToDevice, bs));
+  RN_CUDA(cudaMemcpyAsync(W + o_ip, ip.data(), items * sizeof(int), cudaMemcpyHostToDevice, bs));
+  RN_CUDA(cudaMemcpyAsync(W + o_ic, ic.data(), items * sizeof(int), cudaMemcpyHostToDevice, bs));
+  RN_CUDA(cudaMemcpyAsync(W + o_cb, cb.data(), (grid + 1) * sizeof(int), cudaMemcpyHostToDevice, bs));
+  RN_CUDA(cudaMemsetAsync(W + o_bar, 0, sizeof(unsigned), bs));
+  RN_CUDA(cudaMemsetAsync(W + o_info, 0, 3 * n * sizeof(int), bs));
+  BatchDev B{};
+  B.n_problems = n;
+  B.probs = reinterpret_cast<const MixedParams *>(W + o_probs);
+  B.item_prob = reinterpret_cast<const int *>(W + o_ip);
+  B.item_chain = reinterpret_cast<const int *>(W + o_ic);
+  B.cta_begin = reinterpret_cast<const int *>(W + o_cb);
+  B.barrier = reinterpret_cast<unsigned *>(W + o_bar);
+  B.prob_info = reinterpret_cast<int *>(W + o_info);
+  B.iters = max_iters;
+  B.check_every = fs[0]->opts.check_every;
+  for (int i = 1; i < n; ++i)
+    if (fs[i]->opts.check_every != B.check_every) {
+      set_error("solve_batch: all handles need the same check_every");
+      return RN_ERR_INVAL;
+    }
+  B.refresh_every = fs[0]->opts.refresh_every;
+  B.buf_f = buf_f;
+  B.buf_d = buf_d;
+  B.net_bytes_f = net_f;
+  B.tol = tol > 0.0 ? tol : 0.0;
+  RN_CUDA(cudaEventRecord(fs[0]->ev0, bs));
+  RN_CUDA(launch_batch(B, maxc, grid, block, smem, bs));
+  RN_CUDA(cudaEventRecord(fs[0]->ev1, bs));
+  std::vector<int> info(3 * n);
+  RN_CUDA(cudaMemcpyAsync(info.data(), W + o_info, 3 * n * sizeof(int), cudaMemcpyDeviceToHost, bs));
+  RN_CUDA(cudaStreamSynchronize(bs));
+  float ms = 0.f;
+  RN_CUDA(cudaEventElapsedTime(&ms, fs[0]->ev0, fs[0]->ev1));
+  // errors of any problem (shared wait error words)
+  int any_err = 0;
+  for (int i = 0; i < n; ++i) {
+    int e = 0;
+    RN_CUDA(cudaMemcpy(&e, fs[i]->err, sizeof(int), cudaMemcpyDeviceToHost));
+    any_err |= e;
+  }
+  if (any_err) {
+    set_error("solve_batch: a device-side wait gave up");
+    return RN_ERR_TIMEOUT;
+  }
+  int status = RN_OK;
+  for (int i = 0; i < n; ++i) {
+    rn_factor *f = fs[i];
+    rn_result *out = req[i].out;
+    const int iters = info[3 * i], nchk = info[3 * i + 1], reason = info[3 * i + 2];
+    const int nn = f->plan.n;
+    const float *dfin = ((iters - 1) & 1) ? f->mx.da : f->mx.db;
+    k_gather<<<node_blocks(nn) + 1, 128, 0, f->stream>>>(f->net, f->perm, nn, f->st.uo, f->st.xo,
+                                                         nullptr, f->q, f->x0, out->u, out->x,
+                                                         nullptr);
+    k_gather_mixed_y<<<node_blocks(nn) + 1, 128, 0, f->stream>>>(f->net, f->perm, nn, f->mx.yb,
+                                                                 dfin, out->y);
+    RN_CUDA(cudaGetLastError());
+    double red[3];
+    if ((rc = reduce_nodes(f, 0, nullptr, red))) return rc;
+    std::vector<unsigned long long> hist(std::max(1, nchk));
+    if (nchk > 0)
+      RN_CUDA(cudaMemcpy(hist.data(), f->res, nchk * sizeof(unsigned long long),
+                         cudaMemcpyDeviceToHost));
+    double last = NAN;
+    if (nchk > 0) {
+      std::memcpy(&last, &hist[nchk - 1], sizeof last);
+      last *= 1.0 / f->gamma;
+    }
+    out->iters = iters;
+    out->n_checks = nchk;
+    out->primal_res = last;
+    out->cost = red[0] + red[1];
+    out->ubox_viol = red[2];
+    out->gap = NAN;
+    out->gamma = f->gamma;
+    out->apg_ms = ms;
+    if (reason == 2) status = RN_ERR_DIVERGED;
+    else if (tol > 0.0 && reason != 1 && status == RN_OK) status = RN_NOT_CONVERGED;
+  }
+  if (status == RN_ERR_DIVERGED) set_error("solve_batch: a residual became non-finite");
+  return status;
+}
+
+}  // namespace
+
+extern "C" int rapidnet_solve_batch(rn_factor *const *f, const rn_solve_req *req, int n,
+                                    int max_iters, double tol) {
+  clear_error();
+  return batch_impl(f, req, n, max_iters, tol);
+}

@@ -1,0 +1,98 @@
+"""Batched mode (one persistent launch over many problems) against solo
+solves and against the FP64 oracle.
+
+Each problem of a batch must give the same result as its solo
+mixed-precision solve (same kernels, same arithmetic order per problem:
+the batch shares only the launch, barriers and the stop decision
+schedule) and meet the mixed-precision bar against the FP64 oracle.
+Problems have different networks (nx 6, 16, 63) and uneven trees.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1904_10548_gb300 as rn
+from paper_1904_10548_gb300 import _binding as B
+from synthetic import make_cost, make_data, make_network, random_branching
+from synthetic.configs import Problem
+from tests.test_gpu_parity import rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def batch_problem(i):
+    dims = [(6, 11, 8, 2), (16, 29, 22, 4), (63, 114, 88, 17)][i % 3]
+    net = make_network(*dims, seed=100 + i)
+    tree = random_branching(10 if dims[0] > 16 else 12, seed=200 + i, s_min=4, s_max=24,
+                            branch_stages=4)
+    return Problem(net=net, cost=make_cost(net, seed=100 + i), tree=tree,
+                   data=make_data(net, tree, seed=300 + i))
+
+
+def dev(a):
+    import torch
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def tensors(pb):
+    return (dev(pb.data.x0), dev(pb.data.q), dev(pb.data.demand), dev(pb.data.alpha))
+
+
+@pytest.mark.parametrize("max_ctas", [0, 7])
+def test_batch_equals_solo_and_oracle(max_ctas):
+    pbs = [batch_problem(i) for i in range(9)]
+    gammas = []
+    for pb in pbs:
+        P = O.OracleProblem.from_parts(pb.net, pb.cost, pb.tree)
+        gammas.append(O.step_size(O.power_iteration(P, O.factor(P), 60)))
+    facs = [rn.Factor(pb.net, pb.cost, pb.tree, gamma=g, precision=rn.RN_PREC_MIXED,
+                      max_ctas=max_ctas) for pb, g in zip(pbs, gammas)]
+    iters = 150
+    outs = rn.solve_batch(facs, [tensors(pb) for pb in pbs], iters)
+    for i, (pb, f, o) in enumerate(zip(pbs, facs, outs)):
+        assert o["status"] == B.RN_OK and o["iters"] == iters
+        solo = f.solve(pb.data.x0, pb.data.q, pb.data.demand, pb.data.alpha, max_iters=iters)
+        for k in ("u", "x", "y"):
+            assert np.array_equal(o[k].cpu().numpy(), solo[k]), (i, k)
+        assert o["cost"] == solo["cost"]
+        P = O.OracleProblem.from_parts(pb.net, pb.cost, pb.tree)
+        F = O.factor(P)
+        S = O.solve_consts(P, F, pb.data.x0, pb.data.q, pb.data.demand, pb.data.alpha)
+        ref = O.apg(P, F, S, iters, gammas[i])
+        cost = O.primal_cost(P, S, ref.u, ref.x)
+        assert abs(o["cost"] - cost) <= 1e-3 * abs(cost), i
+        assert rel_err(solo["y"], ref.y) <= 1e-3, i
+    for f in facs:
+        f.close()
+
+
+def test_batch_per_problem_stopping():
+    """Problems stop at their own first converged check; the others go on."""
+    pbs = [batch_problem(i) for i in (0, 1, 3, 4)]
+    facs = [rn.Factor(pb.net, pb.cost, pb.tree, precision=rn.RN_PREC_MIXED) for pb in pbs]
+    tol = 5e-2
+    outs = rn.solve_batch(facs, [tensors(pb) for pb in pbs], 3000, tol)
+    for pb, f, o in zip(pbs, facs, outs):
+        solo = f.solve(pb.data.x0, pb.data.q, pb.data.demand, pb.data.alpha, max_iters=3000,
+                       tol=tol)
+        assert o["iters"] == solo["iters"]
+        assert np.array_equal(o["y"].cpu().numpy(), solo["y"])
+        if o["iters"] < 3000:
+            assert o["primal_res"] <= tol
+    for f in facs:
+        f.close()
+
+
+def test_batch_rejects_fp64_handles():
+    pb = batch_problem(0)
+    f = rn.Factor(pb.net, pb.cost, pb.tree, gamma=1e-3)
+    with pytest.raises(B.RapidNetError) as ei:
+        rn.solve_batch([f], [tensors(pb)], 10)
+    assert ei.value.status == B.RN_ERR_INVAL
+    f.close()
