@@ -102,6 +102,9 @@ typedef struct {
   int refresh_every;   /* RN_PREC_MIXED: FP64 reference refresh period;
                           0 = 20 */
   int max_ctas;        /* cap on the persistent grid; 0 = device maximum */
+  int block_threads;   /* threads per block of the persistent kernels
+                          (multiple of 32, <= 256); 0 = one thread per
+                          component of u or x, at least 64 */
 } rn_opts;
 
 /* Output of a solve.  The caller allocates u (n_nodes*nu), x (n_nodes*nx)

@@ -46,6 +46,7 @@ __device__ int slot_of(const BatchCtx &bc, int p) {
 }
 
 // one FP64 evaluation of the dual gradient for the participating problems
+template <int C>
 __device__ bool batch_fp64_step(const BatchDev &B, BatchCtx &bc, MixedParams &mp,
                                 unsigned char *raw, Smem<float> &smf, Smem<double> &smd,
                                 unsigned step, bool all) {
@@ -54,7 +55,7 @@ __device__ bool batch_fp64_step(const BatchDev &B, BatchCtx &bc, MixedParams &mp
     const int p = B.item_prob[i];
     if (!all && !bc.active[slot_of(bc, p)]) continue;
     load_problem(B, p, bc, mp, raw, smf, smd);
-    chain_backward(mp.d, B.item_chain[i], smd);
+    chain_backward<double, C>(mp.d, B.item_chain[i], smd);
     climb(mp.d, B.item_chain[i], step, smd);
   }
   FwdCtx<double> c{};
@@ -69,12 +70,12 @@ __device__ bool batch_fp64_step(const BatchDev &B, BatchCtx &bc, MixedParams &mp
       __syncthreads();
       if (!smd.flag[1]) return false;
     }
-    chain_forward<double, kFwdPlain, 2>(mp.d, k, c, smd, nullptr);
+    chain_forward<double, kFwdPlain, C>(mp.d, k, c, smd, nullptr);
   }
   return true;
 }
 
-template <int MAXC>
+template <int C>
 __global__ void __launch_bounds__(256) k_batch(BatchDev B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ MixedParams mp;
@@ -99,14 +100,14 @@ __global__ void __launch_bounds__(256) k_batch(BatchDev B) {
   __syncthreads();
   unsigned step = 0;
   int it = 0, ci = 0;
-  bool ok = batch_fp64_step(B, bc, mp, smem_raw, smf, smd, step++, true);
+  bool ok = batch_fp64_step<C>(B, bc, mp, smem_raw, smf, smd, step++, true);
   for (; it < B.iters && ok; ++it) {
     // FP32 backward sweep and top-node reductions
     for (int i = i0; i < i1; ++i) {
       const int p = B.item_prob[i];
       if (!bc.active[slot_of(bc, p)]) continue;
       load_problem(B, p, bc, mp, smem_raw, smf, smd);
-      chain_backward(mp.f, B.item_chain[i], smf);
+      chain_backward<float, C>(mp.f, B.item_chain[i], smf);
       climb(mp.f, B.item_chain[i], step, smf);
     }
     const bool check = ((it + 1) % B.check_every) == 0 || it + 1 == B.iters;
@@ -133,7 +134,7 @@ __global__ void __launch_bounds__(256) k_batch(BatchDev B) {
           break;
         }
       }
-      chain_forward<float, kFwdMixed, MAXC>(mp.f, k, c, smf, &mp.mx);
+      chain_forward<float, kFwdMixed, C>(mp.f, k, c, smf, &mp.mx);
       const unsigned long long r = block_max_u64(c.rbits, smf.redu);
       if (tid == 0 && r > bc.rbits[sl]) bc.rbits[sl] = r;
     }
@@ -192,7 +193,7 @@ __global__ void __launch_bounds__(256) k_batch(BatchDev B) {
         });
         __syncthreads();
       }
-      if (!batch_fp64_step(B, bc, mp, smem_raw, smf, smd, step++, false)) {
+      if (!batch_fp64_step<C>(B, bc, mp, smem_raw, smf, smd, step++, false)) {
         ok = false;
         break;
       }
@@ -207,7 +208,7 @@ __global__ void __launch_bounds__(256) k_batch(BatchDev B) {
       });
       __syncthreads();
     }
-    ok = batch_fp64_step(B, bc, mp, smem_raw, smf, smd, step++, true);
+    ok = batch_fp64_step<C>(B, bc, mp, smem_raw, smf, smd, step++, true);
   }
   // problems that ran to the end
   if (tid == 0) {
@@ -221,8 +222,9 @@ __global__ void __launch_bounds__(256) k_batch(BatchDev B) {
   }
 }
 
-static const void *batch_fn(int maxc) {
-  switch (maxc) {
+static const void *batch_fn(int c) {
+  switch (c) {
+    case 1: return (const void *)k_batch<1>;
     case 2: return (const void *)k_batch<2>;
     case 4: return (const void *)k_batch<4>;
     default: return (const void *)k_batch<8>;

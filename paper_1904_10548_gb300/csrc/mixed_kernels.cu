@@ -17,10 +17,11 @@ namespace rn {
 
 // one FP64 evaluation of the dual gradient from mx.s64 into d.st.uo / xo
 // (and the FP32 copies uref / xref); false on timeout
+template <int C>
 __device__ bool fp64_step(const MixedParams &M, unsigned step, Smem<double> &sm) {
   const KParams<double> &P = M.d;
   for (int k = blockIdx.x; k < P.plan.n_chains; k += gridDim.x) {
-    chain_backward(P, k, sm);
+    chain_backward<double, C>(P, k, sm);
     climb(P, k, step, sm);
   }
   FwdCtx<double> c{};
@@ -31,12 +32,12 @@ __device__ bool fp64_step(const MixedParams &M, unsigned step, Smem<double> &sm)
       __syncthreads();
       if (!sm.flag[1]) return false;
     }
-    chain_forward<double, kFwdPlain, 2>(P, k, c, sm, nullptr);
+    chain_forward<double, kFwdPlain, C>(P, k, c, sm, nullptr);
   }
   return true;
 }
 
-template <int MAXC>
+template <int C>
 __global__ void __launch_bounds__(256) k_mixed(MixedParams M) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<double> smd = carve<double>(smem_raw, M.d.net, M.d.buf_elems);
@@ -50,11 +51,11 @@ __global__ void __launch_bounds__(256) k_mixed(MixedParams M) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   unsigned step = P.step_base;
   int it = 0, ci = 0, reason = 0;  // reason: 0 max iters, 1 converged, 2 non-finite, 3 timeout
-  bool ok = fp64_step(M, step++, smd);
+  bool ok = fp64_step<C>(M, step++, smd);
   if (!ok) reason = 3;
   for (; it < P.iters && ok; ++it) {
     for (int k = blockIdx.x; k < P.plan.n_chains; k += gridDim.x) {
-      chain_backward(P, k, smf);
+      chain_backward<float, C>(P, k, smf);
       climb(P, k, step, smf);
     }
     FwdCtx<float> c;
@@ -78,7 +79,7 @@ __global__ void __launch_bounds__(256) k_mixed(MixedParams M) {
           break;
         }
       }
-      chain_forward<float, kFwdMixed, MAXC>(P, k, c, smf, &M.mx);
+      chain_forward<float, kFwdMixed, C>(P, k, c, smf, &M.mx);
     }
     ++step;
     if (!ok) break;
@@ -129,7 +130,7 @@ __global__ void __launch_bounds__(256) k_mixed(MixedParams M) {
         });
       }
       __syncthreads();
-      if (!fp64_step(M, step++, smd)) {
+      if (!fp64_step<C>(M, step++, smd)) {
         ok = false;
         reason = 3;
         ++it;
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(256) k_mixed(MixedParams M) {
       });
     }
     __syncthreads();
-    if (!fp64_step(M, step++, smd)) reason = 3;
+    if (!fp64_step<C>(M, step++, smd)) reason = 3;
   }
   (void)lane;
   if (blockIdx.x == 0 && tid == 0) {
@@ -155,8 +156,9 @@ __global__ void __launch_bounds__(256) k_mixed(MixedParams M) {
   }
 }
 
-static const void *mixed_fn(int maxc) {
-  switch (maxc) {
+static const void *mixed_fn(int c) {
+  switch (c) {
+    case 1: return (const void *)k_mixed<1>;
     case 2: return (const void *)k_mixed<2>;
     case 4: return (const void *)k_mixed<4>;
     default: return (const void *)k_mixed<8>;

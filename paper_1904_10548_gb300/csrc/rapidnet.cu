@@ -966,7 +966,24 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
 
   // launch configuration: one thread per input component; as many
   // resident blocks as there are chains, up to what the device holds
-  f->block = std::max(64, ((std::max(nu, nx) + 31) / 32) * 32);
+  // block width and components per thread: C = ceil(max(nx, nu) / block),
+  // at least ceil(nx / 32) (a warp updates a node), rounded to 1, 2, 4, 8
+  {
+    int bt = f->opts.block_threads > 0 ? ((f->opts.block_threads + 31) / 32) * 32
+                                        : std::max(64, ((std::max(nx, nu) + 31) / 32) * 32);
+    bt = std::min(bt, 256);
+    auto comps = [&](int b) {
+      int c = std::max((std::max(nx, nu) + b - 1) / b, (nx + 31) / 32);
+      return c <= 1 ? 1 : (c <= 2 ? 2 : (c <= 4 ? 4 : (c <= 8 ? 8 : 16)));
+    };
+    while (comps(bt) > 8 && bt < 256) bt += 32;
+    if (comps(bt) > 8) {
+      set_error("network: nx, nu too large for the block width");
+      return RN_ERR_UNSUPPORTED;
+    }
+    f->block = bt;
+    f->maxc = comps(bt);
+  }
   f->buf_d = smem_buf_elems(8, f->NXP, f->NUP, f->YP, f->SP, f->NEP, 1);
   f->buf_f = smem_buf_elems(4, f->NXP, f->NUP, f->YP, f->SP, f->NEP, 2);
   {
@@ -975,7 +992,6 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
     f->net_bytes_f = (int)net_smem_bytes(nx, nu, ne, nnzB, nnzE, 4);
   }
   f->smem = smem_bytes<double>(f->buf_d) + f->net_bytes_d;
-  f->maxc = nx <= 64 ? 2 : (nx <= 128 ? 4 : 8);
   int bps1 = 0, bps2 = 0, sms = 0;
   RN_CUDA((solve_occupancy<double, true>(f->maxc, f->block, f->smem, &bps1)));
   RN_CUDA((solve_occupancy<double, false>(f->maxc, f->block, f->smem, &bps2)));
@@ -1542,7 +1558,7 @@ int batch_impl(rn_factor *const *fs, const rn_solve_req *req, int n, int max_ite
   cudaStream_t bs = fs[0]->stream;
   int rc;
   // per-problem preparation on each handle's stream
-  int checks = 0, maxc = 2, block = 64, buf_f = 0, buf_d = 0, net_f = 0;
+  int checks = 0, maxc = 1, block = 32, buf_f = 0, buf_d = 0, net_f = 0;
   size_t smem = 0;
   long long items = 0;
   for (int i = 0; i < n; ++i) {
@@ -1558,7 +1574,6 @@ int batch_impl(rn_factor *const *fs, const rn_solve_req *req, int n, int max_ite
     RN_CUDA(cudaGetLastError());
     if ((rc = reset_sync(f))) return rc;
     RN_CUDA(cudaMemsetAsync(f->res, 0, ck * sizeof(unsigned long long), f->stream));
-    maxc = std::max(maxc, f->maxc);
     block = std::max(block, f->block);
     buf_f = std::max(buf_f, f->buf_f);
     buf_d = std::max(buf_d, f->buf_d);
@@ -1566,6 +1581,12 @@ int batch_impl(rn_factor *const *fs, const rn_solve_req *req, int n, int max_ite
     items += f->plan.n_chains;
   }
   for (int i = 0; i < n; ++i) RN_CUDA(cudaStreamSynchronize(fs[i]->stream));
+  for (int i = 0; i < n; ++i) {
+    const int m = std::max(fs[i]->nx, fs[i]->nu);
+    int c = std::max((m + block - 1) / block, (fs[i]->nx + 31) / 32);
+    c = c <= 1 ? 1 : (c <= 2 ? 2 : (c <= 4 ? 4 : 8));
+    maxc = std::max(maxc, c);
+  }
   smem = std::max(smem_bytes<double>(buf_d), smem_bytes<float>(buf_f)) + net_f +
          round16(sizeof(NetDev<double>));
   int bps = 0, sms = 0;

@@ -286,12 +286,14 @@ __device__ void apply_F(const NetDev<T> &nt, int m, Smem<T> &sm, T *zrows) {
 // ---------------------------------------------------------------------------
 // backward sweep over one chain: suffix sums from the leaf to the head
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, int C>
 __device__ void chain_backward(const KParams<T> &P, int k, Smem<T> &sm) {
   const NetDev<T> &nt = *sm.net;
   const int tid = threadIdx.x, bd = blockDim.x;
   const int start = P.plan.ch_start[k], L = P.plan.ch_len[k];
-  T accL = T(0), accG = T(0);
+  T accL[C], accG[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) accL[c] = accG[c] = T(0);
   for (int hi = L; hi > 0; hi -= kSeg) {
     const int lo = hi > kSeg ? hi - kSeg : 0, m = hi - lo;
     {
@@ -303,21 +305,31 @@ __device__ void chain_backward(const KParams<T> &P, int k, Smem<T> &sm) {
     }
     if (tid < m) sm.i2p[tid] = P.st.inv2p[start + lo + tid];
     __syncthreads();
-    if (tid < nt.nx) {
-      for (int q = m - 1; q >= 0; --q) {
-        accL += sm.buf[q * nt.SP + tid];
-        sm.buf[q * nt.SP + tid] = accL;
+    // lambda: suffix sums of w1 + w2 (thread owns components tid + c bd)
+    for (int q = m - 1; q >= 0; --q) {
+      T *row = sm.buf + q * nt.SP;
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const int i = tid + c * bd;
+        if (i < nt.nx) {
+          accL[c] += row[i];
+          row[i] = accL[c];
+        }
       }
     }
     __syncthreads();
-    if (tid < nt.nu) {
-      const int b0 = nt.Bc_ptr[tid], b1 = nt.Bc_ptr[tid + 1];
-      for (int q = m - 1; q >= 0; --q) {
-        const T *row = sm.buf + q * nt.SP;
-        T t = row[nt.NXP + tid];
-        for (int e = b0; e < b1; ++e) t += nt.Bc_val[e] * row[nt.Bc_idx[e]];
-        accG += t;
-        sm.buf[q * nt.SP + nt.NXP + tid] = accG;
+    // ghat: suffix sums of w3 + B' lambda
+    for (int q = m - 1; q >= 0; --q) {
+      T *row = sm.buf + q * nt.SP;
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const int j = tid + c * bd;
+        if (j < nt.nu) {
+          T t = row[nt.NXP + j];
+          for (int e = nt.Bc_ptr[j]; e < nt.Bc_ptr[j + 1]; ++e) t += nt.Bc_val[e] * row[nt.Bc_idx[e]];
+          accG[c] += t;
+          row[nt.NXP + j] = accG[c];
+        }
       }
     }
     __syncthreads();
@@ -337,20 +349,19 @@ __device__ void top_backward(const KParams<T> &P, int v, Smem<T> &sm) {
   const int tid = threadIdx.x, bd = blockDim.x;
   const int c0 = P.plan.top_child_ptr[v], c1 = P.plan.top_child_ptr[v + 1];
   const T *sv = P.st.s + (size_t)v * nt.SP;
-  if (tid < nt.nx) {
-    T acc = ld_l2(sv + tid);
-    for (int c = c0; c < c1; ++c) acc += ld_l2(P.st.up + (size_t)P.plan.top_child[c] * nt.SP + tid);
-    sm.buf[tid] = acc;
+  for (int i = tid; i < nt.nx; i += bd) {
+    T acc = ld_l2(sv + i);
+    for (int c = c0; c < c1; ++c) acc += ld_l2(P.st.up + (size_t)P.plan.top_child[c] * nt.SP + i);
+    sm.buf[i] = acc;
   }
   if (tid == 0) sm.i2p[0] = P.st.inv2p[v];
   __syncthreads();
-  if (tid < nt.nu) {
-    T acc = ld_l2(sv + nt.NXP + tid);
-    for (int e = nt.Bc_ptr[tid]; e < nt.Bc_ptr[tid + 1]; ++e)
-      acc += nt.Bc_val[e] * sm.buf[nt.Bc_idx[e]];
+  for (int j = tid; j < nt.nu; j += bd) {
+    T acc = ld_l2(sv + nt.NXP + j);
+    for (int e = nt.Bc_ptr[j]; e < nt.Bc_ptr[j + 1]; ++e) acc += nt.Bc_val[e] * sm.buf[nt.Bc_idx[e]];
     for (int c = c0; c < c1; ++c)
-      acc += ld_l2(P.st.up + (size_t)P.plan.top_child[c] * nt.SP + nt.NXP + tid);
-    sm.buf[nt.NXP + tid] = acc;
+      acc += ld_l2(P.st.up + (size_t)P.plan.top_child[c] * nt.SP + nt.NXP + j);
+    sm.buf[nt.NXP + j] = acc;
   }
   __syncthreads();
   apply_F(nt, 1, sm, P.st.z + (size_t)v * nt.NUP);
@@ -517,9 +528,10 @@ __device__ void prox_node_warp_mixed(const KParams<float> &P, const NetDev<float
   for (int cc = 0; cc < MAXC; ++cc) {
     const int i = lane + 32 * cc;
     if (i < nt.nx) {
-      // scale toward the ball |y| <= W only when the ball is active
-      const float d1 = q1 < 1.f ? h1[cc] * (q1 - 1.f) + g1[cc] * q1 : g1[cc];
-      const float d2 = q2 < 1.f ? h2[cc] * (q2 - 1.f) + g2[cc] * q2 : g2[cc];
+      // scale toward the ball |y| <= W only when the ball is active (one
+      // fixed rounding sequence, the same in every instantiation)
+      const float d1 = q1 < 1.f ? __fmaf_rn(h1[cc], q1 - 1.f, __fmul_rn(g1[cc], q1)) : g1[cc];
+      const float d2 = q2 < 1.f ? __fmaf_rn(h2[cc], q2 - 1.f, __fmul_rn(g2[cc], q2)) : g2[cc];
       unsigned long long r = abs_bits(d1 - w1[cc]), r2 = abs_bits(d2 - w2[cc]);
       r = r2 > r ? r2 : r;
       c.rbits = r > c.rbits ? r : c.rbits;
@@ -568,7 +580,7 @@ __host__ __device__ inline int fwd_elems_per_node(int NXP, int NUP, int YP, int 
   return 3 * NUP + 2 * NXP + (mode == 1 ? 2 * YP : (mode == 2 ? 3 * YP : 0));
 }
 
-template <typename T, int MODE, int MAXC>
+template <typename T, int MODE, int C>
 __device__ void chain_forward(const KParams<T> &P, int k, FwdCtx<T> &c, Smem<T> &sm,
                               const MixedDev *mx) {
   constexpr int SEGF = SegF<T>::value;
@@ -588,8 +600,13 @@ __device__ void chain_forward(const KParams<T> &P, int k, FwdCtx<T> &c, Smem<T> 
   T *Yh = Yp + SEGF * nt.YP;
   int *nodes = sm.node, *owned = sm.node + kSeg;
   const bool data = (MODE == kFwdMixed) || !P.linear;
-  T Zp = T(0);
-  T xa = (tid < nt.nx && !P.linear) ? P.st.xroot[tid] : T(0);
+  T Zp[C], xa[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    const int i = tid + c * blockDim.x;
+    Zp[c] = T(0);
+    xa[c] = (i < nt.nx && !P.linear) ? P.st.xroot[i] : T(0);
+  }
   for (int q0 = 0; q0 < K; q0 += SEGF) {
     const int ms = K - q0 < SEGF ? K - q0 : SEGF;
     if (tid == 0) {
@@ -622,21 +639,29 @@ __device__ void chain_forward(const KParams<T> &P, int k, FwdCtx<T> &c, Smem<T> 
       }
     }
     __syncthreads();
-    if (tid < nt.nu) {
-      for (int q = 0; q < ms; ++q) {
-        Zp += Zs[q * nt.NUP + tid];
-        const T base = (data && MODE != kFwdMixed) ? Bs[q * nt.NUP + tid] : T(0);
-        Us[q * nt.NUP + tid] = base - Zp;
+    for (int q = 0; q < ms; ++q) {
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const int j = tid + c * blockDim.x;
+        if (j < nt.nu) {
+          Zp[c] += Zs[q * nt.NUP + j];
+          const T base = (data && MODE != kFwdMixed) ? Bs[q * nt.NUP + j] : T(0);
+          Us[q * nt.NUP + j] = base - Zp[c];
+        }
       }
     }
     __syncthreads();
-    if (tid < nt.nx) {
-      const int b0 = nt.Br_ptr[tid], b1 = nt.Br_ptr[tid + 1];
-      for (int q = 0; q < ms; ++q) {
-        T acc = (data && MODE != kFwdMixed) ? Gs[q * nt.NXP + tid] : T(0);
-        for (int e = b0; e < b1; ++e) acc += nt.Br_val[e] * Us[q * nt.NUP + nt.Br_idx[e]];
-        xa += acc;
-        Xs[q * nt.NXP + tid] = xa;
+    for (int q = 0; q < ms; ++q) {
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const int i = tid + c * blockDim.x;
+        if (i < nt.nx) {
+          T acc = (data && MODE != kFwdMixed) ? Gs[q * nt.NXP + i] : T(0);
+          for (int e = nt.Br_ptr[i]; e < nt.Br_ptr[i + 1]; ++e)
+            acc += nt.Br_val[e] * Us[q * nt.NUP + nt.Br_idx[e]];
+          xa[c] += acc;
+          Xs[q * nt.NXP + i] = xa[c];
+        }
       }
     }
     __syncthreads();
@@ -644,10 +669,10 @@ __device__ void chain_forward(const KParams<T> &P, int k, FwdCtx<T> &c, Smem<T> 
       const int q = owned[o];
       const int v = nodes[q];
       if constexpr (MODE == kFwdApg) {
-        prox_node_warp<T, MAXC>(P, nt, v, Us + q * nt.NUP, Xs + q * nt.NXP, Yc + o * nt.YP,
+        prox_node_warp<T, C>(P, nt, v, Us + q * nt.NUP, Xs + q * nt.NXP, Yc + o * nt.YP,
                                 Yp + o * nt.YP, c);
       } else if constexpr (MODE == kFwdMixed) {
-        prox_node_warp_mixed<MAXC>(P, nt, *mx, v, Us + q * nt.NUP, Xs + q * nt.NXP, Yc + o * nt.YP,
+        prox_node_warp_mixed<C>(P, nt, *mx, v, Us + q * nt.NUP, Xs + q * nt.NXP, Yc + o * nt.YP,
                                    Yp + o * nt.YP, Yh + o * nt.YP, Bs + o * nt.NUP,
                                    Gs + o * nt.NXP, c);
       } else {

@@ -25,7 +25,7 @@ namespace rn {
 // the persistent kernel: `iters` APG iterations (APG = true) or one
 // evaluation of the dual gradient (APG = false)
 // ---------------------------------------------------------------------------
-template <typename T, bool APG, int MAXC>
+template <typename T, bool APG, int C>
 __global__ void __launch_bounds__(256) k_solve(KParams<T> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<T> sm = carve<T>(smem_raw, P.net, P.buf_elems);
@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(256) k_solve(KParams<T> P) {
   for (; it < P.iters && ok; ++it) {
     const unsigned step = P.step_base + (unsigned)it;
     for (int k = blockIdx.x; k < P.plan.n_chains; k += gridDim.x) {
-      chain_backward(P, k, sm);
+      chain_backward<T, C>(P, k, sm);
       climb(P, k, step, sm);
     }
     FwdCtx<T> c;
@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(256) k_solve(KParams<T> P) {
           break;
         }
       }
-      chain_forward<T, APG ? kFwdApg : kFwdPlain, MAXC>(P, k, c, sm, nullptr);
+      chain_forward<T, APG ? kFwdApg : kFwdPlain, C>(P, k, c, sm, nullptr);
     }
     if (!ok) break;
     if (check) {
@@ -104,12 +104,12 @@ __global__ void __launch_bounds__(256) k_solve(KParams<T> P) {
 }
 
 template <typename T, bool APG>
-static const void *solve_fn(int maxc) {
-  if (!APG) return (const void *)k_solve<T, false, 2>;
-  switch (maxc) {
-    case 2: return (const void *)k_solve<T, true, 2>;
-    case 4: return (const void *)k_solve<T, true, 4>;
-    default: return (const void *)k_solve<T, true, 8>;
+static const void *solve_fn(int c) {
+  switch (c) {
+    case 1: return (const void *)k_solve<T, APG, 1>;
+    case 2: return (const void *)k_solve<T, APG, 2>;
+    case 4: return (const void *)k_solve<T, APG, 4>;
+    default: return (const void *)k_solve<T, APG, 8>;
   }
 }
 
