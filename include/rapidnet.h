@@ -236,6 +236,62 @@ int rapidnet_dual_gradient_device(rn_factor *f, const double *x0,
 int rapidnet_dual_gradient_noalloc(rn_factor *f, const double *w, double *u,
                                    double *x);
 
+/* ---------------------------------------------------------------------
+ * Serving: continuous batching of solve requests (no counterpart in the
+ * paper, which solves one problem per control step).  A server holds
+ * models (network x tree x cost), each served by one or more slots: a
+ * resident factor handle with its own stream, device buffers and the last
+ * dual it computed (warm start).  Submitted requests wait in a bounded
+ * queue; worker threads take a request as soon as its model has a free
+ * slot, or open a new slot when the device-memory budget allows, and run
+ * it on that slot's stream, so requests that arrive while others run
+ * overlap with them on the device.  Every result equals the same request
+ * solved alone (same kernels, no shared state besides the warm start,
+ * which is off unless asked for).
+ * ------------------------------------------------------------------- */
+typedef struct rn_server rn_server;
+
+typedef struct {
+  int device;
+  long long budget_bytes;  /* device memory the slots may hold; 0 = 8 GiB */
+  int max_queue;           /* pending requests; 0 = 4096 */
+  int workers;             /* concurrent solves (host threads); 0 = 8 */
+  int slots_per_model;     /* slots opened when a model is added (within the
+                              budget); 0 = 1.  Later slots are opened on
+                              demand; opening one allocates device memory,
+                              which briefly stalls the device */
+} rn_server_opts;
+
+typedef struct {
+  long long submitted, completed, rejected;
+  int slots, models;
+  long long bytes_in_use;
+  double p50_s, p99_s;     /* latency (submit -> result ready) of completed */
+  double mean_s;
+} rn_server_stats;
+
+int rapidnet_server_create(const rn_server_opts *opts, rn_server **out);
+/* Adds a model; its first slot (a factor handle) is created now and
+ * charged to the budget.  opts as for rapidnet_factor (device taken from
+ * the server).  *key identifies the model in submit. */
+int rapidnet_server_add_model(rn_server *s, const rn_network *net, const rn_tree *tree,
+                              const rn_cost *cost, const rn_opts *opts, int *key);
+/* Queues one solve; host arrays are copied.  warm != 0 starts from the
+ * last dual of the slot that runs it.  Returns RN_ERR_NOMEM when the queue
+ * is full (retry later), RN_ERR_INVAL for a bad key. */
+int rapidnet_server_submit(rn_server *s, int key, const double *x0, const double *q,
+                           const double *demand, const double *alpha, int max_iters,
+                           double tol, int warm, long long *ticket);
+/* Waits up to timeout_s (< 0: no limit) for a ticket; fills out (host
+ * buffers u, x, y may be NULL) and the latency.  Returns the solve's
+ * status, or RN_ERR_TIMEOUT if it is not done yet.  A ticket is returned
+ * once; later calls give RN_ERR_INVAL. */
+int rapidnet_server_wait(rn_server *s, long long ticket, double timeout_s, rn_result *out,
+                         double *latency_s);
+int rapidnet_server_stats(rn_server *s, rn_server_stats *st);
+/* Finishes the queued requests, then frees every slot. */
+void rapidnet_server_destroy(rn_server *s);
+
 /* Description of the last failure on the calling thread ("" if none). */
 const char *rapidnet_last_error(void);
 

@@ -7,7 +7,7 @@ package only marshals arguments.  Build the library with
 ``__graft_entry__.build()`` (or ``python -m paper_1904_10548_gb300.build``).
 """
 from ._binding import (  # noqa: F401
-    Factor, RapidNetError, load, rapidnet_dual_gradient_device, rapidnet_dual_gradient_noalloc, rapidnet_factor,
+    Factor, RapidNetError, Server, load, rapidnet_dual_gradient_device, rapidnet_dual_gradient_noalloc, rapidnet_factor,
     rapidnet_factor_free, rapidnet_factor_info, rapidnet_last_error, rapidnet_solve,
     rapidnet_solve_device, rapidnet_solve_batch, solve_batch, RN_PREC_FP64, RN_PREC_MIXED, RN_OK, RN_NOT_CONVERGED,
     STATUS_NAMES, EXPORTS, LIB_PATH,

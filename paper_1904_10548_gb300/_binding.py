@@ -71,6 +71,17 @@ class rn_solve_req(ctypes.Structure):
                 ("y_warm", c_void_p), ("out", POINTER(rn_result))]
 
 
+class rn_server_opts(ctypes.Structure):
+    _fields_ = [("device", c_int), ("budget_bytes", c_longlong), ("max_queue", c_int),
+                ("workers", c_int), ("slots_per_model", c_int)]
+
+
+class rn_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", c_longlong), ("completed", c_longlong), ("rejected", c_longlong),
+                ("slots", c_int), ("models", c_int), ("bytes_in_use", c_longlong),
+                ("p50_s", c_double), ("p99_s", c_double), ("mean_s", c_double)]
+
+
 class rn_factor_info(ctypes.Structure):
     _fields_ = [("nx", c_int), ("nu", c_int), ("nd", c_int), ("ne", c_int), ("N", c_int),
                 ("n_nodes", c_int), ("n_chains", c_int), ("n_top", c_int),
@@ -92,6 +103,15 @@ EXPORTS = {
     "rapidnet_dual_gradient_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "rapidnet_solve_batch": (c_int, [POINTER(c_void_p), POINTER(rn_solve_req), c_int, c_int,
                                      c_double]),
+    "rapidnet_server_create": (c_int, [POINTER(rn_server_opts), POINTER(c_void_p)]),
+    "rapidnet_server_add_model": (c_int, [c_void_p, POINTER(rn_network), POINTER(rn_tree),
+                                          POINTER(rn_cost), POINTER(rn_opts), POINTER(c_int)]),
+    "rapidnet_server_submit": (c_int, [c_void_p, c_int, PD, PD, PD, PD, c_int, c_double, c_int,
+                                       POINTER(c_longlong)]),
+    "rapidnet_server_wait": (c_int, [c_void_p, c_longlong, c_double, POINTER(rn_result),
+                                     POINTER(c_double)]),
+    "rapidnet_server_stats": (c_int, [c_void_p, POINTER(rn_server_stats)]),
+    "rapidnet_server_destroy": (None, [c_void_p]),
     "rapidnet_last_error": (ctypes.c_char_p, []),
 }
 
@@ -198,6 +218,73 @@ def solve_batch(factors, data, max_iters: int, tol: float = 0.0, outs=None) -> l
     return out
 
 
+class Server:
+    """Continuous-batching solve server (rapidnet_server_*): models are
+    added once (resident factors), requests are submitted with host arrays
+    and waited for by ticket."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 0, max_queue: int = 0,
+                 workers: int = 0, slots_per_model: int = 0):
+        self.h = c_void_p()
+        _check(load().rapidnet_server_create(
+            ctypes.byref(rn_server_opts(device, budget_bytes, max_queue, workers,
+                                        slots_per_model)),
+            ctypes.byref(self.h)))
+        self.models = {}
+
+    def add_model(self, net, cost, tree, precision: int = RN_PREC_MIXED, gamma: float = 0.0,
+                  **kw) -> int:
+        spec = Factor.__new__(Factor)
+        Factor._marshal(spec, net, cost, tree, precision, gamma, 0, None, **kw)
+        key = c_int()
+        _check(load().rapidnet_server_add_model(self.h, ctypes.byref(spec.net_c),
+                                                ctypes.byref(spec.tree_c),
+                                                ctypes.byref(spec.cost_c),
+                                                ctypes.byref(spec.opts_c), ctypes.byref(key)))
+        self.models[key.value] = spec
+        return key.value
+
+    def submit(self, key: int, x0, q, demand, alpha, max_iters: int, tol: float = 0.0,
+               warm: bool = False) -> int:
+        m = self.models[key]
+        arrs = [_f64(x0, (m.nx,)), _f64(q, (m.nu,)), _f64(demand, (m.n_nodes, m.nd)),
+                _f64(alpha, (m.n_nodes, m.nu))]
+        t = c_longlong()
+        _check(load().rapidnet_server_submit(self.h, key, *[_pd(a) for a in arrs], int(max_iters),
+                                             float(tol), int(warm), ctypes.byref(t)))
+        return t.value
+
+    def wait(self, key: int, ticket: int, timeout_s: float = -1.0) -> dict:
+        m = self.models[key]
+        u = np.empty((m.n_nodes, m.nu))
+        x = np.empty((m.n_nodes, m.nx))
+        y = np.empty((m.n_nodes, m.ny))
+        res = rn_result(_pd(u), _pd(x), _pd(y), None, 0, 0)
+        lat = c_double()
+        rc = _check(load().rapidnet_server_wait(self.h, ticket, float(timeout_s),
+                                                ctypes.byref(res), ctypes.byref(lat)))
+        out = {f: getattr(res, f) for f in ("iters", "n_checks", "primal_res", "ubox_viol",
+                                            "cost", "gap", "gamma", "apg_ms")}
+        out.update(status=rc, u=u, x=x, y=y, latency_s=lat.value)
+        return out
+
+    def stats(self) -> dict:
+        st = rn_server_stats()
+        _check(load().rapidnet_server_stats(self.h, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in rn_server_stats._fields_}
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            load().rapidnet_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def rapidnet_dual_gradient_noalloc(h, w, u, x) -> int:
     return _check(load().rapidnet_dual_gradient_noalloc(h, w, u, x))
 
@@ -234,6 +321,12 @@ class Factor:
     def __init__(self, net, cost, tree, precision: int = RN_PREC_FP64, gamma: float = 0.0,
                  device: int = 0, stream=None, power_iters: int = 0, check_every: int = 0,
                  refresh_every: int = 0, max_ctas: int = 0, block_threads: int = 0):
+        self._marshal(net, cost, tree, precision, gamma, device, stream, power_iters,
+                      check_every, refresh_every, max_ctas, block_threads)
+        self.h = rapidnet_factor(self.net_c, self.tree_c, self.cost_c, self.opts_c)
+
+    def _marshal(self, net, cost, tree, precision, gamma, device, stream, power_iters=0,
+                 check_every=0, refresh_every=0, max_ctas=0, block_threads=0):
         nx, nu, nd, ne = net.nx, net.nu, net.nd, net.ne
         self._keep = [
             _f64(net.A, (nx, nx)), _f64(net.B, (nx, nu)), _f64(net.Gd, (nx, nd)),
@@ -256,7 +349,6 @@ class Factor:
         self.nx, self.nu, self.nd, self.ne = nx, nu, nd, ne
         self.n_nodes = int(tree.stage_ptr[-1])
         self.ny = 2 * nx + nu
-        self.h = rapidnet_factor(self.net_c, self.tree_c, self.cost_c, self.opts_c)
 
     def info(self) -> dict:
         i = rapidnet_factor_info(self.h)

@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "librapidnet.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["plan.cpp", "rapidnet.cu", "solve_kernels.cu", "mixed_kernels.cu", "batch_kernels.cu"]
+SOURCES = ["plan.cpp", "rapidnet.cu", "solve_kernels.cu", "mixed_kernels.cu", "batch_kernels.cu", "server.cpp"]
 
 
 def _nvcc() -> str:

@@ -234,7 +234,7 @@ static const void *batch_fn(int c) {
 cudaError_t launch_batch(const BatchDev &B, int maxc, int grid, int block, size_t smem,
                          cudaStream_t st) {
   const void *fn = batch_fn(maxc);
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_smem(fn);
   if (e != cudaSuccess) return e;
   BatchDev b = B;
   void *args[] = {&b};
@@ -243,7 +243,7 @@ cudaError_t launch_batch(const BatchDev &B, int maxc, int grid, int block, size_
 
 cudaError_t batch_occupancy(int maxc, int block, size_t smem, int *blocks_per_sm) {
   const void *fn = batch_fn(maxc);
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_smem(fn);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, smem);
 }

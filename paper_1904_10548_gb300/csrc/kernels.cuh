@@ -153,6 +153,12 @@ __host__ __device__ inline size_t net_smem_bytes(int nx, int nu, int ne, int nnz
   return round16(sizeof(NetDev<double>)) + round16(ints * 4) + round16(vals * elem);
 }
 
+// Raise a kernel's dynamic shared-memory limit to the device's opt-in
+// maximum, once per kernel: launches then use what they need.  Changing
+// the attribute between launches of a kernel that is running on another
+// stream would serialise the two.
+cudaError_t allow_max_smem(const void *fn);
+
 // host launchers of the persistent kernel (cooperative launch: every block
 // must be resident because blocks wait on flags that other blocks set)
 template <typename T, bool APG>

@@ -168,7 +168,7 @@ static const void *mixed_fn(int c) {
 cudaError_t launch_mixed(const MixedParams &M, int maxc, int grid, int block, size_t smem,
                          cudaStream_t st) {
   const void *fn = mixed_fn(maxc);
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_smem(fn);
   if (e != cudaSuccess) return e;
   MixedParams p = M;
   void *args[] = {&p};
@@ -177,7 +177,7 @@ cudaError_t launch_mixed(const MixedParams &M, int maxc, int grid, int block, si
 
 cudaError_t mixed_occupancy(int maxc, int block, size_t smem, int *blocks_per_sm) {
   const void *fn = mixed_fn(maxc);
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_smem(fn);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, smem);
 }

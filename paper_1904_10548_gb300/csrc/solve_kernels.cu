@@ -17,9 +17,32 @@
 // is scanned by one thread block, top nodes are summed by the block that
 // completes their last child, and every block recomputes the path sums of
 // its chain's top ancestors instead of waiting for them.
+#include <mutex>
+#include <set>
+
 #include "solve_device.cuh"
 
 namespace rn {
+
+cudaError_t allow_max_smem(const void *fn) {
+  static std::mutex mu;
+  static std::set<std::pair<int, const void *>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count({dev, fn})) return cudaSuccess;
+  int optin = 0;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa{};
+  e = cudaFuncGetAttributes(&fa, fn);  // static shared memory counts against the limit
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           optin - (int)fa.sharedSizeBytes);
+  if (e == cudaSuccess) done.insert({dev, fn});
+  return e;
+}
 
 // ---------------------------------------------------------------------------
 // the persistent kernel: `iters` APG iterations (APG = true) or one
@@ -116,7 +139,7 @@ static const void *solve_fn(int c) {
 template <typename T, bool APG>
 cudaError_t launch_solve(const KParams<T> &P, int grid, int block, size_t smem, cudaStream_t st) {
   const void *fn = solve_fn<T, APG>(P.maxc);
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_smem(fn);
   if (e != cudaSuccess) return e;
   KParams<T> p = P;
   void *args[] = {&p};
@@ -126,7 +149,7 @@ cudaError_t launch_solve(const KParams<T> &P, int grid, int block, size_t smem, 
 template <typename T, bool APG>
 cudaError_t solve_occupancy(int maxc, int block, size_t smem, int *blocks_per_sm) {
   const void *fn = solve_fn<T, APG>(maxc);
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_smem(fn);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, smem);
 }
