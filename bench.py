@@ -41,13 +41,19 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
     ap.add_argument("--iters", type=int, default=1000, help="APG iterations per step (solve)")
-    ap.add_argument("--tol-iters", type=int, default=100000,
+    ap.add_argument("--tol-iters", type=int, default=20000,
                     help="cap of the time-to-1e-4 solve (0 = skip)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-modes", action="store_true",
+                    help="skip the FP64-path, batched and serving sections")
+    ap.add_argument("--batch-problems", type=int, default=256)
+    ap.add_argument("--batch-iters", type=int, default=200)
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
     return ap.parse_args()
 
 
@@ -222,6 +228,159 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+
+# ---------------------------------------------------------------------------
+# DRAM traffic of the dominant kernel from a committed ncu summary, used only
+# while the kernel sources are the ones the counters were taken on
+# ---------------------------------------------------------------------------
+KERNEL_SOURCES = ["paper_1904_10548_gb300/csrc/kernels.cuh",
+                  "paper_1904_10548_gb300/csrc/solve_device.cuh",
+                  "paper_1904_10548_gb300/csrc/solve_kernels.cu",
+                  "paper_1904_10548_gb300/csrc/mixed_kernels.cu"]
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kind: str):
+    """Per-iteration DRAM bytes of the persistent kernel from
+    profiles/traffic.json, or None when the sources changed since."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f).get(kind)
+    except (OSError, ValueError):
+        return None
+    if not d or d.get("source_hash") != kernel_source_hash():
+        return None
+    return d["dram_bytes_per_iter"]
+
+
+# ---------------------------------------------------------------------------
+# the other modes: plain FP64 path, batched, serving
+# ---------------------------------------------------------------------------
+def run_fp64_path(rn, pb, tensors, gamma, iters=300, steps=3):
+    import torch
+    f = rn.Factor(pb.net, pb.cost, pb.tree, precision=rn.RN_PREC_FP64, gamma=gamma)
+    x0, q, dem, alp, u, x, y = tensors
+    f.solve_device(x0, q, dem, alp, iters, 0.0, u, x, y)
+    ms = []
+    for _ in range(steps):
+        r = f.solve_device(x0, q, dem, alp, iters, 0.0, u, x, y)
+        ms.append(r["apg_ms"])
+    f.close()
+    us = sum(ms) / len(ms) * 1e3 / iters
+    return {"iters_per_s": 1e6 / us, "us_per_iter": us, "iters_per_step": iters,
+            "precision": "fp64"}
+
+
+def batch_problems(n):
+    from synthetic import make_cost, make_data, make_network, random_branching
+    from synthetic.configs import Problem
+    dims = {16: (16, 29, 22, 4), 63: (63, 114, 88, 17), 128: (128, 230, 179, 35)}
+    out = []
+    for i in range(n):
+        nx = (16, 63, 128)[i % 3]
+        net = make_network(*dims[nx], seed=1000 + i)
+        tree = random_branching(24, seed=2000 + i, s_min=16, s_max=512)
+        out.append(Problem(net=net, cost=make_cost(net, seed=1000 + i), tree=tree,
+                           data=make_data(net, tree, seed=3000 + i)))
+    return out
+
+
+def run_batched(rn, n, iters):
+    """256 problems (nx 16/63/128, uneven trees of 16-512 scenarios, N = 24)
+    in one persistent launch vs the same problems solved one by one."""
+    import numpy as np
+    import torch
+    pbs = batch_problems(n)
+    facs = [rn.Factor(pb.net, pb.cost, pb.tree, precision=rn.RN_PREC_MIXED, power_iters=50)
+            for pb in pbs]
+    dev = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    data = [(dev(pb.data.x0), dev(pb.data.q), dev(pb.data.demand), dev(pb.data.alpha))
+            for pb in pbs]
+    rn.solve_batch(facs, data, iters)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    outs = rn.solve_batch(facs, data, iters)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    # solo FP64 solves of a sample, same step sizes
+    solo, k = 0.0, 0
+    for i in range(0, n, max(1, n // 12)):
+        pb = pbs[i]
+        f = rn.Factor(pb.net, pb.cost, pb.tree, precision=rn.RN_PREC_FP64,
+                      gamma=facs[i].info()["gamma"])
+        nn = pb.tree.n_nodes
+        u = torch.empty((nn, pb.net.nu), dtype=torch.float64, device="cuda")
+        x = torch.empty((nn, pb.net.nx), dtype=torch.float64, device="cuda")
+        y = torch.empty((nn, 2 * pb.net.nx + pb.net.nu), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        f.solve_device(*data[i], iters, 0.0, u, x, y)
+        torch.cuda.synchronize()
+        solo += time.perf_counter() - t1
+        k += 1
+        f.close()
+    for f in facs:
+        f.close()
+    nodes = sum(pb.tree.n_nodes - 1 for pb in pbs)
+    return {"problems": n, "decision_nodes": nodes, "iters_per_solve": iters,
+            "solves_per_s": n / wall, "kernel_ms": outs[0]["apg_ms"],
+            "fp64_solo_solves_per_s": k / solo, "speedup_vs_fp64_solo": (n / wall) / (k / solo),
+            "precision": "mixed"}
+
+
+def run_serving(rn, seconds, rate, max_iters=100, tol=1e-4):
+    """Poisson arrivals (mean `rate` per second) over three models: the 32-
+    and 512-scenario Barcelona-sized trees and an nx = 128 network on a
+    32-scenario tree; warm-started duals kept per slot."""
+    import numpy as np
+    from synthetic import make_cost, make_data, make_network, make_problem, make_tree
+    from synthetic.configs import Problem
+    net128 = make_network(128, 230, 179, 35, seed=7)
+    tree128 = make_tree([4, 2, 2, 2] + [1] * 20, seed=8)
+    models = [make_problem("barcelona32"), make_problem("barcelona512"),
+              Problem(net=net128, cost=make_cost(net128, seed=7), tree=tree128,
+                      data=make_data(net128, tree128, seed=9))]
+    srv = rn.Server(workers=16, slots_per_model=4, budget_bytes=24 << 30, max_queue=256)
+    keys = [srv.add_model(pb.net, pb.cost, pb.tree) for pb in models]
+    rng = np.random.default_rng(4)
+    n = int(seconds * rate)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    which = rng.integers(0, 3, size=n)
+    tickets, rejected = [], 0
+    t0 = time.perf_counter()
+    for k in range(n):
+        now = time.perf_counter() - t0
+        if arrivals[k] > now:
+            time.sleep(arrivals[k] - now)
+        pb = models[which[k]]
+        d = pb.data
+        try:
+            tickets.append((which[k], srv.submit(keys[which[k]], d.x0, d.q, d.demand, d.alpha,
+                                                 max_iters, tol, warm=True)))
+        except Exception:
+            rejected += 1
+    for key, t in tickets:
+        srv.wait(keys[key], t)
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    return {"offered_per_s": rate, "seconds": seconds, "submitted": int(st["submitted"]),
+            "completed": int(st["completed"]), "rejected": rejected,
+            "solves_per_s": st["completed"] / wall, "p50_ms": st["p50_s"] * 1e3,
+            "p99_ms": st["p99_s"] * 1e3, "mean_ms": st["mean_s"] * 1e3, "slots": st["slots"],
+            "max_iters": max_iters, "tol": tol, "warm_start": True,
+            "models": ["barcelona32", "barcelona512", "nx128 on 32 scenarios"],
+            "precision": "mixed"}
+
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
@@ -297,7 +456,8 @@ def main():
         e1.record(stream)
         evs.append((e0, e1))
         apg_ms.append(r["apg_ms"])
-        launches += 8  # kq, prep, x*(0) step, init, APG, gather, reduce, final reduce
+        # kq, prep, x*(0) step, init, APG, gather (+ dual gather in mixed), reduce, final reduce
+        launches += 9 if args.precision == "mixed" else 8
         assert r["iters"] == args.iters
     torch.cuda.synchronize()
     if dist:
@@ -346,6 +506,12 @@ def main():
                    "ms": e0.elapsed_time(e1), "residual": r["primal_res"],
                    "ubox_viol": r["ubox_viol"], "check_every": 10}
 
+    modes = {}
+    if not args.no_modes and world == 1:
+        modes["fp64_path"] = run_fp64_path(rn, pb, (x0, q, dem, alp, u, x, y), info["gamma"])
+        modes["batched"] = run_batched(rn, args.batch_problems, args.batch_iters)
+        modes["serving"] = run_serving(rn, args.serve_seconds, args.serve_rate)
+
     # roofline of the dominant kernel (the persistent APG launch)
     values, flops = node_counts(net)
     nodes = n - 1
@@ -356,15 +522,18 @@ def main():
     flops_launch = flops * nodes * args.iters
     gbs = bytes_launch / apg_avg_s / 1e9
     tfl = flops_launch / apg_avg_s / 1e12
+    traffic_iter = measured_traffic("k_mixed" if args.precision == "mixed" else "k_solve_fp64")
+    traffic = traffic_iter * args.iters if traffic_iter else None
     if args.precision == "fp64":
         roof = {"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": tfl / FP64_PEAK_TFLOPS, "traffic": None,
+                "frac": tfl / FP64_PEAK_TFLOPS, "traffic": traffic,
                 "peak_source": "nominal GB300 FP64 (recipe table)",
                 "hbm_view": {"achieved_gbs": gbs, "peak_gbs": hbm_peak,
                              "frac": gbs / hbm_peak, "peak_source": hbm_src}}
     else:
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
-                "frac": gbs / hbm_peak, "traffic": None, "peak_source": f"{hbm_src} copy bandwidth"}
+                "frac": gbs / hbm_peak, "traffic": traffic,
+                "peak_source": f"{hbm_src} copy bandwidth (of measured)"}
     roof.update(bytes_per_launch=bytes_launch, flops_per_launch=flops_launch,
                 kernel_ms=apg_avg_s * 1e3, us_per_iter=apg_avg_s * 1e6 / args.iters,
                 per_node={"values": values, "bytes": values * bpv, "flops": flops})
@@ -385,7 +554,10 @@ def main():
         "clocks": clk,
         "roofline": roof,
         "time_to_tol": tol_run,
+        "modes": modes or None,
     }
+    if "fp64_path" in modes:
+        modes["fp64_path"]["mixed_speedup"] = value / modes["fp64_path"]["iters_per_s"]
     if cpu is not None:
         cv = cpu["per"] * len(cpu["times"]) / sum(cpu["times"])
         line["cpu_baseline"] = {"value": cv, "unit": "iters/s", "cores": 1, "kind": "oracle",
