@@ -102,9 +102,10 @@ typedef struct {
   int refresh_every;   /* RN_PREC_MIXED: FP64 reference refresh period;
                           0 = 20 */
   int max_ctas;        /* cap on the persistent grid; 0 = device maximum */
-  int block_threads;   /* threads per block of the persistent kernels
-                          (multiple of 32, <= 256); 0 = one thread per
-                          component of u or x, at least 64 */
+  int block_threads;   /* threads of a chain team of the persistent kernels
+                          (multiple of 32, <= 256; a block is two teams);
+                          0 = one thread per component of u or x, at
+                          least 64 */
 } rn_opts;
 
 /* Output of a solve.  The caller allocates u (n_nodes*nu), x (n_nodes*nx)
@@ -139,7 +140,8 @@ typedef struct {
   int nx, nu, nd, ne, N, n_nodes;
   int n_chains;        /* leaves = scenarios */
   int n_top;           /* nodes whose subtree holds more than one leaf */
-  int grid_ctas, block_threads;
+  int grid_ctas;       /* blocks of the FP64 persistent kernel */
+  int block_threads;   /* threads per block (two chain teams) */
   double L;            /* power-iteration estimate of the dual Lipschitz
                           constant (0 if gamma was given) */
   double gamma;

@@ -2,15 +2,16 @@
 // network, tree and step size, solved by the mixed-precision dual APG
 // (mixed_kernels.cu) in one cooperative launch.
 //
-// Work items (problem, chain) are sorted by problem and dealt to blocks in
-// contiguous ranges, so a block touches few problems; when it moves to
-// another problem it loads that problem's parameters and network copy into
-// shared memory.  Every problem keeps its own counters, flags and residual
-// slots; the blocks share one grid barrier at the residual checks, after
-// which each block decides, for the problems it touches, whether they stop
-// (all blocks read the same residuals, so they agree).  A stopped problem's
-// items are skipped; its final FP64 evaluation runs with everybody's at the
-// end.
+// Work items are (problem, group) and (problem, pair of chains), numbered
+// within a problem as in the single-problem kernels (groups first), sorted
+// by problem and dealt to blocks in contiguous ranges, so a block touches
+// few problems; when it moves to another problem it loads that problem's
+// parameters and network copy into shared memory.  Every problem keeps its
+// own counters, flags and residual slots; the blocks share one grid
+// barrier at the residual checks, after which each block decides, for the
+// problems it touches, whether they stop (all blocks read the same
+// residuals, so they agree).  A stopped problem's items are skipped; its
+// final FP64 evaluation runs with everybody's at the end.
 #include "solve_device.cuh"
 
 namespace rn {
@@ -23,18 +24,16 @@ struct BatchCtx {
   int loaded;                     // problem whose parameters sit in mp
 };
 
-// parameters of problem p into shared memory (with its network copy)
+// parameters of problem p into shared memory (with its network copy);
+// every thread of the block calls it at the same points
 __device__ void load_problem(const BatchDev &B, int p, BatchCtx &bc, MixedParams &mp,
-                             unsigned char *raw, Smem<float> &smf, Smem<double> &smd) {
+                             const BlockMem &bm) {
   if (bc.loaded == p) return;
   __syncthreads();
   if (threadIdx.x == 0) mp = B.probs[p];
   __syncthreads();
-  smf = carve<float>(raw, mp.f.net, B.buf_f);
-  smd = carve<double>(raw, mp.d.net, B.buf_d);
-  unsigned char *net_raw = smf.net_raw > smd.net_raw ? smf.net_raw : smd.net_raw;
-  smf.net = stage_net(mp.f.net, net_raw);
-  smd.net = stage_net(mp.d.net, net_raw + B.net_bytes_f, false);
+  stage_net(mp.f.net, bm.net_raw);
+  stage_net(mp.d.net, bm.net_raw + B.net_bytes_f, false);
   if (threadIdx.x == 0) bc.loaded = p;
   __syncthreads();
 }
@@ -45,46 +44,81 @@ __device__ int slot_of(const BatchCtx &bc, int p) {
   return -1;
 }
 
-// one FP64 evaluation of the dual gradient for the participating problems
-template <int C>
-__device__ bool batch_fp64_step(const BatchDev &B, BatchCtx &bc, MixedParams &mp,
-                                unsigned char *raw, Smem<float> &smf, Smem<double> &smd,
-                                unsigned step, bool all) {
+// one evaluation of the dual gradient for the participating problems
+// (all, or the active ones); the phases of eval_step over the block's items
+template <typename T, int MODE, int C, typename CtxF>
+__device__ bool batch_eval(const BatchDev &B, BatchCtx &bc, MixedParams &mp, const BlockMem &bm,
+                           unsigned step, bool all, CtxF make_ctx) {
   const int i0 = B.cta_begin[blockIdx.x], i1 = B.cta_begin[blockIdx.x + 1];
-  for (int i = i0; i < i1; ++i) {
+  const Team tc = chain_team(), tb = block_team();
+  const int ti = team_index();
+  auto params = [&]() -> const KParams<T> & {
+    if constexpr (sizeof(T) == 4) return mp.f; else return mp.d;
+  };
+  auto smem_c = [&]() {
+    const KParams<T> &P = params();
+    return carve<T>(bm.team_raw[ti], P.buf_elems,
+                    reinterpret_cast<const NetDev<T> *>(sizeof(T) == 4 ? bm.net_raw
+                                                                       : bm.net_raw + B.net_bytes_f));
+  };
+  auto smem_g = [&]() {
+    const KParams<T> &P = params();
+    return carve<T>(bm.team_raw[0], P.gbuf_elems,
+                    reinterpret_cast<const NetDev<T> *>(sizeof(T) == 4 ? bm.net_raw
+                                                                       : bm.net_raw + B.net_bytes_f));
+  };
+  auto use = [&](int i) {
     const int p = B.item_prob[i];
-    if (!all && !bc.active[slot_of(bc, p)]) continue;
-    load_problem(B, p, bc, mp, raw, smf, smd);
-    chain_backward<double, C>(mp.d, B.item_chain[i], smd);
-    climb(mp.d, B.item_chain[i], step, smd);
+    return all || bc.active[slot_of(bc, p)];
+  };
+  for (int i = i0; i < i1; ++i) {
+    if (!use(i)) continue;
+    load_problem(B, B.item_prob[i], bc, mp, bm);
+    const KParams<T> &P = params();
+    const int G = P.plan.n_groups, sub = B.item_sub[i], k = 2 * (sub - G) + ti;
+    if (sub >= G && k < P.plan.n_chains) chain_head<T, C>(P, k, smem_c(), tc);
   }
-  FwdCtx<double> c{};
+  bool ok = true;
   for (int i = i0; i < i1; ++i) {
-    const int p = B.item_prob[i];
-    if (!all && !bc.active[slot_of(bc, p)]) continue;
-    load_problem(B, p, bc, mp, raw, smf, smd);
-    const int k = B.item_chain[i];
-    const int f = mp.d.plan.ch_flag[k];
-    if (f >= 0) {
-      if (threadIdx.x == 0) smd.flag[1] = spin_geq(mp.d.st.flags + f, step + 1u, mp.d.st.err);
+    if (!use(i)) continue;
+    load_problem(B, B.item_prob[i], bc, mp, bm);
+    const KParams<T> &P = params();
+    const int sub = B.item_sub[i];
+    if (sub < P.plan.n_groups) {
       __syncthreads();
-      if (!smd.flag[1]) return false;
+      if (!group_step<T>(P, sub, smem_g(), tb, step)) ok = false;
     }
-    chain_forward<double, kFwdPlain, C>(mp.d, k, c, smd, nullptr);
   }
-  return true;
+  for (int i = i0; i < i1; ++i) {
+    if (!use(i)) continue;
+    load_problem(B, B.item_prob[i], bc, mp, bm);
+    const KParams<T> &P = params();
+    const int G = P.plan.n_groups, sub = B.item_sub[i], k = 2 * (sub - G) + ti;
+    if (sub >= G && k < P.plan.n_chains) chain_rest<T, C>(P, k, smem_c(), tc, false);
+  }
+  for (int i = i0; i < i1; ++i) {
+    if (!use(i)) continue;
+    load_problem(B, B.item_prob[i], bc, mp, bm);
+    const KParams<T> &P = params();
+    const int G = P.plan.n_groups, sub = B.item_sub[i], k = 2 * (sub - G) + ti;
+    if (sub >= G && k < P.plan.n_chains && ok) {
+      FwdCtx<T> *c = make_ctx(slot_of(bc, B.item_prob[i]));
+      ok = chain_forward<T, MODE, C>(P, k, *c, smem_c(), tc, &mp.mx, step);
+    }
+  }
+  return ok;
 }
 
 template <int C>
-__global__ void __launch_bounds__(256) k_batch(BatchDev B) {
+__global__ void __launch_bounds__(512) k_batch(BatchDev B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ MixedParams mp;
   __shared__ BatchCtx bc;
-  Smem<float> smf{};
-  Smem<double> smd{};
-  const int tid = threadIdx.x, warp = tid >> 5, nw = blockDim.x >> 5;
+  const BlockMem bm = block_mem(smem_raw, B.net_bytes, B.team_bytes);
+  const Team tc = chain_team();
+  const int ti = team_index();
   const int i0 = B.cta_begin[blockIdx.x], i1 = B.cta_begin[blockIdx.x + 1];
-  if (tid == 0) {
+  if (threadIdx.x == 0) {
     bc.n = 0;
     bc.loaded = -1;
     for (int i = i0; i < i1; ++i) {
@@ -100,70 +134,59 @@ __global__ void __launch_bounds__(256) k_batch(BatchDev B) {
   __syncthreads();
   unsigned step = 0;
   int it = 0, ci = 0;
-  bool ok = batch_fp64_step<C>(B, bc, mp, smem_raw, smf, smd, step++, true);
+  FwdCtx<double> c64{};
+  auto ctx64 = [&](int) { return &c64; };
+  batch_eval<double, kFwdPlain, C>(B, bc, mp, bm, step++, true, ctx64);
+  bool ok = !block_err(bm, B.err);
+  // per-problem FP32 contexts differ only in their residual accumulator
+  FwdCtx<float> cf;
+  unsigned long long rb_local[kBatchMaxDistinct];
   for (; it < B.iters && ok; ++it) {
-    // FP32 backward sweep and top-node reductions
-    for (int i = i0; i < i1; ++i) {
-      const int p = B.item_prob[i];
-      if (!bc.active[slot_of(bc, p)]) continue;
-      load_problem(B, p, bc, mp, smem_raw, smf, smd);
-      chain_backward<float, C>(mp.f, B.item_chain[i], smf);
-      climb(mp.f, B.item_chain[i], step, smf);
-    }
     const bool check = ((it + 1) % B.check_every) == 0 || it + 1 == B.iters;
-    // FP32 forward sweep with the dual update
-    for (int i = i0; i < i1 && ok; ++i) {
-      const int p = B.item_prob[i];
-      const int sl = slot_of(bc, p);
-      if (!bc.active[sl]) continue;
-      load_problem(B, p, bc, mp, smem_raw, smf, smd);
-      const int k = B.item_chain[i];
-      FwdCtx<float> c;
-      c.ycur = (it & 1) ? mp.mx.db : mp.mx.da;
-      c.yprv = (it & 1) ? mp.mx.da : mp.mx.db;
-      c.beta = (float)mp.f.st.beta[it];
-      c.beta_n = (float)mp.f.st.beta[it + 1];
-      c.write_out = check;
-      c.rbits = 0ull;
-      const int f = mp.f.plan.ch_flag[k];
-      if (f >= 0) {
-        if (tid == 0) smf.flag[1] = spin_geq(mp.f.st.flags + f, step + 1u, mp.f.st.err);
-        __syncthreads();
-        if (!smf.flag[1]) {
-          ok = false;
-          break;
-        }
+    for (int s = 0; s < kBatchMaxDistinct; ++s) rb_local[s] = 0ull;
+    int cur = -1;
+    auto ctx32 = [&](int sl) {
+      if (sl != cur) {
+        if (cur >= 0) rb_local[cur] = cf.rbits;
+        cur = sl;
+        cf.ycur = (it & 1) ? mp.mx.db : mp.mx.da;
+        cf.yprv = (it & 1) ? mp.mx.da : mp.mx.db;
+        cf.beta = (float)mp.f.st.beta[it];
+        cf.beta_n = (float)mp.f.st.beta[it + 1];
+        cf.write_out = check;
+        cf.rbits = rb_local[sl];
       }
-      chain_forward<float, kFwdMixed, C>(mp.f, k, c, smf, &mp.mx);
-      const unsigned long long r = block_max_u64(c.rbits, smf.redu);
-      if (tid == 0 && r > bc.rbits[sl]) bc.rbits[sl] = r;
+      return &cf;
+    };
+    batch_eval<float, kFwdMixed, C>(B, bc, mp, bm, step++, false, ctx32);
+    if (cur >= 0) rb_local[cur] = cf.rbits;
+    if (block_err(bm, B.err)) {
+      ok = false;
+      break;
     }
-    ++step;
-    if (!ok) break;
     if (check) {
-      __syncthreads();
-      if (tid == 0) {
-        for (int s = 0; s < bc.n; ++s) {
-          if (!bc.active[s]) continue;
-          atomicMax(B.probs[bc.prob[s]].f.st.res + ci, bc.rbits[s]);
-          bc.rbits[s] = 0ull;
-        }
+      // per problem: block maximum, then one grid barrier for all
+      for (int s = 0; s < bc.n; ++s) {
+        const unsigned long long r = block_max_u64(rb_local[s], bm.redu);
+        if (threadIdx.x == 0 && bc.active[s]) atomicMax(B.probs[bc.prob[s]].f.st.res + ci, r);
+      }
+      if (threadIdx.x == 0) {
         __threadfence();
         atomicAdd(B.barrier, 1u);
-        smf.flag[2] = spin_geq(B.barrier, (unsigned)(ci + 1) * gridDim.x, mp.f.st.err);
+        bm.bflag[1] = spin_geq(B.barrier, (unsigned)(ci + 1) * gridDim.x, B.err);
       }
       __syncthreads();
-      if (!smf.flag[2]) {
+      if (!bm.bflag[1]) {
         ok = false;
         break;
       }
       // the same residuals are visible to every block: consistent stops
-      if (tid == 0) {
+      if (threadIdx.x == 0) {
         for (int s = 0; s < bc.n; ++s) {
           if (!bc.active[s]) continue;
           const MixedParams &q = B.probs[bc.prob[s]];
-          const unsigned long long rb = __ldcg(q.f.st.res + ci);
-          const double rv = __longlong_as_double((long long)rb) * q.f.invgamma;
+          const unsigned long long rbv = __ldcg(q.f.st.res + ci);
+          const double rv = __longlong_as_double((long long)rbv) * q.f.invgamma;
           int reason = -1;
           if (!(rv <= 1.7976931348623157e308)) reason = 2;
           else if (B.tol > 0.0 && rv <= B.tol) reason = 1;
@@ -183,17 +206,21 @@ __global__ void __launch_bounds__(256) k_batch(BatchDev B) {
       for (int i = i0; i < i1; ++i) {
         const int p = B.item_prob[i];
         if (!bc.active[slot_of(bc, p)]) continue;
-        load_problem(B, p, bc, mp, smem_raw, smf, smd);
-        float *dcur = (it & 1) ? mp.mx.db : mp.mx.da;
-        float *dprv = (it & 1) ? mp.mx.da : mp.mx.db;
-        const float bn = (float)mp.f.st.beta[it + 1];
-        int idx = 0;
-        for_owned(mp.f.plan, B.item_chain[i], [&](int v) {
-          if ((idx++ % nw) == warp) refresh_node(mp, v, dprv, dcur, bn);
-        });
-        __syncthreads();
+        load_problem(B, p, bc, mp, bm);
+        const int G = mp.f.plan.n_groups, sub = B.item_sub[i], k = 2 * (sub - G) + ti;
+        if (sub >= G && k < mp.f.plan.n_chains) {
+          float *dcur = (it & 1) ? mp.mx.db : mp.mx.da;
+          float *dprv = (it & 1) ? mp.mx.da : mp.mx.db;
+          const float bn = (float)mp.f.st.beta[it + 1];
+          int idx = 0;
+          for_owned(mp.f.plan, k, [&](int v) {
+            if ((idx++ % tc.nwarps()) == tc.warp()) refresh_node(mp, v, dprv, dcur, bn);
+          });
+        }
+        tc.sync();
       }
-      if (!batch_fp64_step<C>(B, bc, mp, smem_raw, smf, smd, step++, false)) {
+      batch_eval<double, kFwdPlain, C>(B, bc, mp, bm, step++, false, ctx64);
+      if (block_err(bm, B.err)) {
         ok = false;
         break;
       }
@@ -201,17 +228,21 @@ __global__ void __launch_bounds__(256) k_batch(BatchDev B) {
   }
   if (ok) {
     for (int i = i0; i < i1; ++i) {
-      load_problem(B, B.item_prob[i], bc, mp, smem_raw, smf, smd);
-      int idx = 0;
-      for_owned(mp.f.plan, B.item_chain[i], [&](int v) {
-        if ((idx++ % nw) == warp) final_node(mp, v);
-      });
-      __syncthreads();
+      load_problem(B, B.item_prob[i], bc, mp, bm);
+      const int G = mp.f.plan.n_groups, sub = B.item_sub[i], k = 2 * (sub - G) + ti;
+      if (sub >= G && k < mp.f.plan.n_chains) {
+        int idx = 0;
+        for_owned(mp.f.plan, k, [&](int v) {
+          if ((idx++ % tc.nwarps()) == tc.warp()) final_node(mp, v);
+        });
+      }
+      tc.sync();
     }
-    ok = batch_fp64_step<C>(B, bc, mp, smem_raw, smf, smd, step++, true);
+    batch_eval<double, kFwdPlain, C>(B, bc, mp, bm, step++, true, ctx64);
+    ok = !block_err(bm, B.err);
   }
   // problems that ran to the end
-  if (tid == 0) {
+  if (threadIdx.x == 0) {
     for (int s = 0; s < bc.n; ++s) {
       if (!bc.active[s]) continue;
       int *info = B.prob_info + 3 * bc.prob[s];
@@ -239,6 +270,13 @@ cudaError_t launch_batch(const BatchDev &B, int maxc, int grid, int block, size_
   BatchDev b = B;
   void *args[] = {&b};
   return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, smem, st);
+}
+
+cudaError_t batch_static_smem(int maxc, int *bytes) {
+  cudaFuncAttributes fa{};
+  cudaError_t e = cudaFuncGetAttributes(&fa, batch_fn(maxc));
+  if (e == cudaSuccess) *bytes = (int)fa.sharedSizeBytes;
+  return e;
 }
 
 cudaError_t batch_occupancy(int maxc, int block, size_t smem, int *blocks_per_sm) {

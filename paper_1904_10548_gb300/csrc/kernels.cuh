@@ -8,8 +8,12 @@
 //                                      (y1 | y2 | y3), swapped every iteration
 //   ub  [n][NUP] : input offset u0 = x*(0) inputs (or ubar + K q at preparation)
 //   gb  [n][NXP] : Gd d
-//   z   [n][NUP] : F ghat / (2p) of the current dual-gradient evaluation
-//   up  [n][SP]  : subtree sums (lambda | ghat) handed from a node to its parent
+//   z   [n][NUP] : F ghat / (2p) of chain nodes (chains longer than a segment)
+//   up  [n][SP]  : rows 0..K-1: chain-head subtree sums (lambda | ghat) of
+//                  chain k; rows K + v: a group's rows that exceed its
+//                  shared-memory capacity
+//   ux  [n][SP]  : chain nodes: local path sums (X | U) of the chain;
+//                  top nodes: the published (x | Z), Z = sum of z over the path
 //   uo, xo       : inputs and states of the last checked iteration
 #pragma once
 
@@ -19,7 +23,7 @@
 
 namespace rn {
 
-constexpr int kSeg = 16;                    // chain nodes held in shared memory at once
+constexpr int kSeg = 16;                    // ints of a team's node list (halved)
 constexpr long long kWaitNs = 2000000000LL; // bound of every device-side wait (2 s)
 
 template <typename T>
@@ -41,20 +45,24 @@ struct NetDev {
   T Wx, Ws;
 };
 
+// the work schedule (rn::Plan) on the device
 struct PlanDev {
-  int n, n_top, n_chains, n_flags;
-  const int *parent, *top_nchild, *top_child_ptr, *top_child, *top_flag;
-  const int *ch_start, *ch_len, *ch_parent, *ch_path_ptr, *ch_path, *ch_own_from, *ch_flag;
+  int n, n_top, n_chains, n_groups;
+  const int *parent;
+  const int *g_node, *g_chain, *g_lvl, *lvl, *g_ccn, *ccn;
+  const int *g_desc_ptr, *g_desc;  // per-group descriptors (rn::Plan)
+  const int *tc_ptr, *tc, *cc_ptr, *cc;
+  const int *ch_start, *ch_len, *ch_group, *ch_parent, *ch_own_ptr, *ch_own;
 };
 
 template <typename T>
 struct StateDev {
-  T *s, *ya, *yb, *ub, *gb, *z, *up, *uo, *xo;
+  T *s, *ya, *yb, *ub, *gb, *z, *up, *ux, *uo, *xo;
   float *uo32, *xo32;  // optional FP32 copies of uo / xo (plain step)
   const T *inv2p;   // 1 / (2 p) per internal node
   const T *xroot;   // x0 (nx); unused when linear
   const double *beta;  // beta_0 .. beta_iters (APG)
-  unsigned *count, *flags, *barrier;
+  unsigned *count, *flags, *barrier;  // per group: chain arrivals, completion; grid
   unsigned long long *res;  // per check: bits of the non-negative residual
   int *err;                 // 0 ok, 1 timeout
   int *info;                // [iters done, checks done, stop reason]
@@ -69,7 +77,13 @@ struct KParams {
   int check_every;
   int linear;       // 1: constants of the dual gradient are zero
   int maxc;         // state components per lane in the dual update: 2, 4 or 8
-  int buf_elems;    // shared-memory buffer size (elements of T), smem_buf_elems
+  int buf_elems;    // work buffer of a team (elements of T)
+  int gbuf_elems;   // work buffer of a group (elements of T, the block's two team regions)
+  int segb;         // chain rows per backward segment
+  int gcap;         // group rows held in shared memory
+  int hchunk;       // chain-head rows staged at once by a group
+  int fslots;       // staged nodes per warp in the forward sweep (1 or 2)
+  int team_bytes;   // bytes of one team region
   int net_bytes;    // bytes of the block's shared-memory copy of the network
   unsigned step_base;
   double gamma, invgamma, tol;
@@ -101,48 +115,75 @@ cudaError_t launch_mixed(const MixedParams &M, int maxc, int grid, int block, si
                          cudaStream_t st);
 
 // Batched mode: independent problems (each a factor handle in mixed
-// precision) in one cooperative launch.  Work items (problem, chain) are
-// sorted by problem; block b processes items [cta_begin[b], cta_begin[b+1]).
+// precision) in one cooperative launch.  Work items are (problem, sub)
+// with sub numbered as in the single-problem kernels (groups, then chain
+// pairs), sorted by problem; block b processes items
+// [cta_begin[b], cta_begin[b+1]).
 constexpr int kBatchMaxDistinct = 32;  // problems one block may touch
 
 struct BatchDev {
   int n_problems;
-  const MixedParams *probs;  // per problem (device copy)
-  const int *item_prob, *item_chain, *cta_begin;
+  const MixedParams *probs;  // per problem (device copy; their err words are `err`)
+  const int *item_prob, *item_sub, *cta_begin;
   unsigned *barrier;         // grid barrier of the batch
+  int *err;                  // shared error word (a wait gave up)
   int *prob_info;            // per problem: iterations, checks, stop reason
   int iters, check_every, refresh_every;
-  int buf_f, buf_d;          // shared buffer sizes (elements), max over problems
-  int net_bytes_f;           // bytes reserved for a problem's FP32 network copy
+  int net_bytes;             // network region: FP32 copy, then the FP64 header
+  int net_bytes_f;           // offset of the FP64 header in the network region
+  int team_bytes;            // team region (max over problems)
   double tol;
 };
 
 cudaError_t launch_batch(const BatchDev &B, int maxc, int grid, int block, size_t smem,
                          cudaStream_t st);
 cudaError_t batch_occupancy(int maxc, int block, size_t smem, int *blocks_per_sm);
+cudaError_t batch_static_smem(int maxc, int *bytes);
 cudaError_t mixed_occupancy(int maxc, int block, size_t smem, int *blocks_per_sm);
 
-// shared-memory buffer of the persistent kernels, in elements of T: the
-// backward segment (kSeg rows of s plus E/S^-1 work space) or one staged
-// forward segment (SEGF nodes, fwd_elems_per_node each), whichever is larger
-inline int smem_buf_elems(int elem_bytes, int NXP, int NUP, int YP, int SP, int NEP, int mode) {
-  const int segf = elem_bytes == 8 ? 4 : 8;
-  const int back = kSeg * SP + 2 * kSeg * NEP + kSeg;
-  const int fwd = segf * (3 * NUP + 2 * NXP + (mode == 1 ? 2 * YP : (mode == 2 ? 3 * YP : 0)));
-  return back > fwd ? back : fwd;
+// Shared memory of the persistent kernels.  A block is two teams of
+// equal width; a team scans one chain, the whole block sums one group.
+// Dynamic shared memory: [block header | network copy | team 0 | team 1],
+// the group work area spanning both team regions.  Buffers in elements
+// of T (nw: warps of a team, nwb: of the block):
+//   chain backward: segb rows of SP, per-warp E/S^-1 scratch, a vector
+//   forward: the path vectors x_p | Z_p | B Z_p, then per warp `slots`
+//     staged nodes
+//   group: gcap rows, hchunk head rows, per-warp scratch, the descriptor
+__host__ __device__ inline int round4(int e) { return (e + 3) & ~3; }
+
+__host__ __device__ inline int fwd_elems_per_node(int NXP, int NUP, int YP, int SP, int mode) {
+  return SP + (mode == 1 ? 2 * YP : (mode == 2 ? 3 * YP + NUP + NXP : 0));
 }
 
-// dynamic shared memory in bytes for a buffer of buf_elems elements of T
-// (the block's copy of the network data comes on top: net_smem_bytes)
-template <typename T>
-inline size_t smem_bytes(int buf_elems) {
-  size_t b = sizeof(T) * ((size_t)buf_elems + 72);
-  b = (b + 15) & ~(size_t)15;
-  b += 40 * sizeof(unsigned long long) + (4 + 2 * kSeg) * sizeof(int);
-  return (b + 15) & ~(size_t)15;
+__host__ __device__ inline int chain_vec_off(int segb, int SP, int NEP, int nw) {
+  return round4(segb * SP) + round4(2 * nw * NEP);
 }
+
+__host__ __device__ inline int chain_back_elems(int segb, int SP, int NEP, int NXP, int NUP, int nw) {
+  return chain_vec_off(segb, SP, NEP, nw) + round4(2 * NXP + NUP);
+}
+
+__host__ __device__ inline int fwd_elems(int nw, int slots, int NXP, int NUP, int YP, int SP,
+                                         int mode) {
+  return round4(2 * NXP + NUP) + nw * slots * fwd_elems_per_node(NXP, NUP, YP, SP, mode);
+}
+
+__host__ __device__ inline int group_elems(int gcap, int hchunk, int SP, int NEP, int nwb,
+                                           int desc_elems) {
+  return (gcap + hchunk) * SP + round4(2 * nwb * NEP) + desc_elems;
+}
+
+constexpr int kHdrBytes = 512;  // block header: reduction words and flags
 
 __host__ __device__ inline size_t round16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+// bytes of a team region holding buf_elems elements of T (plus the team's
+// reduction words and node lists)
+template <typename T>
+inline size_t team_region_bytes(int buf_elems) {
+  return round16(sizeof(T) * ((size_t)buf_elems + 72)) + round16((4 + 2 * kSeg) * sizeof(int));
+}
 
 // bytes of a block's shared-memory copy of the network data: the NetDev
 // header, the sparse index arrays and the values in elements of elem bytes

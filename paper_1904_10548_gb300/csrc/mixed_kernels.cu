@@ -15,49 +15,42 @@
 
 namespace rn {
 
-// one FP64 evaluation of the dual gradient from mx.s64 into d.st.uo / xo
-// (and the FP32 copies uref / xref); false on timeout
 template <int C>
-__device__ bool fp64_step(const MixedParams &M, unsigned step, Smem<double> &sm) {
-  const KParams<double> &P = M.d;
-  for (int k = blockIdx.x; k < P.plan.n_chains; k += gridDim.x) {
-    chain_backward<double, C>(P, k, sm);
-    climb(P, k, step, sm);
-  }
-  FwdCtx<double> c{};
-  for (int k = blockIdx.x; k < P.plan.n_chains; k += gridDim.x) {
-    const int f = P.plan.ch_flag[k];
-    if (f >= 0) {
-      if (threadIdx.x == 0) sm.flag[1] = spin_geq(P.st.flags + f, step + 1u, P.st.err);
-      __syncthreads();
-      if (!sm.flag[1]) return false;
-    }
-    chain_forward<double, kFwdPlain, C>(P, k, c, sm, nullptr);
-  }
-  return true;
-}
-
-template <int C>
-__global__ void __launch_bounds__(256) k_mixed(MixedParams M) {
+__global__ void __launch_bounds__(512) k_mixed(MixedParams M) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem<double> smd = carve<double>(smem_raw, M.d.net, M.d.buf_elems);
-  Smem<float> smf = carve<float>(smem_raw, M.f.net, M.f.buf_elems);
-  // the FP32 iterations use a shared-memory copy of the network data; the
-  // FP64 refresh steps read theirs from global memory (header only here)
-  unsigned char *net_raw = smf.net_raw > smd.net_raw ? smf.net_raw : smd.net_raw;
-  smf.net = stage_net(M.f.net, net_raw);
-  smd.net = stage_net(M.d.net, net_raw + M.f.net_bytes, false);
+  // network region: the FP32 copy (for the iterations), then the header of
+  // the FP64 data (the rarely run FP64 steps read its arrays from global
+  // memory) at offset M.d.net_bytes
+  const BlockMem bm = block_mem(smem_raw, M.f.net_bytes, M.f.team_bytes);
+  const NetDev<float> *netf = stage_net(M.f.net, bm.net_raw);
+  const NetDev<double> *netd = stage_net(M.d.net, bm.net_raw + M.d.net_bytes, false);
+  const Team tc = chain_team(), tb = block_team();
+  const int ti = team_index();
+  const Smem<float> sfc = carve<float>(bm.team_raw[ti], M.f.buf_elems, netf);
+  const Smem<float> sfg = carve<float>(bm.team_raw[0], M.f.gbuf_elems, netf);
+  const Smem<double> sdc = carve<double>(bm.team_raw[ti], M.d.buf_elems, netd);
+  const Smem<double> sdg = carve<double>(bm.team_raw[0], M.d.gbuf_elems, netd);
   const KParams<float> &P = M.f;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int G = P.plan.n_groups, K = P.plan.n_chains, n_items = G + (K + 1) / 2;
+  const bool keep = (int)gridDim.x >= n_items && (int)blockIdx.x >= G;
+  auto owned = [&](auto fn) {
+    for (int i = blockIdx.x; i < n_items; i += gridDim.x) {
+      const int k = 2 * (i - G) + ti;
+      if (i < G || k >= K) continue;
+      int idx = 0;
+      for_owned(P.plan, k, [&](int v) {
+        if ((idx++ % tc.nwarps()) == tc.warp()) fn(v);
+      });
+    }
+    tc.sync();
+  };
   unsigned step = P.step_base;
   int it = 0, ci = 0, reason = 0;  // reason: 0 max iters, 1 converged, 2 non-finite, 3 timeout
-  bool ok = fp64_step<C>(M, step++, smd);
+  FwdCtx<double> c64{};
+  eval_step<double, kFwdPlain, C>(M.d, c64, nullptr, sdc, sdg, tc, tb, step++, keep);
+  bool ok = !block_err(bm, P.st.err);
   if (!ok) reason = 3;
   for (; it < P.iters && ok; ++it) {
-    for (int k = blockIdx.x; k < P.plan.n_chains; k += gridDim.x) {
-      chain_backward<float, C>(P, k, smf);
-      climb(P, k, step, smf);
-    }
     FwdCtx<float> c;
     float *dcur = (it & 1) ? M.mx.db : M.mx.da;
     float *dprv = (it & 1) ? M.mx.da : M.mx.db;
@@ -68,32 +61,15 @@ __global__ void __launch_bounds__(256) k_mixed(MixedParams M) {
     const bool check = ((it + 1) % P.check_every) == 0 || it + 1 == P.iters;
     c.write_out = check;
     c.rbits = 0ull;
-    for (int k = blockIdx.x; k < P.plan.n_chains; k += gridDim.x) {
-      const int f = P.plan.ch_flag[k];
-      if (f >= 0) {
-        if (tid == 0) smf.flag[1] = spin_geq(P.st.flags + f, step + 1u, P.st.err);
-        __syncthreads();
-        if (!smf.flag[1]) {
-          ok = false;
-          reason = 3;
-          break;
-        }
-      }
-      chain_forward<float, kFwdMixed, C>(P, k, c, smf, &M.mx);
+    eval_step<float, kFwdMixed, C>(P, c, &M.mx, sfc, sfg, tc, tb, step++, keep);
+    if (block_err(bm, P.st.err)) {
+      ok = false;
+      reason = 3;
+      ++it;
+      break;
     }
-    ++step;
-    if (!ok) break;
-    bool stop = false;
     if (check) {
-      const unsigned long long r = block_max_u64(c.rbits, smf.redu);
-      if (tid == 0) {
-        atomicMax(P.st.res + ci, r);
-        __threadfence();
-        atomicAdd(P.st.barrier, 1u);
-        smf.flag[2] = spin_geq(P.st.barrier, (unsigned)(ci + 1) * gridDim.x, P.st.err);
-      }
-      __syncthreads();
-      if (!smf.flag[2]) {
+      if (!grid_check(bm, c.rbits, P.st.res, P.st.barrier, ci, P.st.err)) {
         ok = false;
         reason = 3;
         ++it;
@@ -105,32 +81,20 @@ __global__ void __launch_bounds__(256) k_mixed(MixedParams M) {
       const double rv = (double)__longlong_as_double((long long)rb) * P.invgamma;
       if (!(rv <= 1.7976931348623157e308)) {
         reason = 2;
-        stop = true;
-      } else if (P.tol > 0.0 && rv <= P.tol) {
-        reason = 1;
-        stop = true;
+        ++it;
+        break;
       }
-    }
-    if (*(volatile int *)P.st.err != 0) {
-      ok = false;
-      reason = 3;
-      ++it;
-      break;
-    }
-    if (stop) {
-      ++it;
-      break;
+      if (P.tol > 0.0 && rv <= P.tol) {
+        reason = 1;
+        ++it;
+        break;
+      }
     }
     if ((it + 1) % M.mx.refresh_every == 0 && it + 1 < P.iters) {
       const float bn = (float)P.st.beta[it + 1];
-      for (int k = blockIdx.x; k < P.plan.n_chains; k += gridDim.x) {
-        int idx = 0;
-        for_owned(P.plan, k, [&](int v) {
-          if ((idx++ % nw) == warp) refresh_node(M, v, dprv, dcur, bn);
-        });
-      }
-      __syncthreads();
-      if (!fp64_step<C>(M, step++, smd)) {
+      owned([&](int v) { refresh_node(M, v, dprv, dcur, bn); });
+      eval_step<double, kFwdPlain, C>(M.d, c64, nullptr, sdc, sdg, tc, tb, step++, keep);
+      if (block_err(bm, P.st.err)) {
         ok = false;
         reason = 3;
         ++it;
@@ -139,17 +103,11 @@ __global__ void __launch_bounds__(256) k_mixed(MixedParams M) {
     }
   }
   if (ok) {
-    for (int k = blockIdx.x; k < P.plan.n_chains; k += gridDim.x) {
-      int idx = 0;
-      for_owned(P.plan, k, [&](int v) {
-        if ((idx++ % nw) == warp) final_node(M, v);
-      });
-    }
-    __syncthreads();
-    if (!fp64_step<C>(M, step++, smd)) reason = 3;
+    owned([&](int v) { final_node(M, v); });
+    eval_step<double, kFwdPlain, C>(M.d, c64, nullptr, sdc, sdg, tc, tb, step++, keep);
+    if (block_err(bm, P.st.err)) reason = 3;
   }
-  (void)lane;
-  if (blockIdx.x == 0 && tid == 0) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
     P.st.info[0] = it;
     P.st.info[1] = ci;
     P.st.info[2] = reason;

@@ -134,17 +134,39 @@ int build_plan(const rn_tree *t, Plan &p) {
   p.perm[0] = 0;
   p.iperm[0] = 0;
   int next = 1;
-  for (int v = 1; v < n; ++v)
-    if (leaves[v] >= 2) {
-      p.perm[next] = v;
-      p.iperm[v] = next++;
+  // groups: breadth-first over the top nodes below each stage-1 top node
+  p.g_node.push_back(1);
+  p.g_lvl.push_back(0);
+  std::vector<int> group_of(n, -1);
+  for (int b1 = sp[1]; b1 < sp[2]; ++b1) {
+    if (leaves[b1] < 2) continue;
+    const int g = p.n_groups++;
+    std::vector<int> level{b1};
+    while (!level.empty()) {
+      p.lvl.push_back(next);
+      std::vector<int> below;
+      for (int v : level) {
+        p.perm[next] = v;
+        p.iperm[v] = next++;
+        group_of[v] = g;
+        for (int c = first_child[v]; c < first_child[v] + nchild[v]; ++c)
+          if (leaves[c] >= 2) below.push_back(c);
+      }
+      level.swap(below);
     }
+    p.lvl.push_back(next);
+    p.g_lvl.push_back((int)p.lvl.size());
+    p.g_node.push_back(next);
+    p.max_group = std::max(p.max_group, p.g_node[g + 1] - p.g_node[g]);
+  }
   p.n_top = next - 1;
   // chains, ordered by their leaf (all leaves are at stage N, so this
   // keeps the chains below any node contiguous)
+  std::vector<int> head_chain(n, -1);
   for (int leaf = sp[N]; leaf < n; ++leaf) {
     int head = leaf;
     while (t->anc[head] != 0 && leaves[t->anc[head]] == 1) head = t->anc[head];
+    head_chain[head] = (int)p.ch_start.size();
     p.ch_start.push_back(next);
     int len = 0;
     for (int w = head;; w = first_child[w]) {
@@ -168,52 +190,94 @@ int build_plan(const rn_tree *t, Plan &p) {
     p.prob[i] = t->prob[b];
     if (b > 0) p.parent[i] = p.iperm[t->anc[b]];
   }
-  // top nodes: children lists in breadth-first order, flags at stage 1
-  p.top_nchild.assign(n, 0);
-  p.top_child_ptr.assign(n + 1, 0);
-  p.top_flag.assign(n, -1);
-  for (int i = 1; i <= p.n_top; ++i) {
-    int b = p.perm[i];
-    p.top_nchild[i] = nchild[b];
-    if (stage[b] == 1) p.top_flag[i] = p.n_flags++;
-  }
-  for (int i = 0; i < n; ++i) {
-    p.top_child_ptr[i + 1] = p.top_child_ptr[i];
-    if (i >= 1 && i <= p.n_top) {
-      int b = p.perm[i];
-      for (int c = first_child[b]; c < first_child[b] + nchild[b]; ++c)
-        p.top_child.push_back(p.iperm[c]);
-      p.top_child_ptr[i + 1] = (int)p.top_child.size();
+  // children of the top nodes: top children (internal) and chain children
+  p.tc_ptr.assign(p.n_top + 2, 0);
+  p.cc_ptr.assign(p.n_top + 2, 0);
+  for (int i = 0; i <= p.n_top; ++i) {
+    p.tc_ptr[i + 1] = p.tc_ptr[i];
+    p.cc_ptr[i + 1] = p.cc_ptr[i];
+    if (i == 0) continue;
+    const int b = p.perm[i];
+    for (int c = first_child[b]; c < first_child[b] + nchild[b]; ++c) {
+      if (leaves[c] >= 2) {
+        p.tc.push_back(p.iperm[c]);
+        p.tc_ptr[i + 1]++;
+      } else {
+        p.cc.push_back(head_chain[c]);
+        p.cc_ptr[i + 1]++;
+      }
     }
   }
-  // chain paths (top ancestors from stage 1 down) and ownership: the
-  // first chain below a top node computes that node's proximal step
+  p.g_ccn.assign(1, 0);
+  for (int g = 0; g < p.n_groups; ++g) {
+    for (int v = p.g_node[g]; v < p.g_node[g + 1]; ++v)
+      if (p.cc_ptr[v + 1] > p.cc_ptr[v]) p.ccn.push_back(v);
+    p.g_ccn.push_back((int)p.ccn.size());
+  }
+  // chains: group, parent, owned top nodes (the first chain below a top
+  // node owns it; owned ancestors form a suffix of the path from stage 1)
   std::vector<int> owner(n, -1);
-  p.ch_path_ptr.assign(1, 0);
+  p.ch_own_ptr.assign(1, 0);
+  p.g_chain.assign(2 * (size_t)p.n_groups, -1);
   for (int k = 0; k < p.n_chains; ++k) {
-    int head = p.ch_start[k];
-    p.ch_parent.push_back(p.parent[head]);
+    const int head = p.ch_start[k];
+    const int par = p.parent[head];
+    p.ch_parent.push_back(par);
     std::vector<int> path;
-    for (int a = p.parent[head]; a > 0; a = p.parent[a]) path.push_back(a);
+    for (int a = par; a > 0; a = p.parent[a]) path.push_back(a);
     std::reverse(path.begin(), path.end());
-    int own_from = (int)path.size();
-    for (int j = 0; j < (int)path.size(); ++j)
-      if (owner[path[j]] < 0) {
-        owner[path[j]] = k;
-        own_from = std::min(own_from, j);
+    const int g = path.empty() ? -1 : group_of[p.perm[path[0]]];
+    p.ch_group.push_back(g);
+    if (g >= 0) {
+      if (p.g_chain[2 * g] < 0) p.g_chain[2 * g] = k;
+      if (p.g_chain[2 * g + 1] >= 0 && p.g_chain[2 * g + 1] != k) {
+        set_error("tree: internal error, chains of a group are not contiguous");
+        return RN_ERR_INVAL;
       }
-    // owned ancestors form a suffix of the path
-    for (int j = own_from; j < (int)path.size(); ++j)
-      if (owner[path[j]] != k) {
+      p.g_chain[2 * g + 1] = k + 1;
+    }
+    bool owning = false;
+    for (int a : path) {
+      if (owner[a] < 0) {
+        owner[a] = k;
+        owning = true;
+        p.ch_own.push_back(a);
+      } else if (owning) {
         set_error("tree: internal error in the ownership of top nodes");
         return RN_ERR_INVAL;
       }
-    p.ch_own_from.push_back(own_from);
-    p.ch_flag.push_back(path.empty() ? -1 : p.top_flag[path[0]]);
-    p.max_path_len = std::max(p.max_path_len, (int)path.size());
-    for (int a : path) p.ch_path.push_back(a);
-    p.ch_path_ptr.push_back((int)p.ch_path.size());
+    }
+    p.ch_own_ptr.push_back((int)p.ch_own.size());
   }
+  for (int g = 0; g < p.n_groups; ++g)
+    p.max_group_chains = std::max(p.max_group_chains, p.g_chain[2 * g + 1] - p.g_chain[2 * g]);
+  p.g_desc_ptr.assign(1, 0);
+  for (int g = 0; g < p.n_groups; ++g) {
+    const int g0 = p.g_node[g], m = p.g_node[g + 1] - g0, c0 = p.g_chain[2 * g];
+    const int l0 = p.g_lvl[g], nl = p.g_lvl[g + 1] - l0 - 1;
+    std::vector<int> d{m, nl, p.g_chain[2 * g + 1] - c0, 0};
+    for (int l = 0; l <= nl; ++l) d.push_back(p.lvl[l0 + l] - g0);
+    for (int li = 0; li < m; ++li) d.push_back(p.parent[g0 + li] > 0 ? p.parent[g0 + li] - g0 : -1);
+    int acc = 0;
+    for (int li = 0; li <= m; ++li) {
+      d.push_back(acc);
+      if (li < m) acc += p.tc_ptr[g0 + li + 1] - p.tc_ptr[g0 + li];
+    }
+    for (int li = 0; li < m; ++li)
+      for (int c = p.tc_ptr[g0 + li]; c < p.tc_ptr[g0 + li + 1]; ++c) d.push_back(p.tc[c] - g0);
+    acc = 0;
+    for (int li = 0; li <= m; ++li) {
+      d.push_back(acc);
+      if (li < m) acc += p.cc_ptr[g0 + li + 1] - p.cc_ptr[g0 + li];
+    }
+    for (int li = 0; li < m; ++li)
+      for (int c = p.cc_ptr[g0 + li]; c < p.cc_ptr[g0 + li + 1]; ++c) d.push_back(p.cc[c] - c0);
+    while (d.size() % 4) d.push_back(0);
+    p.max_desc = std::max(p.max_desc, (int)d.size());
+    p.g_desc.insert(p.g_desc.end(), d.begin(), d.end());
+    p.g_desc_ptr.push_back((int)p.g_desc.size());
+  }
+  if (p.g_desc.empty()) p.g_desc.assign(4, 0);
   for (int i = 1; i <= p.n_top; ++i)
     if (owner[i] < 0) {
       set_error("tree: internal error, top node without a chain");

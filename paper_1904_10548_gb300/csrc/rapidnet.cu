@@ -426,6 +426,12 @@ __global__ void k_gather_mixed_y(NetDev<double> nt, const int *perm, int n, cons
 // ---------------------------------------------------------------------------
 // factor handle
 // ---------------------------------------------------------------------------
+// work-buffer sizes of one precision in one kernel's shared-memory layout
+struct Sizes {
+  int team_bytes = 0, net_bytes = 0;  // layout of the block (kernels.cuh)
+  int buf = 0, gbuf = 0, segb = 1, gcap = 0, hchunk = 1, fslots = 1;
+};
+
 struct rn_factor {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -435,8 +441,13 @@ struct rn_factor {
   int nx = 0, nu = 0, nd = 0, ne = 0, NXP = 0, NUP = 0, SP = 0, YP = 0, NEP = 0;
   double W_alpha = 0.0, Ws = 0.0, Wx = 0.0;
   double gamma = 0.0, L = 0.0;
-  int grid = 0, block = 0, maxc = 2, buf_d = 0, buf_f = 0, net_bytes_d = 0, net_bytes_f = 0;
+  // launch layout of the FP64 kernel (APG and plain evaluations)
+  int grid = 0, block = 0, maxc = 2;
   size_t smem = 0;
+  Sizes sz_d{};   // its buffers
+  // launch layout of the mixed-precision kernel (FP32 iterations, FP64 steps)
+  Sizes sz_f{}, sz_dm{};
+  int net_bytes_d = 0, net_bytes_f = 0;
   std::vector<void *> allocs;
   long long bytes = 0;
   NetDev<double> net{};
@@ -448,6 +459,7 @@ struct rn_factor {
   MixedDev mx{};
   int grid_mixed = 0;
   size_t smem_mixed = 0;
+  int net_region_m = 0;  // network region of the mixed kernel
   // device copies of host data
   int *perm = nullptr;
   double *prob = nullptr, *inv2p = nullptr, *alpha0 = nullptr, *wdiag = nullptr;
@@ -567,7 +579,20 @@ std::vector<double> chol_inverse(const std::vector<double> &R, int m) {
   return inv;
 }
 
-KParams<double> base_params(rn_factor *f) {
+template <typename T>
+void set_sizes(KParams<T> &P, const Sizes &z) {
+  P.buf_elems = z.buf;
+  P.gbuf_elems = z.gbuf;
+  P.segb = z.segb;
+  P.gcap = z.gcap;
+  P.hchunk = z.hchunk;
+  P.fslots = z.fslots;
+  P.team_bytes = z.team_bytes;
+  P.net_bytes = z.net_bytes;
+}
+
+// parameters of the FP64 kernel; mixed: of the FP64 steps of the mixed kernel
+KParams<double> base_params(rn_factor *f, bool mixed = false) {
   KParams<double> P{};
   P.net = f->net;
   P.plan = f->pd;
@@ -580,8 +605,7 @@ KParams<double> base_params(rn_factor *f) {
   P.invgamma = f->gamma > 0 ? 1.0 / f->gamma : 0.0;
   P.tol = 0.0;
   P.maxc = f->maxc;
-  P.buf_elems = f->buf_d;
-  P.net_bytes = f->net_bytes_d;
+  set_sizes(P, mixed ? f->sz_dm : f->sz_d);
   return P;
 }
 
@@ -600,9 +624,22 @@ KParams<float> base_params_f(rn_factor *f) {
   P.invgamma = f->gamma > 0 ? 1.0 / f->gamma : 0.0;
   P.tol = 0.0;
   P.maxc = f->maxc;
-  P.buf_elems = f->buf_f;
-  P.net_bytes = f->net_bytes_f;
+  set_sizes(P, f->sz_f);
   return P;
+}
+
+// the mixed kernel's parameters for max_iters iterations
+MixedParams mixed_params(rn_factor *f, int max_iters, double tol) {
+  MixedParams M;
+  M.f = base_params_f(f);
+  M.f.iters = max_iters;
+  M.f.check_every = f->opts.check_every;
+  M.f.tol = tol > 0.0 ? tol : 0.0;
+  M.d = base_params(f, true);
+  M.d.st.uo32 = const_cast<float *>(f->mx.uref);
+  M.d.st.xo32 = const_cast<float *>(f->mx.xref);
+  M.mx = f->mx;
+  return M;
 }
 
 int reset_sync(rn_factor *f) {
@@ -652,6 +689,69 @@ int power_iteration(rn_factor *f, int iters, double *L_out) {
   int rc = check_err(f);
   if (rc) return rc;
   *L_out = std::sqrt(nrm2);
+  return RN_OK;
+}
+
+// Bytes of one team region for a kernel whose blocks hold a network
+// region of net_bytes and static_smem bytes of static shared memory:
+// enough blocks per SM that every work item gets a resident block (up to
+// 4), split evenly.
+int team_budget(int device, int n_items, int net_bytes, int static_smem, int *team_bytes) {
+  int sms = 0, optin = 0, per_sm = 0, reserved = 0;
+  RN_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+  RN_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+  RN_CUDA(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device));
+  RN_CUDA(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, device));
+  const int bpsm = std::max(1, std::min(4, (n_items + sms - 1) / std::max(1, sms)));
+  const int budget = std::min(optin, per_sm / bpsm - reserved) - static_smem;
+  const int tb = ((budget - kHdrBytes - net_bytes) / 2) & ~15;
+  if (tb <= 0) {
+    set_error("shared memory: the network data leave no room for the work buffers");
+    return RN_ERR_UNSUPPORTED;
+  }
+  *team_bytes = tb;
+  return RN_OK;
+}
+
+// Work-buffer sizes of elements of eb bytes in team regions of team_bytes
+// for blocks of `block` threads: the team buffer holds the forward slots of
+// `mode` (two per warp if they fit, else one) and a backward segment (as
+// many chain rows as fit, up to the longest chain); the group buffer (both
+// regions) holds the group's descriptor and as many group rows as fit
+// while leaving room for min(16, chains of the largest group) head rows.
+int fit_sizes(const rn_factor *f, int eb, int team_bytes, int net_bytes, int block, int mode,
+              Sizes *z) {
+  const Plan &p = f->plan;
+  const int misc = (int)round16((4 + 2 * kSeg) * sizeof(int));
+  const int nw = block / 64, nwb = block / 32;
+  z->team_bytes = team_bytes;
+  z->net_bytes = net_bytes;
+  z->buf = ((team_bytes - misc) & ~15) / eb - 72;
+  z->gbuf = ((2 * team_bytes - misc) & ~15) / eb - 72;
+  z->fslots = fwd_elems(nw, 2, f->NXP, f->NUP, f->YP, f->SP, mode) <= z->buf ? 2 : 1;
+  if (fwd_elems(nw, z->fslots, f->NXP, f->NUP, f->YP, f->SP, mode) > z->buf ||
+      chain_back_elems(1, f->SP, f->NEP, f->NXP, f->NUP, nw) > z->buf) {
+    set_error("shared memory: the network is too large for the work buffers");
+    return RN_ERR_UNSUPPORTED;
+  }
+  z->segb = 1;
+  while (z->segb < p.max_chain_len &&
+         chain_back_elems(z->segb + 1, f->SP, f->NEP, f->NXP, f->NUP, nw) <= z->buf)
+    ++z->segb;
+  if (p.n_groups == 0) {
+    z->gcap = 0;
+    z->hchunk = 1;
+    return RN_OK;
+  }
+  const int desc = round4((p.max_desc * 4 + eb - 1) / eb);
+  const int rows = (z->gbuf - group_elems(0, 0, f->SP, f->NEP, nwb, desc)) / f->SP;
+  if (rows < 2) {
+    set_error("shared memory: the network is too large for the group buffer");
+    return RN_ERR_UNSUPPORTED;
+  }
+  const int hmin = std::min(16, p.max_group_chains);
+  z->gcap = std::max(1, std::min(p.max_group, rows - hmin));
+  z->hchunk = std::max(1, std::min(p.max_group_chains, rows - z->gcap));
   return RN_OK;
 }
 
@@ -840,11 +940,13 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
   pd.n = n;
   pd.n_top = p.n_top;
   pd.n_chains = p.n_chains;
-  pd.n_flags = p.n_flags;
-  UP_I(pd.parent, p.parent) UP_I(pd.top_nchild, p.top_nchild) UP_I(pd.top_child_ptr, p.top_child_ptr)
-  UP_I(pd.top_child, p.top_child) UP_I(pd.top_flag, p.top_flag) UP_I(pd.ch_start, p.ch_start)
-  UP_I(pd.ch_len, p.ch_len) UP_I(pd.ch_parent, p.ch_parent) UP_I(pd.ch_path_ptr, p.ch_path_ptr)
-  UP_I(pd.ch_path, p.ch_path) UP_I(pd.ch_own_from, p.ch_own_from) UP_I(pd.ch_flag, p.ch_flag)
+  pd.n_groups = p.n_groups;
+  UP_I(pd.parent, p.parent) UP_I(pd.g_node, p.g_node) UP_I(pd.g_chain, p.g_chain)
+  UP_I(pd.g_lvl, p.g_lvl) UP_I(pd.lvl, p.lvl) UP_I(pd.g_ccn, p.g_ccn) UP_I(pd.ccn, p.ccn)
+  UP_I(pd.g_desc_ptr, p.g_desc_ptr) UP_I(pd.g_desc, p.g_desc)
+  UP_I(pd.tc_ptr, p.tc_ptr) UP_I(pd.tc, p.tc) UP_I(pd.cc_ptr, p.cc_ptr) UP_I(pd.cc, p.cc)
+  UP_I(pd.ch_start, p.ch_start) UP_I(pd.ch_len, p.ch_len) UP_I(pd.ch_group, p.ch_group)
+  UP_I(pd.ch_parent, p.ch_parent) UP_I(pd.ch_own_ptr, p.ch_own_ptr) UP_I(pd.ch_own, p.ch_own)
   UP_I(f->perm, p.perm) UP_D(f->prob, p.prob)
   std::vector<double> inv2p(n, 0.0);
   for (int i = 1; i < n; ++i) inv2p[i] = 1.0 / (2.0 * p.prob[i]);
@@ -854,12 +956,12 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
 
   // state
   StateDev<double> &st = f->st;
-  double *s, *ya, *yb, *ub, *gb, *z, *up, *uo, *xo;
+  double *s, *ya, *yb, *ub, *gb, *z, *up, *ux, *uo, *xo;
   if ((rc = dalloc(f, &s, (size_t)n * f->SP)) || (rc = dalloc(f, &ya, (size_t)n * f->YP)) ||
       (rc = dalloc(f, &yb, (size_t)n * f->YP)) || (rc = dalloc(f, &ub, (size_t)n * f->NUP)) ||
       (rc = dalloc(f, &gb, (size_t)n * f->NXP)) || (rc = dalloc(f, &z, (size_t)n * f->NUP)) ||
-      (rc = dalloc(f, &up, (size_t)n * f->SP)) || (rc = dalloc(f, &uo, (size_t)n * f->NUP)) ||
-      (rc = dalloc(f, &xo, (size_t)n * f->NXP)))
+      (rc = dalloc(f, &up, (size_t)n * f->SP)) || (rc = dalloc(f, &ux, (size_t)n * f->SP)) ||
+      (rc = dalloc(f, &uo, (size_t)n * f->NUP)) || (rc = dalloc(f, &xo, (size_t)n * f->NXP)))
     return rc;
   RN_CUDA(cudaMemset(s, 0, (size_t)n * f->SP * sizeof(double)));
   RN_CUDA(cudaMemset(ya, 0, (size_t)n * f->YP * sizeof(double)));
@@ -868,6 +970,7 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
   RN_CUDA(cudaMemset(gb, 0, (size_t)n * f->NXP * sizeof(double)));
   RN_CUDA(cudaMemset(z, 0, (size_t)n * f->NUP * sizeof(double)));
   RN_CUDA(cudaMemset(up, 0, (size_t)n * f->SP * sizeof(double)));
+  RN_CUDA(cudaMemset(ux, 0, (size_t)n * f->SP * sizeof(double)));
   RN_CUDA(cudaMemset(uo, 0, (size_t)n * f->NUP * sizeof(double)));
   RN_CUDA(cudaMemset(xo, 0, (size_t)n * f->NXP * sizeof(double)));
   st.s = s;
@@ -877,6 +980,7 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
   st.gb = gb;
   st.z = z;
   st.up = up;
+  st.ux = ux;
   st.uo = uo;
   st.xo = xo;
   st.inv2p = f->inv2p;
@@ -887,11 +991,12 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
     return rc;
   RN_CUDA(cudaMemset(f->x0, 0, nx * sizeof(double)));
   st.xroot = f->x0;
-  f->sync_words = (size_t)n + (size_t)std::max(1, p.n_flags) + 1;
+  const size_t ng = (size_t)std::max(1, p.n_groups);
+  f->sync_words = 2 * ng + 1;
   if ((rc = dalloc(f, &f->sync, f->sync_words))) return rc;
   st.count = f->sync;
-  st.flags = f->sync + n;
-  st.barrier = f->sync + n + std::max(1, p.n_flags);
+  st.flags = f->sync + ng;
+  st.barrier = f->sync + 2 * ng;
   st.err = f->err;
   st.info = f->info;
   st.res = nullptr;
@@ -931,15 +1036,17 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
     UP_F(nf.umin, tof(net->umin, nu)) UP_F(nf.umax, tof(net->umax, nu))
     UP_F(f->stf.inv2p, tofv(inv2p))
 #undef UP_F
-    float *s32, *z32, *up32, *da, *db, *ybh, *uref, *xref, *sw;
+    float *s32, *z32, *up32, *ux32, *da, *db, *ybh, *uref, *xref, *sw;
     if ((rc = dalloc(f, &s32, (size_t)n * f->SP)) || (rc = dalloc(f, &z32, (size_t)n * f->NUP)) ||
-        (rc = dalloc(f, &up32, (size_t)n * f->SP)) || (rc = dalloc(f, &da, (size_t)n * f->YP)) ||
+        (rc = dalloc(f, &up32, (size_t)n * f->SP)) || (rc = dalloc(f, &ux32, (size_t)n * f->SP)) ||
+        (rc = dalloc(f, &da, (size_t)n * f->YP)) ||
         (rc = dalloc(f, &db, (size_t)n * f->YP)) || (rc = dalloc(f, &ybh, (size_t)n * f->YP)) ||
         (rc = dalloc(f, &uref, (size_t)n * f->NUP)) || (rc = dalloc(f, &xref, (size_t)n * f->NXP)) ||
         (rc = dalloc(f, &sw, (size_t)n * f->SP)))
       return rc;
     for (auto pr : {std::make_pair((void *)s32, (size_t)n * f->SP), {(void *)z32, (size_t)n * f->NUP},
-                    {(void *)up32, (size_t)n * f->SP}, {(void *)da, (size_t)n * f->YP},
+                    {(void *)up32, (size_t)n * f->SP}, {(void *)ux32, (size_t)n * f->SP},
+                    {(void *)da, (size_t)n * f->YP},
                     {(void *)db, (size_t)n * f->YP}, {(void *)ybh, (size_t)n * f->YP},
                     {(void *)uref, (size_t)n * f->NUP}, {(void *)xref, (size_t)n * f->NXP},
                     {(void *)sw, (size_t)n * f->SP}})
@@ -948,6 +1055,7 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
     sf.s = s32;
     sf.z = z32;
     sf.up = up32;
+    sf.ux = ux32;
     sf.count = st.count;
     sf.flags = st.flags;
     sf.barrier = st.barrier;
@@ -964,55 +1072,67 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
     f->mx.refresh_every = f->opts.refresh_every;
   }
 
-  // launch configuration: one thread per input component; as many
-  // resident blocks as there are chains, up to what the device holds
-  // block width and components per thread: C = ceil(max(nx, nu) / block),
-  // at least ceil(nx / 32) (a warp updates a node), rounded to 1, 2, 4, 8
+  // launch configuration: a block is two chain teams of tw threads (one
+  // thread per input component, at least 64); as many resident blocks as
+  // there are work items (groups and chain pairs), up to what the device
+  // holds
   {
-    int bt = f->opts.block_threads > 0 ? ((f->opts.block_threads + 31) / 32) * 32
+    int tw = f->opts.block_threads > 0 ? ((f->opts.block_threads + 31) / 32) * 32
                                         : std::max(64, ((std::max(nx, nu) + 31) / 32) * 32);
-    bt = std::min(bt, 256);
+    tw = std::min(tw, 256);
     auto comps = [&](int b) {
       int c = std::max((std::max(nx, nu) + b - 1) / b, (nx + 31) / 32);
       return c <= 1 ? 1 : (c <= 2 ? 2 : (c <= 4 ? 4 : (c <= 8 ? 8 : 16)));
     };
-    while (comps(bt) > 8 && bt < 256) bt += 32;
-    if (comps(bt) > 8) {
-      set_error("network: nx, nu too large for the block width");
+    while (comps(tw) > 8 && tw < 256) tw += 32;
+    if (comps(tw) > 8) {
+      set_error("network: nx, nu too large for the team width");
       return RN_ERR_UNSUPPORTED;
     }
-    f->block = bt;
-    f->maxc = comps(bt);
+    f->block = 2 * tw;
+    f->maxc = comps(tw);
   }
-  f->buf_d = smem_buf_elems(8, f->NXP, f->NUP, f->YP, f->SP, f->NEP, 1);
-  f->buf_f = smem_buf_elems(4, f->NXP, f->NUP, f->YP, f->SP, f->NEP, 2);
   {
     const int nnzB = (int)Bc.idx.size(), nnzE = (int)Er.idx.size();
     f->net_bytes_d = (int)net_smem_bytes(nx, nu, ne, nnzB, nnzE, 8);
     f->net_bytes_f = (int)net_smem_bytes(nx, nu, ne, nnzB, nnzE, 4);
   }
-  f->smem = smem_bytes<double>(f->buf_d) + f->net_bytes_d;
-  int bps1 = 0, bps2 = 0, sms = 0;
-  RN_CUDA((solve_occupancy<double, true>(f->maxc, f->block, f->smem, &bps1)));
-  RN_CUDA((solve_occupancy<double, false>(f->maxc, f->block, f->smem, &bps2)));
+  const int n_items = p.n_groups + (p.n_chains + 1) / 2;
+  int sms = 0;
   RN_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, f->device));
-  const int resident = std::min(bps1, bps2) * sms;
-  if (resident < 1) {
-    set_error("the solve kernel does not fit on the device (block %d, smem %zu)", f->block, f->smem);
-    return RN_ERR_UNSUPPORTED;
+  {
+    int team_bytes = 0;
+    if ((rc = team_budget(f->device, n_items, f->net_bytes_d, 0, &team_bytes))) return rc;
+    if ((rc = fit_sizes(f, 8, team_bytes, f->net_bytes_d, f->block, 1, &f->sz_d))) return rc;
+    f->smem = kHdrBytes + f->net_bytes_d + 2 * (size_t)team_bytes;
+    int bps1 = 0, bps2 = 0;
+    RN_CUDA((solve_occupancy<double, true>(f->maxc, f->block, f->smem, &bps1)));
+    RN_CUDA((solve_occupancy<double, false>(f->maxc, f->block, f->smem, &bps2)));
+    const int resident = std::min(bps1, bps2) * sms;
+    if (resident < 1) {
+      set_error("the solve kernel does not fit on the device (block %d, smem %zu)", f->block,
+                f->smem);
+      return RN_ERR_UNSUPPORTED;
+    }
+    f->grid = std::min(n_items, resident);
+    if (f->opts.max_ctas > 0) f->grid = std::min(f->grid, f->opts.max_ctas);
   }
-  f->grid = std::min(p.n_chains, resident);
-  if (f->opts.max_ctas > 0) f->grid = std::min(f->grid, f->opts.max_ctas);
   if (f->opts.precision == RN_PREC_MIXED) {
-    f->smem_mixed = std::max(smem_bytes<double>(f->buf_d), smem_bytes<float>(f->buf_f)) +
-                    f->net_bytes_f + round16(sizeof(NetDev<double>));
+    // network region: the FP32 copy, then the header of the FP64 data
+    f->net_region_m = f->net_bytes_f + (int)round16(sizeof(NetDev<double>));
+    int team_bytes = 0;
+    if ((rc = team_budget(f->device, n_items, f->net_region_m, 0, &team_bytes))) return rc;
+    if ((rc = fit_sizes(f, 4, team_bytes, f->net_region_m, f->block, 2, &f->sz_f)) ||
+        (rc = fit_sizes(f, 8, team_bytes, f->net_bytes_f, f->block, 0, &f->sz_dm)))
+      return rc;
+    f->smem_mixed = kHdrBytes + f->net_region_m + 2 * (size_t)team_bytes;
     int bpm = 0;
     RN_CUDA(mixed_occupancy(f->maxc, f->block, f->smem_mixed, &bpm));
     if (bpm < 1) {
       set_error("the mixed kernel does not fit on the device");
       return RN_ERR_UNSUPPORTED;
     }
-    f->grid_mixed = std::min(p.n_chains, bpm * sms);
+    f->grid_mixed = std::min(n_items, bpm * sms);
     if (f->opts.max_ctas > 0) f->grid_mixed = std::min(f->grid_mixed, f->opts.max_ctas);
   }
 
@@ -1146,15 +1266,7 @@ int solve_device_impl(rn_factor *f, const double *x0, const double *q, const dou
   RN_CUDA(cudaMemsetAsync(f->res, 0, checks * sizeof(unsigned long long), f->stream));
   RN_CUDA(cudaEventRecord(f->ev0, f->stream));
   if (mixed) {
-    MixedParams M;
-    M.f = base_params_f(f);
-    M.f.iters = max_iters;
-    M.f.check_every = f->opts.check_every;
-    M.f.tol = tol > 0.0 ? tol : 0.0;
-    M.d = base_params(f);
-    M.d.st.uo32 = const_cast<float *>(f->mx.uref);
-    M.d.st.xo32 = const_cast<float *>(f->mx.xref);
-    M.mx = f->mx;
+    const MixedParams M = mixed_params(f, max_iters, tol);
     RN_CUDA(launch_mixed(M, f->maxc, f->grid_mixed, f->block, f->smem_mixed, f->stream));
   } else {
     KParams<double> P = base_params(f);
@@ -1448,9 +1560,10 @@ extern "C" int rapidnet_dual_gradient_noalloc(rn_factor *f, const double *w, dou
   }
   const int n = f->plan.n;
   const size_t rows = (size_t)n;
-  const size_t sync_words = rows + (size_t)std::max(1, f->plan.n_flags) + 1;
-  // doubles: s, up (SP), z, uo (NUP), xo (NXP); then sync words, err, info
-  const size_t need_d = rows * (2 * (size_t)f->SP + 2 * (size_t)f->NUP + (size_t)f->NXP);
+  const size_t ng = (size_t)std::max(1, f->plan.n_groups);
+  const size_t sync_words = 2 * ng + 1;
+  // doubles: s, up, ux (SP), z, uo (NUP), xo (NXP); then sync words, err, info
+  const size_t need_d = rows * (3 * (size_t)f->SP + 2 * (size_t)f->NUP + (size_t)f->NXP);
   const size_t need_w = sync_words + 1 + 4;  // 32-bit words
   const size_t need = need_d + (need_w + 1) / 2;
   if (need > kNoAllocDoubles) {
@@ -1469,6 +1582,8 @@ extern "C" int rapidnet_dual_gradient_noalloc(rn_factor *f, const double *w, dou
   p += rows * f->SP;
   st.up = p;
   p += rows * f->SP;
+  st.ux = p;
+  p += rows * f->SP;
   st.z = p;
   p += rows * f->NUP;
   st.uo = p;
@@ -1477,16 +1592,16 @@ extern "C" int rapidnet_dual_gradient_noalloc(rn_factor *f, const double *w, dou
   p += rows * f->NXP;
   unsigned *words = reinterpret_cast<unsigned *>(p);
   st.count = words;
-  st.flags = words + rows;
-  st.barrier = words + rows + std::max(1, f->plan.n_flags);
+  st.flags = words + ng;
+  st.barrier = words + 2 * ng;
   st.err = reinterpret_cast<int *>(words + sync_words);
   st.info = st.err + 1;
   st.res = nullptr;
   st.beta = nullptr;
   // the array keeps the previous call's contents: counters, flags and the
-  // error word must start at zero; padding columns of s and up as well
+  // error word must start at zero; padding columns of s, up and ux as well
   RN_CUDA(cudaMemsetAsync(words, 0, need_w * sizeof(unsigned), f->stream));
-  RN_CUDA(cudaMemsetAsync(st.s, 0, rows * 2 * f->SP * sizeof(double), f->stream));
+  RN_CUDA(cudaMemsetAsync(st.s, 0, rows * 3 * f->SP * sizeof(double), f->stream));
   k_s_from_w<<<node_blocks(n), 128, 0, f->stream>>>(f->net, f->perm, n, w, st.s);
   RN_CUDA(cudaGetLastError());
   KParams<double> P = base_params(f);
@@ -1558,8 +1673,7 @@ int batch_impl(rn_factor *const *fs, const rn_solve_req *req, int n, int max_ite
   cudaStream_t bs = fs[0]->stream;
   int rc;
   // per-problem preparation on each handle's stream
-  int checks = 0, maxc = 1, block = 32, buf_f = 0, buf_d = 0, net_f = 0;
-  size_t smem = 0;
+  int checks = 0, maxc = 1, block = 64, net_region = 0, net_f = 0;
   long long items = 0;
   for (int i = 0; i < n; ++i) {
     rn_factor *f = fs[i];
@@ -1575,20 +1689,29 @@ int batch_impl(rn_factor *const *fs, const rn_solve_req *req, int n, int max_ite
     if ((rc = reset_sync(f))) return rc;
     RN_CUDA(cudaMemsetAsync(f->res, 0, ck * sizeof(unsigned long long), f->stream));
     block = std::max(block, f->block);
-    buf_f = std::max(buf_f, f->buf_f);
-    buf_d = std::max(buf_d, f->buf_d);
     net_f = std::max(net_f, f->net_bytes_f);
-    items += f->plan.n_chains;
+    items += f->plan.n_groups + (f->plan.n_chains + 1) / 2;
   }
+  net_region = net_f + (int)round16(sizeof(NetDev<double>));
   for (int i = 0; i < n; ++i) RN_CUDA(cudaStreamSynchronize(fs[i]->stream));
+  const int tw = block / 2;
   for (int i = 0; i < n; ++i) {
     const int m = std::max(fs[i]->nx, fs[i]->nu);
-    int c = std::max((m + block - 1) / block, (fs[i]->nx + 31) / 32);
+    int c = std::max((m + tw - 1) / tw, (fs[i]->nx + 31) / 32);
     c = c <= 1 ? 1 : (c <= 2 ? 2 : (c <= 4 ? 4 : 8));
     maxc = std::max(maxc, c);
   }
-  smem = std::max(smem_bytes<double>(buf_d), smem_bytes<float>(buf_f)) + net_f +
-         round16(sizeof(NetDev<double>));
+  int static_smem = 0, team_bytes = 0;
+  RN_CUDA(batch_static_smem(maxc, &static_smem));
+  if ((rc = team_budget(dev, (int)std::min<long long>(items, 1 << 30), net_region, static_smem,
+                        &team_bytes)))
+    return rc;
+  std::vector<Sizes> szf(n), szd(n);
+  for (int i = 0; i < n; ++i)
+    if ((rc = fit_sizes(fs[i], 4, team_bytes, net_region, block, 2, &szf[i])) ||
+        (rc = fit_sizes(fs[i], 8, team_bytes, net_f, block, 0, &szd[i])))
+      return rc;
+  const size_t smem = kHdrBytes + net_region + 2 * (size_t)team_bytes;
   int bps = 0, sms = 0;
   RN_CUDA(batch_occupancy(maxc, block, smem, &bps));
   RN_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -1603,7 +1726,7 @@ int batch_impl(rn_factor *const *fs, const rn_solve_req *req, int n, int max_ite
   ip.reserve(items);
   ic.reserve(items);
   for (int i = 0; i < n; ++i)
-    for (int k = 0; k < fs[i]->plan.n_chains; ++k) {
+    for (int k = 0; k < fs[i]->plan.n_groups + (fs[i]->plan.n_chains + 1) / 2; ++k) {
       ip.push_back(i);
       ic.push_back(k);
     }
@@ -1618,26 +1741,14 @@ int batch_impl(rn_factor *const *fs, const rn_solve_req *req, int n, int max_ite
       return RN_ERR_UNSUPPORTED;
     }
   }
-  std::vector<MixedParams> probs(n);
-  for (int i = 0; i < n; ++i) {
-    rn_factor *f = fs[i];
-    MixedParams &M = probs[i];
-    M.f = base_params_f(f);
-    M.f.iters = max_iters;
-    M.f.check_every = f->opts.check_every;
-    M.f.tol = tol > 0.0 ? tol : 0.0;
-    M.d = base_params(f);
-    M.d.st.uo32 = const_cast<float *>(f->mx.uref);
-    M.d.st.xo32 = const_cast<float *>(f->mx.xref);
-    M.mx = f->mx;
-  }
   // device workspace (kept per device, grown on demand)
   const size_t o_probs = 0;
   const size_t o_ip = round16(o_probs + n * sizeof(MixedParams));
   const size_t o_ic = round16(o_ip + items * sizeof(int));
   const size_t o_cb = round16(o_ic + items * sizeof(int));
   const size_t o_bar = round16(o_cb + (grid + 1) * sizeof(int));
-  const size_t o_info = round16(o_bar + sizeof(unsigned));
+  const size_t o_err = round16(o_bar + sizeof(unsigned));
+  const size_t o_info = round16(o_err + sizeof(int));
   const size_t total = round16(o_info + 3 * n * sizeof(int));
   std::lock_guard<std::mutex> lock(g_batch_mu);
   BatchWorkspace &ws = g_batch_ws[dev];
@@ -1655,20 +1766,32 @@ int batch_impl(rn_factor *const *fs, const rn_solve_req *req, int n, int max_ite
     ws.cap = total;
   }
   unsigned char *W = ws.dev;
+  int *berr = reinterpret_cast<int *>(W + o_err);
+  std::vector<MixedParams> probs(n);
+  for (int i = 0; i < n; ++i) {
+    MixedParams &M = probs[i];
+    M = mixed_params(fs[i], max_iters, tol);
+    set_sizes(M.f, szf[i]);
+    set_sizes(M.d, szd[i]);
+    M.f.st.err = berr;
+    M.d.st.err = berr;
+  }
   RN_CUDA(cudaMemcpyAsync(W + o_probs, probs.data(), n * sizeof(MixedParams),
                           cudaMemcpyHostToDevice, bs));
   RN_CUDA(cudaMemcpyAsync(W + o_ip, ip.data(), items * sizeof(int), cudaMemcpyHostToDevice, bs));
   RN_CUDA(cudaMemcpyAsync(W + o_ic, ic.data(), items * sizeof(int), cudaMemcpyHostToDevice, bs));
   RN_CUDA(cudaMemcpyAsync(W + o_cb, cb.data(), (grid + 1) * sizeof(int), cudaMemcpyHostToDevice, bs));
   RN_CUDA(cudaMemsetAsync(W + o_bar, 0, sizeof(unsigned), bs));
+  RN_CUDA(cudaMemsetAsync(W + o_err, 0, sizeof(int), bs));
   RN_CUDA(cudaMemsetAsync(W + o_info, 0, 3 * n * sizeof(int), bs));
   BatchDev B{};
   B.n_problems = n;
   B.probs = reinterpret_cast<const MixedParams *>(W + o_probs);
   B.item_prob = reinterpret_cast<const int *>(W + o_ip);
-  B.item_chain = reinterpret_cast<const int *>(W + o_ic);
+  B.item_sub = reinterpret_cast<const int *>(W + o_ic);
   B.cta_begin = reinterpret_cast<const int *>(W + o_cb);
   B.barrier = reinterpret_cast<unsigned *>(W + o_bar);
+  B.err = berr;
   B.prob_info = reinterpret_cast<int *>(W + o_info);
   B.iters = max_iters;
   B.check_every = fs[0]->opts.check_every;
@@ -1678,9 +1801,9 @@ int batch_impl(rn_factor *const *fs, const rn_solve_req *req, int n, int max_ite
       return RN_ERR_INVAL;
     }
   B.refresh_every = fs[0]->opts.refresh_every;
-  B.buf_f = buf_f;
-  B.buf_d = buf_d;
+  B.net_bytes = net_region;
   B.net_bytes_f = net_f;
+  B.team_bytes = team_bytes;
   B.tol = tol > 0.0 ? tol : 0.0;
   RN_CUDA(cudaEventRecord(fs[0]->ev0, bs));
   RN_CUDA(launch_batch(B, maxc, grid, block, smem, bs));
@@ -1692,11 +1815,7 @@ int batch_impl(rn_factor *const *fs, const rn_solve_req *req, int n, int max_ite
   RN_CUDA(cudaEventElapsedTime(&ms, fs[0]->ev0, fs[0]->ev1));
   // errors of any problem (shared wait error words)
   int any_err = 0;
-  for (int i = 0; i < n; ++i) {
-    int e = 0;
-    RN_CUDA(cudaMemcpy(&e, fs[i]->err, sizeof(int), cudaMemcpyDeviceToHost));
-    any_err |= e;
-  }
+  RN_CUDA(cudaMemcpy(&any_err, berr, sizeof(int), cudaMemcpyDeviceToHost));
   if (any_err) {
     set_error("solve_batch: a device-side wait gave up");
     return RN_ERR_TIMEOUT;

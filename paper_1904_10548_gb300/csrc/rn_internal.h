@@ -27,25 +27,44 @@ Csr dense_to_csc(const double *M, int rows, int cols);  // "rows" of the result 
 // from the highest such node (the chain head) down to its leaf.  Every
 // other non-root node is a *top* node (two or more leaves below it).  The
 // dual gradient is a subtree sum going up and a path sum going down
-// (eq. dual-gradient evaluated by the recursion of §4.4), so a chain is
-// processed sequentially by one thread block, and top nodes are reduced
-// by whichever block completes their last child.
+// (eq. dual-gradient evaluated by the recursion of §4.4).  A chain is
+// scanned by one team of threads.  The top nodes below one stage-1 node
+// form a *group* (the stage-1 subtrees are independent given x0): one
+// thread block sums the group level by level from the chain-head sums,
+// applies F, rolls the path sums back down and publishes them; the chain
+// below each top node that comes first in chain order (its *owner*)
+// performs that node's per-node step.
 //
-// Internal node order: 0 = root, then the top nodes in breadth-first
-// order (internal 1..n_top), then the chains one after another, each
-// from head to leaf.  Chains are ordered by their leaf; all leaves are at
-// stage N, so the chains below any node form a contiguous range.
+// Internal node order: 0 = root, then the top nodes group by group, each
+// group in breadth-first order (so its levels are contiguous ranges),
+// then the chains one after another, each from head to leaf.  Chains are
+// ordered by their leaf; all leaves are at stage N, so the chains below
+// any node form a contiguous range.
 struct Plan {
-  int n = 0, N = 0, n_top = 0, n_chains = 0, max_chain_len = 0, max_path_len = 0;
-  int n_flags = 0;
+  int n = 0, N = 0, n_top = 0, n_chains = 0, n_groups = 0, max_chain_len = 0;
+  int max_group = 0, max_group_chains = 0;
   std::vector<int> perm;     // internal -> breadth-first index
   std::vector<int> iperm;    // breadth-first -> internal
   std::vector<int> parent;   // internal parent index (-1 for the root)
   std::vector<double> prob;  // internal order
-  // top nodes, indexed by internal index (entries for non-top nodes unused)
-  std::vector<int> top_nchild, top_child_ptr, top_child, top_flag;
-  // chains
-  std::vector<int> ch_start, ch_len, ch_parent, ch_path_ptr, ch_path, ch_own_from, ch_flag;
+  // groups: top nodes [g_node[g], g_node[g+1]), chains [g_chain[2g],
+  // g_chain[2g+1]), level boundaries lvl[g_lvl[g]] .. lvl[g_lvl[g+1] - 1]
+  std::vector<int> g_node, g_chain, g_lvl, lvl;
+  // per group the top nodes with chain children: ccn[g_ccn[g] .. g_ccn[g+1])
+  std::vector<int> g_ccn, ccn;
+  // per group a compact descriptor in local indices (li = internal - g_node[g],
+  // chain positions relative to g_chain[2g]), at g_desc[g_desc_ptr[g]],
+  // padded to a multiple of 4 ints:
+  //   m, nl, nch, 0 | lvl[nl + 1] | par[m] (-1: the root) |
+  //   tcp[m + 1], tcl[..] (top children) | ccp[m + 1], ccl[..] (chain children)
+  std::vector<int> g_desc_ptr, g_desc;
+  int max_desc = 0;
+  // top nodes (indexed by internal index 0..n_top): top children and
+  // chain children (chain ids)
+  std::vector<int> tc_ptr, tc, cc_ptr, cc;
+  // chains: first node, length, group (-1 below the root), parent, owned
+  // top nodes [ch_own_ptr[k], ch_own_ptr[k+1]) from stage 1 down
+  std::vector<int> ch_start, ch_len, ch_group, ch_parent, ch_own_ptr, ch_own;
 };
 
 // Validates the tree (see rn_tree) and builds the schedule.  Returns

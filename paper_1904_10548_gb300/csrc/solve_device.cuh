@@ -1,7 +1,7 @@
 // Device building blocks of the persistent solve kernels (solve_kernels.cu,
-// mixed_kernels.cu): bounded waits, block/warp reductions, the backward
-// sweep over chains and top nodes, and the forward sweep with the dual
-// update.
+// mixed_kernels.cu, batch_kernels.cu): bounded waits, reductions, teams
+// and shared-memory staging, the backward and forward sweeps over chains
+// and groups of top nodes, and the dual update.
 #pragma once
 
 #include <cuda/atomic>
@@ -113,42 +113,139 @@ __device__ __forceinline__ unsigned long long abs_bits(float f) {
 }
 
 // ---------------------------------------------------------------------------
-// shared memory of the persistent kernel
+// teams, block layout and shared-memory carving
 // ---------------------------------------------------------------------------
+// A team is a warp-aligned set of threads with its own barrier: the block
+// is two teams (one chain each; named barriers 1 and 2) or, for a group,
+// one team of the whole block (barrier 0).
+struct Team {
+  int tid, nt, bar;
+  __device__ __forceinline__ void sync() const {
+    if (bar == 0)
+      __syncthreads();
+    else
+      asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nt) : "memory");
+  }
+  __device__ __forceinline__ int lane() const { return tid & 31; }
+  __device__ __forceinline__ int warp() const { return tid >> 5; }
+  __device__ __forceinline__ int nwarps() const { return nt >> 5; }
+};
+
+__device__ __forceinline__ Team chain_team() {
+  const int tw = blockDim.x >> 1;
+  return Team{(int)threadIdx.x % tw, tw, 1 + (int)threadIdx.x / tw};
+}
+__device__ __forceinline__ Team block_team() { return Team{(int)threadIdx.x, (int)blockDim.x, 0}; }
+__device__ __forceinline__ int team_index() { return (int)threadIdx.x / (int)(blockDim.x >> 1); }
+
+// [header | network copy | team 0 | team 1]
+struct BlockMem {
+  unsigned long long *redu;  // 40 words for block reductions
+  int *bflag;                // 8 block-wide flags
+  unsigned char *net_raw;
+  unsigned char *team_raw[2];
+};
+
+__device__ __forceinline__ BlockMem block_mem(unsigned char *raw, int net_bytes, int team_bytes) {
+  BlockMem b;
+  b.redu = reinterpret_cast<unsigned long long *>(raw);
+  b.bflag = reinterpret_cast<int *>(raw + 40 * sizeof(unsigned long long));
+  b.net_raw = raw + kHdrBytes;
+  b.team_raw[0] = raw + kHdrBytes + net_bytes;
+  b.team_raw[1] = b.team_raw[0] + team_bytes;
+  return b;
+}
+
 template <typename T>
 struct Smem {
-  T *buf;   // backward: kSeg x SP rows (s, then lambda | ghat), then eb, fb, i2p;
-            // forward: the staged rows of one segment (see chain_forward)
-  T *eb;    // kSeg * NEP  E W^-1 ghat
-  T *fb;    // kSeg * NEP  S^-1 E W^-1 ghat
-  T *i2p;   // kSeg
-  T *red;   // 72
-  unsigned long long *redu;  // 40
+  T *buf;                    // work buffer (layouts in kernels.cuh)
+  T *red;                    // 72
   int *flag;                 // 4
-  int *node;                 // 2 x kSeg: node ids and ownership of a forward segment
-  const NetDev<T> *net;      // the network data in use (a shared-memory copy)
-  unsigned char *net_raw;    // where the block's copy lives
+  int *node;                 // 2 x kSeg: node ids of a staged forward segment
+  const NetDev<T> *net;      // the network data in use
 };
 
 template <typename T>
-__device__ Smem<T> carve(unsigned char *raw, const NetDev<T> &nt, int buf_elems) {
+__device__ __forceinline__ Smem<T> carve(unsigned char *raw, int buf_elems, const NetDev<T> *net) {
   Smem<T> s;
-  T *p = reinterpret_cast<T *>(raw);
-  s.buf = p;
-  s.eb = p + (size_t)kSeg * nt.SP;
-  s.fb = s.eb + (size_t)kSeg * nt.NEP;
-  s.i2p = s.fb + (size_t)kSeg * nt.NEP;
-  p += buf_elems;
-  s.red = p;
-  p += 72;
-  size_t off = (reinterpret_cast<unsigned char *>(p) - raw + 15) & ~(size_t)15;
-  s.redu = reinterpret_cast<unsigned long long *>(raw + off);
-  s.flag = reinterpret_cast<int *>(raw + off + 40 * sizeof(unsigned long long));
+  s.buf = reinterpret_cast<T *>(raw);
+  s.red = s.buf + buf_elems;
+  const size_t off = round16(sizeof(T) * ((size_t)buf_elems + 72));
+  s.flag = reinterpret_cast<int *>(raw + off);
   s.node = s.flag + 4;
-  off = round16(off + 40 * sizeof(unsigned long long) + (4 + 2 * kSeg) * sizeof(int));
-  s.net_raw = raw + off;
-  s.net = nullptr;
+  s.net = net;
   return s;
+}
+
+// ---------------------------------------------------------------------------
+// asynchronous staging global -> shared, 16 bytes per copy, all copies of
+// a team in flight at once.  cg = true reads through L2 only (data other
+// blocks wrote during this launch); cg = false may hit L1 (data this team
+// wrote itself, or constants).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp16(void *dst, const void *src, bool cg) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if (cg)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// n contiguous elements (n * sizeof(T) a multiple of 16)
+template <typename T>
+__device__ __forceinline__ void stage_span(T *dst, const T *src, int n, const Team &tm, bool cg) {
+  constexpr int per = 16 / sizeof(T);
+  for (int e = tm.tid; e < n / per; e += tm.nt) cp16(dst + e * per, src + e * per, cg);
+}
+
+// the first len elements of rows nodes[0..m) of src (pitch spitch) into
+// rows of dst (pitch dpitch); len, pitches multiples of 16 bytes
+template <typename T>
+__device__ __forceinline__ void stage_rows(T *dst, int dpitch, const T *src, int spitch, int len,
+                                           const int *nodes, int m, const Team &tm, bool cg) {
+  constexpr int per = 16 / sizeof(T);
+  const int nv = len / per;
+  for (int e = tm.tid; e < m * nv; e += tm.nt) {
+    const int q = e / nv, c = e - q * nv;
+    cp16(dst + (size_t)q * dpitch + c * per, src + (size_t)nodes[q] * spitch + c * per, cg);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// z = F g / (2p) in place for one node by one warp (g: the input part of a
+// row), F g = W^-1 (g - E' S^-1 E W^-1 g); eb, fb: NEP elements of the
+// warp's scratch
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void warp_F(const NetDev<T> &nt, T *g, T i2p, T *eb, T *fb) {
+  const int lane = threadIdx.x & 31, ne = nt.ne, nu = nt.nu;
+  const int *Er_ptr = nt.Er_ptr, *Er_idx = nt.Er_idx, *Ec_ptr = nt.Ec_ptr, *Ec_idx = nt.Ec_idx;
+  const T *Er_val = nt.Er_val, *Ec_val = nt.Ec_val, *winv = nt.winv, *Sinv = nt.Sinv;
+  if (ne > 0) {
+    for (int r = lane; r < ne; r += 32) {
+      T acc = T(0);
+      for (int e = Er_ptr[r]; e < Er_ptr[r + 1]; ++e) {
+        const int j = Er_idx[e];
+        acc += Er_val[e] * (winv[j] * g[j]);
+      }
+      eb[r] = acc;
+    }
+    __syncwarp();
+    for (int r = lane; r < ne; r += 32) {
+      const T *Si = Sinv + (size_t)r * ne;
+      T acc = T(0);
+      for (int c = 0; c < ne; ++c) acc += Si[c] * eb[c];
+      fb[r] = acc;
+    }
+    __syncwarp();
+  }
+  for (int j = lane; j < nu; j += 32) {
+    T acc = g[j];
+    for (int e = Ec_ptr[j]; e < Ec_ptr[j + 1]; ++e) acc -= Ec_val[e] * fb[Ec_idx[e]];
+    g[j] = (winv[j] * acc) * i2p;
+  }
+  __syncwarp();
 }
 
 // Copy the network data into shared memory at raw (net_smem_bytes of
@@ -227,183 +324,7 @@ __device__ const NetDev<T> *stage_net(const NetDev<T> &g, unsigned char *raw, bo
   return s;
 }
 
-// copy rows `nodes[0..m)` of a row-major array (pitch elements, a multiple
-// of 4) into consecutive shared-memory rows, 16 bytes per load, all
-// threads of the block in flight at once; L2-only loads for data other
-// blocks write in the same launch
-template <typename T>
-__device__ __forceinline__ void stage_rows(T *dst, const T *src, int pitch, const int *nodes, int m,
-                                           bool l2) {
-  using V = typename std::conditional<sizeof(T) == 8, double2, float4>::type;
-  constexpr int per = 16 / sizeof(T);
-  const int nv = pitch / per;
-  V *d = reinterpret_cast<V *>(dst);
-  for (int e = threadIdx.x; e < m * nv; e += blockDim.x) {
-    const int q = e / nv, c = e - q * nv;
-    const V *s = reinterpret_cast<const V *>(src + (size_t)nodes[q] * pitch) + c;
-    d[e] = l2 ? __ldcg(s) : *s;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// z = F ghat / (2p) for m rows of sm.buf (ghat at offset NXP of each row)
-// F ghat = W^-1 (ghat - E' S^-1 E W^-1 ghat)
-// ---------------------------------------------------------------------------
-template <typename T>
-__device__ void apply_F(const NetDev<T> &nt, int m, Smem<T> &sm, T *zrows) {
-  const int tid = threadIdx.x, bd = blockDim.x, ne = nt.ne, nu = nt.nu;
-  if (ne > 0) {
-    for (int idx = tid; idx < m * ne; idx += bd) {
-      const int q = idx / ne, r = idx - q * ne;
-      const T *g = sm.buf + q * nt.SP + nt.NXP;
-      T acc = T(0);
-      for (int e = nt.Er_ptr[r]; e < nt.Er_ptr[r + 1]; ++e) {
-        const int j = nt.Er_idx[e];
-        acc += nt.Er_val[e] * (nt.winv[j] * g[j]);
-      }
-      sm.eb[q * nt.NEP + r] = acc;
-    }
-    __syncthreads();
-    for (int idx = tid; idx < m * ne; idx += bd) {
-      const int q = idx / ne, r = idx - q * ne;
-      const T *Si = nt.Sinv + (size_t)r * ne;
-      const T *e = sm.eb + q * nt.NEP;
-      T acc = T(0);
-      for (int c = 0; c < ne; ++c) acc += Si[c] * e[c];
-      sm.fb[q * nt.NEP + r] = acc;
-    }
-    __syncthreads();
-  }
-  for (int idx = tid; idx < m * nu; idx += bd) {
-    const int q = idx / nu, j = idx - q * nu;
-    T acc = sm.buf[q * nt.SP + nt.NXP + j];
-    for (int e = nt.Ec_ptr[j]; e < nt.Ec_ptr[j + 1]; ++e)
-      acc -= nt.Ec_val[e] * sm.fb[q * nt.NEP + nt.Ec_idx[e]];
-    zrows[(size_t)q * nt.NUP + j] = (nt.winv[j] * acc) * sm.i2p[q];
-  }
-}
-
-// ---------------------------------------------------------------------------
-// backward sweep over one chain: suffix sums from the leaf to the head
-// ---------------------------------------------------------------------------
-template <typename T, int C>
-__device__ void chain_backward(const KParams<T> &P, int k, Smem<T> &sm) {
-  const NetDev<T> &nt = *sm.net;
-  const int tid = threadIdx.x, bd = blockDim.x;
-  const int start = P.plan.ch_start[k], L = P.plan.ch_len[k];
-  T accL[C], accG[C];
-#pragma unroll
-  for (int c = 0; c < C; ++c) accL[c] = accG[c] = T(0);
-  for (int hi = L; hi > 0; hi -= kSeg) {
-    const int lo = hi > kSeg ? hi - kSeg : 0, m = hi - lo;
-    {
-      using V = typename std::conditional<sizeof(T) == 8, double2, float4>::type;
-      constexpr int per = 16 / sizeof(T);
-      const V *src = reinterpret_cast<const V *>(P.st.s + (size_t)(start + lo) * nt.SP);
-      V *dst = reinterpret_cast<V *>(sm.buf);
-      for (int e = tid; e < m * nt.SP / per; e += bd) dst[e] = src[e];
-    }
-    if (tid < m) sm.i2p[tid] = P.st.inv2p[start + lo + tid];
-    __syncthreads();
-    // lambda: suffix sums of w1 + w2 (thread owns components tid + c bd)
-    for (int q = m - 1; q >= 0; --q) {
-      T *row = sm.buf + q * nt.SP;
-#pragma unroll
-      for (int c = 0; c < C; ++c) {
-        const int i = tid + c * bd;
-        if (i < nt.nx) {
-          accL[c] += row[i];
-          row[i] = accL[c];
-        }
-      }
-    }
-    __syncthreads();
-    // ghat: suffix sums of w3 + B' lambda
-    for (int q = m - 1; q >= 0; --q) {
-      T *row = sm.buf + q * nt.SP;
-#pragma unroll
-      for (int c = 0; c < C; ++c) {
-        const int j = tid + c * bd;
-        if (j < nt.nu) {
-          T t = row[nt.NXP + j];
-          for (int e = nt.Bc_ptr[j]; e < nt.Bc_ptr[j + 1]; ++e) t += nt.Bc_val[e] * row[nt.Bc_idx[e]];
-          accG[c] += t;
-          row[nt.NXP + j] = accG[c];
-        }
-      }
-    }
-    __syncthreads();
-    apply_F(nt, m, sm, P.st.z + (size_t)(start + lo) * nt.NUP);
-    if (lo == 0) {
-      T *dst = P.st.up + (size_t)start * nt.SP;
-      for (int e = tid; e < nt.SP; e += bd) dst[e] = sm.buf[e];
-    }
-    __syncthreads();
-  }
-}
-
-// backward step at a top node: own terms plus the children's subtree sums
-template <typename T>
-__device__ void top_backward(const KParams<T> &P, int v, Smem<T> &sm) {
-  const NetDev<T> &nt = *sm.net;
-  const int tid = threadIdx.x, bd = blockDim.x;
-  const int c0 = P.plan.top_child_ptr[v], c1 = P.plan.top_child_ptr[v + 1];
-  const T *sv = P.st.s + (size_t)v * nt.SP;
-  for (int i = tid; i < nt.nx; i += bd) {
-    T acc = ld_l2(sv + i);
-    for (int c = c0; c < c1; ++c) acc += ld_l2(P.st.up + (size_t)P.plan.top_child[c] * nt.SP + i);
-    sm.buf[i] = acc;
-  }
-  if (tid == 0) sm.i2p[0] = P.st.inv2p[v];
-  __syncthreads();
-  for (int j = tid; j < nt.nu; j += bd) {
-    T acc = ld_l2(sv + nt.NXP + j);
-    for (int e = nt.Bc_ptr[j]; e < nt.Bc_ptr[j + 1]; ++e) acc += nt.Bc_val[e] * sm.buf[nt.Bc_idx[e]];
-    for (int c = c0; c < c1; ++c)
-      acc += ld_l2(P.st.up + (size_t)P.plan.top_child[c] * nt.SP + nt.NXP + j);
-    sm.buf[nt.NXP + j] = acc;
-  }
-  __syncthreads();
-  apply_F(nt, 1, sm, P.st.z + (size_t)v * nt.NUP);
-  T *dst = P.st.up + (size_t)v * nt.SP;
-  for (int e = tid; e < nt.SP; e += bd) {
-    const bool pad = (e >= nt.nx && e < nt.NXP) || e >= nt.NXP + nt.nu;
-    dst[e] = pad ? T(0) : sm.buf[e];
-  }
-  __syncthreads();
-}
-
-// After a chain's backward sweep: arrive at the parent; the last child to
-// arrive completes the parent and climbs on.  Completing a stage-1 node
-// releases its flag for the forward sweep.  Returns false on timeout.
-template <typename T>
-__device__ void climb(const KParams<T> &P, int k, unsigned step, Smem<T> &sm) {
-  int v = P.plan.ch_parent[k];
-  while (v > 0) {
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const unsigned old = atomicAdd(P.st.count + v, 1u);
-      sm.flag[0] = ((old + 1u) % (unsigned)P.plan.top_nchild[v]) == 0u;
-    }
-    __syncthreads();
-    if (!sm.flag[0]) break;
-    __threadfence();
-    top_backward(P, v, sm);
-    __threadfence();
-    __syncthreads();
-    const int f = P.plan.top_flag[v];
-    if (f >= 0) {
-      if (threadIdx.x == 0) st_release(P.st.flags + f, step + 1u);
-      break;
-    }
-    v = P.plan.parent[v];
-  }
-}
-
-// ---------------------------------------------------------------------------
-// forward sweep
-// ---------------------------------------------------------------------------
+// state of the forward sweep of one iteration
 template <typename T>
 struct FwdCtx {
   const T *ycur;
@@ -557,140 +478,475 @@ __device__ void prox_node_warp_mixed(const KParams<float> &P, const NetDev<float
   }
 }
 
-// Forward sweep along the path of chain k: its top ancestors (stage 1
-// down; recomputed here, their per-node step done only by the owner) and
-// then the chain itself, in segments of SEGF nodes.  Each segment first
-// stages the rows it reads (z, the data terms, the dual rows of the owned
-// nodes) into shared memory in one round of 16-byte loads, then
-//   A (thread j): Zp += z_nu, u_nu = ub_nu - Zp          (path sum of z)
-//   B (thread i): x_nu = x_a + Gd d_nu + B u_nu           (path sum of B u + Gd d)
-//   C (warp per owned node): MODE 0 writes the outputs of a plain step,
-//     MODE 1 the dual update, MODE 2 the dual update in delta form.
-// Shared layout of a segment (elements): Zs, Us [SEGF][NUP]; Xs [SEGF][NXP];
-// Bs [SEGF][NUP], Gs [SEGF][NXP] (ub, gb; in MODE 2 uref, xref of owned
-// nodes); Yc, Yp [, Yh] [SEGF][YP] of owned nodes (MODE 1, 2).
+// ---------------------------------------------------------------------------
+// chain backward, critical part: the subtree sums at the chain head,
+//   lambda_h = sum_q (w1 + w2)_q,  ghat_h = sum_q w3_q + B' sum_q lambda_q,
+// published in up[k] (then one arrival at the group's counter).  The rows
+// of the segment nearest the head stay in shared memory with lambda_q in
+// place of (w1 + w2)_q for chain_rest.  Thread t owns components t + c nt.
+// ---------------------------------------------------------------------------
+template <typename T, int C>
+__device__ void chain_head(const KParams<T> &P, int k, const Smem<T> &sm, const Team &tm) {
+  const NetDev<T> &nt = *sm.net;
+  const int SP = nt.SP, NXP = nt.NXP, nx = nt.nx, nu = nt.nu;
+  const int start = P.plan.ch_start[k], L = P.plan.ch_len[k], segb = P.segb;
+  const int g = P.plan.ch_group[k];
+  T *rows = sm.buf;
+  T lam[C], Lam[C], g3[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) lam[c] = Lam[c] = g3[c] = T(0);
+  for (int hi = L; hi > 0; hi -= segb) {
+    const int lo = hi > segb ? hi - segb : 0, m = hi - lo;
+    if (hi < L) tm.sync();
+    stage_span(rows, P.st.s + (size_t)(start + lo) * SP, m * SP, tm, false);
+    cp_wait();
+    tm.sync();
+    for (int q = m - 1; q >= 0; --q) {
+      T *row = rows + q * SP;
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const int i = tm.tid + c * tm.nt;
+        if (i < nx) {
+          lam[c] += row[i];
+          row[i] = lam[c];
+          Lam[c] += lam[c];
+        }
+        if (i < nu) g3[c] += row[NXP + i];
+      }
+    }
+  }
+  if (g < 0) return;  // below the root: nobody reads the head sums
+  T *vec = rows + chain_vec_off(segb, SP, nt.NEP, tm.nwarps());
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    const int i = tm.tid + c * tm.nt;
+    if (i < nx) vec[i] = Lam[c];
+  }
+  tm.sync();
+  const int *Bc_ptr = nt.Bc_ptr, *Bc_idx = nt.Bc_idx;
+  const T *Bc_val = nt.Bc_val;
+  T *out = P.st.up + (size_t)k * SP;
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    const int i = tm.tid + c * tm.nt;
+    if (i < nx) out[i] = lam[c];
+    if (i < nu) {
+      T t = g3[c];
+      for (int e = Bc_ptr[i]; e < Bc_ptr[i + 1]; ++e) t += Bc_val[e] * vec[Bc_idx[e]];
+      out[NXP + i] = t;
+    }
+  }
+  tm.sync();
+  if (tm.tid == 0) {
+    __threadfence();
+    atomicAdd(P.st.count + g, 1u);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// chain backward and forward, local part (no dependence on the top nodes):
+// per node ghat_q = sum_{r >= q} (w3_r + B' lambda_r), z_q = F ghat_q/(2p),
+// then from the head down U_q = ub_q - sum_{r <= q} z_r and
+// X_q = sum_{r <= q} (B U_r + Gd d_r), written to ux (X | U).  With the
+// path sum Z_p and state x_p at the chain's parent the forward sweep is
+// then u_q = U_q - Z_p, x_q = x_p + X_q - (q + 1) B Z_p.  Per-node
+// products run one warp per node, the sums along the chain one thread per
+// component.  keep: the rows chain_head left in shared memory are this
+// chain's (one segment).
+// ---------------------------------------------------------------------------
+template <typename T, int C>
+__device__ void chain_rest(const KParams<T> &P, int k, const Smem<T> &sm, const Team &tm, bool keep) {
+  const NetDev<T> &nt = *sm.net;
+  const int SP = nt.SP, NXP = nt.NXP, NUP = nt.NUP, nx = nt.nx, nu = nt.nu, NEP = nt.NEP;
+  const int *Bc_ptr = nt.Bc_ptr, *Bc_idx = nt.Bc_idx, *Br_ptr = nt.Br_ptr, *Br_idx = nt.Br_idx;
+  const T *Bc_val = nt.Bc_val, *Br_val = nt.Br_val;
+  const int start = P.plan.ch_start[k], L = P.plan.ch_len[k], segb = P.segb;
+  const bool multi = L > segb, data = !P.linear;
+  const int lane = tm.lane(), warp = tm.warp(), nw = tm.nwarps();
+  T *rows = sm.buf;
+  T *eb = rows + round4(segb * SP) + 2 * warp * NEP, *fb = eb + NEP;
+  T accL[C], accG[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) accL[c] = accG[c] = T(0);
+  // leaf -> head: ghat and z per node
+  for (int hi = L; hi > 0; hi -= segb) {
+    const int lo = hi > segb ? hi - segb : 0, m = hi - lo;
+    tm.sync();
+    if (multi || !keep) {
+      stage_span(rows, P.st.s + (size_t)(start + lo) * SP, m * SP, tm, false);
+      cp_wait();
+      tm.sync();
+      for (int q = m - 1; q >= 0; --q) {
+        T *row = rows + q * SP;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          const int i = tm.tid + c * tm.nt;
+          if (i < nx) {
+            accL[c] += row[i];
+            row[i] = accL[c];
+          }
+        }
+      }
+      tm.sync();
+    }
+    for (int q = warp; q < m; q += nw) {  // w3 + B' lambda per node
+      T *row = rows + q * SP;
+      for (int j = lane; j < nu; j += 32) {
+        T t = row[NXP + j];
+        for (int e = Bc_ptr[j]; e < Bc_ptr[j + 1]; ++e) t += Bc_val[e] * row[Bc_idx[e]];
+        row[NXP + j] = t;
+      }
+    }
+    tm.sync();
+    for (int q = m - 1; q >= 0; --q) {  // suffix sums along the chain
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const int j = tm.tid + c * tm.nt;
+        if (j < nu) {
+          accG[c] += rows[q * SP + NXP + j];
+          rows[q * SP + NXP + j] = accG[c];
+        }
+      }
+    }
+    tm.sync();
+    for (int q = warp; q < m; q += nw)
+      warp_F(nt, rows + q * SP + NXP, P.st.inv2p[start + lo + q], eb, fb);
+    tm.sync();
+    if (lo > 0) {
+      T *z = P.st.z + (size_t)(start + lo) * NUP;
+      for (int e = tm.tid; e < m * nu; e += tm.nt) {
+        const int q = e / nu, j = e - q * nu;
+        z[(size_t)q * NUP + j] = rows[q * SP + NXP + j];
+      }
+    }
+  }
+  // head -> leaf: local path sums (the head segment is still in place)
+  T accZ[C], accX[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) accZ[c] = accX[c] = T(0);
+  for (int lo = 0; lo < L; lo += segb) {
+    const int m = L - lo < segb ? L - lo : segb;
+    if (lo > 0) {
+      tm.sync();
+      const T *z = P.st.z + (size_t)(start + lo) * NUP;
+      constexpr int per = 16 / sizeof(T);
+      const int nv = NUP / per;
+      for (int e = tm.tid; e < m * nv; e += tm.nt) {
+        const int q = e / nv, c = e - q * nv;
+        cp16(rows + q * SP + NXP + c * per, z + (size_t)q * NUP + c * per, false);
+      }
+      cp_wait();
+      tm.sync();
+    }
+    for (int q = 0; q < m; ++q) {  // U = ub - path sums of z
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const int j = tm.tid + c * tm.nt;
+        if (j < nu) {
+          accZ[c] += rows[q * SP + NXP + j];
+          const T base = data ? P.st.ub[(size_t)(start + lo + q) * NUP + j] : T(0);
+          rows[q * SP + NXP + j] = base - accZ[c];
+        }
+      }
+    }
+    tm.sync();
+    for (int q = warp; q < m; q += nw) {  // B U + Gd d per node
+      T *row = rows + q * SP;
+      for (int i = lane; i < nx; i += 32) {
+        T acc = data ? P.st.gb[(size_t)(start + lo + q) * NXP + i] : T(0);
+        for (int e = Br_ptr[i]; e < Br_ptr[i + 1]; ++e) acc += Br_val[e] * row[NXP + Br_idx[e]];
+        row[i] = acc;
+      }
+    }
+    tm.sync();
+    for (int q = 0; q < m; ++q) {  // prefix sums along the chain
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const int i = tm.tid + c * tm.nt;
+        if (i < nx) {
+          accX[c] += rows[q * SP + i];
+          rows[q * SP + i] = accX[c];
+        }
+      }
+    }
+    tm.sync();
+    {
+      using V = typename std::conditional<sizeof(T) == 8, double2, float4>::type;
+      constexpr int per = 16 / sizeof(T);
+      const V *src = reinterpret_cast<const V *>(rows);
+      V *dst = reinterpret_cast<V *>(P.st.ux + (size_t)(start + lo) * SP);
+      for (int e = tm.tid; e < m * SP / per; e += tm.nt) dst[e] = src[e];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One group (the top nodes below one stage-1 node), whole block: wait for
+// the group's chains, sum the subtree level by level from the deepest,
+// apply F to every node, roll the path sums Z and states x back down and
+// publish (x | Z) in ux, then release the group's flag.  One warp per node;
+// the group's descriptor (levels, parents, children in local indices) is
+// staged with its rows.  Rows beyond the shared-memory capacity live in
+// up[K + v].  False on timeout.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ bool group_step(const KParams<T> &P, int g, const Smem<T> &sm, const Team &tm,
+                           unsigned step) {
+  const NetDev<T> &nt = *sm.net;
+  const PlanDev &pl = P.plan;
+  const int SP = nt.SP, NXP = nt.NXP, NUP = nt.NUP, nx = nt.nx, nu = nt.nu, NEP = nt.NEP;
+  const int *Bc_ptr = nt.Bc_ptr, *Bc_idx = nt.Bc_idx, *Br_ptr = nt.Br_ptr, *Br_idx = nt.Br_idx;
+  const T *Bc_val = nt.Bc_val, *Br_val = nt.Br_val;
+  const int g0 = pl.g_node[g], c0 = pl.g_chain[2 * g], c1 = pl.g_chain[2 * g + 1];
+  const int m = pl.g_node[g + 1] - g0;
+  const int d0 = pl.g_desc_ptr[g], dn = pl.g_desc_ptr[g + 1] - d0;
+  const bool data = !P.linear;
+  const int gcap = P.gcap, hchunk = P.hchunk;
+  const int lane = tm.lane(), warp = tm.warp(), nw = tm.nwarps();
+  T *R = sm.buf;
+  T *H = R + (size_t)gcap * SP;
+  T *eb = H + (size_t)hchunk * SP + 2 * warp * NEP, *fb = eb + NEP;
+  int *desc = reinterpret_cast<int *>(H + (size_t)hchunk * SP + round4(2 * nw * NEP));
+  T *spill = P.st.up + (size_t)(pl.n_chains + g0) * SP;
+  auto row = [&](int li) -> T * { return li < gcap ? R + (size_t)li * SP : spill + (size_t)li * SP; };
+  // all chains of the group have arrived; the counter restarts for the
+  // next evaluation (no chain arrives again before the flag below)
+  if (tm.tid == 0) {
+    sm.flag[0] = spin_geq(P.st.count + g, (unsigned)(c1 - c0), P.st.err);
+    if (sm.flag[0]) atomicExch(P.st.count + g, 0u);
+  }
+  tm.sync();
+  if (!sm.flag[0]) return false;
+  // own terms (w1 + w2 | w3) of the group's nodes, the descriptor, heads
+  const int mr = m < gcap ? m : gcap;
+  stage_span(R, P.st.s + (size_t)g0 * SP, mr * SP, tm, true);
+  for (int e = tm.tid; e < dn / 4; e += tm.nt) cp16(desc + 4 * e, pl.g_desc + d0 + 4 * e, false);
+  for (int e = tm.tid; e < (m - mr) * SP; e += tm.nt)
+    spill[(size_t)mr * SP + e] = __ldcg(P.st.s + (size_t)(g0 + mr) * SP + e);
+  const int nch = c1 - c0;
+  for (int h0 = 0; h0 < nch; h0 += hchunk) {
+    const int h1 = nch - h0 < hchunk ? nch : h0 + hchunk;
+    if (h0 > 0) tm.sync();
+    stage_span(H, P.st.up + (size_t)(c0 + h0) * SP, (h1 - h0) * SP, tm, true);
+    cp_wait();
+    tm.sync();
+    const int nl = desc[1];
+    const int *ccp = desc + 4 + (nl + 1) + m + (m + 1) + desc[4 + (nl + 1) + m + m];
+    const int *ccl = ccp + m + 1;
+    for (int li = warp; li < m; li += nw) {  // heads into their parents
+      const int cs = ccp[li], ce = ccp[li + 1];
+      if (cs == ce) continue;
+      T *r = row(li);
+      for (int col = lane; col < SP; col += 32) {
+        if ((col >= nx && col < NXP) || col >= NXP + nu) continue;
+        T acc = T(0);
+        bool any = false;
+        for (int c = cs; c < ce; ++c) {
+          const int kk = ccl[c];
+          if (kk >= h0 && kk < h1) {
+            acc += H[(size_t)(kk - h0) * SP + col];
+            any = true;
+          }
+        }
+        if (any) r[col] += acc;
+      }
+    }
+  }
+  cp_wait();
+  tm.sync();
+  const int nl = desc[1];
+  const int *lvl = desc + 4, *par = lvl + nl + 1, *tcp = par + m, *tcl = tcp + m + 1;
+  // backward over the levels, deepest first
+  for (int l = nl - 1; l >= 0; --l) {
+    for (int li = lvl[l] + warp; li < lvl[l + 1]; li += nw) {
+      T *r = row(li);
+      const int ts = tcp[li], te = tcp[li + 1];
+      for (int i = lane; i < nx; i += 32) {
+        T acc = r[i];
+        for (int c = ts; c < te; ++c) acc += row(tcl[c])[i];
+        r[i] = acc;
+      }
+      __syncwarp();
+      for (int j = lane; j < nu; j += 32) {
+        T acc = r[NXP + j];
+        for (int e = Bc_ptr[j]; e < Bc_ptr[j + 1]; ++e) acc += Bc_val[e] * r[Bc_idx[e]];
+        for (int c = ts; c < te; ++c) acc += row(tcl[c])[NXP + j];
+        r[NXP + j] = acc;
+      }
+    }
+    tm.sync();
+  }
+  // z = F ghat / (2p) at every node of the group
+  for (int li = warp; li < m; li += nw) warp_F(nt, row(li) + NXP, P.st.inv2p[g0 + li], eb, fb);
+  tm.sync();
+  // forward over the levels: Z_v = Z_a(v) + z_v, x_v = x_a(v) + B u_v + Gd d_v
+  for (int l = 0; l < nl; ++l) {
+    for (int li = lvl[l] + warp; li < lvl[l + 1]; li += nw) {
+      T *r = row(li);
+      const int pa = par[li];
+      if (pa >= 0) {
+        const T *rp = row(pa);
+        for (int j = lane; j < nu; j += 32) r[NXP + j] += rp[NXP + j];
+      }
+      __syncwarp();
+      const int v = g0 + li;
+      for (int i = lane; i < nx; i += 32) {
+        T acc = pa >= 0 ? row(pa)[i] : (data ? P.st.xroot[i] : T(0));
+        if (data) acc += P.st.gb[(size_t)v * NXP + i];
+        for (int e = Br_ptr[i]; e < Br_ptr[i + 1]; ++e) {
+          const int j = Br_idx[e];
+          const T u = (data ? P.st.ub[(size_t)v * NUP + j] : T(0)) - r[NXP + j];
+          acc += Br_val[e] * u;
+        }
+        r[i] = acc;
+      }
+    }
+    tm.sync();
+  }
+  // publish (x | Z)
+  {
+    using V = typename std::conditional<sizeof(T) == 8, double2, float4>::type;
+    constexpr int per = 16 / sizeof(T);
+    const int nv = SP / per;
+    V *dst = reinterpret_cast<V *>(P.st.ux + (size_t)g0 * SP);
+    for (int e = tm.tid; e < m * nv; e += tm.nt) {
+      const int li = e / nv, c = e - li * nv;
+      dst[e] = reinterpret_cast<const V *>(row(li))[c];
+    }
+  }
+  tm.sync();
+  if (tm.tid == 0) {
+    __threadfence();
+    st_release(P.st.flags + g, step + 1u);
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// forward sweep of chain k after its group: the top nodes it owns, then its
+// own nodes.  Warp w takes nodes w, w + nw, ...; it stages a node's rows
+// into one of its P.fslots slots (the next node's copies in flight while
+// it works on the current one), forms (x | u) in place from the published
+// (x | Z) of a top node (u = ub - Z) or from the chain's local sums, then
+//   MODE 0 writes the outputs of a plain step,
+//   MODE 1 the dual update, MODE 2 the dual update in delta form.
+// Slot layout (elements): row [SP]; Yc, Yp [YP] (MODE 1); Yc, Yp, Yh [YP],
+// Ur [NUP], Xr [NXP] (MODE 2).  False on timeout.
+// ---------------------------------------------------------------------------
 constexpr int kFwdPlain = 0, kFwdApg = 1, kFwdMixed = 2;
 
-template <typename T>
-struct SegF {
-  static constexpr int value = sizeof(T) == 8 ? 4 : 8;
-};
-
-__host__ __device__ inline int fwd_elems_per_node(int NXP, int NUP, int YP, int mode) {
-  return 3 * NUP + 2 * NXP + (mode == 1 ? 2 * YP : (mode == 2 ? 3 * YP : 0));
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait_group() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 template <typename T, int MODE, int C>
-__device__ void chain_forward(const KParams<T> &P, int k, FwdCtx<T> &c, Smem<T> &sm,
-                              const MixedDev *mx) {
-  constexpr int SEGF = SegF<T>::value;
+__device__ bool chain_forward(const KParams<T> &P, int k, FwdCtx<T> &c, const Smem<T> &sm,
+                              const Team &tm, const MixedDev *mx, unsigned step) {
   const NetDev<T> &nt = *sm.net;
-  const int tid = threadIdx.x, warp = tid >> 5, nw = blockDim.x >> 5;
-  const int p0 = P.plan.ch_path_ptr[k], m = P.plan.ch_path_ptr[k + 1] - p0;
-  const int own_from = P.plan.ch_own_from[k];
-  const int start = P.plan.ch_start[k], K = m + P.plan.ch_len[k];
-  const int *path = P.plan.ch_path + p0;
-  T *Zs = sm.buf;
-  T *Us = Zs + SEGF * nt.NUP;
-  T *Xs = Us + SEGF * nt.NUP;
-  T *Bs = Xs + SEGF * nt.NXP;
-  T *Gs = Bs + SEGF * nt.NUP;
-  T *Yc = Gs + SEGF * nt.NXP;
-  T *Yp = Yc + SEGF * nt.YP;
-  T *Yh = Yp + SEGF * nt.YP;
-  int *nodes = sm.node, *owned = sm.node + kSeg;
-  const bool data = (MODE == kFwdMixed) || !P.linear;
-  T Zp[C], xa[C];
-#pragma unroll
-  for (int c = 0; c < C; ++c) {
-    const int i = tid + c * blockDim.x;
-    Zp[c] = T(0);
-    xa[c] = (i < nt.nx && !P.linear) ? P.st.xroot[i] : T(0);
+  const PlanDev &pl = P.plan;
+  const int SP = nt.SP, NXP = nt.NXP, NUP = nt.NUP, YP = nt.YP, nx = nt.nx, nu = nt.nu;
+  const int start = pl.ch_start[k], L = pl.ch_len[k], g = pl.ch_group[k], par = pl.ch_parent[k];
+  const int own0 = pl.ch_own_ptr[k], nown = pl.ch_own_ptr[k + 1] - own0;
+  const bool data = !P.linear;
+  const int lane = tm.lane(), warp = tm.warp(), nw = tm.nwarps(), S = P.fslots;
+  T *xp = sm.buf, *Zp = xp + NXP, *BZ = Zp + NUP;
+  const int fpn = fwd_elems_per_node(NXP, NUP, YP, SP, MODE);
+  T *slot0 = sm.buf + round4(2 * NXP + NUP) + (size_t)warp * S * fpn;
+  T *slot1 = slot0 + (size_t)(S - 1) * fpn;
+  if (g >= 0) {
+    if (tm.tid == 0) sm.flag[1] = spin_geq(P.st.flags + g, step + 1u, P.st.err);
+    tm.sync();
+    if (!sm.flag[1]) return false;
+    const T *src = P.st.ux + (size_t)par * SP;
+    for (int e = tm.tid; e < NXP + NUP; e += tm.nt) xp[e] = __ldcg(src + e);
+  } else {
+    for (int e = tm.tid; e < NXP + NUP; e += tm.nt)
+      xp[e] = (e < nx && data) ? P.st.xroot[e] : T(0);
   }
-  for (int q0 = 0; q0 < K; q0 += SEGF) {
-    const int ms = K - q0 < SEGF ? K - q0 : SEGF;
-    if (tid == 0) {
-      int mo = 0;
-      for (int q = 0; q < ms; ++q) {
-        const int gq = q0 + q;
-        nodes[q] = gq < m ? path[gq] : start + (gq - m);
-        if (gq >= m || gq >= own_from) owned[mo++] = q;
-      }
-      sm.flag[3] = mo;
-      for (int q = 0; q < mo; ++q) nodes[SEGF + q] = nodes[owned[q]];
+  tm.sync();
+  {
+    const int *Br_ptr = nt.Br_ptr, *Br_idx = nt.Br_idx;
+    const T *Br_val = nt.Br_val;
+    for (int i = tm.tid; i < nx; i += tm.nt) {
+      T acc = T(0);
+      for (int e = Br_ptr[i]; e < Br_ptr[i + 1]; ++e) acc += Br_val[e] * Zp[Br_idx[e]];
+      BZ[i] = acc;
     }
-    __syncthreads();
-    const int mo = sm.flag[3];
-    stage_rows(Zs, P.st.z, nt.NUP, nodes, ms, true);
-    if constexpr (MODE == kFwdMixed) {
-      stage_rows(Bs, mx->uref, nt.NUP, nodes + SEGF, mo, false);
-      stage_rows(Gs, mx->xref, nt.NXP, nodes + SEGF, mo, false);
-      stage_rows(Yc, c.ycur, nt.YP, nodes + SEGF, mo, false);
-      stage_rows(Yp, c.yprv, nt.YP, nodes + SEGF, mo, false);
-      stage_rows(Yh, (const T *)mx->ybh, nt.YP, nodes + SEGF, mo, false);
-    } else {
-      if (data) {
-        stage_rows(Bs, P.st.ub, nt.NUP, nodes, ms, false);
-        stage_rows(Gs, P.st.gb, nt.NXP, nodes, ms, false);
-      }
-      if constexpr (MODE == kFwdApg) {
-        stage_rows(Yc, c.ycur, nt.YP, nodes + SEGF, mo, false);
-        stage_rows(Yp, c.yprv, nt.YP, nodes + SEGF, mo, false);
-      }
+  }
+  tm.sync();
+  const int K = nown + L;
+  constexpr int per = 16 / sizeof(T);
+  auto node_of = [&](int q) { return q < nown ? pl.ch_own[own0 + q] : start + (q - nown); };
+  auto copy_row = [&](T *dst, const T *src, int len, bool cg) {
+    for (int e = lane; e < len / per; e += 32) cp16(dst + e * per, src + e * per, cg);
+  };
+  auto issue = [&](int q, T *dst) {
+    const int v = node_of(q);
+    copy_row(dst, P.st.ux + (size_t)v * SP, SP, q < nown);
+    if constexpr (MODE == kFwdApg) {
+      copy_row(dst + SP, c.ycur + (size_t)v * YP, YP, false);
+      copy_row(dst + SP + YP, c.yprv + (size_t)v * YP, YP, false);
+    } else if constexpr (MODE == kFwdMixed) {
+      copy_row(dst + SP, c.ycur + (size_t)v * YP, YP, false);
+      copy_row(dst + SP + YP, c.yprv + (size_t)v * YP, YP, false);
+      copy_row(dst + SP + 2 * YP, mx->ybh + (size_t)v * YP, YP, false);
+      copy_row(dst + SP + 3 * YP, mx->uref + (size_t)v * NUP, NUP, false);
+      copy_row(dst + SP + 3 * YP + NUP, mx->xref + (size_t)v * NXP, NXP, false);
     }
-    __syncthreads();
-    for (int q = 0; q < ms; ++q) {
-#pragma unroll
-      for (int c = 0; c < C; ++c) {
-        const int j = tid + c * blockDim.x;
-        if (j < nt.nu) {
-          Zp[c] += Zs[q * nt.NUP + j];
-          const T base = (data && MODE != kFwdMixed) ? Bs[q * nt.NUP + j] : T(0);
-          Us[q * nt.NUP + j] = base - Zp[c];
-        }
-      }
-    }
-    __syncthreads();
-    for (int q = 0; q < ms; ++q) {
-#pragma unroll
-      for (int c = 0; c < C; ++c) {
-        const int i = tid + c * blockDim.x;
-        if (i < nt.nx) {
-          T acc = (data && MODE != kFwdMixed) ? Gs[q * nt.NXP + i] : T(0);
-          for (int e = nt.Br_ptr[i]; e < nt.Br_ptr[i + 1]; ++e)
-            acc += nt.Br_val[e] * Us[q * nt.NUP + nt.Br_idx[e]];
-          xa[c] += acc;
-          Xs[q * nt.NXP + i] = xa[c];
-        }
-      }
-    }
-    __syncthreads();
-    for (int o = warp; o < mo; o += nw) {
-      const int q = owned[o];
-      const int v = nodes[q];
-      if constexpr (MODE == kFwdApg) {
-        prox_node_warp<T, C>(P, nt, v, Us + q * nt.NUP, Xs + q * nt.NXP, Yc + o * nt.YP,
-                                Yp + o * nt.YP, c);
-      } else if constexpr (MODE == kFwdMixed) {
-        prox_node_warp_mixed<C>(P, nt, *mx, v, Us + q * nt.NUP, Xs + q * nt.NXP, Yc + o * nt.YP,
-                                   Yp + o * nt.YP, Yh + o * nt.YP, Bs + o * nt.NUP,
-                                   Gs + o * nt.NXP, c);
+    cp_commit();
+  };
+  if (warp < K) issue(warp, slot0);
+  int t = 0;
+  for (int q = warp; q < K; q += nw, ++t) {
+    T *r = (t & 1) ? slot1 : slot0;
+    const int qn = q + nw;
+    if (S == 2) {
+      if (qn < K) {
+        issue(qn, (t & 1) ? slot0 : slot1);
+        cp_wait_group<1>();
       } else {
-        const int lane = tid & 31;
-        for (int j = lane; j < nt.nu; j += 32) {
-          const T val = Us[q * nt.NUP + j];
-          P.st.uo[(size_t)v * nt.NUP + j] = val;
-          if (P.st.uo32) P.st.uo32[(size_t)v * nt.NUP + j] = (float)val;
-        }
-        for (int i = lane; i < nt.nx; i += 32) {
-          const T val = Xs[q * nt.NXP + i];
-          P.st.xo[(size_t)v * nt.NXP + i] = val;
-          if (P.st.xo32) P.st.xo32[(size_t)v * nt.NXP + i] = (float)val;
-        }
+        cp_wait_group<0>();
+      }
+    } else {
+      if (t > 0) issue(q, slot0);
+      cp_wait_group<0>();
+    }
+    __syncwarp();
+    const int v = node_of(q);
+    if (q < nown) {
+      for (int j = lane; j < nu; j += 32) {
+        const T base = data ? P.st.ub[(size_t)v * NUP + j] : T(0);
+        r[NXP + j] = base - r[NXP + j];
+      }
+    } else {
+      const T depth = (T)(q - nown + 1);
+      for (int i = lane; i < nx; i += 32) r[i] = (xp[i] + r[i]) - depth * BZ[i];
+      for (int j = lane; j < nu; j += 32) r[NXP + j] -= Zp[j];
+    }
+    __syncwarp();
+    if constexpr (MODE == kFwdApg) {
+      prox_node_warp<T, C>(P, nt, v, r + NXP, r, r + SP, r + SP + YP, c);
+    } else if constexpr (MODE == kFwdMixed) {
+      prox_node_warp_mixed<C>(P, nt, *mx, v, r + NXP, r, r + SP, r + SP + YP, r + SP + 2 * YP,
+                              r + SP + 3 * YP, r + SP + 3 * YP + NUP, c);
+    } else {
+      for (int j = lane; j < nu; j += 32) {
+        const T val = r[NXP + j];
+        P.st.uo[(size_t)v * NUP + j] = val;
+        if (P.st.uo32) P.st.uo32[(size_t)v * NUP + j] = (float)val;
+      }
+      for (int i = lane; i < nx; i += 32) {
+        const T val = r[i];
+        P.st.xo[(size_t)v * NXP + i] = val;
+        if (P.st.xo32) P.st.xo32[(size_t)v * NXP + i] = (float)val;
       }
     }
-    __syncthreads();
+    __syncwarp();
   }
+  tm.sync();
+  return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -699,8 +955,7 @@ __device__ void chain_forward(const KParams<T> &P, int k, FwdCtx<T> &c, Smem<T> 
 // apply fn to every node whose per-node work chain k owns
 template <typename F>
 __device__ void for_owned(const PlanDev &pl, int k, F fn) {
-  const int p0 = pl.ch_path_ptr[k], m = pl.ch_path_ptr[k + 1] - p0;
-  for (int q = pl.ch_own_from[k]; q < m; ++q) fn(pl.ch_path[p0 + q]);
+  for (int q = pl.ch_own_ptr[k]; q < pl.ch_own_ptr[k + 1]; ++q) fn(pl.ch_own[q]);
   const int start = pl.ch_start[k], L = pl.ch_len[k];
   for (int q = 0; q < L; ++q) fn(start + q);
 }
@@ -744,6 +999,70 @@ static __device__ void final_node(const MixedParams &M, int v) {
     s64[i] = (M.mx.yb[ro + i] + M.mx.yb[ro + nt.NXP + i]) + (double)sw[i];
   for (int j = lane; j < nt.nu; j += 32)
     s64[nt.NXP + j] = M.mx.yb[ro + 2 * nt.NXP + j] + (double)sw[nt.NXP + j];
+}
+
+
+// ---------------------------------------------------------------------------
+// one evaluation of the dual gradient (with the per-node step of MODE) by a
+// block whose items are i = blockIdx.x, blockIdx.x + gridDim.x, ...: items
+// below n_groups are groups (whole block), the rest pairs of chains (one
+// per team).  Phases: chain heads, groups, the chains' local parts, the
+// forward sweeps.  keep: the block holds one chain pair and no group.
+// False (for the calling team) on timeout.
+// ---------------------------------------------------------------------------
+template <typename T, int MODE, int C>
+__device__ bool eval_step(const KParams<T> &P, FwdCtx<T> &c, const MixedDev *mx,
+                          const Smem<T> &smc, const Smem<T> &smg, const Team &tc,
+                          const Team &tb, unsigned step, bool keep) {
+  const int G = P.plan.n_groups, K = P.plan.n_chains;
+  const int n_items = G + (K + 1) / 2, team = team_index();
+  bool ok = true;
+  for (int i = blockIdx.x; i < n_items; i += gridDim.x) {
+    const int k = 2 * (i - G) + team;
+    if (i >= G && k < K) chain_head<T, C>(P, k, smc, tc);
+  }
+  for (int i = blockIdx.x; i < G; i += gridDim.x) {
+    __syncthreads();
+    if (!group_step<T>(P, i, smg, tb, step)) ok = false;
+  }
+  for (int i = blockIdx.x; i < n_items; i += gridDim.x) {
+    const int k = 2 * (i - G) + team;
+    if (i >= G && k < K) chain_rest<T, C>(P, k, smc, tc, keep);
+  }
+  for (int i = blockIdx.x; i < n_items && ok; i += gridDim.x) {
+    const int k = 2 * (i - G) + team;
+    if (i >= G && k < K) ok = chain_forward<T, MODE, C>(P, k, c, smc, tc, mx, step);
+  }
+  return ok;
+}
+
+// the block agrees on whether a wait has given up anywhere (every thread
+// of the block calls it)
+__device__ __forceinline__ bool block_err(const BlockMem &bm, int *err) {
+  __syncthreads();
+  if (threadIdx.x == 0) bm.bflag[0] = *(volatile int *)err;
+  __syncthreads();
+  const bool e = bm.bflag[0] != 0;
+  __syncthreads();
+  return e;
+}
+
+// residual check: the grid-wide maximum of r (bits of a non-negative
+// value) lands in res[ci]; false on timeout (every thread calls it)
+__device__ __forceinline__ bool grid_check(const BlockMem &bm, unsigned long long r,
+                                           unsigned long long *res, unsigned *barrier, int ci,
+                                           int *err) {
+  r = block_max_u64(r, bm.redu);
+  if (threadIdx.x == 0) {
+    atomicMax(res + ci, r);
+    __threadfence();
+    atomicAdd(barrier, 1u);
+    bm.bflag[1] = spin_geq(barrier, (unsigned)(ci + 1) * gridDim.x, err);
+  }
+  __syncthreads();
+  const bool ok = bm.bflag[1] != 0;
+  __syncthreads();
+  return ok;
 }
 
 }  // namespace rn

@@ -14,9 +14,10 @@
 // solution of E u + Ed d = 0 and the projection of q).  The backward sweep
 // is a subtree sum and the forward sweep a path sum, so there is no
 // dependent matrix product along the tree: each chain (single-leaf path)
-// is scanned by one thread block, top nodes are summed by the block that
-// completes their last child, and every block recomputes the path sums of
-// its chain's top ancestors instead of waiting for them.
+// is scanned by a team of threads, the top nodes below each stage-1 node
+// (a group) are summed, rolled back down and published by one block, and
+// each chain turns the published path sums of its parent into its own by
+// an elementwise correction of its precomputed local sums.
 #include <mutex>
 #include <set>
 
@@ -49,19 +50,18 @@ cudaError_t allow_max_smem(const void *fn) {
 // evaluation of the dual gradient (APG = false)
 // ---------------------------------------------------------------------------
 template <typename T, bool APG, int C>
-__global__ void __launch_bounds__(256) k_solve(KParams<T> P) {
+__global__ void __launch_bounds__(512) k_solve(KParams<T> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem<T> sm = carve<T>(smem_raw, P.net, P.buf_elems);
-  sm.net = stage_net(P.net, sm.net_raw);
-  const int tid = threadIdx.x;
+  const BlockMem bm = block_mem(smem_raw, P.net_bytes, P.team_bytes);
+  const NetDev<T> *net = stage_net(P.net, bm.net_raw);
+  const Team tc = chain_team(), tb = block_team();
+  const Smem<T> smc = carve<T>(bm.team_raw[team_index()], P.buf_elems, net);
+  const Smem<T> smg = carve<T>(bm.team_raw[0], P.gbuf_elems, net);
+  const int G = P.plan.n_groups, n_items = G + (P.plan.n_chains + 1) / 2;
+  const bool keep = (int)gridDim.x >= n_items && (int)blockIdx.x >= G;
   int it = 0, ci = 0, reason = 0;  // reason: 0 max iters, 1 converged, 2 non-finite, 3 timeout
-  bool ok = true;
-  for (; it < P.iters && ok; ++it) {
+  for (; it < P.iters; ++it) {
     const unsigned step = P.step_base + (unsigned)it;
-    for (int k = blockIdx.x; k < P.plan.n_chains; k += gridDim.x) {
-      chain_backward<T, C>(P, k, sm);
-      climb(P, k, step, sm);
-    }
     FwdCtx<T> c;
     c.ycur = (it & 1) ? P.st.yb : P.st.ya;
     c.yprv = (it & 1) ? P.st.ya : P.st.yb;
@@ -70,30 +70,14 @@ __global__ void __launch_bounds__(256) k_solve(KParams<T> P) {
     const bool check = APG && (((it + 1) % P.check_every) == 0 || it + 1 == P.iters);
     c.write_out = !APG || check;
     c.rbits = 0ull;
-    for (int k = blockIdx.x; k < P.plan.n_chains; k += gridDim.x) {
-      const int f = P.plan.ch_flag[k];
-      if (f >= 0) {
-        if (tid == 0) sm.flag[1] = spin_geq(P.st.flags + f, step + 1u, P.st.err);
-        __syncthreads();
-        if (!sm.flag[1]) {
-          ok = false;
-          reason = 3;
-          break;
-        }
-      }
-      chain_forward<T, APG ? kFwdApg : kFwdPlain, C>(P, k, c, sm, nullptr);
+    eval_step<T, APG ? kFwdApg : kFwdPlain, C>(P, c, nullptr, smc, smg, tc, tb, step, keep);
+    if (block_err(bm, P.st.err)) {
+      reason = 3;
+      ++it;
+      break;
     }
-    if (!ok) break;
     if (check) {
-      const unsigned long long r = block_max_u64(c.rbits, sm.redu);
-      if (tid == 0) {
-        atomicMax(P.st.res + ci, r);
-        __threadfence();
-        atomicAdd(P.st.barrier, 1u);
-        sm.flag[2] = spin_geq(P.st.barrier, (unsigned)(ci + 1) * gridDim.x, P.st.err);
-      }
-      __syncthreads();
-      if (!sm.flag[2]) {
+      if (!grid_check(bm, c.rbits, P.st.res, P.st.barrier, ci, P.st.err)) {
         reason = 3;
         ++ci;
         ++it;
@@ -113,13 +97,8 @@ __global__ void __launch_bounds__(256) k_solve(KParams<T> P) {
         break;
       }
     }
-    if (*(volatile int *)P.st.err != 0) {
-      reason = 3;
-      ++it;
-      break;
-    }
   }
-  if (blockIdx.x == 0 && tid == 0) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
     P.st.info[0] = it;
     P.st.info[1] = ci;
     P.st.info[2] = reason;
