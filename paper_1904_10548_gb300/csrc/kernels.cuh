@@ -83,6 +83,7 @@ struct KParams {
   int gcap;         // group rows held in shared memory
   int hchunk;       // chain-head rows staged at once by a group
   int fslots;       // staged nodes per warp in the forward sweep (1 or 2)
+  int fbrows;       // group rows per batch of the F application
   int team_bytes;   // bytes of one team region
   int net_bytes;    // bytes of the block's shared-memory copy of the network
   unsigned step_base;
@@ -146,22 +147,23 @@ cudaError_t mixed_occupancy(int maxc, int block, size_t smem, int *blocks_per_sm
 // Dynamic shared memory: [block header | network copy | team 0 | team 1],
 // the group work area spanning both team regions.  Buffers in elements
 // of T (nw: warps of a team, nwb: of the block):
-//   chain backward: segb rows of SP, per-warp E/S^-1 scratch, a vector
+//   chain backward: segb rows of SP, E/S^-1 work space, 1/(2p), a vector
 //   forward: the path vectors x_p | Z_p | B Z_p, then per warp `slots`
 //     staged nodes
-//   group: gcap rows, hchunk head rows, per-warp scratch, the descriptor
+//   group: gcap rows, hchunk head rows, E/S^-1 work space for fbrows rows,
+//     the descriptor
 __host__ __device__ inline int round4(int e) { return (e + 3) & ~3; }
 
 __host__ __device__ inline int fwd_elems_per_node(int NXP, int NUP, int YP, int SP, int mode) {
   return SP + (mode == 1 ? 2 * YP : (mode == 2 ? 3 * YP + NUP + NXP : 0));
 }
 
-__host__ __device__ inline int chain_vec_off(int segb, int SP, int NEP, int nw) {
-  return round4(segb * SP) + round4(2 * nw * NEP);
+__host__ __device__ inline int chain_vec_off(int segb, int SP, int NEP) {
+  return round4(segb * SP) + round4(2 * segb * NEP + segb);
 }
 
-__host__ __device__ inline int chain_back_elems(int segb, int SP, int NEP, int NXP, int NUP, int nw) {
-  return chain_vec_off(segb, SP, NEP, nw) + round4(2 * NXP + NUP);
+__host__ __device__ inline int chain_back_elems(int segb, int SP, int NEP, int NXP, int NUP) {
+  return chain_vec_off(segb, SP, NEP) + round4(2 * NXP + NUP);
 }
 
 __host__ __device__ inline int fwd_elems(int nw, int slots, int NXP, int NUP, int YP, int SP,
@@ -169,9 +171,9 @@ __host__ __device__ inline int fwd_elems(int nw, int slots, int NXP, int NUP, in
   return round4(2 * NXP + NUP) + nw * slots * fwd_elems_per_node(NXP, NUP, YP, SP, mode);
 }
 
-__host__ __device__ inline int group_elems(int gcap, int hchunk, int SP, int NEP, int nwb,
+__host__ __device__ inline int group_elems(int gcap, int hchunk, int SP, int NEP, int fbrows,
                                            int desc_elems) {
-  return (gcap + hchunk) * SP + round4(2 * nwb * NEP) + desc_elems;
+  return (gcap + hchunk) * SP + round4(2 * fbrows * NEP + fbrows) + desc_elems;
 }
 
 constexpr int kHdrBytes = 512;  // block header: reduction words and flags

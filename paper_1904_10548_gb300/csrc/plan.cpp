@@ -272,6 +272,11 @@ int build_plan(const rn_tree *t, Plan &p) {
     }
     for (int li = 0; li < m; ++li)
       for (int c = p.cc_ptr[g0 + li]; c < p.cc_ptr[g0 + li + 1]; ++c) d.push_back(p.cc[c] - c0);
+    int ncn = 0;
+    for (int li = 0; li < m; ++li) ncn += p.cc_ptr[g0 + li + 1] > p.cc_ptr[g0 + li];
+    d[3] = ncn;
+    for (int li = 0; li < m; ++li)
+      if (p.cc_ptr[g0 + li + 1] > p.cc_ptr[g0 + li]) d.push_back(li);
     while (d.size() % 4) d.push_back(0);
     p.max_desc = std::max(p.max_desc, (int)d.size());
     p.g_desc.insert(p.g_desc.end(), d.begin(), d.end());

@@ -429,7 +429,7 @@ __global__ void k_gather_mixed_y(NetDev<double> nt, const int *perm, int n, cons
 // work-buffer sizes of one precision in one kernel's shared-memory layout
 struct Sizes {
   int team_bytes = 0, net_bytes = 0;  // layout of the block (kernels.cuh)
-  int buf = 0, gbuf = 0, segb = 1, gcap = 0, hchunk = 1, fslots = 1;
+  int buf = 0, gbuf = 0, segb = 1, gcap = 0, hchunk = 1, fslots = 1, fbrows = 1;
 };
 
 struct rn_factor {
@@ -587,6 +587,7 @@ void set_sizes(KParams<T> &P, const Sizes &z) {
   P.gcap = z.gcap;
   P.hchunk = z.hchunk;
   P.fslots = z.fslots;
+  P.fbrows = z.fbrows;
   P.team_bytes = z.team_bytes;
   P.net_bytes = z.net_bytes;
 }
@@ -717,26 +718,26 @@ int team_budget(int device, int n_items, int net_bytes, int static_smem, int *te
 // for blocks of `block` threads: the team buffer holds the forward slots of
 // `mode` (two per warp if they fit, else one) and a backward segment (as
 // many chain rows as fit, up to the longest chain); the group buffer (both
-// regions) holds the group's descriptor and as many group rows as fit
-// while leaving room for min(16, chains of the largest group) head rows.
+// regions) holds the group's descriptor, the rows of a whole group if
+// they fit, and as many chain-head rows as the rest allows.
 int fit_sizes(const rn_factor *f, int eb, int team_bytes, int net_bytes, int block, int mode,
               Sizes *z) {
   const Plan &p = f->plan;
   const int misc = (int)round16((4 + 2 * kSeg) * sizeof(int));
-  const int nw = block / 64, nwb = block / 32;
+  const int nw = block / 64;
   z->team_bytes = team_bytes;
   z->net_bytes = net_bytes;
   z->buf = ((team_bytes - misc) & ~15) / eb - 72;
   z->gbuf = ((2 * team_bytes - misc) & ~15) / eb - 72;
   z->fslots = fwd_elems(nw, 2, f->NXP, f->NUP, f->YP, f->SP, mode) <= z->buf ? 2 : 1;
   if (fwd_elems(nw, z->fslots, f->NXP, f->NUP, f->YP, f->SP, mode) > z->buf ||
-      chain_back_elems(1, f->SP, f->NEP, f->NXP, f->NUP, nw) > z->buf) {
+      chain_back_elems(1, f->SP, f->NEP, f->NXP, f->NUP) > z->buf) {
     set_error("shared memory: the network is too large for the work buffers");
     return RN_ERR_UNSUPPORTED;
   }
   z->segb = 1;
   while (z->segb < p.max_chain_len &&
-         chain_back_elems(z->segb + 1, f->SP, f->NEP, f->NXP, f->NUP, nw) <= z->buf)
+         chain_back_elems(z->segb + 1, f->SP, f->NEP, f->NXP, f->NUP) <= z->buf)
     ++z->segb;
   if (p.n_groups == 0) {
     z->gcap = 0;
@@ -744,13 +745,15 @@ int fit_sizes(const rn_factor *f, int eb, int team_bytes, int net_bytes, int blo
     return RN_OK;
   }
   const int desc = round4((p.max_desc * 4 + eb - 1) / eb);
-  const int rows = (z->gbuf - group_elems(0, 0, f->SP, f->NEP, nwb, desc)) / f->SP;
+  z->fbrows = std::min(p.max_group, 64);
+  const int rows = (z->gbuf - group_elems(0, 0, f->SP, f->NEP, z->fbrows, desc)) / f->SP;
   if (rows < 2) {
     set_error("shared memory: the network is too large for the group buffer");
     return RN_ERR_UNSUPPORTED;
   }
-  const int hmin = std::min(16, p.max_group_chains);
-  z->gcap = std::max(1, std::min(p.max_group, rows - hmin));
+  // every group in shared memory if there is room beside one head row; a
+  // larger group keeps all its rows in global memory
+  z->gcap = std::min(p.max_group, rows - 1);
   z->hchunk = std::max(1, std::min(p.max_group_chains, rows - z->gcap));
   return RN_OK;
 }

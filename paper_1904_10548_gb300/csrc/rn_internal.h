@@ -55,8 +55,9 @@ struct Plan {
   // per group a compact descriptor in local indices (li = internal - g_node[g],
   // chain positions relative to g_chain[2g]), at g_desc[g_desc_ptr[g]],
   // padded to a multiple of 4 ints:
-  //   m, nl, nch, 0 | lvl[nl + 1] | par[m] (-1: the root) |
-  //   tcp[m + 1], tcl[..] (top children) | ccp[m + 1], ccl[..] (chain children)
+  //   m, nl, nch, ncn | lvl[nl + 1] | par[m] (-1: the root) |
+  //   tcp[m + 1], tcl[..] (top children) | ccp[m + 1], ccl[..] (chain children) |
+  //   cn[ncn] (the nodes with chain children)
   std::vector<int> g_desc_ptr, g_desc;
   int max_desc = 0;
   // top nodes (indexed by internal index 0..n_top): top children and

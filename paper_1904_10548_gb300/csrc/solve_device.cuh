@@ -179,16 +179,15 @@ __device__ __forceinline__ Smem<T> carve(unsigned char *raw, int buf_elems, cons
 
 // ---------------------------------------------------------------------------
 // asynchronous staging global -> shared, 16 bytes per copy, all copies of
-// a team in flight at once.  cg = true reads through L2 only (data other
-// blocks wrote during this launch); cg = false may hit L1 (data this team
-// wrote itself, or constants).
+// a team in flight at once, read through L2 (the shared-memory carve-out
+// leaves a small L1, which streamed rows would only evict).  cg marks the
+// copies of data other blocks wrote during this launch, which must not
+// come from L1.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void cp16(void *dst, const void *src, bool cg) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  if (cg)
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+  (void)cg;  // always through L2: staged rows must not evict the small L1
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
@@ -213,39 +212,114 @@ __device__ __forceinline__ void stage_rows(T *dst, int dpitch, const T *src, int
 }
 
 // ---------------------------------------------------------------------------
-// z = F g / (2p) in place for one node by one warp (g: the input part of a
-// row), F g = W^-1 (g - E' S^-1 E W^-1 g); eb, fb: NEP elements of the
-// warp's scratch
+// loops over (row, component) pairs: thread t takes component c0 + k cw of
+// rows r0, r0 + rs, ... (cw the smallest power of two >= the component
+// count, at most the team width), so consecutive lanes take consecutive
+// components and a thread's rows are independent of each other
 // ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ void warp_F(const NetDev<T> &nt, T *g, T i2p, T *eb, T *fb) {
-  const int lane = threadIdx.x & 31, ne = nt.ne, nu = nt.nu;
+struct Map2 {
+  int c0, cw, r0, rs;
+};
+
+__device__ __forceinline__ Map2 map2(const Team &tm, int nc) {
+  int cw = nc <= 1 ? 1 : 1 << (32 - __clz(nc - 1));
+  if (cw > tm.nt) cw = tm.nt;
+  return Map2{tm.tid % cw, cw, tm.tid / cw, tm.nt / cw};
+}
+
+// ---------------------------------------------------------------------------
+// One row of a compressed sparse matrix held in registers for a loop over
+// many nodes (the structure is shared by all nodes): the first CAP entries
+// in registers, any further ones read from the arrays.  dot() adds the
+// entries in storage order, like a plain loop over the row.
+// ---------------------------------------------------------------------------
+template <typename T, int CAP>
+struct Slice {
+  int n, p;
+  int idx[CAP];
+  T val[CAP];
+  __device__ __forceinline__ void load(const int *ptr, const int *ix, const T *vl, int r) {
+    p = ptr[r];
+    n = ptr[r + 1] - p;
+#pragma unroll
+    for (int k = 0; k < CAP; ++k) {
+      idx[k] = k < n ? ix[p + k] : 0;
+      val[k] = k < n ? vl[p + k] : T(0);
+    }
+  }
+  // acc + sum_k val_k f(idx_k)
+  template <typename F>
+  __device__ __forceinline__ T dot(T acc, F f, const int *ix, const T *vl) const {
+#pragma unroll
+    for (int k = 0; k < CAP; ++k)
+      if (k < n) acc += val[k] * f(idx[k]);
+    for (int e = CAP; e < n; ++e) acc += vl[p + e] * f(ix[p + e]);
+    return acc;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// z = F ghat / (2p) in place for m rows (ghat at offset NXP of row(q)),
+// F ghat = W^-1 (ghat - E' S^-1 E W^-1 ghat); eb, fb: m x NEP work space
+// ---------------------------------------------------------------------------
+template <typename T, typename RowF>
+__device__ void apply_F(const NetDev<T> &nt, int m, RowF row, const T *i2p, T *eb, T *fb,
+                        const Team &tm) {
+  const int ne = nt.ne, nu = nt.nu, NXP = nt.NXP, NEP = nt.NEP;
   const int *Er_ptr = nt.Er_ptr, *Er_idx = nt.Er_idx, *Ec_ptr = nt.Ec_ptr, *Ec_idx = nt.Ec_idx;
   const T *Er_val = nt.Er_val, *Ec_val = nt.Ec_val, *winv = nt.winv, *Sinv = nt.Sinv;
   if (ne > 0) {
-    for (int r = lane; r < ne; r += 32) {
-      T acc = T(0);
-      for (int e = Er_ptr[r]; e < Er_ptr[r + 1]; ++e) {
-        const int j = Er_idx[e];
-        acc += Er_val[e] * (winv[j] * g[j]);
+    const Map2 a = map2(tm, ne);
+    for (int r = a.c0; r < ne; r += a.cw) {
+      Slice<T, 6> er;
+      er.load(Er_ptr, Er_idx, Er_val, r);
+      T wv[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) wv[k] = winv[er.idx[k]];
+#pragma unroll 2
+      for (int q = a.r0; q < m; q += a.rs) {
+        const T *g = row(q) + NXP;
+        T acc = T(0);
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+          if (k < er.n) acc += er.val[k] * (wv[k] * g[er.idx[k]]);
+        for (int e = 6; e < er.n; ++e) {
+          const int j = Er_idx[er.p + e];
+          acc += Er_val[er.p + e] * (winv[j] * g[j]);
+        }
+        eb[q * NEP + r] = acc;
       }
-      eb[r] = acc;
     }
-    __syncwarp();
-    for (int r = lane; r < ne; r += 32) {
+    tm.sync();
+    for (int r = a.c0; r < ne; r += a.cw) {
       const T *Si = Sinv + (size_t)r * ne;
-      T acc = T(0);
-      for (int c = 0; c < ne; ++c) acc += Si[c] * eb[c];
-      fb[r] = acc;
+#pragma unroll 2
+      for (int q = a.r0; q < m; q += a.rs) {
+        const T *e = eb + q * NEP;
+        T acc = T(0);
+        for (int c = 0; c < ne; ++c) acc += Si[c] * e[c];
+        fb[q * NEP + r] = acc;
+      }
     }
-    __syncwarp();
+    tm.sync();
   }
-  for (int j = lane; j < nu; j += 32) {
-    T acc = g[j];
-    for (int e = Ec_ptr[j]; e < Ec_ptr[j + 1]; ++e) acc -= Ec_val[e] * fb[Ec_idx[e]];
-    g[j] = (winv[j] * acc) * i2p;
+  const Map2 b = map2(tm, nu);
+  for (int j = b.c0; j < nu; j += b.cw) {
+    Slice<T, 2> ec;
+    ec.load(Ec_ptr, Ec_idx, Ec_val, j);
+    const T wj = winv[j];
+#pragma unroll 4
+    for (int q = b.r0; q < m; q += b.rs) {
+      T *g = row(q) + NXP;
+      const T *f = fb + q * NEP;
+      T acc = g[j];
+#pragma unroll
+      for (int k = 0; k < 2; ++k)
+        if (k < ec.n) acc -= ec.val[k] * f[ec.idx[k]];
+      for (int e = 2; e < ec.n; ++e) acc -= Ec_val[ec.p + e] * f[Ec_idx[ec.p + e]];
+      g[j] = (wj * acc) * i2p[q];
+    }
   }
-  __syncwarp();
 }
 
 // Copy the network data into shared memory at raw (net_smem_bytes of
@@ -516,7 +590,7 @@ __device__ void chain_head(const KParams<T> &P, int k, const Smem<T> &sm, const 
     }
   }
   if (g < 0) return;  // below the root: nobody reads the head sums
-  T *vec = rows + chain_vec_off(segb, SP, nt.NEP, tm.nwarps());
+  T *vec = rows + chain_vec_off(segb, SP, nt.NEP);
 #pragma unroll
   for (int c = 0; c < C; ++c) {
     const int i = tm.tid + c * tm.nt;
@@ -531,9 +605,9 @@ __device__ void chain_head(const KParams<T> &P, int k, const Smem<T> &sm, const 
     const int i = tm.tid + c * tm.nt;
     if (i < nx) out[i] = lam[c];
     if (i < nu) {
-      T t = g3[c];
-      for (int e = Bc_ptr[i]; e < Bc_ptr[i + 1]; ++e) t += Bc_val[e] * vec[Bc_idx[e]];
-      out[NXP + i] = t;
+      Slice<T, 2> bc;
+      bc.load(Bc_ptr, Bc_idx, Bc_val, i);
+      out[NXP + i] = bc.dot(g3[c], [&](int t) { return vec[t]; }, Bc_idx, Bc_val);
     }
   }
   tm.sync();
@@ -562,9 +636,9 @@ __device__ void chain_rest(const KParams<T> &P, int k, const Smem<T> &sm, const 
   const T *Bc_val = nt.Bc_val, *Br_val = nt.Br_val;
   const int start = P.plan.ch_start[k], L = P.plan.ch_len[k], segb = P.segb;
   const bool multi = L > segb, data = !P.linear;
-  const int lane = tm.lane(), warp = tm.warp(), nw = tm.nwarps();
+  const Map2 mu = map2(tm, nu), mx = map2(tm, nx);
   T *rows = sm.buf;
-  T *eb = rows + round4(segb * SP) + 2 * warp * NEP, *fb = eb + NEP;
+  T *eb = rows + round4(segb * SP), *fb = eb + segb * NEP, *i2p = fb + segb * NEP;
   T accL[C], accG[C];
 #pragma unroll
   for (int c = 0; c < C; ++c) accL[c] = accG[c] = T(0);
@@ -587,14 +661,16 @@ __device__ void chain_rest(const KParams<T> &P, int k, const Smem<T> &sm, const 
           }
         }
       }
-      tm.sync();
     }
-    for (int q = warp; q < m; q += nw) {  // w3 + B' lambda per node
-      T *row = rows + q * SP;
-      for (int j = lane; j < nu; j += 32) {
-        T t = row[NXP + j];
-        for (int e = Bc_ptr[j]; e < Bc_ptr[j + 1]; ++e) t += Bc_val[e] * row[Bc_idx[e]];
-        row[NXP + j] = t;
+    for (int q = tm.tid; q < m; q += tm.nt) i2p[q] = P.st.inv2p[start + lo + q];
+    tm.sync();
+    for (int j = mu.c0; j < nu; j += mu.cw) {  // w3 + B' lambda per node
+      Slice<T, 2> bc;
+      bc.load(Bc_ptr, Bc_idx, Bc_val, j);
+#pragma unroll 4
+      for (int q = mu.r0; q < m; q += mu.rs) {
+        T *row = rows + q * SP;
+        row[NXP + j] = bc.dot(row[NXP + j], [&](int t) { return row[t]; }, Bc_idx, Bc_val);
       }
     }
     tm.sync();
@@ -609,8 +685,7 @@ __device__ void chain_rest(const KParams<T> &P, int k, const Smem<T> &sm, const 
       }
     }
     tm.sync();
-    for (int q = warp; q < m; q += nw)
-      warp_F(nt, rows + q * SP + NXP, P.st.inv2p[start + lo + q], eb, fb);
+    apply_F(nt, m, [=](int q) { return rows + q * SP; }, i2p, eb, fb, tm);
     tm.sync();
     if (lo > 0) {
       T *z = P.st.z + (size_t)(start + lo) * NUP;
@@ -650,12 +725,14 @@ __device__ void chain_rest(const KParams<T> &P, int k, const Smem<T> &sm, const 
       }
     }
     tm.sync();
-    for (int q = warp; q < m; q += nw) {  // B U + Gd d per node
-      T *row = rows + q * SP;
-      for (int i = lane; i < nx; i += 32) {
-        T acc = data ? P.st.gb[(size_t)(start + lo + q) * NXP + i] : T(0);
-        for (int e = Br_ptr[i]; e < Br_ptr[i + 1]; ++e) acc += Br_val[e] * row[NXP + Br_idx[e]];
-        row[i] = acc;
+    for (int i = mx.c0; i < nx; i += mx.cw) {  // B U + Gd d per node
+      Slice<T, 6> br;
+      br.load(Br_ptr, Br_idx, Br_val, i);
+#pragma unroll 4
+      for (int q = mx.r0; q < m; q += mx.rs) {
+        T *row = rows + q * SP;
+        const T base = data ? P.st.gb[(size_t)(start + lo + q) * NXP + i] : T(0);
+        row[i] = br.dot(base, [&](int t) { return row[NXP + t]; }, Br_idx, Br_val);
       }
     }
     tm.sync();
@@ -701,14 +778,14 @@ __device__ bool group_step(const KParams<T> &P, int g, const Smem<T> &sm, const 
   const int m = pl.g_node[g + 1] - g0;
   const int d0 = pl.g_desc_ptr[g], dn = pl.g_desc_ptr[g + 1] - d0;
   const bool data = !P.linear;
-  const int gcap = P.gcap, hchunk = P.hchunk;
-  const int lane = tm.lane(), warp = tm.warp(), nw = tm.nwarps();
+  const int gcap = P.gcap, hchunk = P.hchunk, fbr = P.fbrows;
+  const Map2 mx = map2(tm, nx), mu = map2(tm, nu);
   T *R = sm.buf;
   T *H = R + (size_t)gcap * SP;
-  T *eb = H + (size_t)hchunk * SP + 2 * warp * NEP, *fb = eb + NEP;
-  int *desc = reinterpret_cast<int *>(H + (size_t)hchunk * SP + round4(2 * nw * NEP));
-  T *spill = P.st.up + (size_t)(pl.n_chains + g0) * SP;
-  auto row = [&](int li) -> T * { return li < gcap ? R + (size_t)li * SP : spill + (size_t)li * SP; };
+  T *eb = H + (size_t)hchunk * SP, *fb = eb + fbr * NEP, *i2p = fb + fbr * NEP;
+  int *desc = reinterpret_cast<int *>(eb + round4(2 * fbr * NEP + fbr));
+  // all rows in shared memory, or (a group larger than gcap) all in up[K + v]
+  T *const rb = m <= gcap ? R : P.st.up + (size_t)(pl.n_chains + g0) * SP;
   // all chains of the group have arrived; the counter restarts for the
   // next evaluation (no chain arrives again before the flag below)
   if (tm.tid == 0) {
@@ -718,11 +795,12 @@ __device__ bool group_step(const KParams<T> &P, int g, const Smem<T> &sm, const 
   tm.sync();
   if (!sm.flag[0]) return false;
   // own terms (w1 + w2 | w3) of the group's nodes, the descriptor, heads
-  const int mr = m < gcap ? m : gcap;
-  stage_span(R, P.st.s + (size_t)g0 * SP, mr * SP, tm, true);
+  if (m <= gcap) {
+    stage_span(R, P.st.s + (size_t)g0 * SP, m * SP, tm, true);
+  } else {
+    for (int e = tm.tid; e < m * SP; e += tm.nt) rb[e] = __ldcg(P.st.s + (size_t)g0 * SP + e);
+  }
   for (int e = tm.tid; e < dn / 4; e += tm.nt) cp16(desc + 4 * e, pl.g_desc + d0 + 4 * e, false);
-  for (int e = tm.tid; e < (m - mr) * SP; e += tm.nt)
-    spill[(size_t)mr * SP + e] = __ldcg(P.st.s + (size_t)(g0 + mr) * SP + e);
   const int nch = c1 - c0;
   for (int h0 = 0; h0 < nch; h0 += hchunk) {
     const int h1 = nch - h0 < hchunk ? nch : h0 + hchunk;
@@ -730,25 +808,40 @@ __device__ bool group_step(const KParams<T> &P, int g, const Smem<T> &sm, const 
     stage_span(H, P.st.up + (size_t)(c0 + h0) * SP, (h1 - h0) * SP, tm, true);
     cp_wait();
     tm.sync();
-    const int nl = desc[1];
-    const int *ccp = desc + 4 + (nl + 1) + m + (m + 1) + desc[4 + (nl + 1) + m + m];
-    const int *ccl = ccp + m + 1;
-    for (int li = warp; li < m; li += nw) {  // heads into their parents
-      const int cs = ccp[li], ce = ccp[li + 1];
-      if (cs == ce) continue;
-      T *r = row(li);
-      for (int col = lane; col < SP; col += 32) {
-        if ((col >= nx && col < NXP) || col >= NXP + nu) continue;
+    const int nl = desc[1], ncn = desc[3];
+    const int *tcp = desc + 4 + (nl + 1) + m;
+    const int *ccp = tcp + (m + 1) + tcp[m], *ccl = ccp + m + 1, *cn = ccl + ccp[m];
+    // heads into their parents (fixed order of the chain children)
+    for (int o = mx.r0; o < ncn; o += mx.rs) {
+      const int li = cn[o], cs = ccp[li], ce = ccp[li + 1];
+      T *r = rb + (size_t)li * SP;
+      for (int i = mx.c0; i < nx; i += mx.cw) {
         T acc = T(0);
         bool any = false;
         for (int c = cs; c < ce; ++c) {
           const int kk = ccl[c];
           if (kk >= h0 && kk < h1) {
-            acc += H[(size_t)(kk - h0) * SP + col];
+            acc += H[(size_t)(kk - h0) * SP + i];
             any = true;
           }
         }
-        if (any) r[col] += acc;
+        if (any) r[i] += acc;
+      }
+    }
+    for (int o = mu.r0; o < ncn; o += mu.rs) {
+      const int li = cn[o], cs = ccp[li], ce = ccp[li + 1];
+      T *r = rb + (size_t)li * SP + NXP;
+      for (int j = mu.c0; j < nu; j += mu.cw) {
+        T acc = T(0);
+        bool any = false;
+        for (int c = cs; c < ce; ++c) {
+          const int kk = ccl[c];
+          if (kk >= h0 && kk < h1) {
+            acc += H[(size_t)(kk - h0) * SP + NXP + j];
+            any = true;
+          }
+        }
+        if (any) r[j] += acc;
       }
     }
   }
@@ -758,47 +851,65 @@ __device__ bool group_step(const KParams<T> &P, int g, const Smem<T> &sm, const 
   const int *lvl = desc + 4, *par = lvl + nl + 1, *tcp = par + m, *tcl = tcp + m + 1;
   // backward over the levels, deepest first
   for (int l = nl - 1; l >= 0; --l) {
-    for (int li = lvl[l] + warp; li < lvl[l + 1]; li += nw) {
-      T *r = row(li);
+    const int a = lvl[l], b = lvl[l + 1];
+#pragma unroll 2
+    for (int li = a + mx.r0; li < b; li += mx.rs) {
+      T *r = rb + (size_t)li * SP;
       const int ts = tcp[li], te = tcp[li + 1];
-      for (int i = lane; i < nx; i += 32) {
+      for (int i = mx.c0; i < nx; i += mx.cw) {
         T acc = r[i];
-        for (int c = ts; c < te; ++c) acc += row(tcl[c])[i];
+        for (int c = ts; c < te; ++c) acc += rb[(size_t)tcl[c] * SP + i];
         r[i] = acc;
       }
-      __syncwarp();
-      for (int j = lane; j < nu; j += 32) {
-        T acc = r[NXP + j];
-        for (int e = Bc_ptr[j]; e < Bc_ptr[j + 1]; ++e) acc += Bc_val[e] * r[Bc_idx[e]];
-        for (int c = ts; c < te; ++c) acc += row(tcl[c])[NXP + j];
+    }
+    tm.sync();
+    for (int j = mu.c0; j < nu; j += mu.cw) {
+      Slice<T, 2> bc;
+      bc.load(Bc_ptr, Bc_idx, Bc_val, j);
+#pragma unroll 2
+      for (int li = a + mu.r0; li < b; li += mu.rs) {
+        T *r = rb + (size_t)li * SP;
+        const int ts = tcp[li], te = tcp[li + 1];
+        T acc = bc.dot(r[NXP + j], [&](int t) { return r[t]; }, Bc_idx, Bc_val);
+        for (int c = ts; c < te; ++c) acc += rb[(size_t)tcl[c] * SP + NXP + j];
         r[NXP + j] = acc;
       }
     }
     tm.sync();
   }
   // z = F ghat / (2p) at every node of the group
-  for (int li = warp; li < m; li += nw) warp_F(nt, row(li) + NXP, P.st.inv2p[g0 + li], eb, fb);
+  for (int q0 = 0; q0 < m; q0 += fbr) {
+    const int mm = m - q0 < fbr ? m - q0 : fbr;
+    if (q0 > 0) tm.sync();
+    for (int q = tm.tid; q < mm; q += tm.nt) i2p[q] = P.st.inv2p[g0 + q0 + q];
+    tm.sync();
+    apply_F(nt, mm, [=](int q) { return rb + (size_t)(q0 + q) * SP; }, i2p, eb, fb, tm);
+  }
   tm.sync();
   // forward over the levels: Z_v = Z_a(v) + z_v, x_v = x_a(v) + B u_v + Gd d_v
   for (int l = 0; l < nl; ++l) {
-    for (int li = lvl[l] + warp; li < lvl[l + 1]; li += nw) {
-      T *r = row(li);
+    const int a = lvl[l], b = lvl[l + 1];
+#pragma unroll 2
+    for (int li = a + mu.r0; li < b; li += mu.rs) {
       const int pa = par[li];
-      if (pa >= 0) {
-        const T *rp = row(pa);
-        for (int j = lane; j < nu; j += 32) r[NXP + j] += rp[NXP + j];
-      }
-      __syncwarp();
-      const int v = g0 + li;
-      for (int i = lane; i < nx; i += 32) {
-        T acc = pa >= 0 ? row(pa)[i] : (data ? P.st.xroot[i] : T(0));
+      if (pa < 0) continue;
+      T *r = rb + (size_t)li * SP;
+      const T *rp = rb + (size_t)pa * SP;
+      for (int j = mu.c0; j < nu; j += mu.cw) r[NXP + j] += rp[NXP + j];
+    }
+    tm.sync();
+    for (int i = mx.c0; i < nx; i += mx.cw) {
+      Slice<T, 6> br;
+      br.load(Br_ptr, Br_idx, Br_val, i);
+#pragma unroll 2
+      for (int li = a + mx.r0; li < b; li += mx.rs) {
+        const int pa = par[li], v = g0 + li;
+        T *r = rb + (size_t)li * SP;
+        T acc = pa >= 0 ? rb[(size_t)pa * SP + i] : (data ? P.st.xroot[i] : T(0));
         if (data) acc += P.st.gb[(size_t)v * NXP + i];
-        for (int e = Br_ptr[i]; e < Br_ptr[i + 1]; ++e) {
-          const int j = Br_idx[e];
-          const T u = (data ? P.st.ub[(size_t)v * NUP + j] : T(0)) - r[NXP + j];
-          acc += Br_val[e] * u;
-        }
-        r[i] = acc;
+        const T *ubv = P.st.ub + (size_t)v * NUP;
+        r[i] = br.dot(acc, [&](int t) { return (data ? ubv[t] : T(0)) - r[NXP + t]; }, Br_idx,
+                      Br_val);
       }
     }
     tm.sync();
@@ -811,7 +922,7 @@ __device__ bool group_step(const KParams<T> &P, int g, const Smem<T> &sm, const 
     V *dst = reinterpret_cast<V *>(P.st.ux + (size_t)g0 * SP);
     for (int e = tm.tid; e < m * nv; e += tm.nt) {
       const int li = e / nv, c = e - li * nv;
-      dst[e] = reinterpret_cast<const V *>(row(li))[c];
+      dst[e] = reinterpret_cast<const V *>(rb + (size_t)li * SP)[c];
     }
   }
   tm.sync();
@@ -870,9 +981,9 @@ __device__ bool chain_forward(const KParams<T> &P, int k, FwdCtx<T> &c, const Sm
     const int *Br_ptr = nt.Br_ptr, *Br_idx = nt.Br_idx;
     const T *Br_val = nt.Br_val;
     for (int i = tm.tid; i < nx; i += tm.nt) {
-      T acc = T(0);
-      for (int e = Br_ptr[i]; e < Br_ptr[i + 1]; ++e) acc += Br_val[e] * Zp[Br_idx[e]];
-      BZ[i] = acc;
+      Slice<T, 6> br;
+      br.load(Br_ptr, Br_idx, Br_val, i);
+      BZ[i] = br.dot(T(0), [&](int t) { return Zp[t]; }, Br_idx, Br_val);
     }
   }
   tm.sync();
