@@ -50,20 +50,20 @@ template <typename T, int MODE, int C, typename CtxF>
 __device__ bool batch_eval(const BatchDev &B, BatchCtx &bc, MixedParams &mp, const BlockMem &bm,
                            unsigned step, bool all, CtxF make_ctx) {
   const int i0 = B.cta_begin[blockIdx.x], i1 = B.cta_begin[blockIdx.x + 1];
-  const Team tc = chain_team(), tb = block_team();
-  const int ti = team_index();
+  const Team tc = chain_team(B.tpb), tb = block_team();
+  const int ti = team_index(B.tpb);
   auto params = [&]() -> const KParams<T> & {
     if constexpr (sizeof(T) == 4) return mp.f; else return mp.d;
   };
   auto smem_c = [&]() {
     const KParams<T> &P = params();
-    return carve<T>(bm.team_raw[ti], P.buf_elems,
+    return carve<T>(bm.team_raw(ti), P.buf_elems,
                     reinterpret_cast<const NetDev<T> *>(sizeof(T) == 4 ? bm.net_raw
                                                                        : bm.net_raw + B.net_bytes_f));
   };
   auto smem_g = [&]() {
     const KParams<T> &P = params();
-    return carve<T>(bm.team_raw[0], P.gbuf_elems,
+    return carve<T>(bm.team_raw(0), P.gbuf_elems,
                     reinterpret_cast<const NetDev<T> *>(sizeof(T) == 4 ? bm.net_raw
                                                                        : bm.net_raw + B.net_bytes_f));
   };
@@ -75,7 +75,7 @@ __device__ bool batch_eval(const BatchDev &B, BatchCtx &bc, MixedParams &mp, con
     if (!use(i)) continue;
     load_problem(B, B.item_prob[i], bc, mp, bm);
     const KParams<T> &P = params();
-    const int G = P.plan.n_groups, sub = B.item_sub[i], k = 2 * (sub - G) + ti;
+    const int G = P.plan.n_groups, sub = B.item_sub[i], k = B.tpb * (sub - G) + ti;
     if (sub >= G && k < P.plan.n_chains) chain_head<T, C>(P, k, smem_c(), tc);
   }
   bool ok = true;
@@ -93,14 +93,14 @@ __device__ bool batch_eval(const BatchDev &B, BatchCtx &bc, MixedParams &mp, con
     if (!use(i)) continue;
     load_problem(B, B.item_prob[i], bc, mp, bm);
     const KParams<T> &P = params();
-    const int G = P.plan.n_groups, sub = B.item_sub[i], k = 2 * (sub - G) + ti;
+    const int G = P.plan.n_groups, sub = B.item_sub[i], k = B.tpb * (sub - G) + ti;
     if (sub >= G && k < P.plan.n_chains) chain_rest<T, C>(P, k, smem_c(), tc, false);
   }
   for (int i = i0; i < i1; ++i) {
     if (!use(i)) continue;
     load_problem(B, B.item_prob[i], bc, mp, bm);
     const KParams<T> &P = params();
-    const int G = P.plan.n_groups, sub = B.item_sub[i], k = 2 * (sub - G) + ti;
+    const int G = P.plan.n_groups, sub = B.item_sub[i], k = B.tpb * (sub - G) + ti;
     if (sub >= G && k < P.plan.n_chains && ok) {
       FwdCtx<T> *c = make_ctx(slot_of(bc, B.item_prob[i]));
       ok = chain_forward<T, MODE, C>(P, k, *c, smem_c(), tc, &mp.mx, step);
@@ -115,8 +115,8 @@ __global__ void __launch_bounds__(512) k_batch(BatchDev B) {
   __shared__ MixedParams mp;
   __shared__ BatchCtx bc;
   const BlockMem bm = block_mem(smem_raw, B.net_bytes, B.team_bytes);
-  const Team tc = chain_team();
-  const int ti = team_index();
+  const Team tc = chain_team(B.tpb);
+  const int ti = team_index(B.tpb);
   const int i0 = B.cta_begin[blockIdx.x], i1 = B.cta_begin[blockIdx.x + 1];
   if (threadIdx.x == 0) {
     bc.n = 0;
@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(512) k_batch(BatchDev B) {
         const int p = B.item_prob[i];
         if (!bc.active[slot_of(bc, p)]) continue;
         load_problem(B, p, bc, mp, bm);
-        const int G = mp.f.plan.n_groups, sub = B.item_sub[i], k = 2 * (sub - G) + ti;
+        const int G = mp.f.plan.n_groups, sub = B.item_sub[i], k = B.tpb * (sub - G) + ti;
         if (sub >= G && k < mp.f.plan.n_chains) {
           float *dcur = (it & 1) ? mp.mx.db : mp.mx.da;
           float *dprv = (it & 1) ? mp.mx.da : mp.mx.db;
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(512) k_batch(BatchDev B) {
   if (ok) {
     for (int i = i0; i < i1; ++i) {
       load_problem(B, B.item_prob[i], bc, mp, bm);
-      const int G = mp.f.plan.n_groups, sub = B.item_sub[i], k = 2 * (sub - G) + ti;
+      const int G = mp.f.plan.n_groups, sub = B.item_sub[i], k = B.tpb * (sub - G) + ti;
       if (sub >= G && k < mp.f.plan.n_chains) {
         int idx = 0;
         for_owned(mp.f.plan, k, [&](int v) {

@@ -84,6 +84,7 @@ struct KParams {
   int hchunk;       // chain-head rows staged at once by a group
   int fslots;       // staged nodes per warp in the forward sweep (1 or 2)
   int fbrows;       // group rows per batch of the F application
+  int tpb;          // chain teams per block
   int team_bytes;   // bytes of one team region
   int net_bytes;    // bytes of the block's shared-memory copy of the network
   unsigned step_base;
@@ -117,8 +118,8 @@ cudaError_t launch_mixed(const MixedParams &M, int maxc, int grid, int block, si
 
 // Batched mode: independent problems (each a factor handle in mixed
 // precision) in one cooperative launch.  Work items are (problem, sub)
-// with sub numbered as in the single-problem kernels (groups, then chain
-// pairs), sorted by problem; block b processes items
+// with sub numbered as in the single-problem kernels (groups, then sets
+// of tpb chains), sorted by problem; block b processes items
 // [cta_begin[b], cta_begin[b+1]).
 constexpr int kBatchMaxDistinct = 32;  // problems one block may touch
 
@@ -133,6 +134,7 @@ struct BatchDev {
   int net_bytes;             // network region: FP32 copy, then the FP64 header
   int net_bytes_f;           // offset of the FP64 header in the network region
   int team_bytes;            // team region (max over problems)
+  int tpb;                   // chain teams per block
   double tol;
 };
 
@@ -142,10 +144,10 @@ cudaError_t batch_occupancy(int maxc, int block, size_t smem, int *blocks_per_sm
 cudaError_t batch_static_smem(int maxc, int *bytes);
 cudaError_t mixed_occupancy(int maxc, int block, size_t smem, int *blocks_per_sm);
 
-// Shared memory of the persistent kernels.  A block is two teams of
-// equal width; a team scans one chain, the whole block sums one group.
-// Dynamic shared memory: [block header | network copy | team 0 | team 1],
-// the group work area spanning both team regions.  Buffers in elements
+// Shared memory of the persistent kernels.  A block is tpb teams of equal
+// width; a team scans one chain, the whole block sums one group.  Dynamic
+// shared memory: [block header | network copy | team 0 | team 1 | ...],
+// the group work area spanning all team regions.  Buffers in elements
 // of T (nw: warps of a team, nwb: of the block):
 //   chain backward: segb rows of SP, E/S^-1 work space, 1/(2p), a vector
 //   forward: the path vectors x_p | Z_p | B Z_p, then per warp `slots`

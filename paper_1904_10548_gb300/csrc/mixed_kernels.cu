@@ -24,18 +24,19 @@ __global__ void __launch_bounds__(512) k_mixed(MixedParams M) {
   const BlockMem bm = block_mem(smem_raw, M.f.net_bytes, M.f.team_bytes);
   const NetDev<float> *netf = stage_net(M.f.net, bm.net_raw);
   const NetDev<double> *netd = stage_net(M.d.net, bm.net_raw + M.d.net_bytes, false);
-  const Team tc = chain_team(), tb = block_team();
-  const int ti = team_index();
-  const Smem<float> sfc = carve<float>(bm.team_raw[ti], M.f.buf_elems, netf);
-  const Smem<float> sfg = carve<float>(bm.team_raw[0], M.f.gbuf_elems, netf);
-  const Smem<double> sdc = carve<double>(bm.team_raw[ti], M.d.buf_elems, netd);
-  const Smem<double> sdg = carve<double>(bm.team_raw[0], M.d.gbuf_elems, netd);
+  const int tpb = M.f.tpb;
+  const Team tc = chain_team(tpb), tb = block_team();
+  const int ti = team_index(tpb);
+  const Smem<float> sfc = carve<float>(bm.team_raw(ti), M.f.buf_elems, netf);
+  const Smem<float> sfg = carve<float>(bm.team_raw(0), M.f.gbuf_elems, netf);
+  const Smem<double> sdc = carve<double>(bm.team_raw(ti), M.d.buf_elems, netd);
+  const Smem<double> sdg = carve<double>(bm.team_raw(0), M.d.gbuf_elems, netd);
   const KParams<float> &P = M.f;
-  const int G = P.plan.n_groups, K = P.plan.n_chains, n_items = G + (K + 1) / 2;
+  const int G = P.plan.n_groups, K = P.plan.n_chains, n_items = G + (K + tpb - 1) / tpb;
   const bool keep = (int)gridDim.x >= n_items && (int)blockIdx.x >= G;
   auto owned = [&](auto fn) {
     for (int i = blockIdx.x; i < n_items; i += gridDim.x) {
-      const int k = 2 * (i - G) + ti;
+      const int k = tpb * (i - G) + ti;
       if (i < G || k >= K) continue;
       int idx = 0;
       for_owned(P.plan, k, [&](int v) {

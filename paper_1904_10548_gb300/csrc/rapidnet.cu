@@ -429,7 +429,7 @@ __global__ void k_gather_mixed_y(NetDev<double> nt, const int *perm, int n, cons
 // work-buffer sizes of one precision in one kernel's shared-memory layout
 struct Sizes {
   int team_bytes = 0, net_bytes = 0;  // layout of the block (kernels.cuh)
-  int buf = 0, gbuf = 0, segb = 1, gcap = 0, hchunk = 1, fslots = 1, fbrows = 1;
+  int buf = 0, gbuf = 0, segb = 1, gcap = 0, hchunk = 1, fslots = 1, fbrows = 1, tpb = 2;
 };
 
 struct rn_factor {
@@ -442,7 +442,7 @@ struct rn_factor {
   double W_alpha = 0.0, Ws = 0.0, Wx = 0.0;
   double gamma = 0.0, L = 0.0;
   // launch layout of the FP64 kernel (APG and plain evaluations)
-  int grid = 0, block = 0, maxc = 2;
+  int grid = 0, block = 0, maxc = 2, tw = 64, tpb = 2;
   size_t smem = 0;
   Sizes sz_d{};   // its buffers
   // launch layout of the mixed-precision kernel (FP32 iterations, FP64 steps)
@@ -588,6 +588,7 @@ void set_sizes(KParams<T> &P, const Sizes &z) {
   P.hchunk = z.hchunk;
   P.fslots = z.fslots;
   P.fbrows = z.fbrows;
+  P.tpb = z.tpb;
   P.team_bytes = z.team_bytes;
   P.net_bytes = z.net_bytes;
 }
@@ -694,10 +695,10 @@ int power_iteration(rn_factor *f, int iters, double *L_out) {
 }
 
 // Bytes of one team region for a kernel whose blocks hold a network
-// region of net_bytes and static_smem bytes of static shared memory:
-// enough blocks per SM that every work item gets a resident block (up to
-// 4), split evenly.
-int team_budget(int device, int n_items, int net_bytes, int static_smem, int *team_bytes) {
+// region of net_bytes, tpb team regions and static_smem bytes of static
+// shared memory: enough blocks per SM that every work item gets a
+// resident block (up to 4), split evenly.
+int team_budget(int device, int n_items, int tpb, int net_bytes, int static_smem, int *team_bytes) {
   int sms = 0, optin = 0, per_sm = 0, reserved = 0;
   RN_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
   RN_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
@@ -705,7 +706,7 @@ int team_budget(int device, int n_items, int net_bytes, int static_smem, int *te
   RN_CUDA(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, device));
   const int bpsm = std::max(1, std::min(4, (n_items + sms - 1) / std::max(1, sms)));
   const int budget = std::min(optin, per_sm / bpsm - reserved) - static_smem;
-  const int tb = ((budget - kHdrBytes - net_bytes) / 2) & ~15;
+  const int tb = ((budget - kHdrBytes - net_bytes) / tpb) & ~15;
   if (tb <= 0) {
     set_error("shared memory: the network data leave no room for the work buffers");
     return RN_ERR_UNSUPPORTED;
@@ -715,20 +716,21 @@ int team_budget(int device, int n_items, int net_bytes, int static_smem, int *te
 }
 
 // Work-buffer sizes of elements of eb bytes in team regions of team_bytes
-// for blocks of `block` threads: the team buffer holds the forward slots of
+// for teams of tw threads, tpb to a block: the team buffer holds the forward slots of
 // `mode` (two per warp if they fit, else one) and a backward segment (as
-// many chain rows as fit, up to the longest chain); the group buffer (both
+// many chain rows as fit, up to the longest chain); the group buffer (all
 // regions) holds the group's descriptor, the rows of a whole group if
 // they fit, and as many chain-head rows as the rest allows.
-int fit_sizes(const rn_factor *f, int eb, int team_bytes, int net_bytes, int block, int mode,
+int fit_sizes(const rn_factor *f, int eb, int team_bytes, int net_bytes, int tw, int tpb, int mode,
               Sizes *z) {
   const Plan &p = f->plan;
   const int misc = (int)round16((4 + 2 * kSeg) * sizeof(int));
-  const int nw = block / 64;
+  const int nw = tw / 32;
+  z->tpb = tpb;
   z->team_bytes = team_bytes;
   z->net_bytes = net_bytes;
   z->buf = ((team_bytes - misc) & ~15) / eb - 72;
-  z->gbuf = ((2 * team_bytes - misc) & ~15) / eb - 72;
+  z->gbuf = ((tpb * team_bytes - misc) & ~15) / eb - 72;
   z->fslots = fwd_elems(nw, 2, f->NXP, f->NUP, f->YP, f->SP, mode) <= z->buf ? 2 : 1;
   if (fwd_elems(nw, z->fslots, f->NXP, f->NUP, f->YP, f->SP, mode) > z->buf ||
       chain_back_elems(1, f->SP, f->NEP, f->NXP, f->NUP) > z->buf) {
@@ -1092,7 +1094,10 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
       set_error("network: nx, nu too large for the team width");
       return RN_ERR_UNSUPPORTED;
     }
-    f->block = 2 * tw;
+    // four teams (one block per SM, 16 warps for a group) up to 512 threads
+    f->tpb = tw <= 128 ? 4 : 2;
+    f->tw = tw;
+    f->block = f->tpb * tw;
     f->maxc = comps(tw);
   }
   {
@@ -1100,14 +1105,14 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
     f->net_bytes_d = (int)net_smem_bytes(nx, nu, ne, nnzB, nnzE, 8);
     f->net_bytes_f = (int)net_smem_bytes(nx, nu, ne, nnzB, nnzE, 4);
   }
-  const int n_items = p.n_groups + (p.n_chains + 1) / 2;
+  const int n_items = p.n_groups + (p.n_chains + f->tpb - 1) / f->tpb;
   int sms = 0;
   RN_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, f->device));
   {
     int team_bytes = 0;
-    if ((rc = team_budget(f->device, n_items, f->net_bytes_d, 0, &team_bytes))) return rc;
-    if ((rc = fit_sizes(f, 8, team_bytes, f->net_bytes_d, f->block, 1, &f->sz_d))) return rc;
-    f->smem = kHdrBytes + f->net_bytes_d + 2 * (size_t)team_bytes;
+    if ((rc = team_budget(f->device, n_items, f->tpb, f->net_bytes_d, 0, &team_bytes))) return rc;
+    if ((rc = fit_sizes(f, 8, team_bytes, f->net_bytes_d, f->tw, f->tpb, 1, &f->sz_d))) return rc;
+    f->smem = kHdrBytes + f->net_bytes_d + (size_t)f->tpb * team_bytes;
     int bps1 = 0, bps2 = 0;
     RN_CUDA((solve_occupancy<double, true>(f->maxc, f->block, f->smem, &bps1)));
     RN_CUDA((solve_occupancy<double, false>(f->maxc, f->block, f->smem, &bps2)));
@@ -1124,11 +1129,11 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
     // network region: the FP32 copy, then the header of the FP64 data
     f->net_region_m = f->net_bytes_f + (int)round16(sizeof(NetDev<double>));
     int team_bytes = 0;
-    if ((rc = team_budget(f->device, n_items, f->net_region_m, 0, &team_bytes))) return rc;
-    if ((rc = fit_sizes(f, 4, team_bytes, f->net_region_m, f->block, 2, &f->sz_f)) ||
-        (rc = fit_sizes(f, 8, team_bytes, f->net_bytes_f, f->block, 0, &f->sz_dm)))
+    if ((rc = team_budget(f->device, n_items, f->tpb, f->net_region_m, 0, &team_bytes))) return rc;
+    if ((rc = fit_sizes(f, 4, team_bytes, f->net_region_m, f->tw, f->tpb, 2, &f->sz_f)) ||
+        (rc = fit_sizes(f, 8, team_bytes, f->net_bytes_f, f->tw, f->tpb, 0, &f->sz_dm)))
       return rc;
-    f->smem_mixed = kHdrBytes + f->net_region_m + 2 * (size_t)team_bytes;
+    f->smem_mixed = kHdrBytes + f->net_region_m + (size_t)f->tpb * team_bytes;
     int bpm = 0;
     RN_CUDA(mixed_occupancy(f->maxc, f->block, f->smem_mixed, &bpm));
     if (bpm < 1) {
@@ -1676,7 +1681,7 @@ int batch_impl(rn_factor *const *fs, const rn_solve_req *req, int n, int max_ite
   cudaStream_t bs = fs[0]->stream;
   int rc;
   // per-problem preparation on each handle's stream
-  int checks = 0, maxc = 1, block = 64, net_region = 0, net_f = 0;
+  int checks = 0, maxc = 1, tw = 64, net_region = 0, net_f = 0;
   long long items = 0;
   for (int i = 0; i < n; ++i) {
     rn_factor *f = fs[i];
@@ -1691,13 +1696,13 @@ int batch_impl(rn_factor *const *fs, const rn_solve_req *req, int n, int max_ite
     RN_CUDA(cudaGetLastError());
     if ((rc = reset_sync(f))) return rc;
     RN_CUDA(cudaMemsetAsync(f->res, 0, ck * sizeof(unsigned long long), f->stream));
-    block = std::max(block, f->block);
+    tw = std::max(tw, f->tw);
     net_f = std::max(net_f, f->net_bytes_f);
-    items += f->plan.n_groups + (f->plan.n_chains + 1) / 2;
   }
+  const int tpb = tw <= 128 ? 4 : 2, block = tpb * tw;
+  for (int i = 0; i < n; ++i) items += fs[i]->plan.n_groups + (fs[i]->plan.n_chains + tpb - 1) / tpb;
   net_region = net_f + (int)round16(sizeof(NetDev<double>));
   for (int i = 0; i < n; ++i) RN_CUDA(cudaStreamSynchronize(fs[i]->stream));
-  const int tw = block / 2;
   for (int i = 0; i < n; ++i) {
     const int m = std::max(fs[i]->nx, fs[i]->nu);
     int c = std::max((m + tw - 1) / tw, (fs[i]->nx + 31) / 32);
@@ -1706,15 +1711,15 @@ int batch_impl(rn_factor *const *fs, const rn_solve_req *req, int n, int max_ite
   }
   int static_smem = 0, team_bytes = 0;
   RN_CUDA(batch_static_smem(maxc, &static_smem));
-  if ((rc = team_budget(dev, (int)std::min<long long>(items, 1 << 30), net_region, static_smem,
-                        &team_bytes)))
+  if ((rc = team_budget(dev, (int)std::min<long long>(items, 1 << 30), tpb, net_region,
+                        static_smem, &team_bytes)))
     return rc;
   std::vector<Sizes> szf(n), szd(n);
   for (int i = 0; i < n; ++i)
-    if ((rc = fit_sizes(fs[i], 4, team_bytes, net_region, block, 2, &szf[i])) ||
-        (rc = fit_sizes(fs[i], 8, team_bytes, net_f, block, 0, &szd[i])))
+    if ((rc = fit_sizes(fs[i], 4, team_bytes, net_region, tw, tpb, 2, &szf[i])) ||
+        (rc = fit_sizes(fs[i], 8, team_bytes, net_f, tw, tpb, 0, &szd[i])))
       return rc;
-  const size_t smem = kHdrBytes + net_region + 2 * (size_t)team_bytes;
+  const size_t smem = kHdrBytes + net_region + (size_t)tpb * team_bytes;
   int bps = 0, sms = 0;
   RN_CUDA(batch_occupancy(maxc, block, smem, &bps));
   RN_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -1729,7 +1734,7 @@ int batch_impl(rn_factor *const *fs, const rn_solve_req *req, int n, int max_ite
   ip.reserve(items);
   ic.reserve(items);
   for (int i = 0; i < n; ++i)
-    for (int k = 0; k < fs[i]->plan.n_groups + (fs[i]->plan.n_chains + 1) / 2; ++k) {
+    for (int k = 0; k < fs[i]->plan.n_groups + (fs[i]->plan.n_chains + tpb - 1) / tpb; ++k) {
       ip.push_back(i);
       ic.push_back(k);
     }
@@ -1807,6 +1812,7 @@ int batch_impl(rn_factor *const *fs, const rn_solve_req *req, int n, int max_ite
   B.net_bytes = net_region;
   B.net_bytes_f = net_f;
   B.team_bytes = team_bytes;
+  B.tpb = tpb;
   B.tol = tol > 0.0 ? tol : 0.0;
   RN_CUDA(cudaEventRecord(fs[0]->ev0, bs));
   RN_CUDA(launch_batch(B, maxc, grid, block, smem, bs));

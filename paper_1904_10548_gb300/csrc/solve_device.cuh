@@ -116,7 +116,7 @@ __device__ __forceinline__ unsigned long long abs_bits(float f) {
 // teams, block layout and shared-memory carving
 // ---------------------------------------------------------------------------
 // A team is a warp-aligned set of threads with its own barrier: the block
-// is two teams (one chain each; named barriers 1 and 2) or, for a group,
+// is tpb teams (one chain each; named barriers 1 .. tpb) or, for a group,
 // one team of the whole block (barrier 0).
 struct Team {
   int tid, nt, bar;
@@ -131,19 +131,24 @@ struct Team {
   __device__ __forceinline__ int nwarps() const { return nt >> 5; }
 };
 
-__device__ __forceinline__ Team chain_team() {
-  const int tw = blockDim.x >> 1;
+// a block of tpb chain teams: team t is threads [t tw, (t + 1) tw)
+__device__ __forceinline__ Team chain_team(int tpb) {
+  const int tw = blockDim.x / tpb;
   return Team{(int)threadIdx.x % tw, tw, 1 + (int)threadIdx.x / tw};
 }
 __device__ __forceinline__ Team block_team() { return Team{(int)threadIdx.x, (int)blockDim.x, 0}; }
-__device__ __forceinline__ int team_index() { return (int)threadIdx.x / (int)(blockDim.x >> 1); }
+__device__ __forceinline__ int team_index(int tpb) {
+  return (int)threadIdx.x / (int)(blockDim.x / tpb);
+}
 
-// [header | network copy | team 0 | team 1]
+// [header | network copy | team 0 | team 1 | ...]
 struct BlockMem {
   unsigned long long *redu;  // 40 words for block reductions
   int *bflag;                // 8 block-wide flags
   unsigned char *net_raw;
-  unsigned char *team_raw[2];
+  unsigned char *team0;
+  int team_bytes;
+  __device__ __forceinline__ unsigned char *team_raw(int t) const { return team0 + (size_t)t * team_bytes; }
 };
 
 __device__ __forceinline__ BlockMem block_mem(unsigned char *raw, int net_bytes, int team_bytes) {
@@ -151,8 +156,8 @@ __device__ __forceinline__ BlockMem block_mem(unsigned char *raw, int net_bytes,
   b.redu = reinterpret_cast<unsigned long long *>(raw);
   b.bflag = reinterpret_cast<int *>(raw + 40 * sizeof(unsigned long long));
   b.net_raw = raw + kHdrBytes;
-  b.team_raw[0] = raw + kHdrBytes + net_bytes;
-  b.team_raw[1] = b.team_raw[0] + team_bytes;
+  b.team0 = raw + kHdrBytes + net_bytes;
+  b.team_bytes = team_bytes;
   return b;
 }
 
@@ -1116,20 +1121,20 @@ static __device__ void final_node(const MixedParams &M, int v) {
 // ---------------------------------------------------------------------------
 // one evaluation of the dual gradient (with the per-node step of MODE) by a
 // block whose items are i = blockIdx.x, blockIdx.x + gridDim.x, ...: items
-// below n_groups are groups (whole block), the rest pairs of chains (one
-// per team).  Phases: chain heads, groups, the chains' local parts, the
-// forward sweeps.  keep: the block holds one chain pair and no group.
+// below n_groups are groups (whole block), the rest sets of tpb chains
+// (one per team).  Phases: chain heads, groups, the chains' local parts,
+// the forward sweeps.  keep: the block holds one chain set and no group.
 // False (for the calling team) on timeout.
 // ---------------------------------------------------------------------------
 template <typename T, int MODE, int C>
 __device__ bool eval_step(const KParams<T> &P, FwdCtx<T> &c, const MixedDev *mx,
                           const Smem<T> &smc, const Smem<T> &smg, const Team &tc,
                           const Team &tb, unsigned step, bool keep) {
-  const int G = P.plan.n_groups, K = P.plan.n_chains;
-  const int n_items = G + (K + 1) / 2, team = team_index();
+  const int G = P.plan.n_groups, K = P.plan.n_chains, tpb = P.tpb;
+  const int n_items = G + (K + tpb - 1) / tpb, team = team_index(tpb);
   bool ok = true;
   for (int i = blockIdx.x; i < n_items; i += gridDim.x) {
-    const int k = 2 * (i - G) + team;
+    const int k = tpb * (i - G) + team;
     if (i >= G && k < K) chain_head<T, C>(P, k, smc, tc);
   }
   for (int i = blockIdx.x; i < G; i += gridDim.x) {
@@ -1137,11 +1142,11 @@ __device__ bool eval_step(const KParams<T> &P, FwdCtx<T> &c, const MixedDev *mx,
     if (!group_step<T>(P, i, smg, tb, step)) ok = false;
   }
   for (int i = blockIdx.x; i < n_items; i += gridDim.x) {
-    const int k = 2 * (i - G) + team;
+    const int k = tpb * (i - G) + team;
     if (i >= G && k < K) chain_rest<T, C>(P, k, smc, tc, keep);
   }
   for (int i = blockIdx.x; i < n_items && ok; i += gridDim.x) {
-    const int k = 2 * (i - G) + team;
+    const int k = tpb * (i - G) + team;
     if (i >= G && k < K) ok = chain_forward<T, MODE, C>(P, k, c, smc, tc, mx, step);
   }
   return ok;

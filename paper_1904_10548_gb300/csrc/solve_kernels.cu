@@ -54,10 +54,10 @@ __global__ void __launch_bounds__(512) k_solve(KParams<T> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const BlockMem bm = block_mem(smem_raw, P.net_bytes, P.team_bytes);
   const NetDev<T> *net = stage_net(P.net, bm.net_raw);
-  const Team tc = chain_team(), tb = block_team();
-  const Smem<T> smc = carve<T>(bm.team_raw[team_index()], P.buf_elems, net);
-  const Smem<T> smg = carve<T>(bm.team_raw[0], P.gbuf_elems, net);
-  const int G = P.plan.n_groups, n_items = G + (P.plan.n_chains + 1) / 2;
+  const Team tc = chain_team(P.tpb), tb = block_team();
+  const Smem<T> smc = carve<T>(bm.team_raw(team_index(P.tpb)), P.buf_elems, net);
+  const Smem<T> smg = carve<T>(bm.team_raw(0), P.gbuf_elems, net);
+  const int G = P.plan.n_groups, n_items = G + (P.plan.n_chains + P.tpb - 1) / P.tpb;
   const bool keep = (int)gridDim.x >= n_items && (int)blockIdx.x >= G;
   int it = 0, ci = 0, reason = 0;  // reason: 0 max iters, 1 converged, 2 non-finite, 3 timeout
   for (; it < P.iters; ++it) {
