@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(512) k_batch(BatchDev B) {
     if (check) {
       // per problem: block maximum, then one grid barrier for all
       for (int s = 0; s < bc.n; ++s) {
-        const unsigned long long r = block_max_u64(rb_local[s], bm.redu);
+        const unsigned long long r = block_max_u64(widen_bits(rb_local[s]), bm.redu);
         if (threadIdx.x == 0 && bc.active[s]) atomicMax(B.probs[bc.prob[s]].f.st.res + ci, r);
       }
       if (threadIdx.x == 0) {

@@ -25,6 +25,7 @@ namespace rn {
 
 constexpr int kSeg = 16;                    // ints of a team's node list (halved)
 constexpr long long kWaitNs = 2000000000LL; // bound of every device-side wait (2 s)
+constexpr int kChildSlotsDev = 8;           // children per node in a group's children table
 
 template <typename T>
 struct NetDev {
@@ -37,6 +38,7 @@ struct NetDev {
   // E by rows (mixing node r -> flows) and by columns (flow j -> mixing nodes)
   const int *Er_ptr, *Er_idx;
   const T *Er_val;
+  const T *Erw_val;  // E_rj W^-1_jj, aligned with Er_val
   const int *Ec_ptr, *Ec_idx;
   const T *Ec_val;
   const T *winv;  // diagonal of W_u^{-1}
@@ -82,7 +84,7 @@ struct KParams {
   int segb;         // chain rows per backward segment
   int gcap;         // group rows held in shared memory
   int hchunk;       // chain-head rows staged at once by a group
-  int fslots;       // staged nodes per warp in the forward sweep (1 or 2)
+  int fslots;       // staged nodes per warp in the forward sweep (1 to 3)
   int fbrows;       // group rows per batch of the F application
   int tpb;          // chain teams per block
   int team_bytes;   // bytes of one team region
@@ -194,7 +196,7 @@ inline size_t team_region_bytes(int buf_elems) {
 __host__ __device__ inline size_t net_smem_bytes(int nx, int nu, int ne, int nnzB, int nnzE,
                                                  int elem) {
   const size_t ints = (size_t)(nu + 1) + nnzB + (nx + 1) + nnzB + (ne + 1) + nnzE + (nu + 1) + nnzE;
-  const size_t vals = 2 * (size_t)nnzB + 2 * (size_t)nnzE + nu + (size_t)ne * ne + 3 * nx + 2 * nu;
+  const size_t vals = 2 * (size_t)nnzB + 3 * (size_t)nnzE + nu + (size_t)ne * ne + 3 * nx + 2 * nu;
   return round16(sizeof(NetDev<double>)) + round16(ints * 4) + round16(vals * elem);
 }
 

@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(512) k_mixed(MixedParams M) {
       break;
     }
     if (check) {
-      if (!grid_check(bm, c.rbits, P.st.res, P.st.barrier, ci, P.st.err)) {
+      if (!grid_check(bm, widen_bits(c.rbits), P.st.res, P.st.barrier, ci, P.st.err)) {
         ok = false;
         reason = 3;
         ++it;

@@ -277,7 +277,29 @@ int build_plan(const rn_tree *t, Plan &p) {
     d[3] = ncn;
     for (int li = 0; li < m; ++li)
       if (p.cc_ptr[g0 + li + 1] > p.cc_ptr[g0 + li]) d.push_back(li);
+    // children table (16-byte aligned): per node kChildSlots entries, chain
+    // heads first (-2 - head position), then top children (local index),
+    // -1 for none; a node with more children makes the whole group use
+    // the lists above instead (flag in the word after the table offset)
     while (d.size() % 4) d.push_back(0);
+    const int tab = (int)d.size() + 4;
+    bool fits = true;
+    for (int li = 0; li < m; ++li) {
+      const int nc = (p.cc_ptr[g0 + li + 1] - p.cc_ptr[g0 + li]) + (p.tc_ptr[g0 + li + 1] - p.tc_ptr[g0 + li]);
+      if (nc > kChildSlots) fits = false;
+    }
+    d.push_back(tab);
+    d.push_back(fits ? 1 : 0);
+    d.push_back(0);
+    d.push_back(0);
+    for (int li = 0; li < m; ++li) {
+      int k = 0;
+      for (int c = p.cc_ptr[g0 + li]; c < p.cc_ptr[g0 + li + 1] && k < kChildSlots; ++c, ++k)
+        d.push_back(-2 - (p.cc[c] - c0));
+      for (int c = p.tc_ptr[g0 + li]; c < p.tc_ptr[g0 + li + 1] && k < kChildSlots; ++c, ++k)
+        d.push_back(p.tc[c] - g0);
+      for (; k < kChildSlots; ++k) d.push_back(-1);
+    }
     p.max_desc = std::max(p.max_desc, (int)d.size());
     p.g_desc.insert(p.g_desc.end(), d.begin(), d.end());
     p.g_desc_ptr.push_back((int)p.g_desc.size());

@@ -20,6 +20,7 @@
 #include "rn_internal.h"
 
 using namespace rn;
+static_assert(kChildSlots == kChildSlotsDev, "children table width differs between host and device");
 
 // ---------------------------------------------------------------------------
 // helper kernels (FP64)
@@ -717,7 +718,7 @@ int team_budget(int device, int n_items, int tpb, int net_bytes, int static_smem
 
 // Work-buffer sizes of elements of eb bytes in team regions of team_bytes
 // for teams of tw threads, tpb to a block: the team buffer holds the forward slots of
-// `mode` (two per warp if they fit, else one) and a backward segment (as
+// `mode` (up to three per warp) and a backward segment (as
 // many chain rows as fit, up to the longest chain); the group buffer (all
 // regions) holds the group's descriptor, the rows of a whole group if
 // they fit, and as many chain-head rows as the rest allows.
@@ -731,7 +732,9 @@ int fit_sizes(const rn_factor *f, int eb, int team_bytes, int net_bytes, int tw,
   z->net_bytes = net_bytes;
   z->buf = ((team_bytes - misc) & ~15) / eb - 72;
   z->gbuf = ((tpb * team_bytes - misc) & ~15) / eb - 72;
-  z->fslots = fwd_elems(nw, 2, f->NXP, f->NUP, f->YP, f->SP, mode) <= z->buf ? 2 : 1;
+  z->fslots = 3;
+  while (z->fslots > 1 && fwd_elems(nw, z->fslots, f->NXP, f->NUP, f->YP, f->SP, mode) > z->buf)
+    --z->fslots;
   if (fwd_elems(nw, z->fslots, f->NXP, f->NUP, f->YP, f->SP, mode) > z->buf ||
       chain_back_elems(1, f->SP, f->NEP, f->NXP, f->NUP) > z->buf) {
     set_error("shared memory: the network is too large for the work buffers");
@@ -928,7 +931,9 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
   field = dp;
   UP_I(nt.Bc_ptr, Bc.ptr) UP_I(nt.Bc_idx, Bc.idx) UP_D(nt.Bc_val, Bc.val)
   UP_I(nt.Br_ptr, Br.ptr) UP_I(nt.Br_idx, Br.idx) UP_D(nt.Br_val, Br.val)
-  UP_I(nt.Er_ptr, Er.ptr) UP_I(nt.Er_idx, Er.idx) UP_D(nt.Er_val, Er.val)
+  std::vector<double> Erw(Er.val.size());
+  for (size_t e = 0; e < Er.val.size(); ++e) Erw[e] = Er.val[e] * winv[Er.idx[e]];
+  UP_I(nt.Er_ptr, Er.ptr) UP_I(nt.Er_idx, Er.idx) UP_D(nt.Er_val, Er.val) UP_D(nt.Erw_val, Erw)
   UP_I(nt.Ec_ptr, Ec.ptr) UP_I(nt.Ec_idx, Ec.idx) UP_D(nt.Ec_val, Ec.val)
   UP_D(nt.winv, winv) UP_D(nt.Sinv, Sinv)
   UP_D(nt.xmin, std::vector<double>(net->xmin, net->xmin + nx))
@@ -1036,6 +1041,7 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
   if ((rc = upload(f, &fp, vec))) return rc; \
   field = fp;
     UP_F(nf.Bc_val, tofv(Bc.val)) UP_F(nf.Br_val, tofv(Br.val)) UP_F(nf.Er_val, tofv(Er.val))
+    UP_F(nf.Erw_val, tofv(Erw))
     UP_F(nf.Ec_val, tofv(Ec.val)) UP_F(nf.winv, tofv(winv)) UP_F(nf.Sinv, tofv(Sinv))
     UP_F(nf.xmin, tof(net->xmin, nx)) UP_F(nf.xmax, tof(net->xmax, nx)) UP_F(nf.xs, tof(net->xs, nx))
     UP_F(nf.umin, tof(net->umin, nu)) UP_F(nf.umax, tof(net->umax, nu))

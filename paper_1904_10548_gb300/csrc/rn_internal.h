@@ -9,6 +9,8 @@
 
 namespace rn {
 
+constexpr int kChildSlots = 8;  // children per node in a group's children table
+
 // thread-local error message behind rapidnet_last_error()
 void set_error(const char *fmt, ...);
 void clear_error();
@@ -57,7 +59,10 @@ struct Plan {
   // padded to a multiple of 4 ints:
   //   m, nl, nch, ncn | lvl[nl + 1] | par[m] (-1: the root) |
   //   tcp[m + 1], tcl[..] (top children) | ccp[m + 1], ccl[..] (chain children) |
-  //   cn[ncn] (the nodes with chain children)
+  //   cn[ncn] (the nodes with chain children) | pad to 4 | tab, fits, 0, 0 |
+  //   children table at desc + tab: per node kChildSlots entries, chain heads
+  //   first (-2 - head position), then top children (local index), -1 none;
+  //   fits = 0 when some node has more children (the lists are used then)
   std::vector<int> g_desc_ptr, g_desc;
   int max_desc = 0;
   // top nodes (indexed by internal index 0..n_top): top children and

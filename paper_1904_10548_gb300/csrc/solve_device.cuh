@@ -108,8 +108,13 @@ __device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v
 __device__ __forceinline__ unsigned long long abs_bits(double d) {
   return (unsigned long long)__double_as_longlong(d) & 0x7fffffffffffffffULL;
 }
+// bits of |f| for an FP32 value (monotone in |f| as well); the FP32 path
+// keeps its running maximum in these and widens it once per check
 __device__ __forceinline__ unsigned long long abs_bits(float f) {
-  return abs_bits((double)f);
+  return (unsigned long long)(__float_as_uint(f) & 0x7fffffffu);
+}
+__device__ __forceinline__ unsigned long long widen_bits(unsigned long long fbits) {
+  return abs_bits((double)__uint_as_float((unsigned)fbits));
 }
 
 // ---------------------------------------------------------------------------
@@ -272,26 +277,16 @@ __device__ void apply_F(const NetDev<T> &nt, int m, RowF row, const T *i2p, T *e
                         const Team &tm) {
   const int ne = nt.ne, nu = nt.nu, NXP = nt.NXP, NEP = nt.NEP;
   const int *Er_ptr = nt.Er_ptr, *Er_idx = nt.Er_idx, *Ec_ptr = nt.Ec_ptr, *Ec_idx = nt.Ec_idx;
-  const T *Er_val = nt.Er_val, *Ec_val = nt.Ec_val, *winv = nt.winv, *Sinv = nt.Sinv;
+  const T *Erw_val = nt.Erw_val, *Ec_val = nt.Ec_val, *winv = nt.winv, *Sinv = nt.Sinv;
   if (ne > 0) {
     const Map2 a = map2(tm, ne);
     for (int r = a.c0; r < ne; r += a.cw) {
       Slice<T, 6> er;
-      er.load(Er_ptr, Er_idx, Er_val, r);
-      T wv[6];
-#pragma unroll
-      for (int k = 0; k < 6; ++k) wv[k] = winv[er.idx[k]];
+      er.load(Er_ptr, Er_idx, Erw_val, r);
 #pragma unroll 2
       for (int q = a.r0; q < m; q += a.rs) {
         const T *g = row(q) + NXP;
-        T acc = T(0);
-#pragma unroll
-        for (int k = 0; k < 6; ++k)
-          if (k < er.n) acc += er.val[k] * (wv[k] * g[er.idx[k]]);
-        for (int e = 6; e < er.n; ++e) {
-          const int j = Er_idx[er.p + e];
-          acc += Er_val[er.p + e] * (winv[j] * g[j]);
-        }
+        const T acc = er.dot(T(0), [&](int j) { return g[j]; }, Er_idx, Erw_val);
         eb[q * NEP + r] = acc;
       }
     }
@@ -349,7 +344,8 @@ __device__ const NetDev<T> *stage_net(const NetDev<T> &g, unsigned char *raw, bo
   const size_t nints = (size_t)(nu + 1) + nnzB + (nx + 1) + nnzB + (ne + 1) + nnzE + (nu + 1) + nnzE;
   T *vp = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(ip) + round16(nints * 4));
   T *Bc_val = vp, *Br_val = Bc_val + nnzB, *Er_val = Br_val + nnzB, *Ec_val = Er_val + nnzE;
-  T *winv = Ec_val + nnzE, *Sinv = winv + nu, *xmin = Sinv + (size_t)ne * ne, *xmax = xmin + nx;
+  T *Erw_val = Ec_val + nnzE;
+  T *winv = Erw_val + nnzE, *Sinv = winv + nu, *xmin = Sinv + (size_t)ne * ne, *xmax = xmin + nx;
   T *xs = xmax + nx, *umin = xs + nx, *umax = umin + nu;
   const int tid = threadIdx.x, bd = blockDim.x;
   auto cpi = [&](int *dst, const int *src, int m) {
@@ -369,6 +365,7 @@ __device__ const NetDev<T> *stage_net(const NetDev<T> &g, unsigned char *raw, bo
   cpv(Bc_val, g.Bc_val, nnzB);
   cpv(Br_val, g.Br_val, nnzB);
   cpv(Er_val, g.Er_val, nnzE);
+  cpv(Erw_val, g.Erw_val, nnzE);
   cpv(Ec_val, g.Ec_val, nnzE);
   cpv(winv, g.winv, nu);
   cpv(Sinv, g.Sinv, ne * ne);
@@ -388,6 +385,7 @@ __device__ const NetDev<T> *stage_net(const NetDev<T> &g, unsigned char *raw, bo
     s->Er_ptr = Er_ptr;
     s->Er_idx = Er_idx;
     s->Er_val = Er_val;
+    s->Erw_val = Erw_val;
     s->Ec_ptr = Ec_ptr;
     s->Ec_idx = Ec_idx;
     s->Ec_val = Ec_val;
@@ -410,7 +408,7 @@ struct FwdCtx {
   T *yprv;
   T beta, beta_n;
   bool write_out;
-  unsigned long long rbits;  // running max of |y+ - w| (bits)
+  unsigned long long rbits;  // running max of |y+ - w| (abs_bits of T)
 };
 
 // Dual update at one node by one warp: y+ = prox_{gamma g*}(w + gamma H x)
@@ -807,10 +805,14 @@ __device__ bool group_step(const KParams<T> &P, int g, const Smem<T> &sm, const 
   }
   for (int e = tm.tid; e < dn / 4; e += tm.nt) cp16(desc + 4 * e, pl.g_desc + d0 + 4 * e, false);
   const int nch = c1 - c0;
+  // chain heads: all at once (added in the first backward pass below), or
+  // in chunks added to their parents first
+  const bool heads_all = nch <= hchunk;
   for (int h0 = 0; h0 < nch; h0 += hchunk) {
     const int h1 = nch - h0 < hchunk ? nch : h0 + hchunk;
     if (h0 > 0) tm.sync();
     stage_span(H, P.st.up + (size_t)(c0 + h0) * SP, (h1 - h0) * SP, tm, true);
+    if (heads_all) break;
     cp_wait();
     tm.sync();
     const int nl = desc[1], ncn = desc[3];
@@ -854,15 +856,91 @@ __device__ bool group_step(const KParams<T> &P, int g, const Smem<T> &sm, const 
   tm.sync();
   const int nl = desc[1];
   const int *lvl = desc + 4, *par = lvl + nl + 1, *tcp = par + m, *tcl = tcp + m + 1;
+  const int *ccp = tcl + tcp[m], *ccl = ccp + m + 1;
+  // children table (one row of kChildSlotsDev references per node)
+  const int *cn_end = ccl + ccp[m] + desc[3];
+  const int thdr = round4((int)(cn_end - desc));
+  const int *ctab = desc + desc[thdr];
+  const bool table = desc[thdr + 1] != 0 && heads_all;
   // backward over the levels, deepest first
   for (int l = nl - 1; l >= 0; --l) {
     const int a = lvl[l], b = lvl[l + 1];
+    if (table) {
+      // four nodes per thread at a time: all child references, then all
+      // child values, then the sums (no store before the last load)
+      constexpr int NB = 4;
+      for (int i = mx.c0; i < nx; i += mx.cw) {
+        for (int l0 = a + mx.r0; l0 < b; l0 += NB * mx.rs) {
+          T acc[NB];
+#pragma unroll
+          for (int k = 0; k < NB; ++k) {
+            const int li = l0 + k * mx.rs;
+            acc[k] = T(0);
+            if (li < b) {
+              const int4 c0v = reinterpret_cast<const int4 *>(ctab + li * kChildSlotsDev)[0];
+              const int4 c1v = reinterpret_cast<const int4 *>(ctab + li * kChildSlotsDev)[1];
+              const int cr[8] = {c0v.x, c0v.y, c0v.z, c0v.w, c1v.x, c1v.y, c1v.z, c1v.w};
+              T v = rb[(size_t)li * SP + i];
+#pragma unroll
+              for (int e = 0; e < 8; ++e) {
+                const int x = cr[e];
+                if (x != -1) v += x >= 0 ? rb[(size_t)x * SP + i] : H[(size_t)(-2 - x) * SP + i];
+              }
+              acc[k] = v;
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < NB; ++k) {
+            const int li = l0 + k * mx.rs;
+            if (li < b) rb[(size_t)li * SP + i] = acc[k];
+          }
+        }
+      }
+      tm.sync();
+      for (int j = mu.c0; j < nu; j += mu.cw) {
+        Slice<T, 2> bc;
+        bc.load(Bc_ptr, Bc_idx, Bc_val, j);
+        for (int l0 = a + mu.r0; l0 < b; l0 += NB * mu.rs) {
+          T acc[NB];
+#pragma unroll
+          for (int k = 0; k < NB; ++k) {
+            const int li = l0 + k * mu.rs;
+            acc[k] = T(0);
+            if (li < b) {
+              const int4 c0v = reinterpret_cast<const int4 *>(ctab + li * kChildSlotsDev)[0];
+              const int4 c1v = reinterpret_cast<const int4 *>(ctab + li * kChildSlotsDev)[1];
+              const int cr[8] = {c0v.x, c0v.y, c0v.z, c0v.w, c1v.x, c1v.y, c1v.z, c1v.w};
+              const T *r = rb + (size_t)li * SP;
+              T v = r[NXP + j];
+              // heads (negative references) before B' lambda, top children after
+#pragma unroll
+              for (int e = 0; e < 8; ++e)
+                if (cr[e] < -1) v += H[(size_t)(-2 - cr[e]) * SP + NXP + j];
+              v = bc.dot(v, [&](int t) { return r[t]; }, Bc_idx, Bc_val);
+#pragma unroll
+              for (int e = 0; e < 8; ++e)
+                if (cr[e] >= 0) v += rb[(size_t)cr[e] * SP + NXP + j];
+              acc[k] = v;
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < NB; ++k) {
+            const int li = l0 + k * mu.rs;
+            if (li < b) rb[(size_t)li * SP + NXP + j] = acc[k];
+          }
+        }
+      }
+      tm.sync();
+      continue;
+    }
 #pragma unroll 2
     for (int li = a + mx.r0; li < b; li += mx.rs) {
       T *r = rb + (size_t)li * SP;
       const int ts = tcp[li], te = tcp[li + 1];
+      const int cs = heads_all ? ccp[li] : 0, ce = heads_all ? ccp[li + 1] : 0;
       for (int i = mx.c0; i < nx; i += mx.cw) {
         T acc = r[i];
+        for (int c = cs; c < ce; ++c) acc += H[(size_t)ccl[c] * SP + i];
         for (int c = ts; c < te; ++c) acc += rb[(size_t)tcl[c] * SP + i];
         r[i] = acc;
       }
@@ -875,7 +953,10 @@ __device__ bool group_step(const KParams<T> &P, int g, const Smem<T> &sm, const 
       for (int li = a + mu.r0; li < b; li += mu.rs) {
         T *r = rb + (size_t)li * SP;
         const int ts = tcp[li], te = tcp[li + 1];
-        T acc = bc.dot(r[NXP + j], [&](int t) { return r[t]; }, Bc_idx, Bc_val);
+        const int cs = heads_all ? ccp[li] : 0, ce = heads_all ? ccp[li + 1] : 0;
+        T acc = r[NXP + j];
+        for (int c = cs; c < ce; ++c) acc += H[(size_t)ccl[c] * SP + NXP + j];
+        acc = bc.dot(acc, [&](int t) { return r[t]; }, Bc_idx, Bc_val);
         for (int c = ts; c < te; ++c) acc += rb[(size_t)tcl[c] * SP + NXP + j];
         r[NXP + j] = acc;
       }
@@ -892,29 +973,55 @@ __device__ bool group_step(const KParams<T> &P, int g, const Smem<T> &sm, const 
   }
   tm.sync();
   // forward over the levels: Z_v = Z_a(v) + z_v, x_v = x_a(v) + B u_v + Gd d_v
+  // (four nodes per thread at a time: loads, then sums, then stores)
+  constexpr int NF = 4;
   for (int l = 0; l < nl; ++l) {
     const int a = lvl[l], b = lvl[l + 1];
-#pragma unroll 2
-    for (int li = a + mu.r0; li < b; li += mu.rs) {
-      const int pa = par[li];
-      if (pa < 0) continue;
-      T *r = rb + (size_t)li * SP;
-      const T *rp = rb + (size_t)pa * SP;
-      for (int j = mu.c0; j < nu; j += mu.cw) r[NXP + j] += rp[NXP + j];
+    for (int j = mu.c0; j < nu; j += mu.cw) {
+      for (int l0 = a + mu.r0; l0 < b; l0 += NF * mu.rs) {
+        T zv[NF];
+#pragma unroll
+        for (int k = 0; k < NF; ++k) {
+          const int li = l0 + k * mu.rs;
+          zv[k] = T(0);
+          if (li < b) {
+            const int pa = par[li];
+            const T own = rb[(size_t)li * SP + NXP + j];
+            zv[k] = pa >= 0 ? own + rb[(size_t)pa * SP + NXP + j] : own;
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < NF; ++k) {
+          const int li = l0 + k * mu.rs;
+          if (li < b) rb[(size_t)li * SP + NXP + j] = zv[k];
+        }
+      }
     }
     tm.sync();
     for (int i = mx.c0; i < nx; i += mx.cw) {
       Slice<T, 6> br;
       br.load(Br_ptr, Br_idx, Br_val, i);
-#pragma unroll 2
-      for (int li = a + mx.r0; li < b; li += mx.rs) {
-        const int pa = par[li], v = g0 + li;
-        T *r = rb + (size_t)li * SP;
-        T acc = pa >= 0 ? rb[(size_t)pa * SP + i] : (data ? P.st.xroot[i] : T(0));
-        if (data) acc += P.st.gb[(size_t)v * NXP + i];
-        const T *ubv = P.st.ub + (size_t)v * NUP;
-        r[i] = br.dot(acc, [&](int t) { return (data ? ubv[t] : T(0)) - r[NXP + t]; }, Br_idx,
-                      Br_val);
+      for (int l0 = a + mx.r0; l0 < b; l0 += NF * mx.rs) {
+        T xv[NF];
+#pragma unroll
+        for (int k = 0; k < NF; ++k) {
+          const int li = l0 + k * mx.rs;
+          xv[k] = T(0);
+          if (li < b) {
+            const int pa = par[li], v = g0 + li;
+            const T *r = rb + (size_t)li * SP;
+            T acc = pa >= 0 ? rb[(size_t)pa * SP + i] : (data ? P.st.xroot[i] : T(0));
+            if (data) acc += P.st.gb[(size_t)v * NXP + i];
+            const T *ubv = P.st.ub + (size_t)v * NUP;
+            xv[k] = br.dot(acc, [&](int t) { return (data ? ubv[t] : T(0)) - r[NXP + t]; }, Br_idx,
+                           Br_val);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < NF; ++k) {
+          const int li = l0 + k * mx.rs;
+          if (li < b) rb[(size_t)li * SP + i] = xv[k];
+        }
       }
     }
     tm.sync();
@@ -941,8 +1048,8 @@ __device__ bool group_step(const KParams<T> &P, int g, const Smem<T> &sm, const 
 // ---------------------------------------------------------------------------
 // forward sweep of chain k after its group: the top nodes it owns, then its
 // own nodes.  Warp w takes nodes w, w + nw, ...; it stages a node's rows
-// into one of its P.fslots slots (the next node's copies in flight while
-// it works on the current one), forms (x | u) in place from the published
+// into one of its P.fslots slots (the copies of the next nodes in flight
+// while it works on the current one), forms (x | u) in place from the published
 // (x | Z) of a top node (u = ub - Z) or from the chain's local sums, then
 //   MODE 0 writes the outputs of a plain step,
 //   MODE 1 the dual update, MODE 2 the dual update in delta form.
@@ -969,8 +1076,7 @@ __device__ bool chain_forward(const KParams<T> &P, int k, FwdCtx<T> &c, const Sm
   const int lane = tm.lane(), warp = tm.warp(), nw = tm.nwarps(), S = P.fslots;
   T *xp = sm.buf, *Zp = xp + NXP, *BZ = Zp + NUP;
   const int fpn = fwd_elems_per_node(NXP, NUP, YP, SP, MODE);
-  T *slot0 = sm.buf + round4(2 * NXP + NUP) + (size_t)warp * S * fpn;
-  T *slot1 = slot0 + (size_t)(S - 1) * fpn;
+  T *slots = sm.buf + round4(2 * NXP + NUP) + (size_t)warp * S * fpn;
   if (g >= 0) {
     if (tm.tid == 0) sm.flag[1] = spin_geq(P.st.flags + g, step + 1u, P.st.err);
     tm.sync();
@@ -1013,22 +1119,21 @@ __device__ bool chain_forward(const KParams<T> &P, int k, FwdCtx<T> &c, const Sm
     }
     cp_commit();
   };
-  if (warp < K) issue(warp, slot0);
+  // ring of S slots per warp: node t of the warp (q = warp + t nw) lives
+  // in slot t % S; up to S - 1 nodes ahead are in flight
+  int issued = 0;
+  for (; issued < S && warp + issued * nw < K; ++issued)
+    issue(warp + issued * nw, slots + (size_t)issued * fpn);
   int t = 0;
   for (int q = warp; q < K; q += nw, ++t) {
-    T *r = (t & 1) ? slot1 : slot0;
-    const int qn = q + nw;
-    if (S == 2) {
-      if (qn < K) {
-        issue(qn, (t & 1) ? slot0 : slot1);
-        cp_wait_group<1>();
-      } else {
-        cp_wait_group<0>();
-      }
-    } else {
-      if (t > 0) issue(q, slot0);
+    T *r = slots + (size_t)(t % S) * fpn;
+    const int ahead = issued - t - 1;  // groups allowed to stay pending
+    if (ahead >= 2)
+      cp_wait_group<2>();
+    else if (ahead == 1)
+      cp_wait_group<1>();
+    else
       cp_wait_group<0>();
-    }
     __syncwarp();
     const int v = node_of(q);
     if (q < nown) {
@@ -1060,6 +1165,11 @@ __device__ bool chain_forward(const KParams<T> &P, int k, FwdCtx<T> &c, const Sm
       }
     }
     __syncwarp();
+    const int qn = warp + issued * nw;
+    if (qn < K) {
+      issue(qn, r);
+      ++issued;
+    }
   }
   tm.sync();
   return true;
