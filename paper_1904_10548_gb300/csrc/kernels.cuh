@@ -49,8 +49,9 @@ struct NetDev {
 
 // the work schedule (rn::Plan) on the device
 struct PlanDev {
-  int n, n_top, n_chains, n_groups;
+  int n, n_top, n_chains, n_groups, n_roots;
   const int *parent;
+  const int *g_root, *g_hp, *r_node, *r_part, *r_hp;  // parts of split stage-1 subtrees, roots
   const int *g_node, *g_chain, *g_lvl, *lvl, *g_ccn, *ccn;
   const int *g_desc_ptr, *g_desc;  // per-group descriptors (rn::Plan)
   const int *tc_ptr, *tc, *cc_ptr, *cc;
@@ -60,11 +61,12 @@ struct PlanDev {
 template <typename T>
 struct StateDev {
   T *s, *ya, *yb, *ub, *gb, *z, *up, *ux, *uo, *xo;
+  T *hp;            // [hp_rows][SP]: sums (lambda | ghat) at the top nodes of the parts
   float *uo32, *xo32;  // optional FP32 copies of uo / xo (plain step)
   const T *inv2p;   // 1 / (2 p) per internal node
   const T *xroot;   // x0 (nx); unused when linear
   const double *beta;  // beta_0 .. beta_iters (APG)
-  unsigned *count, *flags, *barrier;  // per group: chain arrivals, completion; grid
+  unsigned *count, *flags, *barrier;  // per group, then per root: arrivals, completion; grid
   unsigned long long *res;  // per check: bits of the non-negative residual
   int *err;                 // 0 ok, 1 timeout
   int *info;                // [iters done, checks done, stop reason]

@@ -52,7 +52,7 @@ Csr dense_to_csc(const double *M, int rows, int cols) {
   return c;
 }
 
-int build_plan(const rn_tree *t, Plan &p) {
+int build_plan(const rn_tree *t, Plan &p, int max_groups) {
   if (!t || !t->stage_ptr || !t->anc || !t->prob) {
     set_error("tree: NULL pointer");
     return RN_ERR_INVAL;
@@ -134,14 +134,20 @@ int build_plan(const rn_tree *t, Plan &p) {
   p.perm[0] = 0;
   p.iperm[0] = 0;
   int next = 1;
-  // groups: breadth-first over the top nodes below each stage-1 top node
+  // groups: breadth-first over the top nodes below each stage-1 top node.
+  // A large stage-1 subtree whose stage-1 node has two or more top children
+  // and no chain child is split: its top children are bundled into parts
+  // (as many as max_groups leaves room for), each part a group, and the
+  // stage-1 node becomes a *root*, summed by the last of its parts to
+  // finish; roots follow all groups in the internal order.
   p.g_node.push_back(1);
   p.g_lvl.push_back(0);
-  std::vector<int> group_of(n, -1);
-  for (int b1 = sp[1]; b1 < sp[2]; ++b1) {
-    if (leaves[b1] < 2) continue;
+  std::vector<int> group_of(n, -1), root_orig;
+  auto add_group = [&](const std::vector<int> &tops, int root, int hp0) {
     const int g = p.n_groups++;
-    std::vector<int> level{b1};
+    p.g_root.push_back(root);
+    p.g_hp.push_back(hp0);
+    std::vector<int> level = tops;
     while (!level.empty()) {
       p.lvl.push_back(next);
       std::vector<int> below;
@@ -158,7 +164,58 @@ int build_plan(const rn_tree *t, Plan &p) {
     p.g_lvl.push_back((int)p.lvl.size());
     p.g_node.push_back(next);
     p.max_group = std::max(p.max_group, p.g_node[g + 1] - p.g_node[g]);
+  };
+  std::vector<int> subtree_top(n, 0);  // top nodes in each subtree
+  for (int v = n - 1; v >= 1; --v) {
+    if (leaves[v] >= 2) subtree_top[v] += 1;
+    if (t->anc[v] > 0) subtree_top[t->anc[v]] += subtree_top[v];
   }
+  std::vector<int> stage1, splittable;
+  for (int b1 = sp[1]; b1 < sp[2]; ++b1) {
+    if (leaves[b1] < 2) continue;
+    stage1.push_back(b1);
+    int tops = 0, chains = 0;
+    for (int c = first_child[b1]; c < first_child[b1] + nchild[b1]; ++c) (leaves[c] >= 2 ? tops : chains)++;
+    if (tops >= 2 && chains == 0 && subtree_top[b1] > kSplitAbove) splittable.push_back(b1);
+  }
+  const long long extra = (long long)max_groups - (long long)stage1.size();
+  const int parts_each = splittable.empty() || extra <= 0
+                             ? 1
+                             : (int)std::min<long long>(1 + extra / (long long)splittable.size(), 1 << 20);
+  int hp_rows = 0;
+  for (int b1 : stage1) {
+    std::vector<int> tops;
+    for (int c = first_child[b1]; c < first_child[b1] + nchild[b1]; ++c)
+      if (leaves[c] >= 2) tops.push_back(c);
+    const bool split = parts_each >= 2 &&
+                       std::find(splittable.begin(), splittable.end(), b1) != splittable.end();
+    if (!split) {
+      add_group({b1}, -1, -1);
+      continue;
+    }
+    const int r = (int)root_orig.size(), nt = (int)tops.size();
+    const int ns = std::min(nt, parts_each);
+    root_orig.push_back(b1);
+    p.r_part.push_back(p.n_groups);
+    p.r_hp.push_back(hp_rows);
+    for (int q = 0, c0 = 0; q < ns; ++q) {  // contiguous bundles, sizes differ by one at most
+      const int cnt = nt / ns + (q < nt % ns ? 1 : 0);
+      add_group(std::vector<int>(tops.begin() + c0, tops.begin() + c0 + cnt), r, hp_rows + c0);
+      c0 += cnt;
+    }
+    hp_rows += nt;
+  }
+  p.n_roots = (int)root_orig.size();
+  p.r_part.push_back(p.n_groups);
+  p.r_hp.push_back(hp_rows);
+  p.hp_rows = hp_rows;
+  for (int b1 : root_orig) {
+    p.perm[next] = b1;
+    p.iperm[b1] = next;
+    p.r_node.push_back(next++);
+  }
+  for (int r = 0; r < p.n_roots; ++r)
+    p.max_root_children = std::max(p.max_root_children, p.r_hp[r + 1] - p.r_hp[r]);
   p.n_top = next - 1;
   // chains, ordered by their leaf (all leaves are at stage N, so this
   // keeps the chains below any node contiguous)
@@ -226,7 +283,11 @@ int build_plan(const rn_tree *t, Plan &p) {
     std::vector<int> path;
     for (int a = par; a > 0; a = p.parent[a]) path.push_back(a);
     std::reverse(path.begin(), path.end());
-    const int g = path.empty() ? -1 : group_of[p.perm[path[0]]];
+    const int g = par > 0 ? group_of[p.perm[par]] : -1;
+    if (par > 0 && g < 0) {
+      set_error("tree: internal error, chain below a root");
+      return RN_ERR_INVAL;
+    }
     p.ch_group.push_back(g);
     if (g >= 0) {
       if (p.g_chain[2 * g] < 0) p.g_chain[2 * g] = k;
@@ -257,7 +318,10 @@ int build_plan(const rn_tree *t, Plan &p) {
     const int l0 = p.g_lvl[g], nl = p.g_lvl[g + 1] - l0 - 1;
     std::vector<int> d{m, nl, p.g_chain[2 * g + 1] - c0, 0};
     for (int l = 0; l <= nl; ++l) d.push_back(p.lvl[l0 + l] - g0);
-    for (int li = 0; li < m; ++li) d.push_back(p.parent[g0 + li] > 0 ? p.parent[g0 + li] - g0 : -1);
+    for (int li = 0; li < m; ++li) {
+      const int pa = p.parent[g0 + li];
+      d.push_back(pa >= g0 && pa < g0 + m ? pa - g0 : -1);  // -1: the tree root or the group's root
+    }
     int acc = 0;
     for (int li = 0; li <= m; ++li) {
       d.push_back(acc);

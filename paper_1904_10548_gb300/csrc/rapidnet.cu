@@ -758,8 +758,36 @@ int fit_sizes(const rn_factor *f, int eb, int team_bytes, int net_bytes, int tw,
   }
   // every group in shared memory if there is room beside one head row; a
   // larger group keeps all its rows in global memory
-  z->gcap = std::min(p.max_group, rows - 1);
-  z->hchunk = std::max(1, std::min(p.max_group_chains, rows - z->gcap));
+  const int wrows = p.n_roots > 0 ? p.max_root_children + 1 : 1;  // root_step work rows
+  if (rows < 1 + wrows) {
+    set_error("shared memory: the network is too large for the group buffer");
+    return RN_ERR_UNSUPPORTED;
+  }
+  z->gcap = std::min(p.max_group, rows - wrows);
+  z->hchunk = std::max(wrows, std::min(p.max_group_chains, rows - z->gcap));
+  return RN_OK;
+}
+
+// Team width tw (one thread per input component, at least 64, a multiple
+// of 32, at most 256), components per thread maxc (also ceil(nx / 32) for
+// the per-node dual update: 1, 2, 4 or 8) and teams per block (four up to
+// 512 threads: one block per SM, 16 warps for a group).
+int team_layout(int block_threads, int nx, int nu, int *tw_out, int *tpb_out, int *maxc_out) {
+  int tw = block_threads > 0 ? ((block_threads + 31) / 32) * 32
+                             : std::max(64, ((std::max(nx, nu) + 31) / 32) * 32);
+  tw = std::min(tw, 256);
+  auto comps = [&](int b) {
+    int c = std::max((std::max(nx, nu) + b - 1) / b, (nx + 31) / 32);
+    return c <= 1 ? 1 : (c <= 2 ? 2 : (c <= 4 ? 4 : (c <= 8 ? 8 : 16)));
+  };
+  while (comps(tw) > 8 && tw < 256) tw += 32;
+  if (comps(tw) > 8) {
+    set_error("network: nx, nu too large for the team width");
+    return RN_ERR_UNSUPPORTED;
+  }
+  *tw_out = tw;
+  *tpb_out = tw <= 128 ? 4 : 2;
+  if (maxc_out) *maxc_out = comps(tw);
   return RN_OK;
 }
 
@@ -838,7 +866,7 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
                 const rn_opts *opts, rn_factor *f) {
   int rc = validate_network(net, cost);
   if (rc) return rc;
-  rc = build_plan(tree, f->plan);
+  rc = build_plan(tree, f->plan);  // validation; rebuilt below for the device
   if (rc) return rc;
   f->opts = opts ? *opts : rn_opts{};
   if (f->opts.precision != RN_PREC_FP64 && f->opts.precision != RN_PREC_MIXED) {
@@ -857,6 +885,15 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
     f->own_stream = true;
   }
   const int nx = net->nx, nu = net->nu, nd = net->nd, ne = net->ne;
+  {
+    // groups beyond one per stage-1 subtree only where one block per SM
+    // leaves SMs free next to the chain blocks
+    int sms = 0, tw = 0, tpb = 0;
+    RN_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, f->device));
+    team_layout(f->opts.block_threads, nx, nu, &tw, &tpb, nullptr);
+    const int chain_blocks = (f->plan.n_chains + tpb - 1) / tpb;
+    if ((rc = build_plan(tree, f->plan, std::max(1, sms - chain_blocks)))) return rc;
+  }
   f->nx = nx;
   f->nu = nu;
   f->nd = nd;
@@ -951,6 +988,12 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
   pd.n_top = p.n_top;
   pd.n_chains = p.n_chains;
   pd.n_groups = p.n_groups;
+  pd.n_roots = p.n_roots;
+  UP_I(pd.g_root, p.g_root.empty() ? std::vector<int>(1, -1) : p.g_root)
+  UP_I(pd.r_node, p.r_node.empty() ? std::vector<int>(1, 0) : p.r_node)
+  UP_I(pd.r_part, p.r_part)
+  UP_I(pd.g_hp, p.g_hp.empty() ? std::vector<int>(1, -1) : p.g_hp)
+  UP_I(pd.r_hp, p.r_hp.empty() ? std::vector<int>(1, 0) : p.r_hp)
   UP_I(pd.parent, p.parent) UP_I(pd.g_node, p.g_node) UP_I(pd.g_chain, p.g_chain)
   UP_I(pd.g_lvl, p.g_lvl) UP_I(pd.lvl, p.lvl) UP_I(pd.g_ccn, p.g_ccn) UP_I(pd.ccn, p.ccn)
   UP_I(pd.g_desc_ptr, p.g_desc_ptr) UP_I(pd.g_desc, p.g_desc)
@@ -966,13 +1009,15 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
 
   // state
   StateDev<double> &st = f->st;
-  double *s, *ya, *yb, *ub, *gb, *z, *up, *ux, *uo, *xo;
+  double *s, *ya, *yb, *ub, *gb, *z, *up, *ux, *uo, *xo, *hp;
   if ((rc = dalloc(f, &s, (size_t)n * f->SP)) || (rc = dalloc(f, &ya, (size_t)n * f->YP)) ||
       (rc = dalloc(f, &yb, (size_t)n * f->YP)) || (rc = dalloc(f, &ub, (size_t)n * f->NUP)) ||
       (rc = dalloc(f, &gb, (size_t)n * f->NXP)) || (rc = dalloc(f, &z, (size_t)n * f->NUP)) ||
       (rc = dalloc(f, &up, (size_t)n * f->SP)) || (rc = dalloc(f, &ux, (size_t)n * f->SP)) ||
-      (rc = dalloc(f, &uo, (size_t)n * f->NUP)) || (rc = dalloc(f, &xo, (size_t)n * f->NXP)))
+      (rc = dalloc(f, &uo, (size_t)n * f->NUP)) || (rc = dalloc(f, &xo, (size_t)n * f->NXP)) ||
+      (rc = dalloc(f, &hp, (size_t)std::max(1, p.hp_rows) * f->SP)))
     return rc;
+  RN_CUDA(cudaMemset(hp, 0, (size_t)std::max(1, p.hp_rows) * f->SP * sizeof(double)));
   RN_CUDA(cudaMemset(s, 0, (size_t)n * f->SP * sizeof(double)));
   RN_CUDA(cudaMemset(ya, 0, (size_t)n * f->YP * sizeof(double)));
   RN_CUDA(cudaMemset(yb, 0, (size_t)n * f->YP * sizeof(double)));
@@ -991,6 +1036,7 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
   st.z = z;
   st.up = up;
   st.ux = ux;
+  st.hp = hp;
   st.uo = uo;
   st.xo = xo;
   st.inv2p = f->inv2p;
@@ -1001,7 +1047,7 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
     return rc;
   RN_CUDA(cudaMemset(f->x0, 0, nx * sizeof(double)));
   st.xroot = f->x0;
-  const size_t ng = (size_t)std::max(1, p.n_groups);
+  const size_t ng = (size_t)std::max(1, p.n_groups + p.n_roots);
   f->sync_words = 2 * ng + 1;
   if ((rc = dalloc(f, &f->sync, f->sync_words))) return rc;
   st.count = f->sync;
@@ -1047,9 +1093,10 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
     UP_F(nf.umin, tof(net->umin, nu)) UP_F(nf.umax, tof(net->umax, nu))
     UP_F(f->stf.inv2p, tofv(inv2p))
 #undef UP_F
-    float *s32, *z32, *up32, *ux32, *da, *db, *ybh, *uref, *xref, *sw;
+    float *s32, *z32, *up32, *ux32, *hp32, *da, *db, *ybh, *uref, *xref, *sw;
     if ((rc = dalloc(f, &s32, (size_t)n * f->SP)) || (rc = dalloc(f, &z32, (size_t)n * f->NUP)) ||
         (rc = dalloc(f, &up32, (size_t)n * f->SP)) || (rc = dalloc(f, &ux32, (size_t)n * f->SP)) ||
+        (rc = dalloc(f, &hp32, (size_t)std::max(1, p.hp_rows) * f->SP)) ||
         (rc = dalloc(f, &da, (size_t)n * f->YP)) ||
         (rc = dalloc(f, &db, (size_t)n * f->YP)) || (rc = dalloc(f, &ybh, (size_t)n * f->YP)) ||
         (rc = dalloc(f, &uref, (size_t)n * f->NUP)) || (rc = dalloc(f, &xref, (size_t)n * f->NXP)) ||
@@ -1057,6 +1104,7 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
       return rc;
     for (auto pr : {std::make_pair((void *)s32, (size_t)n * f->SP), {(void *)z32, (size_t)n * f->NUP},
                     {(void *)up32, (size_t)n * f->SP}, {(void *)ux32, (size_t)n * f->SP},
+                    {(void *)hp32, (size_t)std::max(1, p.hp_rows) * f->SP},
                     {(void *)da, (size_t)n * f->YP},
                     {(void *)db, (size_t)n * f->YP}, {(void *)ybh, (size_t)n * f->YP},
                     {(void *)uref, (size_t)n * f->NUP}, {(void *)xref, (size_t)n * f->NXP},
@@ -1067,6 +1115,7 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
     sf.z = z32;
     sf.up = up32;
     sf.ux = ux32;
+    sf.hp = hp32;
     sf.count = st.count;
     sf.flags = st.flags;
     sf.barrier = st.barrier;
@@ -1087,25 +1136,8 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
   // thread per input component, at least 64); as many resident blocks as
   // there are work items (groups and chain pairs), up to what the device
   // holds
-  {
-    int tw = f->opts.block_threads > 0 ? ((f->opts.block_threads + 31) / 32) * 32
-                                        : std::max(64, ((std::max(nx, nu) + 31) / 32) * 32);
-    tw = std::min(tw, 256);
-    auto comps = [&](int b) {
-      int c = std::max((std::max(nx, nu) + b - 1) / b, (nx + 31) / 32);
-      return c <= 1 ? 1 : (c <= 2 ? 2 : (c <= 4 ? 4 : (c <= 8 ? 8 : 16)));
-    };
-    while (comps(tw) > 8 && tw < 256) tw += 32;
-    if (comps(tw) > 8) {
-      set_error("network: nx, nu too large for the team width");
-      return RN_ERR_UNSUPPORTED;
-    }
-    // four teams (one block per SM, 16 warps for a group) up to 512 threads
-    f->tpb = tw <= 128 ? 4 : 2;
-    f->tw = tw;
-    f->block = f->tpb * tw;
-    f->maxc = comps(tw);
-  }
+  if ((rc = team_layout(f->opts.block_threads, nx, nu, &f->tw, &f->tpb, &f->maxc))) return rc;
+  f->block = f->tpb * f->tw;
   {
     const int nnzB = (int)Bc.idx.size(), nnzE = (int)Er.idx.size();
     f->net_bytes_d = (int)net_smem_bytes(nx, nu, ne, nnzB, nnzE, 8);
@@ -1574,10 +1606,13 @@ extern "C" int rapidnet_dual_gradient_noalloc(rn_factor *f, const double *w, dou
   }
   const int n = f->plan.n;
   const size_t rows = (size_t)n;
-  const size_t ng = (size_t)std::max(1, f->plan.n_groups);
+  const size_t ng = (size_t)std::max(1, f->plan.n_groups + f->plan.n_roots);
   const size_t sync_words = 2 * ng + 1;
-  // doubles: s, up, ux (SP), z, uo (NUP), xo (NXP); then sync words, err, info
-  const size_t need_d = rows * (3 * (size_t)f->SP + 2 * (size_t)f->NUP + (size_t)f->NXP);
+  const size_t hrows = (size_t)std::max(1, f->plan.hp_rows);
+  // doubles: s, up, ux (SP), z, uo (NUP), xo (NXP), hp (SP per group);
+  // then sync words, err, info
+  const size_t need_d = rows * (3 * (size_t)f->SP + 2 * (size_t)f->NUP + (size_t)f->NXP) +
+                        hrows * f->SP;
   const size_t need_w = sync_words + 1 + 4;  // 32-bit words
   const size_t need = need_d + (need_w + 1) / 2;
   if (need > kNoAllocDoubles) {
@@ -1604,6 +1639,8 @@ extern "C" int rapidnet_dual_gradient_noalloc(rn_factor *f, const double *w, dou
   p += rows * f->NUP;
   st.xo = p;
   p += rows * f->NXP;
+  st.hp = p;
+  p += hrows * f->SP;
   unsigned *words = reinterpret_cast<unsigned *>(p);
   st.count = words;
   st.flags = words + ng;

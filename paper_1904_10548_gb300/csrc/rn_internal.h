@@ -10,6 +10,7 @@
 namespace rn {
 
 constexpr int kChildSlots = 8;  // children per node in a group's children table
+constexpr int kSplitAbove = 24; // a stage-1 subtree with more top nodes is split
 
 // thread-local error message behind rapidnet_last_error()
 void set_error(const char *fmt, ...);
@@ -44,7 +45,7 @@ Csr dense_to_csc(const double *M, int rows, int cols);  // "rows" of the result 
 // any node form a contiguous range.
 struct Plan {
   int n = 0, N = 0, n_top = 0, n_chains = 0, n_groups = 0, max_chain_len = 0;
-  int max_group = 0, max_group_chains = 0;
+  int max_group = 0, max_group_chains = 0, n_roots = 0, max_root_children = 0, hp_rows = 0;
   std::vector<int> perm;     // internal -> breadth-first index
   std::vector<int> iperm;    // breadth-first -> internal
   std::vector<int> parent;   // internal parent index (-1 for the root)
@@ -52,6 +53,11 @@ struct Plan {
   // groups: top nodes [g_node[g], g_node[g+1]), chains [g_chain[2g],
   // g_chain[2g+1]), level boundaries lvl[g_lvl[g]] .. lvl[g_lvl[g+1] - 1]
   std::vector<int> g_node, g_chain, g_lvl, lvl;
+  // per group its root (-1 unless the group is a part of a split stage-1
+  // subtree) and the first hp row of its top nodes' sums; roots: internal
+  // node r_node[r], parts [r_part[r], r_part[r+1]), the sums of its
+  // children in hp rows [r_hp[r], r_hp[r+1])
+  std::vector<int> g_root, g_hp, r_node, r_part, r_hp;
   // per group the top nodes with chain children: ccn[g_ccn[g] .. g_ccn[g+1])
   std::vector<int> g_ccn, ccn;
   // per group a compact descriptor in local indices (li = internal - g_node[g],
@@ -73,8 +79,10 @@ struct Plan {
   std::vector<int> ch_start, ch_len, ch_group, ch_parent, ch_own_ptr, ch_own;
 };
 
-// Validates the tree (see rn_tree) and builds the schedule.  Returns
-// RN_OK or RN_ERR_INVAL with the error message set.
-int build_plan(const rn_tree *tree, Plan &plan);
+// Validates the tree (see rn_tree) and builds the schedule with at most
+// max_groups groups where a split is possible (at least one group per
+// stage-1 subtree).  Returns RN_OK or RN_ERR_INVAL with the error message
+// set.
+int build_plan(const rn_tree *tree, Plan &plan, int max_groups = 1 << 30);
 
 }  // namespace rn

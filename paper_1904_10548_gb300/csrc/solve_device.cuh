@@ -761,17 +761,77 @@ __device__ void chain_rest(const KParams<T> &P, int k, const Smem<T> &sm, const 
 }
 
 // ---------------------------------------------------------------------------
-// One group (the top nodes below one stage-1 node), whole block: wait for
-// the group's chains, sum the subtree level by level from the deepest,
-// apply F to every node, roll the path sums Z and states x back down and
-// publish (x | Z) in ux, then release the group's flag.  One warp per node;
-// the group's descriptor (levels, parents, children in local indices) is
-// staged with its rows.  Rows beyond the shared-memory capacity live in
-// up[K + v].  False on timeout.
+// The root of a split stage-1 subtree (one node), whole block, by the last
+// of its parts to finish phase 0: own terms plus its children's sums in hp,
+// F, then (x | Z) with the tree root as parent, published in ux before the
+// root's flag.  W: rows of work space (children + 1), eb/fb/i2p as for F.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ void root_step(const KParams<T> &P, int root, const Smem<T> &sm, const Team &tm,
+                          unsigned step, T *W, T *eb, T *fb, T *i2p) {
+  const NetDev<T> &nt = *sm.net;
+  const PlanDev &pl = P.plan;
+  const int SP = nt.SP, NXP = nt.NXP, NUP = nt.NUP, nx = nt.nx, nu = nt.nu;
+  const int v = pl.r_node[root], q0 = pl.r_hp[root], np = pl.r_hp[root + 1] - q0;
+  const bool data = !P.linear;
+  T *Rr = W, *Hp = W + SP;
+  stage_span(Rr, P.st.s + (size_t)v * SP, SP, tm, true);
+  stage_span(Hp, P.st.hp + (size_t)q0 * SP, np * SP, tm, true);
+  if (tm.tid == 0) i2p[0] = P.st.inv2p[v];
+  cp_wait();
+  tm.sync();
+  for (int i = tm.tid; i < nx; i += tm.nt) {
+    T acc = Rr[i];
+    for (int q = 0; q < np; ++q) acc += Hp[(size_t)q * SP + i];
+    Rr[i] = acc;
+  }
+  tm.sync();
+  for (int j = tm.tid; j < nu; j += tm.nt) {
+    Slice<T, 2> bc;
+    bc.load(nt.Bc_ptr, nt.Bc_idx, nt.Bc_val, j);
+    T acc = bc.dot(Rr[NXP + j], [&](int t) { return Rr[t]; }, nt.Bc_idx, nt.Bc_val);
+    for (int q = 0; q < np; ++q) acc += Hp[(size_t)q * SP + NXP + j];
+    Rr[NXP + j] = acc;
+  }
+  tm.sync();
+  apply_F(nt, 1, [=](int) { return Rr; }, i2p, eb, fb, tm);
+  tm.sync();
+  // Z = z (the parent is the tree root), x = x0 + Gd d + B u
+  T *out = P.st.ux + (size_t)v * SP;
+  for (int i = tm.tid; i < nx; i += tm.nt) {
+    Slice<T, 6> br;
+    br.load(nt.Br_ptr, nt.Br_idx, nt.Br_val, i);
+    T acc = data ? P.st.xroot[i] + P.st.gb[(size_t)v * NXP + i] : T(0);
+    const T *ubv = P.st.ub + (size_t)v * NUP;
+    out[i] = br.dot(acc, [&](int t) { return (data ? ubv[t] : T(0)) - Rr[NXP + t]; }, nt.Br_idx,
+                    nt.Br_val);
+  }
+  for (int j = tm.tid; j < nu; j += tm.nt) out[NXP + j] = Rr[NXP + j];
+  tm.sync();
+  if (tm.tid == 0) {
+    __threadfence();
+    st_release(P.st.flags + pl.n_groups + root, step + 1u);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One group of top nodes, whole block: wait for the group's chains, sum
+// the subtree level by level from the deepest, apply F to every node, roll
+// the path sums Z and states x back down and publish (x | Z) in ux, then
+// release the group's flag.  The group's descriptor (levels, parents,
+// children in local indices) is staged with its rows; rows of a group
+// larger than the shared-memory capacity live in up[K + v].
+//
+// A group that is a part of a split stage-1 subtree works in two phases:
+// phase 0 sums the part, publishes the sums at its top node in hp[g] and
+// arrives at its root (the last part to arrive completes the root node,
+// root_step), then applies F and leaves z in ux; phase 1 waits for the
+// root and rolls down from it.  An unsplit group does everything in
+// phase 0.  False on timeout.
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ bool group_step(const KParams<T> &P, int g, const Smem<T> &sm, const Team &tm,
-                           unsigned step) {
+                           unsigned step, int phase) {
   const NetDev<T> &nt = *sm.net;
   const PlanDev &pl = P.plan;
   const int SP = nt.SP, NXP = nt.NXP, NUP = nt.NUP, nx = nt.nx, nu = nt.nu, NEP = nt.NEP;
@@ -789,6 +849,34 @@ __device__ bool group_step(const KParams<T> &P, int g, const Smem<T> &sm, const 
   int *desc = reinterpret_cast<int *>(eb + round4(2 * fbr * NEP + fbr));
   // all rows in shared memory, or (a group larger than gcap) all in up[K + v]
   T *const rb = m <= gcap ? R : P.st.up + (size_t)(pl.n_chains + g0) * SP;
+  const int root = pl.g_root[g];
+  T *base = nullptr;  // (x | Z) at the parent of the group's top node, if not the tree root
+  int nl = 0;
+  const int *lvl = nullptr, *par = nullptr;
+  if (phase == 1) {
+    if (root < 0) return true;
+    // the root's (x | Z), the descriptor and the z rows of phase 0
+    const int rv = pl.r_node[root];
+    if (tm.tid == 0) sm.flag[0] = spin_geq(P.st.flags + pl.n_groups + root, step + 1u, P.st.err);
+    tm.sync();
+    if (!sm.flag[0]) return false;
+    base = H;  // the heads are not needed in phase 1
+    for (int e = tm.tid; e < NXP + NUP; e += tm.nt) base[e] = __ldcg(P.st.ux + (size_t)rv * SP + e);
+    for (int e = tm.tid; e < dn / 4; e += tm.nt) cp16(desc + 4 * e, pl.g_desc + d0 + 4 * e, false);
+    constexpr int per = 16 / sizeof(T);
+    const int nv = NUP / per;
+    for (int e = tm.tid; e < m * nv; e += tm.nt) {
+      const int li = e / nv, c = e - li * nv;
+      cp16(rb + (size_t)li * SP + NXP + c * per, P.st.ux + (size_t)(g0 + li) * SP + NXP + c * per,
+           true);
+    }
+    cp_wait();
+    tm.sync();
+    nl = desc[1];
+    lvl = desc + 4;
+    par = lvl + nl + 1;
+  }
+  if (phase == 0) {
   // all chains of the group have arrived; the counter restarts for the
   // next evaluation (no chain arrives again before the flag below)
   if (tm.tid == 0) {
@@ -854,8 +942,10 @@ __device__ bool group_step(const KParams<T> &P, int g, const Smem<T> &sm, const 
   }
   cp_wait();
   tm.sync();
-  const int nl = desc[1];
-  const int *lvl = desc + 4, *par = lvl + nl + 1, *tcp = par + m, *tcl = tcp + m + 1;
+  nl = desc[1];
+  lvl = desc + 4;
+  par = lvl + nl + 1;
+  const int *tcp = par + m, *tcl = tcp + m + 1;
   const int *ccp = tcl + tcp[m], *ccl = ccp + m + 1;
   // children table (one row of kChildSlotsDev references per node)
   const int *cn_end = ccl + ccp[m] + desc[3];
@@ -963,6 +1053,25 @@ __device__ bool group_step(const KParams<T> &P, int g, const Smem<T> &sm, const 
     }
     tm.sync();
   }
+  if (root >= 0) {
+    // a part: its top nodes' sums to the root; the last part completes it
+    const int m0 = lvl[1] - lvl[0];
+    T *hpg = P.st.hp + (size_t)pl.g_hp[g] * SP;
+    for (int e = tm.tid; e < m0 * SP; e += tm.nt) hpg[e] = rb[e];
+    tm.sync();
+    if (tm.tid == 0) {
+      __threadfence();
+      const unsigned np = (unsigned)(pl.r_part[root + 1] - pl.r_part[root]);
+      const unsigned old = atomicAdd(P.st.count + pl.n_groups + root, 1u);
+      sm.flag[1] = old + 1u == np;
+      if (sm.flag[1]) {
+        __threadfence();
+        atomicExch(P.st.count + pl.n_groups + root, 0u);
+      }
+    }
+    tm.sync();
+    if (sm.flag[1]) root_step(P, root, sm, tm, step, H, eb, fb, i2p);
+  }
   // z = F ghat / (2p) at every node of the group
   for (int q0 = 0; q0 < m; q0 += fbr) {
     const int mm = m - q0 < fbr ? m - q0 : fbr;
@@ -972,6 +1081,19 @@ __device__ bool group_step(const KParams<T> &P, int g, const Smem<T> &sm, const 
     apply_F(nt, mm, [=](int q) { return rb + (size_t)(q0 + q) * SP; }, i2p, eb, fb, tm);
   }
   tm.sync();
+  if (root >= 0) {
+    // z rows for phase 1
+    constexpr int per = 16 / sizeof(T);
+    const int nv = NUP / per;
+    using V = typename std::conditional<sizeof(T) == 8, double2, float4>::type;
+    for (int e = tm.tid; e < m * nv; e += tm.nt) {
+      const int li = e / nv, c = e - li * nv;
+      reinterpret_cast<V *>(P.st.ux + (size_t)(g0 + li) * SP + NXP)[c] =
+          reinterpret_cast<const V *>(rb + (size_t)li * SP + NXP)[c];
+    }
+    return true;
+  }
+  }  // phase 0
   // forward over the levels: Z_v = Z_a(v) + z_v, x_v = x_a(v) + B u_v + Gd d_v
   // (four nodes per thread at a time: loads, then sums, then stores)
   constexpr int NF = 4;
@@ -987,7 +1109,8 @@ __device__ bool group_step(const KParams<T> &P, int g, const Smem<T> &sm, const 
           if (li < b) {
             const int pa = par[li];
             const T own = rb[(size_t)li * SP + NXP + j];
-            zv[k] = pa >= 0 ? own + rb[(size_t)pa * SP + NXP + j] : own;
+            zv[k] = pa >= 0 ? own + rb[(size_t)pa * SP + NXP + j]
+                            : (base ? own + base[NXP + j] : own);
           }
         }
 #pragma unroll
@@ -1010,7 +1133,8 @@ __device__ bool group_step(const KParams<T> &P, int g, const Smem<T> &sm, const 
           if (li < b) {
             const int pa = par[li], v = g0 + li;
             const T *r = rb + (size_t)li * SP;
-            T acc = pa >= 0 ? rb[(size_t)pa * SP + i] : (data ? P.st.xroot[i] : T(0));
+            T acc = pa >= 0 ? rb[(size_t)pa * SP + i]
+                            : (base ? base[i] : (data ? P.st.xroot[i] : T(0)));
             if (data) acc += P.st.gb[(size_t)v * NXP + i];
             const T *ubv = P.st.ub + (size_t)v * NUP;
             xv[k] = br.dot(acc, [&](int t) { return (data ? ubv[t] : T(0)) - r[NXP + t]; }, Br_idx,
@@ -1232,8 +1356,9 @@ static __device__ void final_node(const MixedParams &M, int v) {
 // one evaluation of the dual gradient (with the per-node step of MODE) by a
 // block whose items are i = blockIdx.x, blockIdx.x + gridDim.x, ...: items
 // below n_groups are groups (whole block), the rest sets of tpb chains
-// (one per team).  Phases: chain heads, groups, the chains' local parts,
-// the forward sweeps.  keep: the block holds one chain set and no group.
+// (one per team).  Phases: chain heads, groups (phase 0), the chains'
+// local parts, parts of split subtrees (phase 1), the forward sweeps.
+// keep: the block holds one chain set and no group.
 // False (for the calling team) on timeout.
 // ---------------------------------------------------------------------------
 template <typename T, int MODE, int C>
@@ -1249,11 +1374,16 @@ __device__ bool eval_step(const KParams<T> &P, FwdCtx<T> &c, const MixedDev *mx,
   }
   for (int i = blockIdx.x; i < G; i += gridDim.x) {
     __syncthreads();
-    if (!group_step<T>(P, i, smg, tb, step)) ok = false;
+    if (!group_step<T>(P, i, smg, tb, step, 0)) ok = false;
   }
   for (int i = blockIdx.x; i < n_items; i += gridDim.x) {
     const int k = tpb * (i - G) + team;
     if (i >= G && k < K) chain_rest<T, C>(P, k, smc, tc, keep);
+  }
+  for (int i = blockIdx.x; i < G; i += gridDim.x) {
+    if (P.plan.g_root[i] < 0) continue;
+    __syncthreads();
+    if (!group_step<T>(P, i, smg, tb, step, 1)) ok = false;
   }
   for (int i = blockIdx.x; i < n_items && ok; i += gridDim.x) {
     const int k = tpb * (i - G) + team;
