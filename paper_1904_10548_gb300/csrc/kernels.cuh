@@ -51,7 +51,9 @@ struct NetDev {
 struct PlanDev {
   int n, n_top, n_chains, n_groups, n_roots;
   const int *parent;
-  const int *g_root, *g_hp, *r_node, *r_part, *r_hp;  // parts of split stage-1 subtrees, roots
+  // parts of split stage-1 subtrees: root of each group, its first hp row;
+  // roots: node, parts [r_part[2r], r_part[2r+1]), hp rows [r_hp[r], r_hp[r+1])
+  const int *g_root, *g_hp, *r_node, *r_part, *r_hp;
   const int *g_node, *g_chain, *g_lvl, *lvl, *g_ccn, *ccn;
   const int *g_desc_ptr, *g_desc;  // per-group descriptors (rn::Plan)
   const int *tc_ptr, *tc, *cc_ptr, *cc;

@@ -196,17 +196,17 @@ int build_plan(const rn_tree *t, Plan &p, int max_groups) {
     const int r = (int)root_orig.size(), nt = (int)tops.size();
     const int ns = std::min(nt, parts_each);
     root_orig.push_back(b1);
-    p.r_part.push_back(p.n_groups);
+    p.r_part.push_back(p.n_groups);  // [begin, end) of the root's parts
     p.r_hp.push_back(hp_rows);
     for (int q = 0, c0 = 0; q < ns; ++q) {  // contiguous bundles, sizes differ by one at most
       const int cnt = nt / ns + (q < nt % ns ? 1 : 0);
       add_group(std::vector<int>(tops.begin() + c0, tops.begin() + c0 + cnt), r, hp_rows + c0);
       c0 += cnt;
     }
+    p.r_part.push_back(p.n_groups);
     hp_rows += nt;
   }
   p.n_roots = (int)root_orig.size();
-  p.r_part.push_back(p.n_groups);
   p.r_hp.push_back(hp_rows);
   p.hp_rows = hp_rows;
   for (int b1 : root_orig) {
@@ -216,6 +216,7 @@ int build_plan(const rn_tree *t, Plan &p, int max_groups) {
   }
   for (int r = 0; r < p.n_roots; ++r)
     p.max_root_children = std::max(p.max_root_children, p.r_hp[r + 1] - p.r_hp[r]);
+  if (p.r_part.empty()) p.r_part.assign(2, 0);
   p.n_top = next - 1;
   // chains, ordered by their leaf (all leaves are at stage N, so this
   // keeps the chains below any node contiguous)

@@ -656,7 +656,10 @@ int check_err(rn_factor *f) {
   RN_CUDA(cudaMemcpyAsync(&e, f->err, sizeof(int), cudaMemcpyDeviceToHost, f->stream));
   RN_CUDA(cudaStreamSynchronize(f->stream));
   if (e) {
-    set_error("a device-side wait gave up after %.1f s", kWaitNs * 1e-9);
+    static const char *site[] = {"?", "chain arrivals at a group", "a group's flag",
+                                 "a root's flag", "the grid barrier"};
+    set_error("a device-side wait (%s) gave up after %.1f s", site[e >= 1 && e <= 4 ? e : 0],
+              kWaitNs * 1e-9);
     return RN_ERR_TIMEOUT;
   }
   return RN_OK;

@@ -55,7 +55,7 @@ struct Plan {
   std::vector<int> g_node, g_chain, g_lvl, lvl;
   // per group its root (-1 unless the group is a part of a split stage-1
   // subtree) and the first hp row of its top nodes' sums; roots: internal
-  // node r_node[r], parts [r_part[r], r_part[r+1]), the sums of its
+  // node r_node[r], parts [r_part[2r], r_part[2r+1]), the sums of its
   // children in hp rows [r_hp[r], r_hp[r+1])
   std::vector<int> g_root, g_hp, r_node, r_part, r_hp;
   // per group the top nodes with chain children: ccn[g_ccn[g] .. g_ccn[g+1])

@@ -36,15 +36,17 @@ __device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
   a.store(v, cuda::memory_order_release);
 }
 
-// bounded spin of one thread until *p >= target; false on timeout or error
-static __device__ bool spin_geq(const unsigned *p, unsigned target, int *err) {
+// bounded spin of one thread until *p >= target; false on timeout or error.
+// The first wait to give up records `site` in *err (1 chain arrivals at a
+// group, 2 a group's flag, 3 a root's flag, 4 the grid barrier).
+static __device__ bool spin_geq(const unsigned *p, unsigned target, int *err, int site = 1) {
   if (ld_acquire(p) >= target) return true;
   const unsigned long long t0 = global_ns();
   while (true) {
     if (ld_acquire(p) >= target) return true;
     if (*(volatile int *)err != 0) return false;
     if ((long long)(global_ns() - t0) > kWaitNs) {
-      atomicExch(err, 1);
+      atomicCAS(err, 0, site);
       return false;
     }
     __nanosleep(64);
@@ -857,7 +859,8 @@ __device__ bool group_step(const KParams<T> &P, int g, const Smem<T> &sm, const 
     if (root < 0) return true;
     // the root's (x | Z), the descriptor and the z rows of phase 0
     const int rv = pl.r_node[root];
-    if (tm.tid == 0) sm.flag[0] = spin_geq(P.st.flags + pl.n_groups + root, step + 1u, P.st.err);
+    if (tm.tid == 0)
+      sm.flag[0] = spin_geq(P.st.flags + pl.n_groups + root, step + 1u, P.st.err, 3);
     tm.sync();
     if (!sm.flag[0]) return false;
     base = H;  // the heads are not needed in phase 1
@@ -1061,7 +1064,7 @@ __device__ bool group_step(const KParams<T> &P, int g, const Smem<T> &sm, const 
     tm.sync();
     if (tm.tid == 0) {
       __threadfence();
-      const unsigned np = (unsigned)(pl.r_part[root + 1] - pl.r_part[root]);
+      const unsigned np = (unsigned)(pl.r_part[2 * root + 1] - pl.r_part[2 * root]);
       const unsigned old = atomicAdd(P.st.count + pl.n_groups + root, 1u);
       sm.flag[1] = old + 1u == np;
       if (sm.flag[1]) {
@@ -1202,7 +1205,7 @@ __device__ bool chain_forward(const KParams<T> &P, int k, FwdCtx<T> &c, const Sm
   const int fpn = fwd_elems_per_node(NXP, NUP, YP, SP, MODE);
   T *slots = sm.buf + round4(2 * NXP + NUP) + (size_t)warp * S * fpn;
   if (g >= 0) {
-    if (tm.tid == 0) sm.flag[1] = spin_geq(P.st.flags + g, step + 1u, P.st.err);
+    if (tm.tid == 0) sm.flag[1] = spin_geq(P.st.flags + g, step + 1u, P.st.err, 2);
     tm.sync();
     if (!sm.flag[1]) return false;
     const T *src = P.st.ux + (size_t)par * SP;
@@ -1413,7 +1416,7 @@ __device__ __forceinline__ bool grid_check(const BlockMem &bm, unsigned long lon
     atomicMax(res + ci, r);
     __threadfence();
     atomicAdd(barrier, 1u);
-    bm.bflag[1] = spin_geq(barrier, (unsigned)(ci + 1) * gridDim.x, err);
+    bm.bflag[1] = spin_geq(barrier, (unsigned)(ci + 1) * gridDim.x, err, 4);
   }
   __syncthreads();
   const bool ok = bm.bflag[1] != 0;

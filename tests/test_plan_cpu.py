@@ -86,11 +86,14 @@ TREES = {
     "ne0": lambda: make_tree([3, 2, 1, 2, 1, 1, 1], seed=9),
     "stage1_chains": lambda: _build([[4], [1, 2, 1, 3], [1, 1, 2, 1, 1, 1, 1], [1] * 8, [1] * 8,
                                      [1] * 8], 12),
+    # three stage-1 subtrees: split, unsplit, split (with room for more groups)
+    "mixed_split": lambda: random_branching(24, seed=2006, s_min=16, s_max=512),
 }
 
 
 @pytest.mark.parametrize("name,max_groups", [(t, 1 << 30) for t in sorted(TREES)] +
-                         [("barcelona512", 24), ("barcelona512", 16), ("barcelona512", 8)])
+                         [("barcelona512", 24), ("barcelona512", 16), ("barcelona512", 8),
+                          ("mixed_split", 82)])
 def test_schedule_invariants(driver, name, max_groups):
     tree = TREES[name]()
     p = plan_of(driver, tree, max_groups)
@@ -132,7 +135,7 @@ def test_schedule_invariants(driver, name, max_groups):
             assert perm[top] in stage1_top and parent[top] == 0 and b[1] == top + 1
         else:
             r = g_root[g]
-            assert r_part[r] <= g < r_part[r + 1]
+            assert r_part[2 * r] <= g < r_part[2 * r + 1]
             # the group's top nodes are consecutive children of the root, and
             # their sums go to the root's hp rows in child order
             kids = sorted(i for i in range(1, n) if parent[i] == r_node[r])
@@ -152,9 +155,12 @@ def test_schedule_invariants(driver, name, max_groups):
     assert covered_stage1 == set(stage1_top)
     for r in range(R):
         kids = [i for i in range(1, n) if parent[i] == r_node[r]]
-        tops = [v for g in range(r_part[r], r_part[r + 1]) for v in range(lvl[g_lvl[g]], lvl[g_lvl[g] + 1])]
+        tops = [v for g in range(r_part[2 * r], r_part[2 * r + 1])
+                for v in range(lvl[g_lvl[g]], lvl[g_lvl[g] + 1])]
         assert sorted(kids) == sorted(tops) and p["r_hp"][r + 1] - p["r_hp"][r] == len(kids)
     assert G <= max(max_groups, len(stage1_top))
+    for r in range(R):
+        assert [g for g in range(G) if g_root[g] == r] == list(range(r_part[2 * r], r_part[2 * r + 1]))
     if G:
         assert max(g_node[g + 1] - g_node[g] for g in range(G)) == p["max_group"]
     # children lists of the top nodes
@@ -225,7 +231,7 @@ def test_schedule_sizes_of_the_benchmark_tree(driver):
     assert p["n_groups"] == 32 and p["n_roots"] == 8 and p["max_group"] == 1 + 4 + 8
     assert p["max_group_chains"] == 16 and p["max_chain_len"] == 20
     assert p["n_chains"] == 512 and p["n_top"] == 8 * 53
-    assert p["r_part"] == [4 * r for r in range(9)]
+    assert p["r_part"] == [x for r in range(8) for x in (4 * r, 4 * r + 4)]
 
 
 def test_benchmark_tree_within_a_group_budget(driver):
