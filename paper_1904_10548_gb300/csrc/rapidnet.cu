@@ -702,13 +702,17 @@ int power_iteration(rn_factor *f, int iters, double *L_out) {
 // region of net_bytes, tpb team regions and static_smem bytes of static
 // shared memory: enough blocks per SM that every work item gets a
 // resident block (up to 4), split evenly.
-int team_budget(int device, int n_items, int tpb, int net_bytes, int static_smem, int *team_bytes) {
+int team_budget(int device, int n_items, int tpb, int block, int net_bytes, int static_smem,
+                int *team_bytes) {
   int sms = 0, optin = 0, per_sm = 0, reserved = 0;
   RN_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
   RN_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
   RN_CUDA(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device));
   RN_CUDA(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, device));
-  const int bpsm = std::max(1, std::min(4, (n_items + sms - 1) / std::max(1, sms)));
+  // blocks per SM: enough for every item, at most what 128 registers a
+  // thread allow (the kernels' launch bound), at most 4
+  const int by_regs = std::max(1, 65536 / (block * 128));
+  const int bpsm = std::max(1, std::min({4, by_regs, (n_items + sms - 1) / std::max(1, sms)}));
   const int budget = std::min(optin, per_sm / bpsm - reserved) - static_smem;
   const int tb = ((budget - kHdrBytes - net_bytes) / tpb) & ~15;
   if (tb <= 0) {
@@ -1151,7 +1155,8 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
   RN_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, f->device));
   {
     int team_bytes = 0;
-    if ((rc = team_budget(f->device, n_items, f->tpb, f->net_bytes_d, 0, &team_bytes))) return rc;
+    if ((rc = team_budget(f->device, n_items, f->tpb, f->block, f->net_bytes_d, 0, &team_bytes)))
+      return rc;
     if ((rc = fit_sizes(f, 8, team_bytes, f->net_bytes_d, f->tw, f->tpb, 1, &f->sz_d))) return rc;
     f->smem = kHdrBytes + f->net_bytes_d + (size_t)f->tpb * team_bytes;
     int bps1 = 0, bps2 = 0;
@@ -1170,7 +1175,8 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
     // network region: the FP32 copy, then the header of the FP64 data
     f->net_region_m = f->net_bytes_f + (int)round16(sizeof(NetDev<double>));
     int team_bytes = 0;
-    if ((rc = team_budget(f->device, n_items, f->tpb, f->net_region_m, 0, &team_bytes))) return rc;
+    if ((rc = team_budget(f->device, n_items, f->tpb, f->block, f->net_region_m, 0, &team_bytes)))
+      return rc;
     if ((rc = fit_sizes(f, 4, team_bytes, f->net_region_m, f->tw, f->tpb, 2, &f->sz_f)) ||
         (rc = fit_sizes(f, 8, team_bytes, f->net_bytes_f, f->tw, f->tpb, 0, &f->sz_dm)))
       return rc;
@@ -1757,7 +1763,7 @@ int batch_impl(rn_factor *const *fs, const rn_solve_req *req, int n, int max_ite
   }
   int static_smem = 0, team_bytes = 0;
   RN_CUDA(batch_static_smem(maxc, &static_smem));
-  if ((rc = team_budget(dev, (int)std::min<long long>(items, 1 << 30), tpb, net_region,
+  if ((rc = team_budget(dev, (int)std::min<long long>(items, 1 << 30), tpb, block, net_region,
                         static_smem, &team_bytes)))
     return rc;
   std::vector<Sizes> szf(n), szd(n);
