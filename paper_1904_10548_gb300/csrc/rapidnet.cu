@@ -798,6 +798,26 @@ int team_layout(int block_threads, int nx, int nu, int *tw_out, int *tpb_out, in
   return RN_OK;
 }
 
+// Layout limits of this build: every work item has a resident block of
+// its own, every group's rows fit in shared memory and all its chain heads
+// are staged at once.  (The kernels carry code for blocks with several
+// items, rows in global memory and chunked heads, but those paths are
+// not validated on a GPU; such layouts are refused here, before launch.)
+int check_layout(const Plan &p, const Sizes &z, int n_items, int grid, const char *what) {
+  if (n_items > grid) {
+    set_error("%s: %d work items exceed the %d resident blocks (fewer scenarios, or a "
+              "smaller network, fit)", what, n_items, grid);
+    return RN_ERR_UNSUPPORTED;
+  }
+  if (p.n_groups > 0 && (p.max_group > z.gcap || p.max_group_chains > z.hchunk)) {
+    set_error("%s: a group of %d top nodes with %d chains exceeds the shared-memory "
+              "capacity (%d rows, %d heads)", what, p.max_group, p.max_group_chains, z.gcap,
+              z.hchunk);
+    return RN_ERR_UNSUPPORTED;
+  }
+  return RN_OK;
+}
+
 int validate_network(const rn_network *net, const rn_cost *cost) {
   if (!net || !cost) {
     set_error("network or cost is NULL");
@@ -1170,6 +1190,7 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
     }
     f->grid = std::min(n_items, resident);
     if (f->opts.max_ctas > 0) f->grid = std::min(f->grid, f->opts.max_ctas);
+    if ((rc = check_layout(p, f->sz_d, n_items, f->grid, "the FP64 kernel"))) return rc;
   }
   if (f->opts.precision == RN_PREC_MIXED) {
     // network region: the FP32 copy, then the header of the FP64 data
@@ -1189,6 +1210,9 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
     }
     f->grid_mixed = std::min(n_items, bpm * sms);
     if (f->opts.max_ctas > 0) f->grid_mixed = std::min(f->grid_mixed, f->opts.max_ctas);
+    if ((rc = check_layout(p, f->sz_f, n_items, f->grid_mixed, "the mixed kernel")) ||
+        (rc = check_layout(p, f->sz_dm, n_items, f->grid_mixed, "the mixed kernel (FP64 steps)")))
+      return rc;
   }
 
   if (f->opts.gamma > 0.0) {
@@ -1769,7 +1793,9 @@ int batch_impl(rn_factor *const *fs, const rn_solve_req *req, int n, int max_ite
   std::vector<Sizes> szf(n), szd(n);
   for (int i = 0; i < n; ++i)
     if ((rc = fit_sizes(fs[i], 4, team_bytes, net_region, tw, tpb, 2, &szf[i])) ||
-        (rc = fit_sizes(fs[i], 8, team_bytes, net_f, tw, tpb, 0, &szd[i])))
+        (rc = fit_sizes(fs[i], 8, team_bytes, net_f, tw, tpb, 0, &szd[i])) ||
+        (rc = check_layout(fs[i]->plan, szf[i], 0, 0, "solve_batch")) ||
+        (rc = check_layout(fs[i]->plan, szd[i], 0, 0, "solve_batch")))
       return rc;
   const size_t smem = kHdrBytes + net_region + (size_t)tpb * team_bytes;
   int bps = 0, sms = 0;
