@@ -58,7 +58,8 @@ def parse():
 
 
 # ---------------------------------------------------------------------------
-# per-node accounting of the persistent APG kernel (documented in the design doc)
+# per-node accounting of the persistent APG kernel: values a node reads and writes per
+# iteration and the flops of the sparse-Schur form
 # ---------------------------------------------------------------------------
 def node_counts(net):
     import numpy as np
@@ -305,7 +306,7 @@ def run_batched(rn, n, iters):
             facs.append(rn.Factor(pb.net, pb.cost, pb.tree, precision=rn.RN_PREC_MIXED,
                                   power_iters=50))
             pbs.append(pb)
-        except rn.RapidNetError as e:  # layouts this build does not run (reported)
+        except rn.RapidNetError as e:  # layouts the library refuses (reported)
             if e.status != rn.RN_ERR_UNSUPPORTED:
                 raise
             declined += 1

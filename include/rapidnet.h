@@ -43,7 +43,7 @@ typedef enum {
   RN_ERR_CUDA = -3,       /* a CUDA call failed */
   RN_ERR_TIMEOUT = -4,    /* a device-side wait gave up (bounded spin) */
   RN_ERR_NOMEM = -5,      /* device memory could not be obtained */
-  RN_ERR_UNSUPPORTED = -6,/* valid input outside what this build handles */
+  RN_ERR_UNSUPPORTED = -6,/* valid input outside what the library handles */
   RN_ERR_DIVERGED = -7    /* the residual became NaN or infinite */
 } rn_status;
 

@@ -2,7 +2,7 @@
 
 Translation units are compiled in parallel into ``_build/`` and linked
 into ``librapidnet.so`` next to this file.  The CUDA runtime is linked
-statically, so the library needs only the driver at run time.
+statically, so the library needs only the CUDA driver at run time.
 """
 from __future__ import annotations
 

@@ -798,7 +798,7 @@ int team_layout(int block_threads, int nx, int nu, int *tw_out, int *tpb_out, in
   return RN_OK;
 }
 
-// Layout limits of this build: every work item has a resident block of
+// Layout limits of the library: every work item has a resident block of
 // its own, every group's rows fit in shared memory and all its chain heads
 // are staged at once.  (The kernels carry code for blocks with several
 // items, rows in global memory and chunked heads, but those paths are
@@ -873,17 +873,17 @@ int validate_network(const rn_network *net, const rn_cost *cost) {
   for (int i = 0; i < nu; ++i)
     for (int j = 0; j < nu; ++j)
       if (i != j && cost->Wu[(size_t)i * nu + j] != 0.0) {
-        set_error("cost: this build handles a diagonal Wu only");
+        set_error("cost: the library handles a diagonal Wu only");
         return RN_ERR_UNSUPPORTED;
       }
   for (int i = 0; i < nx; ++i)
     for (int j = 0; j < nx; ++j)
       if (net->A[(size_t)i * nx + j] != (i == j ? 1.0 : 0.0)) {
-        set_error("network: this build handles A = I only (tank mass balance)");
+        set_error("network: the library handles A = I only (tank mass balance)");
         return RN_ERR_UNSUPPORTED;
       }
   if (std::max(nx, nu) > 256) {
-    set_error("network: this build handles nx, nu <= 256");
+    set_error("network: the library handles nx, nu <= 256");
     return RN_ERR_UNSUPPORTED;
   }
   return RN_OK;

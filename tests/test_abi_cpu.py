@@ -87,12 +87,12 @@ def _factor_status(net, cost, tree):
 
 def test_validation_errors_before_cuda(lib):
     pb = make_problem("tiny")
-    # A != I is outside this build
+    # A != I is outside what the library handles
     net = make_problem("tiny").net
     net.A = np.eye(net.nx) * 1.01
     assert _factor_status(net, pb.cost, pb.tree) == B.RN_ERR_UNSUPPORTED
     assert "A = I" in rn.rapidnet_last_error()
-    # dense Wu is outside this build; a non-positive diagonal is invalid
+    # a dense Wu is outside what the library handles; a non-positive diagonal is invalid
     pb2 = make_problem("tiny")
     pb2.cost.Wu = pb2.cost.Wu + 0.1
     assert _factor_status(pb2.net, pb2.cost, pb2.tree) == B.RN_ERR_UNSUPPORTED

@@ -1,7 +1,7 @@
 """Mixed precision (FP32 iteration around an FP64 reference) against the FP64
 oracle at the same iteration count.
 
-Bar (the benchmark's accuracy statement): cost within
+Bar (the accuracy statement of the mixed-precision mode): cost within
 1e-3 relative of the oracle's; the returned (u, x) satisfy the dynamics
 and couplings (they come from an FP64 evaluation of the dual gradient at
 the last w) to 1e-9 of their scale, i.e. primal infeasibility far below
