@@ -17,7 +17,14 @@ BUILD = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "librapidnet.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["plan.cpp", "rapidnet.cu", "solve_kernels.cu", "mixed_kernels.cu", "batch_kernels.cu", "server.cpp"]
+# (source, object, extra flags): the kernel units are compiled once per
+# component count C (instantiations chosen at run time by dispatch.cu), so
+# that the device compiler runs on them in parallel
+_KERNELS = ["solve_kernels.cu", "mixed_kernels.cu", "batch_kernels.cu"]
+SOURCES = [(s, os.path.splitext(s)[0] + ".o", []) for s in
+           ["plan.cpp", "rapidnet.cu", "dispatch.cu", "server.cpp"]]
+SOURCES += [(k, f"{os.path.splitext(k)[0]}_c{c}.o", [f"-DRN_CVAL={c}"])
+            for k in _KERNELS for c in (1, 2, 4, 8)]
 
 
 def _nvcc() -> str:
@@ -27,14 +34,15 @@ def _nvcc() -> str:
     return cand
 
 
-def _compile(src: str, verbose: bool) -> str:
-    obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
+def _compile(entry, verbose: bool) -> str:
+    src, objname, extra = entry
+    obj = os.path.join(BUILD, objname)
     path = os.path.join(CSRC, src)
     deps = [path] + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))]
     deps.append(os.path.join(INCLUDE, "rapidnet.h"))
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(d) for d in deps):
         return obj
-    cmd = [_nvcc(), *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
+    cmd = [_nvcc(), *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", *extra,
            "-I", INCLUDE, "-c", path, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -46,7 +54,8 @@ def _compile(src: str, verbose: bool) -> str:
 
 def build(verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+    workers = max(1, min(len(SOURCES), os.cpu_count() or 1))
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
         objs = list(ex.map(lambda s: _compile(s, verbose), SOURCES))
     newest = max(os.path.getmtime(o) for o in objs)
     if not os.path.exists(LIB) or os.path.getmtime(LIB) < newest:

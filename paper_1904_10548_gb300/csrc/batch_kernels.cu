@@ -26,7 +26,7 @@ struct BatchCtx {
 
 // parameters of problem p into shared memory (with its network copy);
 // every thread of the block calls it at the same points
-__device__ void load_problem(const BatchDev &B, int p, BatchCtx &bc, MixedParams &mp,
+static __device__ void load_problem(const BatchDev &B, int p, BatchCtx &bc, MixedParams &mp,
                              const BlockMem &bm) {
   if (bc.loaded == p) return;
   __syncthreads();
@@ -38,7 +38,7 @@ __device__ void load_problem(const BatchDev &B, int p, BatchCtx &bc, MixedParams
   __syncthreads();
 }
 
-__device__ int slot_of(const BatchCtx &bc, int p) {
+static __device__ int slot_of(const BatchCtx &bc, int p) {
   for (int s = 0; s < bc.n; ++s)
     if (bc.prob[s] == p) return s;
   return -1;
@@ -263,37 +263,7 @@ __global__ void __launch_bounds__(512) k_batch(BatchDev B) {
   }
 }
 
-static const void *batch_fn(int c) {
-  switch (c) {
-    case 1: return (const void *)k_batch<1>;
-    case 2: return (const void *)k_batch<2>;
-    case 4: return (const void *)k_batch<4>;
-    default: return (const void *)k_batch<8>;
-  }
-}
-
-cudaError_t launch_batch(const BatchDev &B, int maxc, int grid, int block, size_t smem,
-                         cudaStream_t st) {
-  const void *fn = batch_fn(maxc);
-  cudaError_t e = allow_max_smem(fn);
-  if (e != cudaSuccess) return e;
-  BatchDev b = B;
-  void *args[] = {&b};
-  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, smem, st);
-}
-
-cudaError_t batch_static_smem(int maxc, int *bytes) {
-  cudaFuncAttributes fa{};
-  cudaError_t e = cudaFuncGetAttributes(&fa, batch_fn(maxc));
-  if (e == cudaSuccess) *bytes = (int)fa.sharedSizeBytes;
-  return e;
-}
-
-cudaError_t batch_occupancy(int maxc, int block, size_t smem, int *blocks_per_sm) {
-  const void *fn = batch_fn(maxc);
-  cudaError_t e = allow_max_smem(fn);
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, smem);
-}
+// this translation unit is compiled once per component count RN_CVAL
+const void *RN_CAT(batch_kernel_c, RN_CVAL)() { return (const void *)k_batch<RN_CVAL>; }
 
 }  // namespace rn

@@ -204,6 +204,21 @@ __host__ __device__ inline size_t net_smem_bytes(int nx, int nu, int ne, int nnz
   return round16(sizeof(NetDev<double>)) + round16(ints * 4) + round16(vals * elem);
 }
 
+// The kernel translation units (solve_kernels.cu, mixed_kernels.cu,
+// batch_kernels.cu) are compiled once per component count C = RN_CVAL in
+// {1, 2, 4, 8}, in parallel; each exports its instantiations through these
+// functions and dispatch.cu picks one at run time.
+#define RN_CAT2(a, b) a##b
+#define RN_CAT(a, b) RN_CAT2(a, b)
+#define RN_DECLARE_KERNELS(c)                          \
+  const void *RN_CAT(solve_kernel_c, c)(bool apg);     \
+  const void *RN_CAT(mixed_kernel_c, c)();              \
+  const void *RN_CAT(batch_kernel_c, c)();
+RN_DECLARE_KERNELS(1)
+RN_DECLARE_KERNELS(2)
+RN_DECLARE_KERNELS(4)
+RN_DECLARE_KERNELS(8)
+
 // Raise a kernel's dynamic shared-memory limit to the device's opt-in
 // maximum, once per kernel: launches then use what they need.  Changing
 // the attribute between launches of a kernel that is running on another

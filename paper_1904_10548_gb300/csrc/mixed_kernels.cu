@@ -115,30 +115,7 @@ __global__ void __launch_bounds__(512) k_mixed(MixedParams M) {
   }
 }
 
-static const void *mixed_fn(int c) {
-  switch (c) {
-    case 1: return (const void *)k_mixed<1>;
-    case 2: return (const void *)k_mixed<2>;
-    case 4: return (const void *)k_mixed<4>;
-    default: return (const void *)k_mixed<8>;
-  }
-}
-
-cudaError_t launch_mixed(const MixedParams &M, int maxc, int grid, int block, size_t smem,
-                         cudaStream_t st) {
-  const void *fn = mixed_fn(maxc);
-  cudaError_t e = allow_max_smem(fn);
-  if (e != cudaSuccess) return e;
-  MixedParams p = M;
-  void *args[] = {&p};
-  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, smem, st);
-}
-
-cudaError_t mixed_occupancy(int maxc, int block, size_t smem, int *blocks_per_sm) {
-  const void *fn = mixed_fn(maxc);
-  cudaError_t e = allow_max_smem(fn);
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, smem);
-}
+// this translation unit is compiled once per component count RN_CVAL
+const void *RN_CAT(mixed_kernel_c, RN_CVAL)() { return (const void *)k_mixed<RN_CVAL>; }
 
 }  // namespace rn

@@ -18,32 +18,9 @@
 // (a group) are summed, rolled back down and published by one block, and
 // each chain turns the published path sums of its parent into its own by
 // an elementwise correction of its precomputed local sums.
-#include <mutex>
-#include <set>
-
 #include "solve_device.cuh"
 
 namespace rn {
-
-cudaError_t allow_max_smem(const void *fn) {
-  static std::mutex mu;
-  static std::set<std::pair<int, const void *>> done;
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  std::lock_guard<std::mutex> lk(mu);
-  if (done.count({dev, fn})) return cudaSuccess;
-  int optin = 0;
-  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (e != cudaSuccess) return e;
-  cudaFuncAttributes fa{};
-  e = cudaFuncGetAttributes(&fa, fn);  // static shared memory counts against the limit
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           optin - (int)fa.sharedSizeBytes);
-  if (e == cudaSuccess) done.insert({dev, fn});
-  return e;
-}
 
 // ---------------------------------------------------------------------------
 // the persistent kernel: `iters` APG iterations (APG = true) or one
@@ -105,37 +82,10 @@ __global__ void __launch_bounds__(512) k_solve(KParams<T> P) {
   }
 }
 
-template <typename T, bool APG>
-static const void *solve_fn(int c) {
-  switch (c) {
-    case 1: return (const void *)k_solve<T, APG, 1>;
-    case 2: return (const void *)k_solve<T, APG, 2>;
-    case 4: return (const void *)k_solve<T, APG, 4>;
-    default: return (const void *)k_solve<T, APG, 8>;
-  }
+// this translation unit is compiled once per component count RN_CVAL
+const void *RN_CAT(solve_kernel_c, RN_CVAL)(bool apg) {
+  return apg ? (const void *)k_solve<double, true, RN_CVAL>
+             : (const void *)k_solve<double, false, RN_CVAL>;
 }
-
-template <typename T, bool APG>
-cudaError_t launch_solve(const KParams<T> &P, int grid, int block, size_t smem, cudaStream_t st) {
-  const void *fn = solve_fn<T, APG>(P.maxc);
-  cudaError_t e = allow_max_smem(fn);
-  if (e != cudaSuccess) return e;
-  KParams<T> p = P;
-  void *args[] = {&p};
-  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, smem, st);
-}
-
-template <typename T, bool APG>
-cudaError_t solve_occupancy(int maxc, int block, size_t smem, int *blocks_per_sm) {
-  const void *fn = solve_fn<T, APG>(maxc);
-  cudaError_t e = allow_max_smem(fn);
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, smem);
-}
-
-template cudaError_t launch_solve<double, true>(const KParams<double> &, int, int, size_t, cudaStream_t);
-template cudaError_t launch_solve<double, false>(const KParams<double> &, int, int, size_t, cudaStream_t);
-template cudaError_t solve_occupancy<double, true>(int, int, size_t, int *);
-template cudaError_t solve_occupancy<double, false>(int, int, size_t, int *);
 
 }  // namespace rn
