@@ -154,7 +154,11 @@ typedef struct {
  * its inverse (FP64), uploads everything to the device, and, unless
  * opts->gamma > 0, estimates the Lipschitz constant of the dual gradient
  * by FP64 power iteration.  On success *out owns device memory until
- * rapidnet_factor_free.  opts may be NULL (defaults). */
+ * rapidnet_factor_free.  opts may be NULL (defaults).  Returns
+ * RN_ERR_UNSUPPORTED, before any launch, for a non-diagonal W_u, A != I,
+ * nx or nu above 256, or a tree whose schedule needs more work items than
+ * the device keeps resident (one item per group of top nodes and per four
+ * chains) or a group larger than the shared-memory capacity. */
 int rapidnet_factor(const rn_network *net, const rn_tree *tree,
                     const rn_cost *cost, const rn_opts *opts,
                     rn_factor **out);
@@ -198,7 +202,9 @@ typedef struct {
  * stops at its own first check with residual <= tol (tol <= 0: exactly
  * max_iters).  Returns RN_OK when every problem converged (or tol <= 0),
  * RN_NOT_CONVERGED when some did not, or an error; per-problem results in
- * req[i].out.  Synchronises the streams of all handles. */
+ * req[i].out.  Synchronises the streams of all handles.  RN_ERR_UNSUPPORTED
+ * (before any launch) when a problem's group of top nodes does not fit the
+ * batch's shared-memory layout. */
 int rapidnet_solve_batch(rn_factor *const *f, const rn_solve_req *req, int n,
                          int max_iters, double tol);
 
