@@ -868,10 +868,18 @@ __device__ bool group_step(const KParams<T> &P, int g, const Smem<T> &sm, const 
     for (int e = tm.tid; e < dn / 4; e += tm.nt) cp16(desc + 4 * e, pl.g_desc + d0 + 4 * e, false);
     constexpr int per = 16 / sizeof(T);
     const int nv = NUP / per;
-    for (int e = tm.tid; e < m * nv; e += tm.nt) {
-      const int li = e / nv, c = e - li * nv;
-      cp16(rb + (size_t)li * SP + NXP + c * per, P.st.ux + (size_t)(g0 + li) * SP + NXP + c * per,
-           true);
+    if (m <= gcap) {
+      for (int e = tm.tid; e < m * nv; e += tm.nt) {
+        const int li = e / nv, c = e - li * nv;
+        cp16(rb + (size_t)li * SP + NXP + c * per,
+             P.st.ux + (size_t)(g0 + li) * SP + NXP + c * per, true);
+      }
+    } else {
+      // rows in global memory: the asynchronous copy writes shared memory only
+      for (int e = tm.tid; e < m * NUP; e += tm.nt) {
+        const int li = e / NUP, j = e - li * NUP;
+        rb[(size_t)li * SP + NXP + j] = __ldcg(P.st.ux + (size_t)(g0 + li) * SP + NXP + j);
+      }
     }
     cp_wait();
     tm.sync();
