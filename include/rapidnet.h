@@ -147,6 +147,8 @@ typedef struct {
   double gamma;
   int precision;
   long long device_bytes;  /* device memory held by the handle */
+  double collapse_dev;     /* factor check: max |2 p Phi - F| / max |F| over
+                              the sampled nodes of the general recursion */
 } rn_factor_info;
 
 /* Factor step (paper Table 2 Engine::factorStep, §4.4): validates the
@@ -154,7 +156,12 @@ typedef struct {
  * its inverse (FP64), uploads everything to the device, and, unless
  * opts->gamma > 0, estimates the Lipschitz constant of the dual gradient
  * by FP64 power iteration.  On success *out owns device memory until
- * rapidnet_factor_free.  opts may be NULL (defaults).  Returns
+ * rapidnet_factor_free.  opts may be NULL (defaults).
+ * The factor check runs one step of the general per-node recursion
+ * (Q = 2 p W_u + sum of the children's P, Phi = L (L' Q L)^-1 L', L a
+ * basis of ker E) in FP64 at the first node of stages 1, N/2 and N, and
+ * returns RN_ERR_RANK if 2 p Phi differs from the shared operator F by more
+ * than 1e-8 relative (E W_u^-1 E' too ill-conditioned).  Returns
  * RN_ERR_UNSUPPORTED, before any launch, for a non-diagonal W_u, A != I,
  * nx or nu above 256, or a tree whose schedule needs more work items than
  * the device keeps resident (one item per group of top nodes and per four

@@ -86,7 +86,8 @@ class rn_factor_info(ctypes.Structure):
     _fields_ = [("nx", c_int), ("nu", c_int), ("nd", c_int), ("ne", c_int), ("N", c_int),
                 ("n_nodes", c_int), ("n_chains", c_int), ("n_top", c_int),
                 ("grid_ctas", c_int), ("block_threads", c_int), ("L", c_double),
-                ("gamma", c_double), ("precision", c_int), ("device_bytes", c_longlong)]
+                ("gamma", c_double), ("precision", c_int), ("device_bytes", c_longlong),
+                ("collapse_dev", c_double)]
 
 
 EXPORTS = {

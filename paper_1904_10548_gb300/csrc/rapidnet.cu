@@ -442,6 +442,7 @@ struct rn_factor {
   int nx = 0, nu = 0, nd = 0, ne = 0, NXP = 0, NUP = 0, SP = 0, YP = 0, NEP = 0;
   double W_alpha = 0.0, Ws = 0.0, Wx = 0.0;
   double gamma = 0.0, L = 0.0;
+  double collapse_dev = 0.0;  // factor check of the shared operator
   // launch layout of the FP64 kernel (APG and plain evaluations)
   int grid = 0, block = 0, maxc = 2, tw = 64, tpb = 2;
   size_t smem = 0;
@@ -539,45 +540,6 @@ bool finite_all(const double *p, size_t n) {
   for (size_t i = 0; i < n; ++i)
     if (!std::isfinite(p[i])) return false;
   return true;
-}
-
-// Cholesky A = R R' of an SPD m x m matrix in place (lower).  Returns false
-// if a pivot is not positive relative to the diagonal scale.
-bool cholesky(std::vector<double> &A, int m) {
-  double scale = 0.0;
-  for (int i = 0; i < m; ++i) scale = std::max(scale, std::fabs(A[(size_t)i * m + i]));
-  for (int j = 0; j < m; ++j) {
-    double d = A[(size_t)j * m + j];
-    for (int k = 0; k < j; ++k) d -= A[(size_t)j * m + k] * A[(size_t)j * m + k];
-    if (!(d > 1e-13 * scale)) return false;
-    d = std::sqrt(d);
-    A[(size_t)j * m + j] = d;
-    for (int i = j + 1; i < m; ++i) {
-      double v = A[(size_t)i * m + j];
-      for (int k = 0; k < j; ++k) v -= A[(size_t)i * m + k] * A[(size_t)j * m + k];
-      A[(size_t)i * m + j] = v / d;
-    }
-  }
-  return true;
-}
-
-// inverse of an SPD matrix from its Cholesky factor (columns of R^-T R^-1)
-std::vector<double> chol_inverse(const std::vector<double> &R, int m) {
-  std::vector<double> inv((size_t)m * m, 0.0), col(m);
-  for (int c = 0; c < m; ++c) {
-    for (int i = 0; i < m; ++i) {
-      double v = (i == c) ? 1.0 : 0.0;
-      for (int k = 0; k < i; ++k) v -= R[(size_t)i * m + k] * col[k];
-      col[i] = v / R[(size_t)i * m + i];
-    }
-    for (int i = m - 1; i >= 0; --i) {
-      double v = col[i];
-      for (int k = i + 1; k < m; ++k) v -= R[(size_t)k * m + i] * col[k];
-      col[i] = v / R[(size_t)i * m + i];
-    }
-    for (int i = 0; i < m; ++i) inv[(size_t)i * m + c] = col[i];
-  }
-  return inv;
 }
 
 template <typename T>
@@ -957,6 +919,14 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
       return RN_ERR_RANK;
     }
     Sinv = chol_inverse(R, ne);
+  }
+  // the shared operator must stand for every node's factor of the general
+  // recursion (it does in exact arithmetic; this bounds the rounding)
+  f->collapse_dev = collapse_deviation(tree, nu, ne, net->E, winv.data(), Sinv.data());
+  if (!(f->collapse_dev <= kCollapseTol)) {
+    set_error("factor check: 2 p Phi differs from the shared operator F by %.3g (relative) at a "
+              "sampled node; E W_u^-1 E' is too ill-conditioned", f->collapse_dev);
+    return RN_ERR_RANK;
   }
 
   const Plan &p = f->plan;
@@ -1471,6 +1441,7 @@ extern "C" int rapidnet_factor_info(const rn_factor *f, rn_factor_info *info) {
   info->gamma = f->gamma;
   info->precision = f->opts.precision;
   info->device_bytes = f->bytes;
+  info->collapse_dev = f->collapse_dev;
   return RN_OK;
 }
 

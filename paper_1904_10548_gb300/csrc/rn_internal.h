@@ -85,4 +85,21 @@ struct Plan {
 // set.
 int build_plan(const rn_tree *tree, Plan &plan, int max_groups = 1 << 30);
 
+// Dense FP64 helpers of the factor step (factor_check.cpp).  cholesky:
+// A = R R' of an SPD m x m matrix in place (lower); false if a pivot is
+// not positive relative to the diagonal scale.  chol_inverse: the inverse
+// from that factor.
+bool cholesky(std::vector<double> &A, int m);
+std::vector<double> chol_inverse(const std::vector<double> &R, int m);
+
+// Largest relative deviation max|2 p Phi - F| / max|F| of one step of the
+// general per-node recursion (paper §4.4) from the shared operator
+// F = W^-1 - W^-1 E' S^-1 E W^-1, at the first node of stages 1, N/2 and N,
+// with the children's P_c formed from F.  E: ne x nu row-major; winv: the
+// diagonal of W_u^-1; Sinv: (E W^-1 E')^-1, ne x ne.  Infinity if L' Q L is
+// not positive definite or E' loses rank.
+double collapse_deviation(const rn_tree *tree, int nu, int ne, const double *E,
+                          const double *winv, const double *Sinv);
+constexpr double kCollapseTol = 1e-8;
+
 }  // namespace rn
