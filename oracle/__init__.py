@@ -24,8 +24,9 @@ Every function follows the paper's steps in its order and notation:
 
 Parity: pinned against a dense KKT solve of the tree QP, constraint
 residuals, brute-force prox minimisation, the Moreau identity, the theta
-identity, a scipy QP solve of the input-box-only problem and a vanishing
-duality gap (tests/test_oracle_*.py).
+identity, a scipy QP solve of the input-box-only problem, a scipy NLP of
+the full problem with active soft terms (epigraph form, no duality) and a
+vanishing duality gap (tests/test_oracle_*.py).
 """
 from .smpc import (
     OracleProblem, Factor, SolveConsts, factor, solve_consts, dual_gradient,
