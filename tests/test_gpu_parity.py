@@ -222,6 +222,16 @@ def test_repeat_solves_are_bitwise_reproducible():
         assert np.array_equal(a[k], b[k])
 
 
+@pytest.mark.parametrize("kind", ["tiny", "barcelona32", "ne0"])
+def test_factor_check_of_the_shared_operator(kind):
+    """The factor step's check of the general per-node recursion (§4.4)
+    against the shared F: rounding-level on well-conditioned networks."""
+    fac = gpu_factor(problem(kind), gamma=1.0)
+    dev = fac.info()["collapse_dev"]
+    fac.close()
+    assert 0.0 <= dev < 1e-12
+
+
 def test_rank_deficient_coupling_is_rejected():
     pb = problem("tiny")
     pb.net.E = np.vstack([pb.net.E[:1], pb.net.E[:1]])
