@@ -55,7 +55,7 @@ typedef enum {
 /* Water network, paper §2.1 (eqs. dynamics, input-disturbance-coupling,
  * state-constraints, input-constraints).  Shapes: A nx*nx, B nx*nu,
  * Gd nx*nd, E ne*nu, Ed ne*nd; xmin, xmax, xs: nx; umin, umax: nu.
- * ne may be 0 (then E, Ed may be NULL).  This build requires A = I (the
+ * ne may be 0 (then E, Ed may be NULL).  The library requires A = I (the
  * exact discretisation of the tank mass balance, eq. tank-dynamics);
  * other A give RN_ERR_UNSUPPORTED. */
 typedef struct {
@@ -79,7 +79,7 @@ typedef struct {
 
 /* Cost weights, paper §3.1 (eqs. cost:linear, cost:smooth,
  * cost:non-smooth): W_alpha > 0, alpha0 (nu), W_u (nu*nu, symmetric
- * positive definite), W_s >= 0, W_x >= 0.  This build requires a
+ * positive definite), W_s >= 0, W_x >= 0.  The library requires a
  * diagonal W_u (the paper's choice W_u = w I); a dense W_u gives
  * RN_ERR_UNSUPPORTED.  W_u not positive definite gives RN_ERR_INVAL. */
 typedef struct {
