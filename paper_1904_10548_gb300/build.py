@@ -22,7 +22,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # that the device compiler runs on them in parallel
 _KERNELS = ["solve_kernels.cu", "mixed_kernels.cu", "batch_kernels.cu"]
 SOURCES = [(s, os.path.splitext(s)[0] + ".o", []) for s in
-           ["plan.cpp", "factor_check.cpp", "rapidnet.cu", "dispatch.cu", "server.cpp"]]
+           ["plan.cpp", "factor_check.cpp", "layout.cpp", "rapidnet.cu", "dispatch.cu", "server.cpp"]]
 SOURCES += [(k, f"{os.path.splitext(k)[0]}_c{c}.o", [f"-DRN_CVAL={c}"])
             for k in _KERNELS for c in (1, 2, 4, 8)]
 

@@ -210,6 +210,22 @@ __host__ __device__ inline size_t net_smem_bytes(int nx, int nu, int ne, int nnz
 // functions and dispatch.cu picks one at run time.
 #define RN_CAT2(a, b) a##b
 #define RN_CAT(a, b) RN_CAT2(a, b)
+// work-buffer sizes of one precision in one kernel's shared-memory layout
+struct Sizes {
+  int team_bytes = 0, net_bytes = 0;  // layout of the block
+  int buf = 0, gbuf = 0, segb = 1, gcap = 0, hchunk = 1, fslots = 1, fbrows = 1, tpb = 2;
+};
+// padded row lengths of a factor's network (elements)
+struct RowDims {
+  int NXP, NUP, YP, SP, NEP;
+};
+// host layout rules (layout.cpp)
+struct Plan;
+int layout_sizes(const Plan &p, const RowDims &f, int eb, int team_bytes, int net_bytes, int tw,
+                 int tpb, int mode, Sizes *z);
+int team_layout(int block_threads, int nx, int nu, int *tw_out, int *tpb_out, int *maxc_out);
+int check_layout(const Plan &p, const Sizes &z, int n_items, int grid, const char *what);
+
 #define RN_DECLARE_KERNELS(c)                          \
   const void *RN_CAT(solve_kernel_c, c)(bool apg);     \
   const void *RN_CAT(mixed_kernel_c, c)();              \
