@@ -224,6 +224,8 @@ struct Plan;
 int layout_sizes(const Plan &p, const RowDims &f, int eb, int team_bytes, int net_bytes, int tw,
                  int tpb, int mode, Sizes *z);
 int team_layout(int block_threads, int nx, int nu, int *tw_out, int *tpb_out, int *maxc_out);
+int team_bytes_for(int sms, int optin, int per_sm, int reserved, int n_items, int tpb, int block,
+                   int net_bytes, int static_smem, int *team_bytes, int *blocks_per_sm);
 int check_layout(const Plan &p, const Sizes &z, int n_items, int grid, const char *what);
 
 #define RN_DECLARE_KERNELS(c)                          \

@@ -10,6 +10,27 @@
 
 namespace rn {
 
+// Bytes of one team region: the block's shared memory (the opt-in limit, or
+// the SM's share when several blocks must sit on one SM) less the
+// reserved and static parts, the block header and the network copy, split
+// among tpb teams (16-byte multiples).  Blocks per SM: enough for every
+// item, at most what 128 registers a thread allow (the kernels' launch
+// bound), at most 4.
+int team_bytes_for(int sms, int optin, int per_sm, int reserved, int n_items, int tpb, int block,
+                   int net_bytes, int static_smem, int *team_bytes, int *blocks_per_sm) {
+  const int by_regs = std::max(1, 65536 / (block * 128));
+  const int bpsm = std::max(1, std::min({4, by_regs, (n_items + sms - 1) / std::max(1, sms)}));
+  const int budget = std::min(optin, per_sm / bpsm - reserved) - static_smem;
+  const int tb = ((budget - kHdrBytes - net_bytes) / tpb) & ~15;
+  if (blocks_per_sm) *blocks_per_sm = bpsm;
+  if (tb <= 0) {
+    set_error("shared memory: the network data leave no room for the work buffers");
+    return RN_ERR_UNSUPPORTED;
+  }
+  *team_bytes = tb;
+  return RN_OK;
+}
+
 // Work-buffer sizes of elements of eb bytes in team regions of team_bytes
 // for teams of tw threads, tpb to a block: the team buffer holds the forward slots of
 // `mode` (up to three per warp) and a backward segment (as

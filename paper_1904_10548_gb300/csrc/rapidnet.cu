@@ -665,18 +665,8 @@ int team_budget(int device, int n_items, int tpb, int block, int net_bytes, int 
   RN_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
   RN_CUDA(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device));
   RN_CUDA(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, device));
-  // blocks per SM: enough for every item, at most what 128 registers a
-  // thread allow (the kernels' launch bound), at most 4
-  const int by_regs = std::max(1, 65536 / (block * 128));
-  const int bpsm = std::max(1, std::min({4, by_regs, (n_items + sms - 1) / std::max(1, sms)}));
-  const int budget = std::min(optin, per_sm / bpsm - reserved) - static_smem;
-  const int tb = ((budget - kHdrBytes - net_bytes) / tpb) & ~15;
-  if (tb <= 0) {
-    set_error("shared memory: the network data leave no room for the work buffers");
-    return RN_ERR_UNSUPPORTED;
-  }
-  *team_bytes = tb;
-  return RN_OK;
+  return team_bytes_for(sms, optin, per_sm, reserved, n_items, tpb, block, net_bytes, static_smem,
+                        team_bytes, nullptr);
 }
 
 int fit_sizes(const rn_factor *f, int eb, int team_bytes, int net_bytes, int tw, int tpb, int mode,

@@ -4,8 +4,9 @@ and the layouts that factor creation refuses before any launch.
 
 layout.cpp and plan.cpp are compiled with g++ against a small driver that
 replays factor creation's layout decision for given device attributes
-(the per-block budget is the same arithmetic as the library's, with the
-attributes passed in instead of queried).  The attributes below are
+(team_bytes_for gets the attributes that the library queries from the
+device; the grid is the blocks per SM times the SMs, as the occupancy
+query gives for these kernels).  The attributes below are
 those of a GB300 (sm_103): 152 SMs, 227 KB of shared memory per block
 (opt-in), 228 KB per SM, 1 KB reserved per block."""
 import json
@@ -31,13 +32,13 @@ DRIVER = r"""
 #include "rn_internal.h"
 using namespace rn;
 static int ceil4(int v) { return (v + 3) & ~3; }
-// per-team bytes for `net` bytes of network data (the library's budget rule)
+// per-team bytes for `net` bytes of network data (0 if none are left)
 static int budget(int n_items, int tpb, int block, int net, int sms, int optin, int per_sm,
                   int reserved, int *bpsm_out) {
-  const int by_regs = std::max(1, 65536 / (block * 128));
-  const int bpsm = std::max(1, std::min({4, by_regs, (n_items + sms - 1) / sms}));
-  *bpsm_out = bpsm;
-  return ((std::min(optin, per_sm / bpsm - reserved) - kHdrBytes - net) / tpb) & ~15;
+  int tb = 0;
+  if (team_bytes_for(sms, optin, per_sm, reserved, n_items, tpb, block, net, 0, &tb, bpsm_out))
+    return 0;
+  return tb;
 }
 static void dump(const char *k, const Sizes &z) {
   std::printf("\"%s\": {\"buf\": %d, \"gbuf\": %d, \"segb\": %d, \"gcap\": %d, \"hchunk\": %d,"
