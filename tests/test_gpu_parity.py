@@ -155,6 +155,28 @@ def test_apg_matches_oracle(kind, iters):
     assert abs(out["gap"] - gap) <= 1e-6 * max(abs(cost), 1.0)
 
 
+@pytest.mark.parametrize("kind", ["tiny", "barcelona32", "tight"])
+def test_first_ten_iterates_match_oracle(kind):
+    """Iterate by iterate: the GPU solve stopped after k = 1 .. 10
+    iterations against the oracle's k-th APG iterate (eqs. apg:1 / apg:2),
+    all ten on the scale of the whole trajectory."""
+    pb = problem(kind)
+    P, F, S = oracle_for(kind, pb)
+    gamma = O.step_size(O.power_iteration(P, F, 100))
+    fac = gpu_factor(pb, gamma=gamma)
+    got, ref = {k: [] for k in "uxy"}, {k: [] for k in "uxy"}
+    for it in range(1, 11):
+        out = fac.solve(pb.data.x0, pb.data.q, pb.data.demand, pb.data.alpha, max_iters=it)
+        r = O.apg(P, F, S, it, gamma)
+        assert out["iters"] == it
+        for k in "uxy":
+            got[k].append(out[k])
+            ref[k].append(getattr(r, k))
+    fac.close()
+    for k in "uxy":
+        assert rel_err(np.stack(got[k]), np.stack(ref[k])) <= RTOL, k
+
+
 def test_tolerance_stop_and_residual_history():
     pb = problem("tiny")
     P, F, S = oracle_for("tiny", pb)
