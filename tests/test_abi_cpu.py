@@ -129,3 +129,29 @@ def test_valid_input_reaches_cuda_or_succeeds(lib):
     pb = make_problem("tiny")
     st = _factor_status(pb.net, pb.cost, pb.tree)
     assert st in (B.RN_OK, B.RN_ERR_CUDA, B.RN_ERR_NOMEM)
+
+
+def test_server_argument_validation(lib):
+    """The serving calls reject NULL or malformed arguments with
+    RN_ERR_INVAL before touching a device; creation without a GPU fails in
+    its CUDA call (RN_ERR_CUDA) and hands out no handle."""
+    null = ctypes.c_void_p()
+    assert lib.rapidnet_server_create(None, None) == B.RN_ERR_INVAL
+    h = ctypes.c_void_p()
+    st = lib.rapidnet_server_create(None, ctypes.byref(h))
+    if st != B.RN_OK:
+        assert st == B.RN_ERR_CUDA and not h.value
+    else:
+        lib.rapidnet_server_destroy(h)
+    key = ctypes.c_int()
+    assert lib.rapidnet_server_add_model(null, None, None, None, None, ctypes.byref(key)) == \
+        B.RN_ERR_INVAL
+    ticket = ctypes.c_longlong()
+    v = np.zeros(8)
+    pv = v.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert lib.rapidnet_server_submit(null, 0, pv, pv, pv, pv, 10, 0.0, 0,
+                                      ctypes.byref(ticket)) == B.RN_ERR_INVAL
+    assert lib.rapidnet_server_wait(null, 0, 0.0, None, None) == B.RN_ERR_INVAL
+    assert lib.rapidnet_server_stats(null, None) == B.RN_ERR_INVAL
+    lib.rapidnet_server_destroy(null)  # a NULL handle is ignored
+    assert "NULL" in lib.rapidnet_last_error().decode()
