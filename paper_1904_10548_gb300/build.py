@@ -19,12 +19,15 @@ LIB = os.path.join(HERE, "librapidnet.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # (source, object, extra flags): the kernel units are compiled once per
 # component count C (instantiations chosen at run time by dispatch.cu), so
-# that the device compiler runs on them in parallel
-_KERNELS = ["solve_kernels.cu", "mixed_kernels.cu", "batch_kernels.cu"]
-SOURCES = [(s, os.path.splitext(s)[0] + ".o", []) for s in
-           ["plan.cpp", "factor_check.cpp", "layout.cpp", "rapidnet.cu", "dispatch.cu", "server.cpp"]]
-SOURCES += [(k, f"{os.path.splitext(k)[0]}_c{c}.o", [f"-DRN_CVAL={c}"])
-            for k in _KERNELS for c in (1, 2, 4, 8)]
+# that the device compiler runs on them in parallel; the longest compiles
+# (batched, then mixed kernels) are submitted first so that the slowest one
+# starts at once
+_KERNELS = ["batch_kernels.cu", "mixed_kernels.cu", "solve_kernels.cu"]
+SOURCES = [(k, f"{os.path.splitext(k)[0]}_c{c}.o", [f"-DRN_CVAL={c}"])
+           for k in _KERNELS for c in (8, 4, 2, 1)]
+SOURCES += [(s, os.path.splitext(s)[0] + ".o", []) for s in
+            ["rapidnet.cu", "dispatch.cu", "server.cpp", "plan.cpp", "factor_check.cpp",
+             "layout.cpp"]]
 
 
 def _nvcc() -> str:
