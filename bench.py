@@ -295,6 +295,20 @@ def batch_problems(n):
     return out
 
 
+def max_over_ranks(ms, dist, device):
+    """The job's time: the slowest rank's (all ranks get it)."""
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(total_ms, world, steps, iters):
+    """Whole-job throughput: the iterations of all ranks over the job's time."""
+    return world * steps * iters / (total_ms / 1e3)
+
+
 def run_batched(rn, n, iters):
     """256 problems (nx 16/63/128, uneven trees of 16-512 scenarios, N = 24)
     in one persistent launch vs the same problems solved one by one."""
@@ -473,12 +487,8 @@ def main():
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    total_ms = sum(a.elapsed_time(b) for a, b in evs)
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    value = world * args.steps * args.iters / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), dist, "cuda")
+    value = job_value(total_ms, world, args.steps, args.iters)
 
     # end to end through the host entry point: pinned host inputs and outputs
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).pin_memory()
