@@ -311,10 +311,15 @@ def prox_gstar(P: OracleProblem, z: np.ndarray, gamma: float):
 # ----------------------------------------------------------------------------
 # accelerated proximal gradient on the dual (§4.3)
 # ----------------------------------------------------------------------------
-def theta_beta(n: int):
-    """theta_{-1} = theta_0 = 1, theta_{nu+1} = (sqrt(theta^4 + 4 theta^2)
-    - theta^2) / 2, beta_nu = theta_nu (1/theta_{nu-1} - 1) (§4.3).
+def theta_beta(n: int, rule: str = "equality"):
+    """theta_{-1} = theta_0 = 1 and beta_nu = theta_nu (1/theta_{nu-1} - 1)
+    (§4.3), with theta_{nu+1} = (sqrt(theta^4 + 4 theta^2) - theta^2) / 2
+    (rule "equality", the paper's choice, which meets the requirement
+    1 - theta_{nu+1} <= theta_{nu+1}^2 / theta_nu^2 with equality) or
+    theta_nu = 2 / (nu + 2) (rule "simple", the other choice §4.3 names).
     Returns (beta[0..n-1], theta[0..n])."""
+    if rule not in ("equality", "simple"):
+        raise ValueError("rule must be 'equality' or 'simple'")
     theta = np.empty(n + 1)
     theta[0] = 1.0
     beta = np.empty(n)
@@ -322,7 +327,10 @@ def theta_beta(n: int):
     for k in range(n):
         beta[k] = theta[k] * (1.0 / prev - 1.0)
         th = theta[k]
-        theta[k + 1] = 0.5 * (np.sqrt(th ** 4 + 4.0 * th ** 2) - th ** 2)
+        if rule == "equality":
+            theta[k + 1] = 0.5 * (np.sqrt(th ** 4 + 4.0 * th ** 2) - th ** 2)
+        else:
+            theta[k + 1] = 2.0 / (k + 3)
         prev = th
     return beta, theta
 
@@ -337,31 +345,47 @@ class ApgResult:
     res_hist: np.ndarray
     gamma: float
     converged: bool
+    u_avg: np.ndarray = None  # averaged primal iterate (average=True): inputs
+    x_avg: np.ndarray = None  # ... and states
 
 
 def apg(P: OracleProblem, F: Factor, S: SolveConsts, iters: int, gamma: float,
-        tol: float = 0.0, check_every: int = 1, y0=None, y_prev0=None) -> ApgResult:
+        tol: float = 0.0, check_every: int = 1, y0=None, y_prev0=None,
+        theta_rule: str = "equality", average: bool = False) -> ApgResult:
     """Eqs. apg:1 / apg:2 from y^0 = y^{-1} = 0 (or a warm start):
         w^nu     = y^nu + beta_nu (y^nu - y^{nu-1})
         y^{nu+1} = prox_{gamma g*}(w^nu + gamma H grad f*(-H' w^nu)).
     The residual of iteration nu is |H x*(w^nu) - t^nu|_inf where t^nu is
     the prox of g/gamma inside the Moreau decomposition; it is compared
     with tol at every check_every-th iteration and at the last one.
+    theta_rule picks the extrapolation sequence (theta_beta).  average
+    also returns the averaged primal iterate that §4.3 credits with the
+    O(1/nu^2) rate; the paper does not print it, and the reading taken is
+    the averaging of the accelerated dual method it cites,
+        xbar^nu = (1 - theta_nu) xbar^{nu-1} + theta_nu x*(w^nu),
+    which with theta_0 = 1 starts at xbar^0 = x*(w^0).
     """
     n = P.n_nodes
     y = np.zeros((n, P.ny)) if y0 is None else np.array(y0, float).reshape(n, P.ny)
     y_prev = y.copy() if y_prev0 is None else np.array(y_prev0, float).reshape(n, P.ny)
     y[0] = 0.0
     y_prev[0] = 0.0
-    beta, _ = theta_beta(max(iters, 1))
+    beta, theta = theta_beta(max(iters, 1), theta_rule)
     hist = np.zeros(iters)
     u = x = None
+    u_avg = x_avg = None
     res = np.inf
     done = 0
     converged = False
     for k in range(iters):
         w = y + beta[k] * (y - y_prev)
         u, x = dual_gradient(P, F, S, w)
+        if average:
+            if u_avg is None:
+                u_avg, x_avg = u.copy(), x.copy()
+            else:
+                u_avg = (1.0 - theta[k]) * u_avg + theta[k] * u
+                x_avg = (1.0 - theta[k]) * x_avg + theta[k] * x
         Hx = apply_H(P, u, x)
         y_new, t = prox_gstar(P, w + gamma * Hx, gamma)
         y_new[0] = 0.0
@@ -373,7 +397,7 @@ def apg(P: OracleProblem, F: Factor, S: SolveConsts, iters: int, gamma: float,
             converged = True
             break
     return ApgResult(y=y, u=u, x=x, iters=done, residual=res, res_hist=hist[:done],
-                     gamma=gamma, converged=converged)
+                     gamma=gamma, converged=converged, u_avg=u_avg, x_avg=x_avg)
 
 
 # ----------------------------------------------------------------------------

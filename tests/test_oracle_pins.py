@@ -530,6 +530,61 @@ def test_soft_terms_match_scipy_epigraph_nlp(variant):
     assert abs(upper - pc) <= 5e-5 * upper
 
 
+def test_simple_theta_rule_meets_requirement_with_slack():
+    """theta_nu = 2/(nu+2) (§4.3's simple choice): 1 - theta_{nu+1} <=
+    theta_{nu+1}^2 / theta_nu^2, with slack exactly 1/(nu+3)^2 since
+    (nu+1)(nu+3) = (nu+2)^2 - 1."""
+    beta, theta = O.theta_beta(10000, "simple")
+    nu = np.arange(10000)
+    slack = theta[1:] ** 2 / theta[:-1] ** 2 - (1.0 - theta[1:])
+    assert np.all(slack > 0)
+    # a difference of two terms near 1: absolute rounding of order 1e-16
+    assert np.abs(slack - 1.0 / (nu + 3.0) ** 2).max() <= 1e-14
+    assert theta[0] == 1.0 and beta[0] == 0.0
+
+
+def test_averaged_primal_keeps_dynamics_and_coupling():
+    """The averaged iterate is a convex combination of x*(w^k), each of
+    which meets the (affine) dynamics and coupling exactly, so it does too."""
+    P, data = random_problem(seed=11)
+    F = O.factor(P)
+    S = consts(P, F, data)
+    gamma = O.step_size(O.power_iteration(P, F, 100))
+    R = O.apg(P, F, S, 40, gamma, average=True)
+    u, x = R.u_avg, R.x_avg
+    assert not np.allclose(u, R.u)
+    scale = max(np.abs(x).max(), np.abs(u).max(), 1.0)
+    for v in range(1, P.n_nodes):
+        a = P.anc[v]
+        xa = S.x0 if a == 0 else x[a]
+        assert np.abs(x[v] - (P.A @ xa + P.B @ u[v] + P.Gd @ S.d[v])).max() <= 1e-12 * scale
+        assert np.abs(P.E @ u[v] + P.Ed @ S.d[v]).max() <= 1e-12 * scale
+
+
+@pytest.mark.slow
+def test_averaged_primal_rate_and_theta_rules():
+    """Input-box-only tiny problem: the averaged primal iterate approaches
+    the solution at the O(1/nu^2) rate §4.3 cites (error x nu^2 about
+    constant from 2,000 to 5,000 iterations), and both theta rules reach
+    the same solution."""
+    P, data = synth("tiny")
+    P.Wx = 0.0
+    P.Ws = 0.0
+    F = O.factor(P)
+    S = consts(P, F, data)
+    gamma = O.step_size(O.power_iteration(P, F, 200))
+    ref = O.apg(P, F, S, 20000, gamma)
+    simple = O.apg(P, F, S, 20000, gamma, theta_rule="simple")
+    assert np.abs(simple.u - ref.u).max() <= 1e-7 * np.abs(ref.u).max()
+    err = {}
+    for iters in (2000, 5000):
+        R = O.apg(P, F, S, iters, gamma, average=True)
+        err[iters] = np.abs(R.u_avg - ref.u).max() / np.abs(ref.u).max()
+    assert err[2000] > err[5000] > 0
+    ratio = (err[2000] * 2000 ** 2) / (err[5000] * 5000 ** 2)
+    assert 0.5 < ratio < 2.0, ratio
+
+
 def test_single_scenario_is_deterministic_mpc():
     P, data = random_problem(branching=(1,) * 6, seed=6, general_A=False)
     F, S, R = _run(P, data, 4000)
