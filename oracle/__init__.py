@@ -18,7 +18,9 @@ Every function follows the paper's steps in its order and notation:
   prox and box projection) and the Moreau decomposition (§4.2);
 * ``apg``: Nesterov's accelerated proximal gradient on the Fenchel dual,
   eqs. apg:1 / apg:2, with the theta rule that meets the requirement
-  with equality (§4.3);
+  with equality (§4.3), or theta_nu = 2/(nu+2), and optionally the
+  averaged primal iterate (the averaging of the cited accelerated dual
+  method; the paper does not print it);
 * ``power_iteration``: the Lipschitz constant of the dual gradient used
   to pick the step gamma (the paper does not state its step size).
 
