@@ -160,6 +160,7 @@ S = O.solve_consts(P, F, pb.data.x0, pb.data.q, pb.data.demand, pb.data.alpha)
 gamma = O.step_size(O.power_iteration(P, F, 3))
 O.apg(P, F, S, 1, gamma)
 times = []
+w0 = time.time()
 t_end = time.perf_counter() + {seconds}
 while True:
     t0 = time.perf_counter()
@@ -167,7 +168,7 @@ while True:
     times.append(time.perf_counter() - t0)
     if time.perf_counter() > t_end or len(times) >= {max_steps}:
         break
-print(json.dumps(dict(times=times, per=int({per}))))
+print(json.dumps(dict(times=times, per=int({per}), wall=[w0, time.time()])))
 """
 
 
@@ -189,15 +190,32 @@ def cpu_model() -> str:
     return platform.processor() or platform.machine()
 
 
-def run_oracle_sample(seconds: float, per: int = 1, max_steps: int = 1000) -> dict:
+def run_oracle_sample(seconds: float, per: int = 1, max_steps: int = 1000, procs: int = 1):
+    """The oracle as it stands, one thread per process.  procs > 1 runs that
+    many independent copies of the same solve at once, one per host core,
+    and returns each copy's record (the all-cores throughput is their
+    iterations over the span of their timed loops)."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     code = ORACLE_SAMPLE.format(root=ROOT, cfg=CONFIG_NAME, seconds=seconds, per=per,
                                 max_steps=max_steps)
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
-    if r.returncode != 0:
-        raise RuntimeError("oracle sample failed:\n" + r.stderr[-2000:])
-    return json.loads(r.stdout.strip().splitlines()[-1])
+    ps = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE,
+                           stderr=subprocess.PIPE, text=True, env=env) for _ in range(procs)]
+    outs = []
+    for p in ps:
+        so, se = p.communicate()
+        if p.returncode != 0:
+            raise RuntimeError("oracle sample failed:\n" + se[-2000:])
+        outs.append(json.loads(so.strip().splitlines()[-1]))
+    return outs[0] if procs == 1 else outs
+
+
+def all_cores_rate(recs) -> float:
+    """Iterations of all copies over the span from the first copy's start to
+    the last copy's end of its timed loop."""
+    iters = sum(r["per"] * len(r["times"]) for r in recs)
+    span = max(r["wall"][1] for r in recs) - min(r["wall"][0] for r in recs)
+    return iters / span
 
 
 # ---------------------------------------------------------------------------
@@ -425,10 +443,14 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    # the oracle's CPU sample runs first, in a fresh process, before any GPU work
-    cpu = None
+    # the oracle's CPU samples run first, in fresh processes, before any GPU
+    # work: one thread, then one copy per host core
+    cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = run_oracle_sample(args.cpu_seconds)
+        ncores = os.cpu_count() or 1
+        if ncores > 1:
+            cpu_all = run_oracle_sample(args.cpu_seconds, procs=ncores)
 
     import __graft_entry__
     __graft_entry__.build()
@@ -580,10 +602,21 @@ def main():
         modes["fp64_path"]["mixed_speedup"] = value / modes["fp64_path"]["iters_per_s"]
     if cpu is not None:
         cv = cpu["per"] * len(cpu["times"]) / sum(cpu["times"])
-        line["cpu_baseline"] = {"value": cv, "unit": "iters/s", "cores": 1, "kind": "oracle",
-                                "sample": f"{len(cpu['times'])} FP64 oracle APG iterations on "
-                                          f"{CONFIG_NAME}, one thread, host {cpu_model()} "
-                                          f"({os.cpu_count()} cores present)"}
+        one = {"value": cv, "unit": "iters/s", "cores": 1, "kind": "oracle",
+               "sample": f"{len(cpu['times'])} FP64 oracle APG iterations on "
+                         f"{CONFIG_NAME}, one thread, host {cpu_model()} "
+                         f"({os.cpu_count()} cores present)"}
+        line["cpu_baseline"] = one
+        if cpu_all:
+            its = sum(r["per"] * len(r["times"]) for r in cpu_all)
+            line["cpu_baseline"] = {
+                "value": all_cores_rate(cpu_all), "unit": "iters/s", "cores": len(cpu_all),
+                "kind": "oracle",
+                "sample": f"{len(cpu_all)} independent copies of the FP64 oracle's solve of "
+                          f"{CONFIG_NAME} at once, one per host core ({its} APG iterations "
+                          f"in all; value = their iterations over the span of their timed "
+                          f"loops), host {cpu_model()}",
+                "single_thread": one}
     if rank == 0:
         print(json.dumps(line))
     fac.close()

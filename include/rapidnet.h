@@ -101,12 +101,35 @@ typedef struct {
   int check_every;     /* residual test every k iterations; 0 = 10 */
   int refresh_every;   /* RN_PREC_MIXED: FP64 reference refresh period;
                           0 = 20 */
-  int max_ctas;        /* cap on the persistent grid; 0 = device maximum */
+  int max_ctas;        /* cap on the persistent grid; 0 = device maximum.
+                          The handle's own kernels need one resident block
+                          per work item (one per group of top nodes and per
+                          set of chain teams, grid_ctas of
+                          rapidnet_factor_info with max_ctas = 0): a smaller
+                          cap gives RN_ERR_UNSUPPORTED at factor creation.
+                          rapidnet_solve_batch takes the cap of its first
+                          handle for the batch's grid, where a block may
+                          take several work items. */
   int block_threads;   /* threads of a chain team of the persistent kernels
-                          (multiple of 32, <= 256; a block is two teams);
-                          0 = one thread per component of u or x, at
-                          least 64 */
+                          (multiple of 32, <= 256; a block is two or four
+                          teams); 0 = one thread per component of u or x,
+                          at least 64 */
+  int wait_us;         /* bound of every device-side wait (a block waiting
+                          for another block's flag or counter), in
+                          microseconds; 0 = 2 s.  A wait that runs out ends
+                          the launch with RN_ERR_TIMEOUT and the site of the
+                          wait in rapidnet_last_error(); the handle stays
+                          usable. */
+  int theta_rule;      /* extrapolation sequence of the APG (paper §4.3,
+                          which names two admissible choices):
+                          RN_THETA_EQUALITY (0, default) theta_{nu+1} =
+                          (sqrt(theta^4 + 4 theta^2) - theta^2) / 2, or
+                          RN_THETA_SIMPLE theta_nu = 2 / (nu + 2); both from
+                          theta_0 = theta_{-1} = 1 and beta_nu = theta_nu
+                          (1 / theta_{nu-1} - 1) */
 } rn_opts;
+
+enum { RN_THETA_EQUALITY = 0, RN_THETA_SIMPLE = 1 };
 
 /* Output of a solve.  The caller allocates u (n_nodes*nu), x (n_nodes*nx)
  * and y (n_nodes*(2 nx + nu)) in the memory space of the call (host for
@@ -131,6 +154,10 @@ typedef struct {
   double gamma;        /* step size used */
   double apg_ms;       /* device time of the APG iterations (CUDA events on
                           the handle's stream around the persistent launch) */
+  long long t_begin_ns, t_end_ns;  /* device clock (%globaltimer, ns) when the
+                          persistent launch began and when its first block
+                          finished; comparable between launches on one
+                          device (0 from rapidnet_solve_batch) */
 } rn_result;
 
 typedef struct rn_factor rn_factor;
@@ -149,6 +176,9 @@ typedef struct {
   long long device_bytes;  /* device memory held by the handle */
   double collapse_dev;     /* factor check: max |2 p Phi - F| / max |F| over
                               the sampled nodes of the general recursion */
+  long long noalloc_bytes; /* scratch that rapidnet_dual_gradient_noalloc
+                              needs for this handle's tree (compare with
+                              RN_NOALLOC_SCRATCH_BYTES) */
 } rn_factor_info;
 
 /* Factor step (paper Table 2 Engine::factorStep, §4.4): validates the
@@ -234,20 +264,25 @@ int rapidnet_dual_gradient_device(rn_factor *f, const double *x0,
  * rapidnet_dual_gradient_device for the data of that last solve: w in
  * (n_nodes*(2nx+nu)), u (n_nodes*nu) and x (n_nodes*nx) out, all device
  * pointers, FP64.
- * Scratch: one fixed array of 8 MiB of device memory inside the library,
- * held by every device that loads the library until the process exits.
- * A tree needs 8 n (2 (nxp + nup) + 2 nup + nxp) + 4 (n + max(s,1) + 6) bytes
- * (n = n_nodes, s = number of stage-1 nodes with two or more leaves,
- * nxp / nup = nx / nu rounded up to multiples of 4); larger trees get
- * RN_ERR_INVAL.  About 1,590 nodes of the Barcelona-sized network fit:
- * the 32-scenario tree does, the 512-scenario tree does not.
+ * Scratch: one fixed array of RN_NOALLOC_SCRATCH_BYTES (8 MiB) of device
+ * memory inside the library, held by every device that loads the library
+ * until the process exits.  A tree needs
+ *   8 (n (3 sp + 2 nup + nxp) + max(h, 1) sp) + 4 (2 max(g, 1) + 6)
+ * bytes (rounded up to 8), with n = n_nodes, nxp / nup = nx / nu rounded
+ * up to multiples of 4, sp = nxp + nup, h the rows of partial sums of
+ * split stage-1 subtrees and g the groups plus roots of the schedule
+ * (h, g < n); rapidnet_factor_info's noalloc_bytes gives the exact figure.
+ * Larger trees get RN_ERR_INVAL.  The Barcelona-sized network needs 836
+ * doubles per node, so about 1,250 nodes fit: its 32-scenario tree (701
+ * nodes) does, its 512-scenario tree does not.
  * No cudaMalloc, cudaFree or allocating routine is called.  The first
  * call on a device looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
  * Every call shares the one array and finds the previous call's contents
  * in it: calls that overlap on the GPU (other streams, handles or host
- * threads) race and must be serialised by the caller.  Synchronises the
- * handle's stream. */
+ * threads) race and must be serialised by the caller.  Copies the error
+ * word back and synchronises the handle's stream before returning. */
+#define RN_NOALLOC_SCRATCH_BYTES (8LL << 20)
 int rapidnet_dual_gradient_noalloc(rn_factor *f, const double *w, double *u,
                                    double *x);
 

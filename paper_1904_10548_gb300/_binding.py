@@ -28,7 +28,10 @@ RN_ERR_NOMEM = -5
 RN_ERR_UNSUPPORTED = -6
 RN_ERR_DIVERGED = -7
 RN_PREC_FP64 = 0
+RN_NOALLOC_SCRATCH_BYTES = 8 << 20  # rapidnet.h
 RN_PREC_MIXED = 1
+RN_THETA_EQUALITY = 0
+RN_THETA_SIMPLE = 1
 
 STATUS_NAMES = {0: "RN_OK", 1: "RN_NOT_CONVERGED", -1: "RN_ERR_INVAL", -2: "RN_ERR_RANK",
                 -3: "RN_ERR_CUDA", -4: "RN_ERR_TIMEOUT", -5: "RN_ERR_NOMEM",
@@ -56,14 +59,20 @@ class rn_cost(ctypes.Structure):
 class rn_opts(ctypes.Structure):
     _fields_ = [("device", c_int), ("stream", c_void_p), ("precision", c_int),
                 ("gamma", c_double), ("power_iters", c_int), ("check_every", c_int),
-                ("refresh_every", c_int), ("max_ctas", c_int), ("block_threads", c_int)]
+                ("refresh_every", c_int), ("max_ctas", c_int), ("block_threads", c_int),
+                ("wait_us", c_int), ("theta_rule", c_int)]
 
 
 class rn_result(ctypes.Structure):
     _fields_ = [("u", PD), ("x", PD), ("y", PD), ("res_hist", PD), ("res_hist_len", c_int),
                 ("compute_gap", c_int), ("iters", c_int), ("n_checks", c_int),
                 ("primal_res", c_double), ("ubox_viol", c_double), ("cost", c_double),
-                ("gap", c_double), ("gamma", c_double), ("apg_ms", c_double)]
+                ("gap", c_double), ("gamma", c_double), ("apg_ms", c_double),
+                ("t_begin_ns", c_longlong), ("t_end_ns", c_longlong)]
+
+
+RESULT_SCALARS = ("iters", "n_checks", "primal_res", "ubox_viol", "cost", "gap", "gamma",
+                  "apg_ms", "t_begin_ns", "t_end_ns")
 
 
 class rn_solve_req(ctypes.Structure):
@@ -87,7 +96,7 @@ class rn_factor_info(ctypes.Structure):
                 ("n_nodes", c_int), ("n_chains", c_int), ("n_top", c_int),
                 ("grid_ctas", c_int), ("block_threads", c_int), ("L", c_double),
                 ("gamma", c_double), ("precision", c_int), ("device_bytes", c_longlong),
-                ("collapse_dev", c_double)]
+                ("collapse_dev", c_double), ("noalloc_bytes", c_longlong)]
 
 
 EXPORTS = {
@@ -264,8 +273,7 @@ class Server:
         lat = c_double()
         rc = _check(load().rapidnet_server_wait(self.h, ticket, float(timeout_s),
                                                 ctypes.byref(res), ctypes.byref(lat)))
-        out = {f: getattr(res, f) for f in ("iters", "n_checks", "primal_res", "ubox_viol",
-                                            "cost", "gap", "gamma", "apg_ms")}
+        out = {f: getattr(res, f) for f in RESULT_SCALARS}
         out.update(status=rc, u=u, x=x, y=y, latency_s=lat.value)
         return out
 
@@ -321,13 +329,15 @@ class Factor:
 
     def __init__(self, net, cost, tree, precision: int = RN_PREC_FP64, gamma: float = 0.0,
                  device: int = 0, stream=None, power_iters: int = 0, check_every: int = 0,
-                 refresh_every: int = 0, max_ctas: int = 0, block_threads: int = 0):
+                 refresh_every: int = 0, max_ctas: int = 0, block_threads: int = 0,
+                 wait_us: int = 0, theta_rule: int = 0):
         self._marshal(net, cost, tree, precision, gamma, device, stream, power_iters,
-                      check_every, refresh_every, max_ctas, block_threads)
+                      check_every, refresh_every, max_ctas, block_threads, wait_us, theta_rule)
         self.h = rapidnet_factor(self.net_c, self.tree_c, self.cost_c, self.opts_c)
 
     def _marshal(self, net, cost, tree, precision, gamma, device, stream, power_iters=0,
-                 check_every=0, refresh_every=0, max_ctas=0, block_threads=0):
+                 check_every=0, refresh_every=0, max_ctas=0, block_threads=0, wait_us=0,
+                 theta_rule=0):
         nx, nu, nd, ne = net.nx, net.nu, net.nd, net.ne
         self._keep = [
             _f64(net.A, (nx, nx)), _f64(net.B, (nx, nu)), _f64(net.Gd, (nx, nd)),
@@ -346,7 +356,7 @@ class Factor:
                               float(cost.Wx))
         st = None if stream is None else c_void_p(getattr(stream, "cuda_stream", stream))
         self.opts_c = rn_opts(device, st, precision, gamma, power_iters, check_every,
-                              refresh_every, max_ctas, block_threads)
+                              refresh_every, max_ctas, block_threads, wait_us, theta_rule)
         self.nx, self.nu, self.nd, self.ne = nx, nu, nd, ne
         self.n_nodes = int(tree.stage_ptr[-1])
         self.ny = 2 * nx + nu
@@ -379,8 +389,7 @@ class Factor:
                         res_hist_len, int(compute_gap))
         rc = rapidnet_solve(self.h, _pd(x0), _pd(q), _pd(demand), _pd(alpha), max_iters, tol,
                             None if yw is None else _pd(yw), res)
-        out = {f: getattr(res, f) for f in ("iters", "n_checks", "primal_res", "ubox_viol",
-                                            "cost", "gap", "gamma", "apg_ms")}
+        out = {f: getattr(res, f) for f in RESULT_SCALARS}
         out.update(status=rc, u=u, x=x, y=y,
                    res_hist=hist[:min(res_hist_len, res.n_checks)] if res_hist_len else None)
         return out
@@ -394,8 +403,7 @@ class Factor:
                         0 if res_hist is None else res_hist.numel(), int(compute_gap))
         rc = rapidnet_solve_device(self.h, _dev_ptr(x0), _dev_ptr(q), _dev_ptr(demand),
                                    _dev_ptr(alpha), max_iters, tol, _dev_ptr(y_warm), res)
-        out = {f: getattr(res, f) for f in ("iters", "n_checks", "primal_res", "ubox_viol",
-                                            "cost", "gap", "gamma", "apg_ms")}
+        out = {f: getattr(res, f) for f in RESULT_SCALARS}
         out["status"] = rc
         return out
 

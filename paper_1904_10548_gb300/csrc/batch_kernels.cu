@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(512) k_batch(BatchDev B) {
       if (threadIdx.x == 0) {
         __threadfence();
         atomicAdd(B.barrier, 1u);
-        bm.bflag[1] = spin_geq(B.barrier, (unsigned)(ci + 1) * gridDim.x, B.err, 4);
+        bm.bflag[1] = spin_geq(B.barrier, (unsigned)(ci + 1) * gridDim.x, B.err, B.wait_ns, 4);
       }
       __syncthreads();
       if (!bm.bflag[1]) {

@@ -24,7 +24,7 @@
 namespace rn {
 
 constexpr int kSeg = 16;                    // ints of a team's node list (halved)
-constexpr long long kWaitNs = 2000000000LL; // bound of every device-side wait (2 s)
+constexpr long long kWaitNs = 2000000000LL; // default bound of every device-side wait (2 s)
 constexpr int kChildSlotsDev = 8;           // children per node in a group's children table
 
 template <typename T>
@@ -70,8 +70,11 @@ struct StateDev {
   const double *beta;  // beta_0 .. beta_iters (APG)
   unsigned *count, *flags, *barrier;  // per group, then per root: arrivals, completion; grid
   unsigned long long *res;  // per check: bits of the non-negative residual
-  int *err;                 // 0 ok, 1 timeout
-  int *info;                // [iters done, checks done, stop reason]
+  int *err;                 // 0 ok, else the site of the wait that gave up (1-4)
+  int *info;                // [iters done, checks done, stop reason, 0, t_begin, t_end]:
+                            // %globaltimer at the start and end of an APG launch as
+                            // 64-bit words at info + 4 (8-byte aligned)
+  long long wait_ns;        // bound of every device-side wait
 };
 
 template <typename T>
@@ -137,6 +140,7 @@ struct BatchDev {
   int *err;                  // shared error word (a wait gave up)
   int *prob_info;            // per problem: iterations, checks, stop reason
   int iters, check_every, refresh_every;
+  long long wait_ns;         // bound of every device-side wait
   int net_bytes;             // network region: FP32 copy, then the FP64 header
   int net_bytes_f;           // offset of the FP64 header in the network region
   int team_bytes;            // team region (max over problems)

@@ -18,6 +18,7 @@ namespace rn {
 template <int C>
 __global__ void __launch_bounds__(512) k_mixed(MixedParams M) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (blockIdx.x == 0 && threadIdx.x == 0) stamp_time(M.f.st.info, 0);
   // network region: the FP32 copy (for the iterations), then the header of
   // the FP64 data (the rarely run FP64 steps read its arrays from global
   // memory) at offset M.d.net_bytes
@@ -70,7 +71,8 @@ __global__ void __launch_bounds__(512) k_mixed(MixedParams M) {
       break;
     }
     if (check) {
-      if (!grid_check(bm, widen_bits(c.rbits), P.st.res, P.st.barrier, ci, P.st.err)) {
+      if (!grid_check(bm, widen_bits(c.rbits), P.st.res, P.st.barrier, ci, P.st.err,
+                      P.st.wait_ns)) {
         ok = false;
         reason = 3;
         ++it;
@@ -112,6 +114,7 @@ __global__ void __launch_bounds__(512) k_mixed(MixedParams M) {
     P.st.info[0] = it;
     P.st.info[1] = ci;
     P.st.info[2] = reason;
+    stamp_time(P.st.info, 1);
   }
 }
 

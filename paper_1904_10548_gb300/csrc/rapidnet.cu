@@ -601,23 +601,34 @@ MixedParams mixed_params(rn_factor *f, int max_iters, double tol) {
   return M;
 }
 
+// counters, flags and the grid barrier start at zero for every launch
 int reset_sync(rn_factor *f) {
   RN_CUDA(cudaMemsetAsync(f->sync, 0, f->sync_words * sizeof(unsigned), f->stream));
+  return RN_OK;
+}
+
+// the error word is cleared once per call of the ABI, so that a wait that
+// gave up in any launch of the call is reported (and later launches of the
+// call leave their waits at once)
+int clear_err(rn_factor *f) {
   RN_CUDA(cudaMemsetAsync(f->err, 0, sizeof(int), f->stream));
   return RN_OK;
+}
+
+// the error word of a kernel that recorded a timed-out wait (site 1-4)
+int timeout_error(const char *who, int e, long long wait_ns) {
+  static const char *site[] = {"?", "chain arrivals at a group", "a group's flag",
+                               "a root's flag", "the grid barrier"};
+  set_error("%sa device-side wait (%s, site %d) gave up after %.6g s", who,
+            site[e >= 1 && e <= 4 ? e : 0], e, wait_ns * 1e-9);
+  return RN_ERR_TIMEOUT;
 }
 
 int check_err(rn_factor *f) {
   int e = 0;
   RN_CUDA(cudaMemcpyAsync(&e, f->err, sizeof(int), cudaMemcpyDeviceToHost, f->stream));
   RN_CUDA(cudaStreamSynchronize(f->stream));
-  if (e) {
-    static const char *site[] = {"?", "chain arrivals at a group", "a group's flag",
-                                 "a root's flag", "the grid barrier"};
-    set_error("a device-side wait (%s) gave up after %.1f s", site[e >= 1 && e <= 4 ? e : 0],
-              kWaitNs * 1e-9);
-    return RN_ERR_TIMEOUT;
-  }
+  if (e) return timeout_error("", e, f->st.wait_ns);
   return RN_OK;
 }
 
@@ -635,6 +646,7 @@ int node_blocks(int n) { return std::max(1, std::min(n - 1, 4096)); }
 
 int power_iteration(rn_factor *f, int iters, double *L_out) {
   const int n = f->plan.n;
+  if (int rc = clear_err(f)) return rc;
   k_power_start<<<node_blocks(n), 128, 0, f->stream>>>(f->net, f->perm, n, f->st.s);
   RN_CUDA(cudaGetLastError());
   for (int k = 0; k < iters; ++k) {
@@ -760,6 +772,15 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
   if (f->opts.power_iters <= 0) f->opts.power_iters = 200;
   if (f->opts.check_every <= 0) f->opts.check_every = 10;
   if (f->opts.refresh_every <= 0) f->opts.refresh_every = 20;
+  if (f->opts.theta_rule != RN_THETA_EQUALITY && f->opts.theta_rule != RN_THETA_SIMPLE) {
+    set_error("theta_rule must be RN_THETA_EQUALITY or RN_THETA_SIMPLE");
+    return RN_ERR_INVAL;
+  }
+  if (f->opts.wait_us < 0) {
+    set_error("wait_us must be >= 0");
+    return RN_ERR_INVAL;
+  }
+  const long long wait_ns = f->opts.wait_us > 0 ? 1000LL * f->opts.wait_us : kWaitNs;
   f->device = f->opts.device;
   RN_CUDA(cudaSetDevice(f->device));
   if (f->opts.stream) {
@@ -935,7 +956,7 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
   if ((rc = dalloc(f, &f->x0, nx)) || (rc = dalloc(f, &f->q, nu)) || (rc = dalloc(f, &f->kq, nu)) ||
       (rc = dalloc(f, &f->demand, (size_t)n * nd)) || (rc = dalloc(f, &f->alpha, (size_t)n * nu)) ||
       (rc = dalloc(f, &f->partial, 3 * kRedBlocks)) || (rc = dalloc(f, &f->scal, 4)) ||
-      (rc = dalloc(f, &f->err, 1)) || (rc = dalloc(f, &f->info, 4)))
+      (rc = dalloc(f, &f->err, 1)) || (rc = dalloc(f, &f->info, 8)))
     return rc;
   RN_CUDA(cudaMemset(f->x0, 0, nx * sizeof(double)));
   st.xroot = f->x0;
@@ -949,6 +970,7 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
   st.info = f->info;
   st.res = nullptr;
   st.beta = nullptr;
+  st.wait_ns = wait_ns;
 
   if (f->opts.precision == RN_PREC_MIXED) {
     // FP32 copies of the network data (index arrays shared) and FP32 state
@@ -1013,6 +1035,7 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
     sf.barrier = st.barrier;
     sf.err = st.err;
     sf.info = st.info;
+    sf.wait_ns = wait_ns;
     f->mx.yb = st.ya;  // the FP64 iterate buffer holds the base
     f->mx.ybh = ybh;
     f->mx.da = da;
@@ -1103,14 +1126,17 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
 int ensure_beta(rn_factor *f, int iters) {
   if (iters + 1 <= f->beta_cap) return RN_OK;
   int cap = std::max(iters + 1, 2 * f->beta_cap);
-  // beta_nu = theta_nu (1 / theta_{nu-1} - 1), theta_{nu+1} = (sqrt(theta^4
-  // + 4 theta^2) - theta^2) / 2 from theta_0 = theta_{-1} = 1 (paper §4.3)
+  // beta_nu = theta_nu (1 / theta_{nu-1} - 1) from theta_0 = theta_{-1} = 1
+  // with theta_{nu+1} = (sqrt(theta^4 + 4 theta^2) - theta^2) / 2 or
+  // theta_nu = 2 / (nu + 2) (paper §4.3)
   std::vector<double> b(cap);
   double th = 1.0, prev = 1.0;
   for (int k = 0; k < cap; ++k) {
     b[k] = th * (1.0 / prev - 1.0);
     const double t2 = th * th;
-    const double nt = 0.5 * (std::sqrt(t2 * t2 + 4.0 * t2) - t2);
+    const double nt = f->opts.theta_rule == RN_THETA_SIMPLE
+                          ? 2.0 / (k + 3)
+                          : 0.5 * (std::sqrt(t2 * t2 + 4.0 * t2) - t2);
     prev = th;
     th = nt;
   }
@@ -1196,7 +1222,7 @@ int solve_device_impl(rn_factor *f, const double *x0, const double *q, const dou
   const int checks = (max_iters + f->opts.check_every - 1) / f->opts.check_every + 1;
   int rc;
   if ((rc = ensure_beta(f, max_iters)) || (rc = ensure_res(f, checks))) return rc;
-  if ((rc = prepare(f, x0, q, demand, alpha))) return rc;
+  if ((rc = clear_err(f)) || (rc = prepare(f, x0, q, demand, alpha))) return rc;
   const bool mixed = f->opts.precision == RN_PREC_MIXED;
   if (mixed)
     k_mixed_init<<<node_blocks(n), 128, 0, f->stream>>>(f->net, f->perm, n, y_warm, f->mx.yb,
@@ -1220,10 +1246,16 @@ int solve_device_impl(rn_factor *f, const double *x0, const double *q, const dou
     RN_CUDA((launch_solve<double, true>(P, f->grid, f->block, f->smem, f->stream)));
   }
   RN_CUDA(cudaEventRecord(f->ev1, f->stream));
-  int info[3] = {0, 0, 0};
-  RN_CUDA(cudaMemcpyAsync(info, f->info, 3 * sizeof(int), cudaMemcpyDeviceToHost, f->stream));
+  int info[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  RN_CUDA(cudaMemcpyAsync(info, f->info, 8 * sizeof(int), cudaMemcpyDeviceToHost, f->stream));
   if ((rc = check_err(f))) return rc;
   const int iters = info[0], nchk = info[1], reason = info[2];
+  {
+    unsigned long long stamps[2];
+    std::memcpy(stamps, info + 4, sizeof stamps);
+    out->t_begin_ns = (long long)stamps[0];
+    out->t_end_ns = (long long)stamps[1];
+  }
   float apg_ms = 0.f;
   RN_CUDA(cudaEventElapsedTime(&apg_ms, f->ev0, f->ev1));
   out->apg_ms = apg_ms;
@@ -1281,12 +1313,21 @@ int solve_device_impl(rn_factor *f, const double *x0, const double *q, const dou
     set_error("the residual became non-finite after %d iterations", iters);
     return RN_ERR_DIVERGED;
   }
-  if (reason == 3) {
-    set_error("a device-side wait gave up");
-    return RN_ERR_TIMEOUT;
-  }
+  if (reason == 3) return timeout_error("", 0, f->st.wait_ns);
   if (tol > 0.0 && reason != 1) return RN_NOT_CONVERGED;
   return RN_OK;
+}
+
+// Scratch of the allocation-free dual gradient: doubles for s, up, ux (SP
+// per node), z, uo (NUP), xo (NXP) and the partial sums hp (SP per row),
+// then 32-bit words for the counters and flags of the groups and roots,
+// the grid barrier, the error word and the info words.
+void noalloc_need(const rn_factor *f, size_t *need_d, size_t *need_w) {
+  const size_t rows = (size_t)f->plan.n;
+  const size_t ng = (size_t)std::max(1, f->plan.n_groups + f->plan.n_roots);
+  const size_t hrows = (size_t)std::max(1, f->plan.hp_rows);
+  *need_d = rows * (3 * (size_t)f->SP + 2 * (size_t)f->NUP + (size_t)f->NXP) + hrows * f->SP;
+  *need_w = 2 * ng + 1 + 1 + 4;
 }
 
 }  // namespace
@@ -1337,6 +1378,9 @@ extern "C" int rapidnet_factor_info(const rn_factor *f, rn_factor_info *info) {
   info->precision = f->opts.precision;
   info->device_bytes = f->bytes;
   info->collapse_dev = f->collapse_dev;
+  size_t need_d = 0, need_w = 0;
+  noalloc_need(f, &need_d, &need_w);
+  info->noalloc_bytes = (long long)(8 * (need_d + (need_w + 1) / 2));
   return RN_OK;
 }
 
@@ -1428,11 +1472,12 @@ extern "C" int rapidnet_dual_gradient_device(rn_factor *f, const double *x0, con
       set_error("dual_gradient: give all of x0, q, demand, alpha or none");
       return RN_ERR_INVAL;
     }
-    if ((rc = prepare(f, x0, q, demand, alpha))) return rc;
+    if ((rc = clear_err(f)) || (rc = prepare(f, x0, q, demand, alpha))) return rc;
   } else if (!f->have_data) {
     set_error("dual_gradient: no data yet (give x0, q, demand, alpha)");
     return RN_ERR_INVAL;
   }
+  if (!(x0 || q || demand || alpha) && (rc = clear_err(f))) return rc;
   const int n = f->plan.n;
   k_s_from_w<<<node_blocks(n), 128, 0, f->stream>>>(f->net, f->perm, n, w, f->st.s);
   RN_CUDA(cudaGetLastError());
@@ -1448,8 +1493,8 @@ extern "C" int rapidnet_dual_gradient_device(rn_factor *f, const double *x0, con
 //
 // For callers that must not allocate device memory once they are running:
 // a real-time control loop that forbids allocation after start-up for
-// predictable timing, a host that hands the GPU to us inside a memory pool
-// or a captured region it owns, or an embedding that counts every byte.
+// predictable timing, a host application that owns the device memory pool
+// and hands none of it to libraries, or an embedding that counts every byte.
 // Such a caller creates the factor handle (and runs one solve or
 // rapidnet_dual_gradient_device with data) during set-up; afterwards
 // rapidnet_dual_gradient_noalloc evaluates x*(w) with the per-call scratch
@@ -1462,6 +1507,8 @@ namespace {
 
 // 8 MiB of doubles, held by every device that loads the library until exit
 constexpr size_t kNoAllocDoubles = (size_t)1 << 20;
+static_assert(kNoAllocDoubles * sizeof(double) == (size_t)RN_NOALLOC_SCRATCH_BYTES,
+              "scratch size differs from the header");
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
 
 constexpr int kMaxDevices = 64;
@@ -1506,13 +1553,9 @@ extern "C" int rapidnet_dual_gradient_noalloc(rn_factor *f, const double *w, dou
   const int n = f->plan.n;
   const size_t rows = (size_t)n;
   const size_t ng = (size_t)std::max(1, f->plan.n_groups + f->plan.n_roots);
-  const size_t sync_words = 2 * ng + 1;
   const size_t hrows = (size_t)std::max(1, f->plan.hp_rows);
-  // doubles: s, up, ux (SP), z, uo (NUP), xo (NXP), hp (SP per group);
-  // then sync words, err, info
-  const size_t need_d = rows * (3 * (size_t)f->SP + 2 * (size_t)f->NUP + (size_t)f->NXP) +
-                        hrows * f->SP;
-  const size_t need_w = sync_words + 1 + 4;  // 32-bit words
+  size_t need_d = 0, need_w = 0;
+  noalloc_need(f, &need_d, &need_w);
   const size_t need = need_d + (need_w + 1) / 2;
   if (need > kNoAllocDoubles) {
     set_error("dual_gradient_noalloc: this tree needs %zu bytes of scratch, more than the "
@@ -1544,7 +1587,7 @@ extern "C" int rapidnet_dual_gradient_noalloc(rn_factor *f, const double *w, dou
   st.count = words;
   st.flags = words + ng;
   st.barrier = words + 2 * ng;
-  st.err = reinterpret_cast<int *>(words + sync_words);
+  st.err = reinterpret_cast<int *>(words + 2 * ng + 1);
   st.info = st.err + 1;
   st.res = nullptr;
   st.beta = nullptr;
@@ -1563,10 +1606,7 @@ extern "C" int rapidnet_dual_gradient_noalloc(rn_factor *f, const double *w, dou
   int e = 0;
   RN_CUDA(cudaMemcpyAsync(&e, st.err, sizeof(int), cudaMemcpyDeviceToHost, f->stream));
   RN_CUDA(cudaStreamSynchronize(f->stream));
-  if (e) {
-    set_error("dual_gradient_noalloc: a device-side wait gave up");
-    return RN_ERR_TIMEOUT;
-  }
+  if (e) return timeout_error("dual_gradient_noalloc: ", e, st.wait_ns);
   return RN_OK;
 }
 
@@ -1630,7 +1670,8 @@ int batch_impl(rn_factor *const *fs, const rn_solve_req *req, int n, int max_ite
     const int ck = (max_iters + f->opts.check_every - 1) / f->opts.check_every + 1;
     checks = std::max(checks, ck);
     if ((rc = ensure_beta(f, max_iters)) || (rc = ensure_res(f, ck))) return rc;
-    if ((rc = prepare(f, req[i].x0, req[i].q, req[i].demand, req[i].alpha))) return rc;
+    if ((rc = clear_err(f)) || (rc = prepare(f, req[i].x0, req[i].q, req[i].demand, req[i].alpha)))
+      return rc;
     const int nn = f->plan.n;
     k_mixed_init<<<node_blocks(nn), 128, 0, f->stream>>>(f->net, f->perm, nn, req[i].y_warm,
                                                          f->mx.yb, f->mx.ybh, f->mx.da,
@@ -1644,7 +1685,9 @@ int batch_impl(rn_factor *const *fs, const rn_solve_req *req, int n, int max_ite
   const int tpb = tw <= 128 ? 4 : 2, block = tpb * tw;
   for (int i = 0; i < n; ++i) items += fs[i]->plan.n_groups + (fs[i]->plan.n_chains + tpb - 1) / tpb;
   net_region = net_f + (int)round16(sizeof(NetDev<double>));
-  for (int i = 0; i < n; ++i) RN_CUDA(cudaStreamSynchronize(fs[i]->stream));
+  // each handle's preparation (its x*(0) evaluation) must have finished its waits
+  for (int i = 0; i < n; ++i)
+    if ((rc = check_err(fs[i]))) return rc;
   for (int i = 0; i < n; ++i) {
     const int m = std::max(fs[i]->nx, fs[i]->nu);
     int c = std::max((m + tw - 1) / tw, (fs[i]->nx + 31) / 32);
@@ -1753,6 +1796,7 @@ int batch_impl(rn_factor *const *fs, const rn_solve_req *req, int n, int max_ite
       return RN_ERR_INVAL;
     }
   B.refresh_every = fs[0]->opts.refresh_every;
+  B.wait_ns = fs[0]->st.wait_ns;
   B.net_bytes = net_region;
   B.net_bytes_f = net_f;
   B.team_bytes = team_bytes;
@@ -1769,10 +1813,7 @@ int batch_impl(rn_factor *const *fs, const rn_solve_req *req, int n, int max_ite
   // errors of any problem (shared wait error words)
   int any_err = 0;
   RN_CUDA(cudaMemcpy(&any_err, berr, sizeof(int), cudaMemcpyDeviceToHost));
-  if (any_err) {
-    set_error("solve_batch: a device-side wait gave up");
-    return RN_ERR_TIMEOUT;
-  }
+  if (any_err) return timeout_error("solve_batch: ", any_err, B.wait_ns);
   int status = RN_OK;
   for (int i = 0; i < n; ++i) {
     rn_factor *f = fs[i];
@@ -1805,6 +1846,7 @@ int batch_impl(rn_factor *const *fs, const rn_solve_req *req, int n, int max_ite
     out->gap = NAN;
     out->gamma = f->gamma;
     out->apg_ms = ms;
+    out->t_begin_ns = out->t_end_ns = 0;
     if (reason == 2) status = RN_ERR_DIVERGED;
     else if (tol > 0.0 && reason != 1 && status == RN_OK) status = RN_NOT_CONVERGED;
   }

@@ -21,6 +21,12 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
+// %globaltimer into the k-th 64-bit stamp word at info + 4 (0: launch began,
+// 1: block 0 finished)
+__device__ __forceinline__ void stamp_time(int *info, int k) {
+  reinterpret_cast<unsigned long long *>(info + 4)[k] = global_ns();
+}
+
 template <typename T>
 __device__ __forceinline__ T ld_l2(const T *p) {
   return __ldcg(p);
@@ -37,15 +43,16 @@ __device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
 }
 
 // bounded spin of one thread until *p >= target; false on timeout or error.
-// The first wait to give up records `site` in *err (1 chain arrivals at a
-// group, 2 a group's flag, 3 a root's flag, 4 the grid barrier).
-static __device__ bool spin_geq(const unsigned *p, unsigned target, int *err, int site = 1) {
+// The first wait to give up (after limit_ns) records `site` in *err (1 chain
+// arrivals at a group, 2 a group's flag, 3 a root's flag, 4 the grid barrier).
+static __device__ bool spin_geq(const unsigned *p, unsigned target, int *err, long long limit_ns,
+                                int site) {
   if (ld_acquire(p) >= target) return true;
   const unsigned long long t0 = global_ns();
   while (true) {
     if (ld_acquire(p) >= target) return true;
     if (*(volatile int *)err != 0) return false;
-    if ((long long)(global_ns() - t0) > kWaitNs) {
+    if ((long long)(global_ns() - t0) > limit_ns) {
       atomicCAS(err, 0, site);
       return false;
     }
@@ -860,7 +867,7 @@ __device__ bool group_step(const KParams<T> &P, int g, const Smem<T> &sm, const 
     // the root's (x | Z), the descriptor and the z rows of phase 0
     const int rv = pl.r_node[root];
     if (tm.tid == 0)
-      sm.flag[0] = spin_geq(P.st.flags + pl.n_groups + root, step + 1u, P.st.err, 3);
+      sm.flag[0] = spin_geq(P.st.flags + pl.n_groups + root, step + 1u, P.st.err, P.st.wait_ns, 3);
     tm.sync();
     if (!sm.flag[0]) return false;
     base = H;  // the heads are not needed in phase 1
@@ -891,7 +898,7 @@ __device__ bool group_step(const KParams<T> &P, int g, const Smem<T> &sm, const 
   // all chains of the group have arrived; the counter restarts for the
   // next evaluation (no chain arrives again before the flag below)
   if (tm.tid == 0) {
-    sm.flag[0] = spin_geq(P.st.count + g, (unsigned)(c1 - c0), P.st.err);
+    sm.flag[0] = spin_geq(P.st.count + g, (unsigned)(c1 - c0), P.st.err, P.st.wait_ns, 1);
     if (sm.flag[0]) atomicExch(P.st.count + g, 0u);
   }
   tm.sync();
@@ -1213,7 +1220,7 @@ __device__ bool chain_forward(const KParams<T> &P, int k, FwdCtx<T> &c, const Sm
   const int fpn = fwd_elems_per_node(NXP, NUP, YP, SP, MODE);
   T *slots = sm.buf + round4(2 * NXP + NUP) + (size_t)warp * S * fpn;
   if (g >= 0) {
-    if (tm.tid == 0) sm.flag[1] = spin_geq(P.st.flags + g, step + 1u, P.st.err, 2);
+    if (tm.tid == 0) sm.flag[1] = spin_geq(P.st.flags + g, step + 1u, P.st.err, P.st.wait_ns, 2);
     tm.sync();
     if (!sm.flag[1]) return false;
     const T *src = P.st.ux + (size_t)par * SP;
@@ -1418,13 +1425,13 @@ __device__ __forceinline__ bool block_err(const BlockMem &bm, int *err) {
 // value) lands in res[ci]; false on timeout (every thread calls it)
 __device__ __forceinline__ bool grid_check(const BlockMem &bm, unsigned long long r,
                                            unsigned long long *res, unsigned *barrier, int ci,
-                                           int *err) {
+                                           int *err, long long wait_ns) {
   r = block_max_u64(r, bm.redu);
   if (threadIdx.x == 0) {
     atomicMax(res + ci, r);
     __threadfence();
     atomicAdd(barrier, 1u);
-    bm.bflag[1] = spin_geq(barrier, (unsigned)(ci + 1) * gridDim.x, err, 4);
+    bm.bflag[1] = spin_geq(barrier, (unsigned)(ci + 1) * gridDim.x, err, wait_ns, 4);
   }
   __syncthreads();
   const bool ok = bm.bflag[1] != 0;

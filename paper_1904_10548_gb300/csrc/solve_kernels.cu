@@ -29,6 +29,7 @@ namespace rn {
 template <typename T, bool APG, int C>
 __global__ void __launch_bounds__(512) k_solve(KParams<T> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (APG && blockIdx.x == 0 && threadIdx.x == 0) stamp_time(P.st.info, 0);
   const BlockMem bm = block_mem(smem_raw, P.net_bytes, P.team_bytes);
   const NetDev<T> *net = stage_net(P.net, bm.net_raw);
   const Team tc = chain_team(P.tpb), tb = block_team();
@@ -54,7 +55,7 @@ __global__ void __launch_bounds__(512) k_solve(KParams<T> P) {
       break;
     }
     if (check) {
-      if (!grid_check(bm, c.rbits, P.st.res, P.st.barrier, ci, P.st.err)) {
+      if (!grid_check(bm, c.rbits, P.st.res, P.st.barrier, ci, P.st.err, P.st.wait_ns)) {
         reason = 3;
         ++ci;
         ++it;
@@ -79,6 +80,7 @@ __global__ void __launch_bounds__(512) k_solve(KParams<T> P) {
     P.st.info[0] = it;
     P.st.info[1] = ci;
     P.st.info[2] = reason;
+    if (APG) stamp_time(P.st.info, 1);
   }
 }
 

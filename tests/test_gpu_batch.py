@@ -44,13 +44,27 @@ def tensors(pb):
     return (dev(pb.data.x0), dev(pb.data.q), dev(pb.data.demand), dev(pb.data.alpha))
 
 
-@pytest.mark.parametrize("max_ctas", [0, 7])
-def test_batch_equals_solo_and_oracle(max_ctas):
+def work_items(pb, gamma):
+    """Work items of a problem's own kernels: the grid of a handle without a cap."""
+    f = rn.Factor(pb.net, pb.cost, pb.tree, gamma=gamma, precision=rn.RN_PREC_MIXED)
+    n = f.info()["grid_ctas"]
+    f.close()
+    return n
+
+
+@pytest.mark.parametrize("capped", [False, True])
+def test_batch_equals_solo_and_oracle(capped):
+    """capped: the batch's grid is capped at the largest problem's work-item
+    count, far below the batch's total, so that blocks take several items
+    of several problems."""
     pbs = [batch_problem(i) for i in range(9)]
     gammas = []
     for pb in pbs:
         P = O.OracleProblem.from_parts(pb.net, pb.cost, pb.tree)
         gammas.append(O.step_size(O.power_iteration(P, O.factor(P), 60)))
+    items = [work_items(pb, g) for pb, g in zip(pbs, gammas)]
+    max_ctas = max(items) if capped else 0
+    assert not capped or max_ctas < sum(items)
     facs = [rn.Factor(pb.net, pb.cost, pb.tree, gamma=g, precision=rn.RN_PREC_MIXED,
                       max_ctas=max_ctas) for pb, g in zip(pbs, gammas)]
     iters = 150
@@ -96,3 +110,16 @@ def test_batch_rejects_fp64_handles():
         rn.solve_batch([f], [tensors(pb)], 10)
     assert ei.value.status == B.RN_ERR_INVAL
     f.close()
+
+
+def test_cap_below_the_work_items_is_refused():
+    """A handle's own kernels need one resident block per work item: a
+    smaller cap is refused at factor creation, before any launch."""
+    pb = batch_problem(2)
+    n = work_items(pb, 1e-3)
+    assert n > 1
+    with pytest.raises(B.RapidNetError) as ei:
+        rn.Factor(pb.net, pb.cost, pb.tree, gamma=1e-3, precision=rn.RN_PREC_MIXED,
+                  max_ctas=n - 1)
+    assert ei.value.status == B.RN_ERR_UNSUPPORTED
+    assert "work items" in str(ei.value)

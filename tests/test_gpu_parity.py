@@ -155,6 +155,67 @@ def test_apg_matches_oracle(kind, iters):
     assert abs(out["gap"] - gap) <= 1e-6 * max(abs(cost), 1.0)
 
 
+@pytest.mark.parametrize("kind,precision", [("uneven1", rn.RN_PREC_FP64),
+                                             ("barcelona32", rn.RN_PREC_FP64),
+                                             ("uneven1", rn.RN_PREC_MIXED)])
+def test_simple_theta_rule_matches_oracle(kind, precision):
+    """The second extrapolation sequence of §4.3, theta_nu = 2 / (nu + 2),
+    against the oracle's APG with the same rule (FP64: 1e-6; mixed: the
+    mixed-precision bar of 1e-3)."""
+    pb = problem(kind)
+    P, F, S = oracle_for(kind, pb)
+    gamma = O.step_size(O.power_iteration(P, F, 100))
+    iters = 300
+    ref = O.apg(P, F, S, iters, gamma, theta_rule="simple")
+    fac = gpu_factor(pb, gamma=gamma, precision=precision, theta_rule=B.RN_THETA_SIMPLE)
+    out = fac.solve(pb.data.x0, pb.data.q, pb.data.demand, pb.data.alpha, max_iters=iters)
+    fac.close()
+    tol = RTOL if precision == rn.RN_PREC_FP64 else 1e-3
+    assert out["status"] == B.RN_OK and out["iters"] == iters
+    for k in "uxy":
+        assert rel_err(out[k], getattr(ref, k)) <= tol, k
+    # the rule matters: the equality rule's iterate is elsewhere
+    other = O.apg(P, F, S, iters, gamma)
+    assert rel_err(other.y, ref.y) > 100 * tol
+
+
+@pytest.mark.parametrize("kind,precision,rule", [("tiny", rn.RN_PREC_FP64, "equality"),
+                                                  ("barcelona32", rn.RN_PREC_FP64, "simple"),
+                                                  ("uneven2", rn.RN_PREC_FP64, "equality"),
+                                                  ("uneven1", rn.RN_PREC_MIXED, "simple"),
+                                                  ("tight", rn.RN_PREC_MIXED, "equality")])
+def test_averaged_primal_matches_oracle(kind, precision, rule):
+    """The averaged primal iterate of §4.3, xbar^nu = (1 - theta_nu)
+    xbar^{nu-1} + theta_nu x*(w^nu), against the oracle's (FP64: 1e-6;
+    mixed: 1e-3).  Being an average of primal points that satisfy the
+    dynamics and couplings, it satisfies them too."""
+    pb = problem(kind)
+    P, F, S = oracle_for(kind, pb)
+    gamma = O.step_size(O.power_iteration(P, F, 100))
+    iters = 250
+    ref = O.apg(P, F, S, iters, gamma, theta_rule=rule, average=True)
+    fac = gpu_factor(pb, gamma=gamma, precision=precision,
+                     theta_rule=B.RN_THETA_SIMPLE if rule == "simple" else B.RN_THETA_EQUALITY)
+    out = fac.solve(pb.data.x0, pb.data.q, pb.data.demand, pb.data.alpha, max_iters=iters,
+                    average=True)
+    plain = fac.solve(pb.data.x0, pb.data.q, pb.data.demand, pb.data.alpha, max_iters=iters)
+    fac.close()
+    tol = RTOL if precision == rn.RN_PREC_FP64 else 1e-3
+    assert rel_err(out["u_avg"], ref.u_avg) <= tol
+    assert rel_err(out["x_avg"], ref.x_avg) <= tol
+    # averaging changes nothing else
+    for k in "uxy":
+        assert np.array_equal(out[k], plain[k]), k
+    net, tree, d = pb.net, pb.tree, pb.data
+    u, x = out["u_avg"], out["x_avg"]
+    a = tree.anc[1:]
+    dyn = x[1:] - x[a] - u[1:] @ net.B.T - d.demand[1:] @ net.Gd.T
+    assert np.abs(dyn).max() <= (1e-9 if precision == rn.RN_PREC_FP64 else 1e-5) * np.abs(x).max()
+    if net.ne:
+        cpl = u[1:] @ net.E.T + d.demand[1:] @ net.Ed.T
+        assert np.abs(cpl).max() <= (1e-9 if precision == rn.RN_PREC_FP64 else 1e-5) * np.abs(u).max()
+
+
 @pytest.mark.parametrize("kind", ["tiny", "barcelona32", "tight"])
 def test_first_ten_iterates_match_oracle(kind):
     """Iterate by iterate: the GPU solve stopped after k = 1 .. 10

@@ -39,6 +39,7 @@ def test_noalloc_matches_allocating_entry_point_twice(name):
     ny = 2 * nx + nu
     dev = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
     fac = rn.Factor(pb.net, pb.cost, pb.tree, gamma=1e-3)
+    assert fac.info()["noalloc_bytes"] <= B.RN_NOALLOC_SCRATCH_BYTES
     rng = np.random.default_rng(4)
     u_ref = torch.empty((n, nu), dtype=torch.float64, device="cuda")
     x_ref = torch.empty((n, nx), dtype=torch.float64, device="cuda")
@@ -61,6 +62,7 @@ def test_noalloc_matches_allocating_entry_point_twice(name):
 def test_noalloc_rejects_trees_beyond_the_static_scratch():
     pb = make_problem("barcelona512")
     fac = rn.Factor(pb.net, pb.cost, pb.tree, gamma=1e-3)
+    assert fac.info()["noalloc_bytes"] > B.RN_NOALLOC_SCRATCH_BYTES
     import torch
     n, nx, nu = pb.tree.n_nodes, pb.net.nx, pb.net.nu
     fac.solve(pb.data.x0, pb.data.q, pb.data.demand, pb.data.alpha, max_iters=1)
