@@ -158,6 +158,14 @@ typedef struct {
                           persistent launch began and when its first block
                           finished; comparable between launches on one
                           device (0 from rapidnet_solve_batch) */
+  double *u_avg, *x_avg;  /* NULL, or caller-allocated like u and x: the
+                          averaged primal iterate of paper §4.3, which the
+                          paper credits with an O(1/nu^2) rate,
+                          xbar^nu = (1 - theta_nu) xbar^{nu-1} + theta_nu
+                          x*(w^nu) from xbar^0 = x*(w^0) (theta_0 = 1),
+                          accumulated in FP64 over the iterations.  Give
+                          both or neither; rapidnet_solve_batch refuses them
+                          (RN_ERR_UNSUPPORTED). */
 } rn_result;
 
 typedef struct rn_factor rn_factor;

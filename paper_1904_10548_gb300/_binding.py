@@ -68,7 +68,8 @@ class rn_result(ctypes.Structure):
                 ("compute_gap", c_int), ("iters", c_int), ("n_checks", c_int),
                 ("primal_res", c_double), ("ubox_viol", c_double), ("cost", c_double),
                 ("gap", c_double), ("gamma", c_double), ("apg_ms", c_double),
-                ("t_begin_ns", c_longlong), ("t_end_ns", c_longlong)]
+                ("t_begin_ns", c_longlong), ("t_end_ns", c_longlong),
+                ("u_avg", PD), ("x_avg", PD)]
 
 
 RESULT_SCALARS = ("iters", "n_checks", "primal_res", "ubox_viol", "cost", "gap", "gamma",
@@ -366,9 +367,11 @@ class Factor:
         return {f: getattr(i, f) for f, _ in rn_factor_info._fields_}
 
     def solve(self, x0, q, demand, alpha, max_iters: int, tol: float = 0.0, y_warm=None,
-              compute_gap: bool = False, res_hist_len: int = 0, out=None) -> dict:
+              compute_gap: bool = False, res_hist_len: int = 0, out=None,
+              average: bool = False) -> dict:
         """Host arrays in and out (rapidnet_solve).  ``out`` may supply
-        contiguous float64 arrays (u, x, y), e.g. views of pinned memory."""
+        contiguous float64 arrays (u, x, y), e.g. views of pinned memory.
+        average: also return the averaged primal iterate (u_avg, x_avg)."""
         n = self.n_nodes
         x0 = _f64(x0, (self.nx,))
         q = _f64(q, (self.nu,))
@@ -387,20 +390,29 @@ class Factor:
         hist = np.zeros(max(res_hist_len, 1))
         res = rn_result(_pd(u), _pd(x), _pd(y), _pd(hist) if res_hist_len else None,
                         res_hist_len, int(compute_gap))
+        if average:
+            ua, xa = np.empty((n, self.nu)), np.empty((n, self.nx))
+            res.u_avg, res.x_avg = _pd(ua), _pd(xa)
         rc = rapidnet_solve(self.h, _pd(x0), _pd(q), _pd(demand), _pd(alpha), max_iters, tol,
                             None if yw is None else _pd(yw), res)
         out = {f: getattr(res, f) for f in RESULT_SCALARS}
         out.update(status=rc, u=u, x=x, y=y,
                    res_hist=hist[:min(res_hist_len, res.n_checks)] if res_hist_len else None)
+        if average:
+            out.update(u_avg=ua, x_avg=xa)
         return out
 
     def solve_device(self, x0, q, demand, alpha, max_iters: int, tol: float, u, x, y,
-                     y_warm=None, compute_gap: bool = False, res_hist=None) -> dict:
+                     y_warm=None, compute_gap: bool = False, res_hist=None, u_avg=None,
+                     x_avg=None) -> dict:
         """torch CUDA float64 tensors in and out (rapidnet_solve_device)."""
         res = rn_result(ctypes.cast(_dev_ptr(u), PD), ctypes.cast(_dev_ptr(x), PD),
                         ctypes.cast(_dev_ptr(y), PD),
                         ctypes.cast(_dev_ptr(res_hist), PD) if res_hist is not None else None,
                         0 if res_hist is None else res_hist.numel(), int(compute_gap))
+        if u_avg is not None or x_avg is not None:
+            res.u_avg = ctypes.cast(_dev_ptr(u_avg), PD)
+            res.x_avg = ctypes.cast(_dev_ptr(x_avg), PD)
         rc = rapidnet_solve_device(self.h, _dev_ptr(x0), _dev_ptr(q), _dev_ptr(demand),
                                    _dev_ptr(alpha), max_iters, tol, _dev_ptr(y_warm), res)
         out = {f: getattr(res, f) for f in RESULT_SCALARS}

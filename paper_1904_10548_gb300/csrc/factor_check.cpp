@@ -10,7 +10,7 @@
 //   Phi_nu = L (L' Q_nu L)^-1 L'
 //   P_nu   = 2 p_nu W_u - (2 p_nu W_u) Phi_nu (2 p_nu W_u)
 // The kernels use instead one operator for every node,
-//   F = W^-1 - W^-1 E' S^-1 E W^-1,  S = E W^-1 E'  (W = W_u diagonal),
+//   F = W^-1 - W^-1 E' S^-1 E W^-1,  S = E W^-1 E'  (W = W_u, diagonal or dense),
 // with Phi_nu = F / (2 p_nu).  That is exact by induction from the leaves:
 // F = L (L' W L)^-1 L', so a leaf (Q = 2 p W) has 2 p Phi = F; and when
 // every child has Phi_c = F / (2 p_c), then P_c = 2 p_c (W - W F W), which
@@ -139,8 +139,7 @@ void matmul_tn(const double *A, const double *B, double *C, int k, int m, int n)
 
 double collapse_deviation(const rn_tree *tree, int nu, int ne, const double *E,
                           const double *winv, const double *Sinv) {
-  const int nv = nu - ne, N = tree->N;
-  if (nv <= 0) return 0.0;  // u is fixed by E u + Ed d = 0: nothing to factor
+  if (nu - ne <= 0) return 0.0;  // u is fixed by E u + Ed d = 0: nothing to factor
   // F (dense, nu x nu) from the same W^-1 and S^-1 the kernels receive
   std::vector<double> EW((size_t)std::max(1, ne) * nu), F((size_t)nu * nu, 0.0);
   for (int r = 0; r < ne; ++r)
@@ -159,6 +158,16 @@ double collapse_deviation(const rn_tree *tree, int nu, int ne, const double *E,
       for (int j = 0; j < nu; ++j) F[(size_t)i * nu + j] -= a * T[(size_t)r * nu + j];
     }
   }
+  std::vector<double> W((size_t)nu * nu, 0.0);
+  for (int i = 0; i < nu; ++i) W[(size_t)i * nu + i] = 1.0 / winv[i];
+  return collapse_deviation_dense(tree, nu, ne, E, W.data(), F.data());
+}
+
+double collapse_deviation_dense(const rn_tree *tree, int nu, int ne, const double *E,
+                                const double *W, const double *Fp) {
+  const int nv = nu - ne, N = tree->N;
+  if (nv <= 0) return 0.0;
+  const std::vector<double> F(Fp, Fp + (size_t)nu * nu);
   double fmax = 0.0;
   for (double a : F) fmax = std::max(fmax, std::fabs(a));
   std::vector<double> L;
@@ -175,12 +184,11 @@ double collapse_deviation(const rn_tree *tree, int nu, int ne, const double *E,
   // D = W - W F W: a child's P_c / (2 p_c) under the induction hypothesis.
   // L' Q L = 2 p_v L'W L + 2 (sum of the children's p) L'D L.
   std::vector<double> D((size_t)nu * nu), WL((size_t)nu * nv), DL((size_t)nu * nv);
-  for (int i = 0; i < nu; ++i)
-    for (int j = 0; j < nu; ++j)
-      D[(size_t)i * nu + j] = (i == j ? 1.0 / winv[i] : 0.0) -
-                              F[(size_t)i * nu + j] / (winv[i] * winv[j]);
-  for (int i = 0; i < nu; ++i)
-    for (int c = 0; c < nv; ++c) WL[(size_t)i * nv + c] = L[(size_t)i * nv + c] / winv[i];
+  std::vector<double> WF((size_t)nu * nu), WFW((size_t)nu * nu);
+  matmul(W, F.data(), WF.data(), nu, nu, nu);
+  matmul(WF.data(), W, WFW.data(), nu, nu, nu);
+  for (size_t e = 0; e < D.size(); ++e) D[e] = W[e] - WFW[e];
+  matmul(W, L.data(), WL.data(), nu, nu, nv);
   matmul(D.data(), L.data(), DL.data(), nu, nu, nv);
   std::vector<double> LWL((size_t)nv * nv), LDL((size_t)nv * nv);
   matmul_tn(L.data(), WL.data(), LWL.data(), nu, nv, nv);

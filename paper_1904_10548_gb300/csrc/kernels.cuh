@@ -26,6 +26,7 @@ namespace rn {
 constexpr int kSeg = 16;                    // ints of a team's node list (halved)
 constexpr long long kWaitNs = 2000000000LL; // default bound of every device-side wait (2 s)
 constexpr int kChildSlotsDev = 8;           // children per node in a group's children table
+constexpr int kTcTiles = 4;                 // n-tiles of 8 columns of F a warp keeps (dense W_u)
 
 template <typename T>
 struct NetDev {
@@ -43,6 +44,12 @@ struct NetDev {
   const T *Ec_val;
   const T *winv;  // diagonal of W_u^{-1}
   const T *Sinv;  // (E W_u^{-1} E')^{-1}, ne x ne
+  // dense W_u (null for a diagonal one): F = W^-1 - W^-1 E' S^-1 E W^-1
+  // (nu x nu, row-major), its TF32 fragments for the tensor cores (FP32
+  // steps, dense_f.cuh) and W^-1 E' S^-1 (nu x ne) for the data terms
+  const T *Fd;
+  const float4 *Ft;
+  const T *Gm;
   const T *xmin, *xmax, *xs, *umin, *umax;
   T Wx, Ws;
 };
@@ -68,6 +75,9 @@ struct StateDev {
   const T *inv2p;   // 1 / (2 p) per internal node
   const T *xroot;   // x0 (nx); unused when linear
   const double *beta;  // beta_0 .. beta_iters (APG)
+  const double *theta; // theta_0 .. theta_iters (APG, the averaged primal)
+  double *uavg, *xavg; // averaged primal iterate (internal rows of NUP / NXP),
+                       // updated in FP64 by the APG iterations; null = off
   unsigned *count, *flags, *barrier;  // per group, then per root: arrivals, completion; grid
   unsigned long long *res;  // per check: bits of the non-negative residual
   int *err;                 // 0 ok, else the site of the wait that gave up (1-4)

@@ -62,6 +62,8 @@ __global__ void __launch_bounds__(512) k_mixed(MixedParams M) {
     c.beta_n = (float)P.st.beta[it + 1];
     const bool check = ((it + 1) % P.check_every) == 0 || it + 1 == P.iters;
     c.write_out = check;
+    c.avg = P.st.uavg != nullptr;
+    c.theta = P.st.theta[it];
     c.rbits = 0ull;
     eval_step<float, kFwdMixed, C>(P, c, &M.mx, sfc, sfg, tc, tb, step++, keep);
     if (block_err(bm, P.st.err)) {

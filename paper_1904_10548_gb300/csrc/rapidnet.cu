@@ -36,6 +36,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // kq = q - W^-1 E' S^-1 E q: the input q projected on ker E in the W metric
+// (dense W_u: kq = q - Gm E q with Gm = W^-1 E' S^-1)
 __global__ void k_kq(NetDev<double> nt, const double *q, double *kq) {
   extern __shared__ double sh[];
   double *e = sh, *f = sh + nt.NEP;
@@ -46,6 +47,14 @@ __global__ void k_kq(NetDev<double> nt, const double *q, double *kq) {
     e[r] = acc;
   }
   __syncthreads();
+  if (nt.Gm) {
+    for (int j = tid; j < nt.nu; j += blockDim.x) {
+      double acc = 0.0;
+      for (int r = 0; r < nt.ne; ++r) acc += nt.Gm[(size_t)j * nt.ne + r] * e[r];
+      kq[j] = q[j] - acc;
+    }
+    return;
+  }
   for (int r = tid; r < nt.ne; r += blockDim.x) {
     double acc = 0.0;
     for (int c = 0; c < nt.ne; ++c) acc += nt.Sinv[(size_t)r * nt.ne + c] * e[c];
@@ -88,7 +97,7 @@ __global__ void k_prep(NetDev<double> nt, PrepArgs a, int n, double *s, double *
       e[r] = acc;
     }
     __syncthreads();
-    for (int r = tid; r < nt.ne; r += blockDim.x) {
+    for (int r = tid; r < nt.ne && !nt.Gm; r += blockDim.x) {
       double acc = 0.0;
       for (int c = 0; c < nt.ne; ++c) acc += nt.Sinv[(size_t)r * nt.ne + c] * e[c];
       f[r] = acc;
@@ -99,8 +108,14 @@ __global__ void k_prep(NetDev<double> nt, PrepArgs a, int n, double *s, double *
       if (j < nt.nu) {
         c0 = p * a.W_alpha * (a.alpha0[j] + al[j]);
         double acc = 0.0;
-        for (int k = nt.Ec_ptr[j]; k < nt.Ec_ptr[j + 1]; ++k) acc += nt.Ec_val[k] * f[nt.Ec_idx[k]];
-        u = a.kq[j] - nt.winv[j] * acc;
+        if (nt.Gm) {  // dense W_u: W^-1 E' S^-1 (Ed d)
+          for (int r = 0; r < nt.ne; ++r) acc += nt.Gm[(size_t)j * nt.ne + r] * e[r];
+          u = a.kq[j] - acc;
+        } else {
+          for (int k = nt.Ec_ptr[j]; k < nt.Ec_ptr[j + 1]; ++k)
+            acc += nt.Ec_val[k] * f[nt.Ec_idx[k]];
+          u = a.kq[j] - nt.winv[j] * acc;
+        }
       }
       s[(size_t)v * nt.SP + nt.NXP + j] = c0;
       ub[(size_t)v * nt.NUP + j] = u;
@@ -186,6 +201,7 @@ __global__ void k_gather(NetDev<double> nt, const int *perm, int n, const double
 struct ReduceArgs {
   const int *parent, *perm;
   const double *prob, *alpha, *alpha0, *wdiag, *q;
+  const double *wdense;    // dense W_u (nu x nu) or null (diagonal: wdiag)
   const double *uo, *xo;   // internal rows
   const double *y;         // internal rows (gap) or null
   double W_alpha;
@@ -210,7 +226,12 @@ __global__ void k_node_reduce(NetDev<double> nt, ReduceArgs a, int n, double *pa
       const double p = a.prob[v];
       for (int j = lane; j < nt.nu; j += 32) {
         const double du = u[j] - ua[j];
-        t += p * (a.W_alpha * (a.alpha0[j] + al[j]) * u[j] + a.wdiag[j] * du * du);
+        double wdu = a.wdiag[j] * du;
+        if (a.wdense) {
+          wdu = 0.0;
+          for (int k = 0; k < nt.nu; ++k) wdu += a.wdense[(size_t)j * nt.nu + k] * (u[k] - ua[k]);
+        }
+        t += p * (a.W_alpha * (a.alpha0[j] + al[j]) * u[j] + wdu * du);
         m = fmax(m, fmax(nt.umin[j] - u[j], u[j] - nt.umax[j]));
       }
       for (int i = lane; i < nt.nx; i += 32) {
@@ -459,6 +480,8 @@ struct rn_factor {
   // device copies of host data
   int *perm = nullptr;
   double *prob = nullptr, *inv2p = nullptr, *alpha0 = nullptr, *wdiag = nullptr;
+  double *wdense = nullptr;  // a dense W_u (null for a diagonal one)
+  bool dense_w = false;
   int *Gd_ptr = nullptr, *Gd_idx = nullptr, *Ed_ptr = nullptr, *Ed_idx = nullptr;
   double *Gd_val = nullptr, *Ed_val = nullptr;
   // per-solve data owned by the handle
@@ -475,6 +498,8 @@ struct rn_factor {
   bool have_data = false;
   // host staging for rapidnet_solve (host pointers)
   double *io_y = nullptr, *io_u = nullptr, *io_x = nullptr, *io_hist = nullptr;
+  // averaged primal iterate (internal rows) and its host staging
+  double *uavg = nullptr, *xavg = nullptr, *io_uavg = nullptr, *io_xavg = nullptr;
   int io_hist_cap = 0;
 
   ~rn_factor() {
@@ -575,6 +600,7 @@ KParams<float> base_params_f(rn_factor *f) {
   P.st = f->stf;
   P.st.res = f->st.res;
   P.st.beta = f->st.beta;
+  P.st.theta = f->st.theta;
   P.iters = 1;
   P.check_every = 1;
   P.linear = 1;
@@ -687,6 +713,48 @@ int fit_sizes(const rn_factor *f, int eb, int team_bytes, int net_bytes, int tw,
                       net_bytes, tw, tpb, mode, z);
 }
 
+// a W_u with a nonzero entry off the diagonal
+bool is_dense(const double *W, int nu) {
+  for (int i = 0; i < nu; ++i)
+    for (int j = 0; j < nu; ++j)
+      if (i != j && W[(size_t)i * nu + j] != 0.0) return true;
+  return false;
+}
+
+// TF32 head of an FP32 value on the host, as the device's cvt.rna.tf32.f32:
+// round to nearest, ties away from zero, keep 10 mantissa bits
+float tf32_round(float a) {
+  unsigned u;
+  std::memcpy(&u, &a, 4);
+  if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x1000u) & ~0x1fffu;
+  float r;
+  std::memcpy(&r, &u, 4);
+  return r;
+}
+
+// B fragments of F for mma.m16n8k8 (row.col), per (k-step ks, n-tile nt,
+// lane): b0 = B[8 ks + t][8 nt + g], b1 = B[8 ks + t + 4][8 nt + g] with
+// g = lane / 4, t = lane % 4 and B[k][j] = F[j][k] (zero outside nu x nu),
+// each as TF32 head and tail: {b0 head, b1 head, b0 tail, b1 tail}
+std::vector<float> dense_f_fragments(const std::vector<double> &F, int nu) {
+  const int NT = (nu + 7) / 8;
+  std::vector<float> out((size_t)NT * NT * 32 * 4);
+  auto Bkj = [&](int k, int j) { return (k < nu && j < nu) ? F[(size_t)j * nu + k] : 0.0; };
+  for (int ks = 0; ks < NT; ++ks)
+    for (int nt = 0; nt < NT; ++nt)
+      for (int lane = 0; lane < 32; ++lane) {
+        const int g = lane / 4, t = lane % 4;
+        const double b[2] = {Bkj(8 * ks + t, 8 * nt + g), Bkj(8 * ks + t + 4, 8 * nt + g)};
+        float *o = &out[(((size_t)ks * NT + nt) * 32 + lane) * 4];
+        for (int e = 0; e < 2; ++e) {
+          const float head = tf32_round((float)b[e]);
+          o[e] = head;
+          o[2 + e] = tf32_round((float)(b[e] - (double)head));
+        }
+      }
+  return out;
+}
+
 int validate_network(const rn_network *net, const rn_cost *cost) {
   if (!net || !cost) {
     set_error("network or cost is NULL");
@@ -739,12 +807,13 @@ int validate_network(const rn_network *net, const rn_cost *cost) {
       set_error("cost: Wu is not positive definite (diagonal entry %d)", i);
       return RN_ERR_INVAL;
     }
-  for (int i = 0; i < nu; ++i)
-    for (int j = 0; j < nu; ++j)
-      if (i != j && cost->Wu[(size_t)i * nu + j] != 0.0) {
-        set_error("cost: the library handles a diagonal Wu only");
-        return RN_ERR_UNSUPPORTED;
-      }
+  if (is_dense(cost->Wu, nu)) {
+    std::vector<double> R(cost->Wu, cost->Wu + (size_t)nu * nu);
+    if (!cholesky(R, nu)) {
+      set_error("cost: Wu is not positive definite (Cholesky breaks down)");
+      return RN_ERR_INVAL;
+    }
+  }
   for (int i = 0; i < nx; ++i)
     for (int j = 0; j < nx; ++j)
       if (net->A[(size_t)i * nx + j] != (i == j ? 1.0 : 0.0)) {
@@ -820,7 +889,56 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
     winv[j] = 1.0 / wdiag[j];
   }
   std::vector<double> Sinv(std::max(1, ne * ne), 0.0);
-  if (ne > 0) {
+  // dense W_u: W^-1 by Cholesky, S = E W^-1 E', F = W^-1 - W^-1 E' S^-1 E W^-1
+  // and Gm = W^-1 E' S^-1 as dense matrices (FP64)
+  f->dense_w = is_dense(cost->Wu, nu);
+  std::vector<double> Fdense, Gm;
+  if (f->dense_w) {
+    std::vector<double> R(cost->Wu, cost->Wu + (size_t)nu * nu);
+    if (!cholesky(R, nu)) {
+      set_error("cost: Wu is not positive definite (Cholesky breaks down)");
+      return RN_ERR_INVAL;
+    }
+    const std::vector<double> Wi = chol_inverse(R, nu);
+    for (int j = 0; j < nu; ++j) winv[j] = Wi[(size_t)j * nu + j];
+    std::vector<double> EWi((size_t)std::max(1, ne) * nu, 0.0);  // E W^-1
+    for (int r = 0; r < ne; ++r)
+      for (int k = 0; k < nu; ++k) {
+        const double e = net->E[(size_t)r * nu + k];
+        if (e == 0.0) continue;
+        for (int j = 0; j < nu; ++j) EWi[(size_t)r * nu + j] += e * Wi[(size_t)k * nu + j];
+      }
+    Gm.assign((size_t)nu * std::max(1, ne), 0.0);
+    if (ne > 0) {
+      std::vector<double> S((size_t)ne * ne, 0.0);
+      for (int r = 0; r < ne; ++r)
+        for (int c = 0; c < ne; ++c) {
+          double acc = 0.0;
+          for (int j = 0; j < nu; ++j) acc += EWi[(size_t)r * nu + j] * net->E[(size_t)c * nu + j];
+          S[(size_t)r * ne + c] = acc;
+        }
+      std::vector<double> RS = S;
+      if (!cholesky(RS, ne)) {
+        set_error("E does not have full row rank (E W^-1 E' is singular)");
+        return RN_ERR_RANK;
+      }
+      Sinv = chol_inverse(RS, ne);
+      for (int j = 0; j < nu; ++j)
+        for (int r = 0; r < ne; ++r) {
+          double acc = 0.0;
+          for (int c = 0; c < ne; ++c) acc += EWi[(size_t)c * nu + j] * Sinv[(size_t)c * ne + r];
+          Gm[(size_t)j * ne + r] = acc;
+        }
+    }
+    Fdense = Wi;
+    for (int i = 0; i < nu; ++i)
+      for (int r = 0; r < ne; ++r) {
+        const double a = Gm[(size_t)i * ne + r];
+        if (a == 0.0) continue;
+        for (int j = 0; j < nu; ++j) Fdense[(size_t)i * nu + j] -= a * EWi[(size_t)r * nu + j];
+      }
+  }
+  if (ne > 0 && !f->dense_w) {
     std::vector<double> S((size_t)ne * ne, 0.0);
     for (int r = 0; r < ne; ++r)
       for (int c = 0; c < ne; ++c) {
@@ -838,7 +956,9 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
   }
   // the shared operator must stand for every node's factor of the general
   // recursion (it does in exact arithmetic; this bounds the rounding)
-  f->collapse_dev = collapse_deviation(tree, nu, ne, net->E, winv.data(), Sinv.data());
+  f->collapse_dev = f->dense_w ? collapse_deviation_dense(tree, nu, ne, net->E, cost->Wu,
+                                                         Fdense.data())
+                              : collapse_deviation(tree, nu, ne, net->E, winv.data(), Sinv.data());
   if (!(f->collapse_dev <= kCollapseTol)) {
     set_error("factor check: 2 p Phi differs from the shared operator F by %.3g (relative) at a "
               "sampled node; E W_u^-1 E' is too ill-conditioned", f->collapse_dev);
@@ -893,6 +1013,10 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
   UP_D(nt.umax, std::vector<double>(net->umax, net->umax + nu))
   UP_D(f->alpha0, std::vector<double>(cost->alpha0, cost->alpha0 + nu))
   UP_D(f->wdiag, wdiag)
+  if (f->dense_w) {
+    UP_D(nt.Fd, Fdense) UP_D(nt.Gm, Gm)
+    UP_D(f->wdense, std::vector<double>(cost->Wu, cost->Wu + (size_t)nu * nu))
+  }
   UP_I(f->Gd_ptr, Gdr.ptr) UP_I(f->Gd_idx, Gdr.idx) UP_D(f->Gd_val, Gdr.val)
   UP_I(f->Ed_ptr, Edr.ptr) UP_I(f->Ed_idx, Edr.idx) UP_D(f->Ed_val, Edr.val)
 
@@ -1006,6 +1130,12 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
     UP_F(nf.xmin, tof(net->xmin, nx)) UP_F(nf.xmax, tof(net->xmax, nx)) UP_F(nf.xs, tof(net->xs, nx))
     UP_F(nf.umin, tof(net->umin, nu)) UP_F(nf.umax, tof(net->umax, nu))
     UP_F(f->stf.inv2p, tofv(inv2p))
+    if (f->dense_w) {
+      UP_F(nf.Fd, tofv(Fdense))
+      const std::vector<float> frag = dense_f_fragments(Fdense, nu);
+      UP_F(fp, frag)
+      nf.Ft = reinterpret_cast<const float4 *>(fp);
+    }
 #undef UP_F
     float *s32, *z32, *up32, *ux32, *hp32, *da, *db, *ybh, *uref, *xref, *sw;
     if ((rc = dalloc(f, &s32, (size_t)n * f->SP)) || (rc = dalloc(f, &z32, (size_t)n * f->NUP)) ||
@@ -1053,6 +1183,16 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
   // holds
   if ((rc = team_layout(f->opts.block_threads, nx, nu, &f->tw, &f->tpb, &f->maxc))) return rc;
   f->block = f->tpb * f->tw;
+  if (f->dense_w) {
+    // the dense F product: at most two components per thread (FP64) and
+    // kTcTiles column tiles per warp (tensor cores)
+    const int ntiles = (nu + 7) / 8, nw = f->tw / 32;
+    if (2 * f->tw < nu || (ntiles + nw - 1) / nw > kTcTiles) {
+      set_error("a dense Wu needs chain teams of at least %d threads (block_threads)",
+                std::max((nu + 1) / 2, 32 * ((ntiles + kTcTiles - 1) / kTcTiles)));
+      return RN_ERR_UNSUPPORTED;
+    }
+  }
   {
     const int nnzB = (int)Bc.idx.size(), nnzE = (int)Er.idx.size();
     f->net_bytes_d = (int)net_smem_bytes(nx, nu, ne, nnzB, nnzE, 8);
@@ -1129,10 +1269,12 @@ int ensure_beta(rn_factor *f, int iters) {
   // beta_nu = theta_nu (1 / theta_{nu-1} - 1) from theta_0 = theta_{-1} = 1
   // with theta_{nu+1} = (sqrt(theta^4 + 4 theta^2) - theta^2) / 2 or
   // theta_nu = 2 / (nu + 2) (paper §4.3)
-  std::vector<double> b(cap);
+  // beta at [0, cap), theta_0 .. theta_{cap-1} at [cap, 2 cap)
+  std::vector<double> b(2 * (size_t)cap);
   double th = 1.0, prev = 1.0;
   for (int k = 0; k < cap; ++k) {
     b[k] = th * (1.0 / prev - 1.0);
+    b[cap + k] = th;
     const double t2 = th * th;
     const double nt = f->opts.theta_rule == RN_THETA_SIMPLE
                           ? 2.0 / (k + 3)
@@ -1146,6 +1288,7 @@ int ensure_beta(rn_factor *f, int iters) {
   if (rc) return rc;
   f->beta_cap = cap;
   f->st.beta = f->beta;
+  f->st.theta = f->beta + cap;
   return RN_OK;
 }
 
@@ -1193,7 +1336,7 @@ int prepare(rn_factor *f, const double *x0, const double *q, const double *deman
 
 int reduce_nodes(rn_factor *f, int mode, const double *y, double out[3]) {
   ReduceArgs a{f->pd.parent, f->perm, f->prob, f->alpha, f->alpha0, f->wdiag, f->q,
-               f->st.uo, f->st.xo, y, f->W_alpha, mode};
+               f->wdense, f->st.uo, f->st.xo, y, f->W_alpha, mode};
   k_node_reduce<<<kRedBlocks, 256, 0, f->stream>>>(f->net, a, f->plan.n, f->partial);
   k_final_reduce<<<1, 32, 0, f->stream>>>(f->partial, kRedBlocks, f->scal);
   RN_CUDA(cudaGetLastError());
@@ -1217,6 +1360,11 @@ int solve_device_impl(rn_factor *f, const double *x0, const double *q, const dou
     set_error("solve: tol is NaN");
     return RN_ERR_INVAL;
   }
+  if ((out->u_avg == nullptr) != (out->x_avg == nullptr)) {
+    set_error("solve: give both u_avg and x_avg, or neither");
+    return RN_ERR_INVAL;
+  }
+  const bool avg = out->u_avg != nullptr;
   RN_CUDA(cudaSetDevice(f->device));
   const int n = f->plan.n;
   const int checks = (max_iters + f->opts.check_every - 1) / f->opts.check_every + 1;
@@ -1234,15 +1382,27 @@ int solve_device_impl(rn_factor *f, const double *x0, const double *q, const dou
   RN_CUDA(cudaGetLastError());
   if ((rc = reset_sync(f))) return rc;
   RN_CUDA(cudaMemsetAsync(f->res, 0, checks * sizeof(unsigned long long), f->stream));
+  if (avg) {
+    // the averaged primal starts at zero (theta_0 = 1 replaces it by x*(w^0))
+    if (!f->uavg && ((rc = dalloc(f, &f->uavg, (size_t)n * f->NUP)) ||
+                     (rc = dalloc(f, &f->xavg, (size_t)n * f->NXP))))
+      return rc;
+    RN_CUDA(cudaMemsetAsync(f->uavg, 0, (size_t)n * f->NUP * sizeof(double), f->stream));
+    RN_CUDA(cudaMemsetAsync(f->xavg, 0, (size_t)n * f->NXP * sizeof(double), f->stream));
+  }
   RN_CUDA(cudaEventRecord(f->ev0, f->stream));
   if (mixed) {
-    const MixedParams M = mixed_params(f, max_iters, tol);
+    MixedParams M = mixed_params(f, max_iters, tol);
+    M.f.st.uavg = avg ? f->uavg : nullptr;
+    M.f.st.xavg = avg ? f->xavg : nullptr;
     RN_CUDA(launch_mixed(M, f->maxc, f->grid_mixed, f->block, f->smem_mixed, f->stream));
   } else {
     KParams<double> P = base_params(f);
     P.iters = max_iters;
     P.check_every = f->opts.check_every;
     P.tol = tol > 0.0 ? tol : 0.0;
+    P.st.uavg = avg ? f->uavg : nullptr;
+    P.st.xavg = avg ? f->xavg : nullptr;
     RN_CUDA((launch_solve<double, true>(P, f->grid, f->block, f->smem, f->stream)));
   }
   RN_CUDA(cudaEventRecord(f->ev1, f->stream));
@@ -1272,6 +1432,10 @@ int solve_device_impl(rn_factor *f, const double *x0, const double *q, const dou
     k_gather<<<node_blocks(n) + 1, 128, 0, f->stream>>>(f->net, f->perm, n, f->st.uo, f->st.xo,
                                                         yfin, f->q, f->x0, out->u, out->x, out->y);
   }
+  if (avg)
+    k_gather<<<node_blocks(n) + 1, 128, 0, f->stream>>>(f->net, f->perm, n, f->uavg, f->xavg,
+                                                        nullptr, f->q, f->x0, out->u_avg,
+                                                        out->x_avg, nullptr);
   RN_CUDA(cudaGetLastError());
   std::vector<unsigned long long> hist(std::max(1, nchk));
   if (nchk > 0)
@@ -1422,6 +1586,17 @@ extern "C" int rapidnet_solve(rn_factor *f, const double *x0, const double *q,
   dres.u = f->io_u;
   dres.x = f->io_x;
   dres.y = f->io_y;
+  if ((out->u_avg == nullptr) != (out->x_avg == nullptr)) {
+    set_error("solve: give both u_avg and x_avg, or neither");
+    return RN_ERR_INVAL;
+  }
+  if (out->u_avg) {
+    if (!f->io_uavg && ((rc = dalloc(f, &f->io_uavg, (size_t)n * f->nu)) ||
+                        (rc = dalloc(f, &f->io_xavg, (size_t)n * f->nx))))
+      return rc;
+    dres.u_avg = f->io_uavg;
+    dres.x_avg = f->io_xavg;
+  }
   std::vector<double> hist;
   if (out->res_hist && out->res_hist_len > 0) {
     if (out->res_hist_len > f->io_hist_cap) {
@@ -1443,17 +1618,26 @@ extern "C" int rapidnet_solve(rn_factor *f, const double *x0, const double *q,
                           cudaMemcpyDeviceToHost, f->stream));
   RN_CUDA(cudaMemcpyAsync(out->y, f->io_y, (size_t)n * ny * sizeof(double),
                           cudaMemcpyDeviceToHost, f->stream));
+  if (out->u_avg) {
+    RN_CUDA(cudaMemcpyAsync(out->u_avg, f->io_uavg, (size_t)n * f->nu * sizeof(double),
+                            cudaMemcpyDeviceToHost, f->stream));
+    RN_CUDA(cudaMemcpyAsync(out->x_avg, f->io_xavg, (size_t)n * f->nx * sizeof(double),
+                            cudaMemcpyDeviceToHost, f->stream));
+  }
   if (dres.res_hist)
     RN_CUDA(cudaMemcpyAsync(out->res_hist, f->io_hist,
                             std::min(out->res_hist_len, std::max(dres.n_checks, 0)) * sizeof(double),
                             cudaMemcpyDeviceToHost, f->stream));
   RN_CUDA(cudaStreamSynchronize(f->stream));
   double *hu = out->u, *hx = out->x, *hy = out->y, *hh = out->res_hist;
+  double *hua = out->u_avg, *hxa = out->x_avg;
   *out = dres;
   out->u = hu;
   out->x = hx;
   out->y = hy;
   out->res_hist = hh;
+  out->u_avg = hua;
+  out->x_avg = hxa;
   return rc;
 }
 
@@ -1644,6 +1828,11 @@ int batch_impl(rn_factor *const *fs, const rn_solve_req *req, int n, int max_ite
     if (f->opts.precision != RN_PREC_MIXED) {
       set_error("solve_batch: handle %d is not RN_PREC_MIXED", i);
       return RN_ERR_INVAL;
+    }
+    if (r.out->u_avg || r.out->x_avg) {
+      set_error("solve_batch: the averaged primal iterate is not available in a batch "
+                "(request %d)", i);
+      return RN_ERR_UNSUPPORTED;
     }
     if (f->device != dev) {
       set_error("solve_batch: handles on different devices");

@@ -100,6 +100,10 @@ std::vector<double> chol_inverse(const std::vector<double> &R, int m);
 // not positive definite or E' loses rank.
 double collapse_deviation(const rn_tree *tree, int nu, int ne, const double *E,
                           const double *winv, const double *Sinv);
+// The same for a dense W_u (nu x nu) and the dense F (nu x nu) the factor
+// step computed from it.
+double collapse_deviation_dense(const rn_tree *tree, int nu, int ne, const double *E,
+                                const double *W, const double *F);
 constexpr double kCollapseTol = 1e-8;
 
 }  // namespace rn

@@ -277,13 +277,25 @@ struct Slice {
   }
 };
 
+}  // namespace rn
+#include "dense_f.cuh"
+namespace rn {
+
 // ---------------------------------------------------------------------------
 // z = F ghat / (2p) in place for m rows (ghat at offset NXP of row(q)),
-// F ghat = W^-1 (ghat - E' S^-1 E W^-1 ghat); eb, fb: m x NEP work space
+// F ghat = W^-1 (ghat - E' S^-1 E W^-1 ghat) for a diagonal W_u; eb, fb:
+// m x NEP work space.  A dense W_u takes the dense product (dense_f.cuh).
 // ---------------------------------------------------------------------------
 template <typename T, typename RowF>
 __device__ void apply_F(const NetDev<T> &nt, int m, RowF row, const T *i2p, T *eb, T *fb,
                         const Team &tm) {
+  if (nt.Fd) {
+    if constexpr (sizeof(T) == 8)
+      apply_F_dense(nt, m, row, i2p, tm);
+    else
+      apply_F_tc(nt, m, row, i2p, tm);
+    return;
+  }
   const int ne = nt.ne, nu = nt.nu, NXP = nt.NXP, NEP = nt.NEP;
   const int *Er_ptr = nt.Er_ptr, *Er_idx = nt.Er_idx, *Ec_ptr = nt.Ec_ptr, *Ec_idx = nt.Ec_idx;
   const T *Erw_val = nt.Erw_val, *Ec_val = nt.Ec_val, *winv = nt.winv, *Sinv = nt.Sinv;
@@ -417,6 +429,8 @@ struct FwdCtx {
   T *yprv;
   T beta, beta_n;
   bool write_out;
+  bool avg;                  // update the averaged primal with weight theta
+  double theta;
   unsigned long long rbits;  // running max of |y+ - w| (abs_bits of T)
 };
 
@@ -470,6 +484,10 @@ __device__ void prox_node_warp(const KParams<T> &P, const NetDev<T> &nt, int v, 
       ypg[nt.NXP + i] = y2;
       srow[i] = (y1 + c.beta_n * (y1 - a1[cc])) + (y2 + c.beta_n * (y2 - a2[cc]));
       if (c.write_out) P.st.xo[(size_t)v * nt.NXP + i] = Xq[i];
+      if (c.avg) {
+        double *xa = P.st.xavg + (size_t)v * nt.NXP + i;
+        *xa = (1.0 - c.theta) * *xa + c.theta * (double)Xq[i];
+      }
     }
   }
   for (int j = lane; j < nt.nu; j += 32) {
@@ -483,6 +501,10 @@ __device__ void prox_node_warp(const KParams<T> &P, const NetDev<T> &nt, int v, 
     ypg[2 * nt.NXP + j] = y3;
     srow[nt.NXP + j] = y3 + c.beta_n * (y3 - a3);
     if (c.write_out) P.st.uo[(size_t)v * nt.NUP + j] = uj;
+    if (c.avg) {
+      double *ua = P.st.uavg + (size_t)v * nt.NUP + j;
+      *ua = (1.0 - c.theta) * *ua + c.theta * (double)uj;
+    }
   }
 }
 
@@ -515,6 +537,10 @@ __device__ void prox_node_warp_mixed(const KParams<float> &P, const NetDev<float
       h1[cc] = bh[i];
       h2[cc] = bh[nt.NXP + i];
       const float x = xr[i] + Xq[i];
+      if (c.avg) {
+        double *xa = P.st.xavg + (size_t)v * nt.NXP + i;
+        *xa = (1.0 - c.theta) * *xa + c.theta * (double)x;
+      }
       const float lo = g * (nt.xmin[i] - x), hi = g * (nt.xmax[i] - x);
       const float wa = h1[cc] + w1[cc];
       g1[cc] = wa > hi ? w1[cc] - hi : (wa < lo ? w1[cc] - lo : -h1[cc]);
@@ -553,6 +579,10 @@ __device__ void prox_node_warp_mixed(const KParams<float> &P, const NetDev<float
     const float w3 = a3 + c.beta * (a3 - dp[2 * nt.NXP + j]);
     const float h3 = bh[2 * nt.NXP + j];
     const float u = ur[j] + Uq[j];
+    if (c.avg) {
+      double *ua = P.st.uavg + (size_t)v * nt.NUP + j;
+      *ua = (1.0 - c.theta) * *ua + c.theta * (double)u;
+    }
     const float lo = g * (nt.umin[j] - u), hi = g * (nt.umax[j] - u);
     const float wa = h3 + w3;
     const float d3 = wa > hi ? w3 - hi : (wa < lo ? w3 - lo : -h3);

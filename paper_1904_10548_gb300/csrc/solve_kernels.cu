@@ -47,6 +47,8 @@ __global__ void __launch_bounds__(512) k_solve(KParams<T> P) {
     c.beta_n = APG ? (T)P.st.beta[it + 1] : T(0);
     const bool check = APG && (((it + 1) % P.check_every) == 0 || it + 1 == P.iters);
     c.write_out = !APG || check;
+    c.avg = APG && P.st.uavg != nullptr;
+    c.theta = APG ? P.st.theta[it] : 0.0;
     c.rbits = 0ull;
     eval_step<T, APG ? kFwdApg : kFwdPlain, C>(P, c, nullptr, smc, smg, tc, tb, step, keep);
     if (block_err(bm, P.st.err)) {

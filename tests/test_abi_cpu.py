@@ -92,13 +92,20 @@ def test_validation_errors_before_cuda(lib):
     net.A = np.eye(net.nx) * 1.01
     assert _factor_status(net, pb.cost, pb.tree) == B.RN_ERR_UNSUPPORTED
     assert "A = I" in rn.rapidnet_last_error()
-    # a dense Wu is outside what the library handles; a non-positive diagonal is invalid
+    # a dense symmetric positive definite Wu passes validation (the next step
+    # needs a device: RN_ERR_CUDA without one); an indefinite or
+    # non-positive one is invalid
     pb2 = make_problem("tiny")
     pb2.cost.Wu = pb2.cost.Wu + 0.1
-    assert _factor_status(pb2.net, pb2.cost, pb2.tree) == B.RN_ERR_UNSUPPORTED
+    assert _factor_status(pb2.net, pb2.cost, pb2.tree) in (B.RN_OK, B.RN_ERR_CUDA)
     pb3 = make_problem("tiny")
     pb3.cost.Wu = -pb3.cost.Wu
     assert _factor_status(pb3.net, pb3.cost, pb3.tree) == B.RN_ERR_INVAL
+    pb3b = make_problem("tiny")
+    # positive diagonal (8) but indefinite: -12 I + 20 (all ones)
+    pb3b.cost.Wu = pb3b.cost.Wu + 20.0 - 25.0 * np.eye(pb3b.net.nu)
+    assert _factor_status(pb3b.net, pb3b.cost, pb3b.tree) == B.RN_ERR_INVAL
+    assert "positive definite" in rn.rapidnet_last_error()
     # box with xmin > xmax
     pb4 = make_problem("tiny")
     pb4.net.xmin = pb4.net.xmax + 1

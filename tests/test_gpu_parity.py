@@ -53,6 +53,18 @@ def problem(kind):
         net = make_network(6, 9, 5, 0, seed=8)
         tree = make_tree([3, 2, 1, 2, 1, 1, 1], seed=9)
         return Problem(net=net, cost=make_cost(net, seed=8), tree=tree, data=make_data(net, tree, 10))
+    if kind.startswith("dense_"):
+        # a dense symmetric positive definite W_u: the shared operator F is
+        # applied as a dense product (tensor cores in the FP32 steps)
+        base = kind[6:]
+        if base in ("tiny", "barcelona32"):
+            pb = make_problem(base)
+            pb.cost.Wu = make_cost(pb.net, seed=41, dense_wu=True).Wu
+            return pb
+        net = make_network(16, 29, 22, 4, seed=43)
+        tree = random_branching(12, seed=44, s_min=6, s_max=40, branch_stages=5)
+        return Problem(net=net, cost=make_cost(net, seed=43, dense_wu=True), tree=tree,
+                       data=make_data(net, tree, seed=45))
     if kind == "stage1_chains":
         # stage-1 nodes with one leaf next to stage-1 nodes that branch later
         net = make_network(10, 18, 12, 3, seed=11)
@@ -176,7 +188,7 @@ def test_simple_theta_rule_matches_oracle(kind, precision):
         assert rel_err(out[k], getattr(ref, k)) <= tol, k
     # the rule matters: the equality rule's iterate is elsewhere
     other = O.apg(P, F, S, iters, gamma)
-    assert rel_err(other.y, ref.y) > 100 * tol
+    assert rel_err(other.y, ref.y) > 100 * RTOL
 
 
 @pytest.mark.parametrize("kind,precision,rule", [("tiny", rn.RN_PREC_FP64, "equality"),
@@ -374,3 +386,74 @@ def test_full_size_properties_after_many_iterations():
     assert np.all(np.linalg.norm(y[1:, nx:2 * nx], axis=1) <= pb.cost.Ws * (1 + 1e-9))
     assert np.isfinite(out["gap"]) and np.isfinite(out["cost"])
     assert np.array_equal(u[0], d.q) and np.array_equal(x[0], d.x0)
+
+
+# ---------------------------------------------------------------------------
+# dense W_u: F as a dense product (FP64 FMAs; TF32 tensor cores with a
+# head/tail split in the FP32 steps of the mixed path)
+# ---------------------------------------------------------------------------
+DENSE = ["dense_tiny", "dense_uneven", "dense_barcelona32"]
+
+
+@pytest.mark.parametrize("kind", DENSE)
+def test_dense_wu_dual_gradient_matches_oracle(kind):
+    import torch
+    pb = problem(kind)
+    assert np.count_nonzero(pb.cost.Wu - np.diag(np.diag(pb.cost.Wu))) > 0
+    P, F, S = oracle_for(kind, pb)
+    rng = np.random.default_rng(2)
+    w = rng.standard_normal((P.n_nodes, P.ny)) * 3.0
+    w[0] = 0.0
+    u_o, x_o = O.dual_gradient(P, F, S, w)
+    fac = gpu_factor(pb, gamma=1.0)
+    assert 0.0 <= fac.info()["collapse_dev"] < 1e-12
+    dev = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    u = torch.empty((P.n_nodes, P.nu), dtype=torch.float64, device="cuda")
+    x = torch.empty((P.n_nodes, P.nx), dtype=torch.float64, device="cuda")
+    fac.dual_gradient_device(dev(w), u, x, dev(pb.data.x0), dev(pb.data.q), dev(pb.data.demand),
+                             dev(pb.data.alpha))
+    torch.cuda.synchronize()
+    fac.close()
+    assert rel_err(u.cpu().numpy(), u_o) <= 1e-9
+    assert rel_err(x.cpu().numpy(), x_o) <= 1e-9
+
+
+@pytest.mark.parametrize("kind,iters", [("dense_tiny", 400), ("dense_uneven", 300),
+                                        ("dense_barcelona32", 200)])
+def test_dense_wu_apg_matches_oracle(kind, iters):
+    pb = problem(kind)
+    P, F, S = oracle_for(kind, pb)
+    L_o = O.power_iteration(P, F, 100)
+    gamma = O.step_size(L_o)
+    ref = O.apg(P, F, S, iters, gamma)
+    cost = O.primal_cost(P, S, ref.u, ref.x)
+    fac = gpu_factor(pb, gamma=gamma)
+    out = fac.solve(pb.data.x0, pb.data.q, pb.data.demand, pb.data.alpha, max_iters=iters)
+    fac.close()
+    for k in "uxy":
+        assert rel_err(out[k], getattr(ref, k)) <= RTOL, k
+    assert abs(out["cost"] - cost) <= RTOL * abs(cost)
+    # step size by the library's own power iteration
+    auto = gpu_factor(pb, power_iters=100)
+    assert abs(auto.info()["L"] - L_o) <= 1e-9 * L_o
+    auto.close()
+
+
+@pytest.mark.parametrize("kind,iters", [("dense_tiny", 400), ("dense_uneven", 300),
+                                        ("dense_barcelona32", 200)])
+def test_dense_wu_mixed_matches_oracle(kind, iters):
+    """The FP32 steps apply F on the tensor cores (TF32 head/tail split):
+    the mixed-precision bar of 1e-3 against the FP64 oracle."""
+    pb = problem(kind)
+    P, F, S = oracle_for(kind, pb)
+    gamma = O.step_size(O.power_iteration(P, F, 100))
+    ref = O.apg(P, F, S, iters, gamma)
+    cost = O.primal_cost(P, S, ref.u, ref.x)
+    fac = gpu_factor(pb, gamma=gamma, precision=rn.RN_PREC_MIXED)
+    out = fac.solve(pb.data.x0, pb.data.q, pb.data.demand, pb.data.alpha, max_iters=iters)
+    fac.close()
+    msg = (f"{kind}: cost {abs(out['cost'] - cost) / abs(cost):.2e} u {rel_err(out['u'], ref.u):.2e}"
+           f" y {rel_err(out['y'], ref.y):.2e}")
+    assert abs(out["cost"] - cost) <= 1e-3 * abs(cost), msg
+    assert rel_err(out["u"], ref.u) <= 1e-3, msg
+    assert rel_err(out["y"], ref.y) <= 1e-3, msg
