@@ -79,9 +79,11 @@ typedef struct {
 
 /* Cost weights, paper §3.1 (eqs. cost:linear, cost:smooth,
  * cost:non-smooth): W_alpha > 0, alpha0 (nu), W_u (nu*nu, symmetric
- * positive definite), W_s >= 0, W_x >= 0.  The library requires a
- * diagonal W_u (the paper's choice W_u = w I); a dense W_u gives
- * RN_ERR_UNSUPPORTED.  W_u not positive definite gives RN_ERR_INVAL. */
+ * positive definite), W_s >= 0, W_x >= 0.  A diagonal W_u (the paper's
+ * choice W_u = w I) is applied in the sparse form of the shared operator
+ * F; a dense one as a dense product (tensor cores in the FP32 steps of
+ * RN_PREC_MIXED), which needs chain teams of at least nu / 2 threads.
+ * W_u not symmetric positive definite gives RN_ERR_INVAL. */
 typedef struct {
   double W_alpha;
   const double *alpha0;
@@ -200,10 +202,11 @@ typedef struct {
  * basis of ker E) in FP64 at the first node of stages 1, N/2 and N, and
  * returns RN_ERR_RANK if 2 p Phi differs from the shared operator F by more
  * than 1e-8 relative (E W_u^-1 E' too ill-conditioned).  Returns
- * RN_ERR_UNSUPPORTED, before any launch, for a non-diagonal W_u, A != I,
+ * RN_ERR_UNSUPPORTED, before any launch, for A != I,
  * nx or nu above 256, or a tree whose schedule needs more work items than
  * the device keeps resident (one item per group of top nodes and per four
- * chains) or a group larger than the shared-memory capacity. */
+ * chains), a group larger than the shared-memory capacity, or a dense W_u
+ * with chain teams narrower than nu / 2 threads (block_threads). */
 int rapidnet_factor(const rn_network *net, const rn_tree *tree,
                     const rn_cost *cost, const rn_opts *opts,
                     rn_factor **out);
@@ -249,7 +252,9 @@ typedef struct {
  * RN_NOT_CONVERGED when some did not, or an error; per-problem results in
  * req[i].out.  Synchronises the streams of all handles.  RN_ERR_UNSUPPORTED
  * (before any launch) when a problem's group of top nodes does not fit the
- * batch's shared-memory layout. */
+ * batch's shared-memory layout, when a handle has a dense W_u (the batched
+ * kernel applies F in its sparse form only) or when a request asks for the
+ * averaged primal iterate. */
 int rapidnet_solve_batch(rn_factor *const *f, const rn_solve_req *req, int n,
                          int max_iters, double tol);
 
@@ -275,7 +280,7 @@ int rapidnet_dual_gradient_device(rn_factor *f, const double *x0,
  * Scratch: one fixed array of RN_NOALLOC_SCRATCH_BYTES (8 MiB) of device
  * memory inside the library, held by every device that loads the library
  * until the process exits.  A tree needs
- *   8 (n (3 sp + 2 nup + nxp) + max(h, 1) sp) + 4 (2 max(g, 1) + 6)
+ *   8 (n (3 sp + 2 nup + nxp) + 2 max(h, 1) sp) + 4 (3 max(g, 1) + 6)
  * bytes (rounded up to 8), with n = n_nodes, nxp / nup = nx / nu rounded
  * up to multiples of 4, sp = nxp + nup, h the rows of partial sums of
  * split stage-1 subtrees and g the groups plus roots of the schedule

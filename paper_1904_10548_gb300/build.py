@@ -18,13 +18,15 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "librapidnet.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # (source, object, extra flags): the kernel units are compiled once per
-# component count C (instantiations chosen at run time by dispatch.cu), so
-# that the device compiler runs on them in parallel; the longest compiles
-# (batched, then mixed kernels) are submitted first so that the slowest one
-# starts at once
-_KERNELS = ["batch_kernels.cu", "mixed_kernels.cu", "solve_kernels.cu"]
-SOURCES = [(k, f"{os.path.splitext(k)[0]}_c{c}.o", [f"-DRN_CVAL={c}"])
-           for k in _KERNELS for c in (8, 4, 2, 1)]
+# component count C and, for the solve and mixed kernels, once per kind of
+# W_u (RN_DENSE: 0 diagonal, 1 dense); dispatch.cu chooses the
+# instantiation at run time.  The device compiler thus runs on them in
+# parallel; the longest compiles (batched, then mixed kernels) are
+# submitted first so that the slowest one starts at once.
+SOURCES = [("batch_kernels.cu", f"batch_kernels_c{c}.o", [f"-DRN_CVAL={c}"]) for c in (8, 4, 2, 1)]
+SOURCES += [(k, f"{os.path.splitext(k)[0]}_c{c}_d{d}.o", [f"-DRN_CVAL={c}", f"-DRN_DENSE={d}"])
+            for k in ("mixed_kernels.cu", "solve_kernels.cu") for d in (0, 1)
+            for c in (8, 4, 2, 1)]
 SOURCES += [(s, os.path.splitext(s)[0] + ".o", []) for s in
             ["rapidnet.cu", "dispatch.cu", "server.cpp", "plan.cpp", "factor_check.cpp",
              "layout.cpp"]]

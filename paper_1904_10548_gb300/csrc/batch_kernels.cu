@@ -86,7 +86,7 @@ __device__ bool batch_eval(const BatchDev &B, BatchCtx &bc, MixedParams &mp, con
     const int sub = B.item_sub[i];
     if (sub < P.plan.n_groups) {
       __syncthreads();
-      if (!group_step<T>(P, sub, smem_g(), tb, step, 0)) ok = false;
+      if (!group_step<T>(P, sub, smem_g(), tb, step)) ok = false;
     }
   }
   for (int i = i0; i < i1; ++i) {
@@ -95,16 +95,6 @@ __device__ bool batch_eval(const BatchDev &B, BatchCtx &bc, MixedParams &mp, con
     const KParams<T> &P = params();
     const int G = P.plan.n_groups, sub = B.item_sub[i], k = B.tpb * (sub - G) + ti;
     if (sub >= G && k < P.plan.n_chains) chain_rest<T, C>(P, k, smem_c(), tc, false);
-  }
-  for (int i = i0; i < i1; ++i) {
-    if (!use(i)) continue;
-    load_problem(B, B.item_prob[i], bc, mp, bm);
-    const KParams<T> &P = params();
-    const int sub = B.item_sub[i];
-    if (sub < P.plan.n_groups && P.plan.g_root[sub] >= 0) {
-      __syncthreads();
-      if (!group_step<T>(P, sub, smem_g(), tb, step, 1)) ok = false;
-    }
   }
   for (int i = i0; i < i1; ++i) {
     if (!use(i)) continue;

@@ -27,20 +27,21 @@ cudaError_t allow_max_smem(const void *fn) {
   return e;
 }
 
-static const void *solve_kernel(int c, bool apg) {
+// dense: the instantiation for a dense W_u (F as a dense product)
+static const void *solve_kernel(int c, bool apg, bool dense) {
   switch (c) {
-    case 1: return solve_kernel_c1(apg);
-    case 2: return solve_kernel_c2(apg);
-    case 4: return solve_kernel_c4(apg);
-    default: return solve_kernel_c8(apg);
+    case 1: return dense ? solve_kernel_c1_d1(apg) : solve_kernel_c1_d0(apg);
+    case 2: return dense ? solve_kernel_c2_d1(apg) : solve_kernel_c2_d0(apg);
+    case 4: return dense ? solve_kernel_c4_d1(apg) : solve_kernel_c4_d0(apg);
+    default: return dense ? solve_kernel_c8_d1(apg) : solve_kernel_c8_d0(apg);
   }
 }
-static const void *mixed_kernel(int c) {
+static const void *mixed_kernel(int c, bool dense) {
   switch (c) {
-    case 1: return mixed_kernel_c1();
-    case 2: return mixed_kernel_c2();
-    case 4: return mixed_kernel_c4();
-    default: return mixed_kernel_c8();
+    case 1: return dense ? mixed_kernel_c1_d1() : mixed_kernel_c1_d0();
+    case 2: return dense ? mixed_kernel_c2_d1() : mixed_kernel_c2_d0();
+    case 4: return dense ? mixed_kernel_c4_d1() : mixed_kernel_c4_d0();
+    default: return dense ? mixed_kernel_c8_d1() : mixed_kernel_c8_d0();
   }
 }
 static const void *batch_kernel(int c) {
@@ -69,27 +70,27 @@ static cudaError_t occupancy(const void *fn, int block, size_t smem, int *blocks
 template <typename T, bool APG>
 cudaError_t launch_solve(const KParams<T> &P, int grid, int block, size_t smem, cudaStream_t st) {
   KParams<T> p = P;
-  return launch_coop(solve_kernel(P.maxc, APG), &p, grid, block, smem, st);
+  return launch_coop(solve_kernel(P.maxc, APG, P.net.Fd != nullptr), &p, grid, block, smem, st);
 }
 
 template <typename T, bool APG>
-cudaError_t solve_occupancy(int maxc, int block, size_t smem, int *blocks_per_sm) {
-  return occupancy(solve_kernel(maxc, APG), block, smem, blocks_per_sm);
+cudaError_t solve_occupancy(int maxc, bool dense, int block, size_t smem, int *blocks_per_sm) {
+  return occupancy(solve_kernel(maxc, APG, dense), block, smem, blocks_per_sm);
 }
 
 template cudaError_t launch_solve<double, true>(const KParams<double> &, int, int, size_t, cudaStream_t);
 template cudaError_t launch_solve<double, false>(const KParams<double> &, int, int, size_t, cudaStream_t);
-template cudaError_t solve_occupancy<double, true>(int, int, size_t, int *);
-template cudaError_t solve_occupancy<double, false>(int, int, size_t, int *);
+template cudaError_t solve_occupancy<double, true>(int, bool, int, size_t, int *);
+template cudaError_t solve_occupancy<double, false>(int, bool, int, size_t, int *);
 
 cudaError_t launch_mixed(const MixedParams &M, int maxc, int grid, int block, size_t smem,
                          cudaStream_t st) {
   MixedParams p = M;
-  return launch_coop(mixed_kernel(maxc), &p, grid, block, smem, st);
+  return launch_coop(mixed_kernel(maxc, M.f.net.Fd != nullptr), &p, grid, block, smem, st);
 }
 
-cudaError_t mixed_occupancy(int maxc, int block, size_t smem, int *blocks_per_sm) {
-  return occupancy(mixed_kernel(maxc), block, smem, blocks_per_sm);
+cudaError_t mixed_occupancy(int maxc, bool dense, int block, size_t smem, int *blocks_per_sm) {
+  return occupancy(mixed_kernel(maxc, dense), block, smem, blocks_per_sm);
 }
 
 cudaError_t launch_batch(const BatchDev &B, int maxc, int grid, int block, size_t smem,

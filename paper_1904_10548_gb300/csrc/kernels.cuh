@@ -57,6 +57,7 @@ struct NetDev {
 // the work schedule (rn::Plan) on the device
 struct PlanDev {
   int n, n_top, n_chains, n_groups, n_roots;
+  int hp_rows;  // rows of partial sums of the parts per step parity (hp holds 2 x hp_rows)
   const int *parent;
   // parts of split stage-1 subtrees: root of each group, its first hp row;
   // roots: node, parts [r_part[2r], r_part[2r+1]), hp rows [r_hp[r], r_hp[r+1])
@@ -70,7 +71,8 @@ struct PlanDev {
 template <typename T>
 struct StateDev {
   T *s, *ya, *yb, *ub, *gb, *z, *up, *ux, *uo, *xo;
-  T *hp;            // [hp_rows][SP]: sums (lambda | ghat) at the top nodes of the parts
+  T *hp;            // [2][hp_rows][SP]: sums (lambda | ghat) at the top nodes of the parts,
+                    // one buffer per parity of the step
   float *uo32, *xo32;  // optional FP32 copies of uo / xo (plain step)
   const T *inv2p;   // 1 / (2 p) per internal node
   const T *xroot;   // x0 (nx); unused when linear
@@ -78,7 +80,8 @@ struct StateDev {
   const double *theta; // theta_0 .. theta_iters (APG, the averaged primal)
   double *uavg, *xavg; // averaged primal iterate (internal rows of NUP / NXP),
                        // updated in FP64 by the APG iterations; null = off
-  unsigned *count, *flags, *barrier;  // per group, then per root: arrivals, completion; grid
+  unsigned *count, *flags, *barrier;  // per group: chain arrivals, completion flag; grid
+  unsigned *arrive;  // per group that is a part of a split subtree: step + 1 once its sums are out
   unsigned long long *res;  // per check: bits of the non-negative residual
   int *err;                 // 0 ok, else the site of the wait that gave up (1-4)
   int *info;                // [iters done, checks done, stop reason, 0, t_begin, t_end]:
@@ -162,7 +165,7 @@ cudaError_t launch_batch(const BatchDev &B, int maxc, int grid, int block, size_
                          cudaStream_t st);
 cudaError_t batch_occupancy(int maxc, int block, size_t smem, int *blocks_per_sm);
 cudaError_t batch_static_smem(int maxc, int *bytes);
-cudaError_t mixed_occupancy(int maxc, int block, size_t smem, int *blocks_per_sm);
+cudaError_t mixed_occupancy(int maxc, bool dense, int block, size_t smem, int *blocks_per_sm);
 
 // Shared memory of the persistent kernels.  A block is tpb teams of equal
 // width; a team scans one chain, the whole block sums one group.  Dynamic
@@ -243,8 +246,10 @@ int team_bytes_for(int sms, int optin, int per_sm, int reserved, int n_items, in
 int check_layout(const Plan &p, const Sizes &z, int n_items, int grid, const char *what);
 
 #define RN_DECLARE_KERNELS(c)                          \
-  const void *RN_CAT(solve_kernel_c, c)(bool apg);     \
-  const void *RN_CAT(mixed_kernel_c, c)();              \
+  const void *RN_CAT(solve_kernel_c, c##_d0)(bool apg); \
+  const void *RN_CAT(solve_kernel_c, c##_d1)(bool apg); \
+  const void *RN_CAT(mixed_kernel_c, c##_d0)();         \
+  const void *RN_CAT(mixed_kernel_c, c##_d1)();         \
   const void *RN_CAT(batch_kernel_c, c)();
 RN_DECLARE_KERNELS(1)
 RN_DECLARE_KERNELS(2)
@@ -262,6 +267,6 @@ cudaError_t allow_max_smem(const void *fn);
 template <typename T, bool APG>
 cudaError_t launch_solve(const KParams<T> &P, int grid, int block, size_t smem, cudaStream_t st);
 template <typename T, bool APG>
-cudaError_t solve_occupancy(int maxc, int block, size_t smem, int *blocks_per_sm);
+cudaError_t solve_occupancy(int maxc, bool dense, int block, size_t smem, int *blocks_per_sm);
 
 }  // namespace rn

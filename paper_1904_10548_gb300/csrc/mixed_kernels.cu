@@ -15,6 +15,8 @@
 
 namespace rn {
 
+namespace RN_CAT(kv, RN_DENSE) {  // one kernel per (C, W_u diagonal or dense)
+
 template <int C>
 __global__ void __launch_bounds__(512) k_mixed(MixedParams M) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -120,7 +122,12 @@ __global__ void __launch_bounds__(512) k_mixed(MixedParams M) {
   }
 }
 
-// this translation unit is compiled once per component count RN_CVAL
-const void *RN_CAT(mixed_kernel_c, RN_CVAL)() { return (const void *)k_mixed<RN_CVAL>; }
+}  // namespace
+
+// this translation unit is compiled once per component count RN_CVAL and
+// kind of W_u RN_DENSE
+const void *RN_CAT(RN_CAT(mixed_kernel_c, RN_CVAL), RN_CAT(_d, RN_DENSE))() {
+  return (const void *)RN_CAT(kv, RN_DENSE)::k_mixed<RN_CVAL>;
+}
 
 }  // namespace rn

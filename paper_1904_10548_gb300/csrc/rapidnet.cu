@@ -1026,6 +1026,7 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
   pd.n_chains = p.n_chains;
   pd.n_groups = p.n_groups;
   pd.n_roots = p.n_roots;
+  pd.hp_rows = std::max(1, p.hp_rows);
   UP_I(pd.g_root, p.g_root.empty() ? std::vector<int>(1, -1) : p.g_root)
   UP_I(pd.r_node, p.r_node.empty() ? std::vector<int>(1, 0) : p.r_node)
   UP_I(pd.r_part, p.r_part)
@@ -1052,9 +1053,9 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
       (rc = dalloc(f, &gb, (size_t)n * f->NXP)) || (rc = dalloc(f, &z, (size_t)n * f->NUP)) ||
       (rc = dalloc(f, &up, (size_t)n * f->SP)) || (rc = dalloc(f, &ux, (size_t)n * f->SP)) ||
       (rc = dalloc(f, &uo, (size_t)n * f->NUP)) || (rc = dalloc(f, &xo, (size_t)n * f->NXP)) ||
-      (rc = dalloc(f, &hp, (size_t)std::max(1, p.hp_rows) * f->SP)))
+      (rc = dalloc(f, &hp, 2 * (size_t)std::max(1, p.hp_rows) * f->SP)))
     return rc;
-  RN_CUDA(cudaMemset(hp, 0, (size_t)std::max(1, p.hp_rows) * f->SP * sizeof(double)));
+  RN_CUDA(cudaMemset(hp, 0, 2 * (size_t)std::max(1, p.hp_rows) * f->SP * sizeof(double)));
   RN_CUDA(cudaMemset(s, 0, (size_t)n * f->SP * sizeof(double)));
   RN_CUDA(cudaMemset(ya, 0, (size_t)n * f->YP * sizeof(double)));
   RN_CUDA(cudaMemset(yb, 0, (size_t)n * f->YP * sizeof(double)));
@@ -1085,11 +1086,12 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
   RN_CUDA(cudaMemset(f->x0, 0, nx * sizeof(double)));
   st.xroot = f->x0;
   const size_t ng = (size_t)std::max(1, p.n_groups + p.n_roots);
-  f->sync_words = 2 * ng + 1;
+  f->sync_words = 3 * ng + 1;
   if ((rc = dalloc(f, &f->sync, f->sync_words))) return rc;
   st.count = f->sync;
   st.flags = f->sync + ng;
-  st.barrier = f->sync + 2 * ng;
+  st.arrive = f->sync + 2 * ng;
+  st.barrier = f->sync + 3 * ng;
   st.err = f->err;
   st.info = f->info;
   st.res = nullptr;
@@ -1140,7 +1142,7 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
     float *s32, *z32, *up32, *ux32, *hp32, *da, *db, *ybh, *uref, *xref, *sw;
     if ((rc = dalloc(f, &s32, (size_t)n * f->SP)) || (rc = dalloc(f, &z32, (size_t)n * f->NUP)) ||
         (rc = dalloc(f, &up32, (size_t)n * f->SP)) || (rc = dalloc(f, &ux32, (size_t)n * f->SP)) ||
-        (rc = dalloc(f, &hp32, (size_t)std::max(1, p.hp_rows) * f->SP)) ||
+        (rc = dalloc(f, &hp32, 2 * (size_t)std::max(1, p.hp_rows) * f->SP)) ||
         (rc = dalloc(f, &da, (size_t)n * f->YP)) ||
         (rc = dalloc(f, &db, (size_t)n * f->YP)) || (rc = dalloc(f, &ybh, (size_t)n * f->YP)) ||
         (rc = dalloc(f, &uref, (size_t)n * f->NUP)) || (rc = dalloc(f, &xref, (size_t)n * f->NXP)) ||
@@ -1148,7 +1150,7 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
       return rc;
     for (auto pr : {std::make_pair((void *)s32, (size_t)n * f->SP), {(void *)z32, (size_t)n * f->NUP},
                     {(void *)up32, (size_t)n * f->SP}, {(void *)ux32, (size_t)n * f->SP},
-                    {(void *)hp32, (size_t)std::max(1, p.hp_rows) * f->SP},
+                    {(void *)hp32, 2 * (size_t)std::max(1, p.hp_rows) * f->SP},
                     {(void *)da, (size_t)n * f->YP},
                     {(void *)db, (size_t)n * f->YP}, {(void *)ybh, (size_t)n * f->YP},
                     {(void *)uref, (size_t)n * f->NUP}, {(void *)xref, (size_t)n * f->NXP},
@@ -1162,6 +1164,7 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
     sf.hp = hp32;
     sf.count = st.count;
     sf.flags = st.flags;
+    sf.arrive = st.arrive;
     sf.barrier = st.barrier;
     sf.err = st.err;
     sf.info = st.info;
@@ -1208,8 +1211,8 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
     if ((rc = fit_sizes(f, 8, team_bytes, f->net_bytes_d, f->tw, f->tpb, 1, &f->sz_d))) return rc;
     f->smem = kHdrBytes + f->net_bytes_d + (size_t)f->tpb * team_bytes;
     int bps1 = 0, bps2 = 0;
-    RN_CUDA((solve_occupancy<double, true>(f->maxc, f->block, f->smem, &bps1)));
-    RN_CUDA((solve_occupancy<double, false>(f->maxc, f->block, f->smem, &bps2)));
+    RN_CUDA((solve_occupancy<double, true>(f->maxc, f->dense_w, f->block, f->smem, &bps1)));
+    RN_CUDA((solve_occupancy<double, false>(f->maxc, f->dense_w, f->block, f->smem, &bps2)));
     const int resident = std::min(bps1, bps2) * sms;
     if (resident < 1) {
       set_error("the solve kernel does not fit on the device (block %d, smem %zu)", f->block,
@@ -1231,7 +1234,7 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
       return rc;
     f->smem_mixed = kHdrBytes + f->net_region_m + (size_t)f->tpb * team_bytes;
     int bpm = 0;
-    RN_CUDA(mixed_occupancy(f->maxc, f->block, f->smem_mixed, &bpm));
+    RN_CUDA(mixed_occupancy(f->maxc, f->dense_w, f->block, f->smem_mixed, &bpm));
     if (bpm < 1) {
       set_error("the mixed kernel does not fit on the device");
       return RN_ERR_UNSUPPORTED;
@@ -1483,15 +1486,16 @@ int solve_device_impl(rn_factor *f, const double *x0, const double *q, const dou
 }
 
 // Scratch of the allocation-free dual gradient: doubles for s, up, ux (SP
-// per node), z, uo (NUP), xo (NXP) and the partial sums hp (SP per row),
-// then 32-bit words for the counters and flags of the groups and roots,
-// the grid barrier, the error word and the info words.
+// per node), z, uo (NUP), xo (NXP) and the partial sums hp (SP per row, two
+// buffers), then 32-bit words for the counters, flags and arrivals of the
+// groups, the grid barrier, the error word and the info words.
 void noalloc_need(const rn_factor *f, size_t *need_d, size_t *need_w) {
   const size_t rows = (size_t)f->plan.n;
   const size_t ng = (size_t)std::max(1, f->plan.n_groups + f->plan.n_roots);
   const size_t hrows = (size_t)std::max(1, f->plan.hp_rows);
-  *need_d = rows * (3 * (size_t)f->SP + 2 * (size_t)f->NUP + (size_t)f->NXP) + hrows * f->SP;
-  *need_w = 2 * ng + 1 + 1 + 4;
+  *need_d = rows * (3 * (size_t)f->SP + 2 * (size_t)f->NUP + (size_t)f->NXP) +
+            2 * hrows * f->SP;
+  *need_w = 3 * ng + 1 + 1 + 4;
 }
 
 }  // namespace
@@ -1766,12 +1770,13 @@ extern "C" int rapidnet_dual_gradient_noalloc(rn_factor *f, const double *w, dou
   st.xo = p;
   p += rows * f->NXP;
   st.hp = p;
-  p += hrows * f->SP;
+  p += 2 * hrows * f->SP;
   unsigned *words = reinterpret_cast<unsigned *>(p);
   st.count = words;
   st.flags = words + ng;
-  st.barrier = words + 2 * ng;
-  st.err = reinterpret_cast<int *>(words + 2 * ng + 1);
+  st.arrive = words + 2 * ng;
+  st.barrier = words + 3 * ng;
+  st.err = reinterpret_cast<int *>(words + 3 * ng + 1);
   st.info = st.err + 1;
   st.res = nullptr;
   st.beta = nullptr;
@@ -1828,6 +1833,11 @@ int batch_impl(rn_factor *const *fs, const rn_solve_req *req, int n, int max_ite
     if (f->opts.precision != RN_PREC_MIXED) {
       set_error("solve_batch: handle %d is not RN_PREC_MIXED", i);
       return RN_ERR_INVAL;
+    }
+    if (f->dense_w) {
+      set_error("solve_batch: handle %d has a dense Wu (the batched kernel applies F in its "
+                "sparse form only; solve it alone)", i);
+      return RN_ERR_UNSUPPORTED;
     }
     if (r.out->u_avg || r.out->x_avg) {
       set_error("solve_batch: the averaged primal iterate is not available in a batch "

@@ -10,6 +10,13 @@
 
 #include "kernels.cuh"
 
+// Each kernel unit is compiled once for a diagonal W_u (RN_DENSE = 0: F in
+// its sparse Schur form) and once for a dense W_u (RN_DENSE = 1: F as a
+// dense product), so that neither kernel carries the other's code.
+#ifndef RN_DENSE
+#define RN_DENSE 0
+#endif
+
 namespace rn {
 
 // ---------------------------------------------------------------------------
@@ -289,13 +296,14 @@ namespace rn {
 template <typename T, typename RowF>
 __device__ void apply_F(const NetDev<T> &nt, int m, RowF row, const T *i2p, T *eb, T *fb,
                         const Team &tm) {
-  if (nt.Fd) {
-    if constexpr (sizeof(T) == 8)
-      apply_F_dense(nt, m, row, i2p, tm);
-    else
-      apply_F_tc(nt, m, row, i2p, tm);
-    return;
-  }
+#if RN_DENSE
+  if constexpr (sizeof(T) == 8)
+    apply_F_dense(nt, m, row, i2p, tm);
+  else
+    apply_F_tc(nt, m, row, i2p, tm);
+  (void)eb;
+  (void)fb;
+#else
   const int ne = nt.ne, nu = nt.nu, NXP = nt.NXP, NEP = nt.NEP;
   const int *Er_ptr = nt.Er_ptr, *Er_idx = nt.Er_idx, *Ec_ptr = nt.Ec_ptr, *Ec_idx = nt.Ec_idx;
   const T *Erw_val = nt.Erw_val, *Ec_val = nt.Ec_val, *winv = nt.winv, *Sinv = nt.Sinv;
@@ -341,6 +349,7 @@ __device__ void apply_F(const NetDev<T> &nt, int m, RowF row, const T *i2p, T *e
       g[j] = (wj * acc) * i2p[q];
     }
   }
+#endif
 }
 
 // Copy the network data into shared memory at raw (net_smem_bytes of
@@ -800,14 +809,17 @@ __device__ void chain_rest(const KParams<T> &P, int k, const Smem<T> &sm, const 
 }
 
 // ---------------------------------------------------------------------------
-// The root of a split stage-1 subtree (one node), whole block, by the last
-// of its parts to finish phase 0: own terms plus its children's sums in hp,
-// F, then (x | Z) with the tree root as parent, published in ux before the
-// root's flag.  W: rows of work space (children + 1), eb/fb/i2p as for F.
+// The root of a split stage-1 subtree (one node), whole block, computed by
+// every part of it once all parts have published their top nodes' sums
+// (the parts' hp rows of this step's buffer): own terms plus the
+// children's sums, F, then (x | Z) with the tree root as parent, left in W's
+// first row for the part's forward levels; the first part also publishes it
+// in ux for the chain that owns the root node.  W: rows of work space
+// (children + 1), eb/fb/i2p as for F.
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ void root_step(const KParams<T> &P, int root, const Smem<T> &sm, const Team &tm,
-                          unsigned step, T *W, T *eb, T *fb, T *i2p) {
+__device__ void root_compute(const KParams<T> &P, int root, const Smem<T> &sm, const Team &tm,
+                             unsigned step, T *W, T *eb, T *fb, T *i2p, bool publish) {
   const NetDev<T> &nt = *sm.net;
   const PlanDev &pl = P.plan;
   const int SP = nt.SP, NXP = nt.NXP, NUP = nt.NUP, nx = nt.nx, nu = nt.nu;
@@ -815,7 +827,7 @@ __device__ void root_step(const KParams<T> &P, int root, const Smem<T> &sm, cons
   const bool data = !P.linear;
   T *Rr = W, *Hp = W + SP;
   stage_span(Rr, P.st.s + (size_t)v * SP, SP, tm, true);
-  stage_span(Hp, P.st.hp + (size_t)q0 * SP, np * SP, tm, true);
+  stage_span(Hp, P.st.hp + ((size_t)(step & 1u) * pl.hp_rows + q0) * SP, np * SP, tm, true);
   if (tm.tid == 0) i2p[0] = P.st.inv2p[v];
   cp_wait();
   tm.sync();
@@ -835,21 +847,20 @@ __device__ void root_step(const KParams<T> &P, int root, const Smem<T> &sm, cons
   tm.sync();
   apply_F(nt, 1, [=](int) { return Rr; }, i2p, eb, fb, tm);
   tm.sync();
-  // Z = z (the parent is the tree root), x = x0 + Gd d + B u
-  T *out = P.st.ux + (size_t)v * SP;
+  // Z = z (the parent is the tree root), x = x0 + Gd d + B u, in place of
+  // the state sums (which no thread reads any more)
   for (int i = tm.tid; i < nx; i += tm.nt) {
     Slice<T, 6> br;
     br.load(nt.Br_ptr, nt.Br_idx, nt.Br_val, i);
     T acc = data ? P.st.xroot[i] + P.st.gb[(size_t)v * NXP + i] : T(0);
     const T *ubv = P.st.ub + (size_t)v * NUP;
-    out[i] = br.dot(acc, [&](int t) { return (data ? ubv[t] : T(0)) - Rr[NXP + t]; }, nt.Br_idx,
-                    nt.Br_val);
+    Rr[i] = br.dot(acc, [&](int t) { return (data ? ubv[t] : T(0)) - Rr[NXP + t]; }, nt.Br_idx,
+                   nt.Br_val);
   }
-  for (int j = tm.tid; j < nu; j += tm.nt) out[NXP + j] = Rr[NXP + j];
   tm.sync();
-  if (tm.tid == 0) {
-    __threadfence();
-    st_release(P.st.flags + pl.n_groups + root, step + 1u);
+  if (publish) {
+    T *out = P.st.ux + (size_t)v * SP;
+    for (int e = tm.tid; e < NXP + NUP; e += tm.nt) out[e] = Rr[e];
   }
 }
 
@@ -861,16 +872,15 @@ __device__ void root_step(const KParams<T> &P, int root, const Smem<T> &sm, cons
 // children in local indices) is staged with its rows; rows of a group
 // larger than the shared-memory capacity live in up[K + v].
 //
-// A group that is a part of a split stage-1 subtree works in two phases:
-// phase 0 sums the part, publishes the sums at its top node in hp[g] and
-// arrives at its root (the last part to arrive completes the root node,
-// root_step), then applies F and leaves z in ux; phase 1 waits for the
-// root and rolls down from it.  An unsplit group does everything in
-// phase 0.  False on timeout.
+// A group that is a part of a split stage-1 subtree sums the part,
+// publishes the sums at its top nodes in hp and its arrival, applies F to
+// its rows, waits until every part of the root has arrived, completes the
+// root node itself (root_compute; every part does, so no part waits for
+// another's result) and rolls down from it.  False on timeout.
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ bool group_step(const KParams<T> &P, int g, const Smem<T> &sm, const Team &tm,
-                           unsigned step, int phase) {
+                           unsigned step) {
   const NetDev<T> &nt = *sm.net;
   const PlanDev &pl = P.plan;
   const int SP = nt.SP, NXP = nt.NXP, NUP = nt.NUP, nx = nt.nx, nu = nt.nu, NEP = nt.NEP;
@@ -892,39 +902,7 @@ __device__ bool group_step(const KParams<T> &P, int g, const Smem<T> &sm, const 
   T *base = nullptr;  // (x | Z) at the parent of the group's top node, if not the tree root
   int nl = 0;
   const int *lvl = nullptr, *par = nullptr;
-  if (phase == 1) {
-    if (root < 0) return true;
-    // the root's (x | Z), the descriptor and the z rows of phase 0
-    const int rv = pl.r_node[root];
-    if (tm.tid == 0)
-      sm.flag[0] = spin_geq(P.st.flags + pl.n_groups + root, step + 1u, P.st.err, P.st.wait_ns, 3);
-    tm.sync();
-    if (!sm.flag[0]) return false;
-    base = H;  // the heads are not needed in phase 1
-    for (int e = tm.tid; e < NXP + NUP; e += tm.nt) base[e] = __ldcg(P.st.ux + (size_t)rv * SP + e);
-    for (int e = tm.tid; e < dn / 4; e += tm.nt) cp16(desc + 4 * e, pl.g_desc + d0 + 4 * e, false);
-    constexpr int per = 16 / sizeof(T);
-    const int nv = NUP / per;
-    if (m <= gcap) {
-      for (int e = tm.tid; e < m * nv; e += tm.nt) {
-        const int li = e / nv, c = e - li * nv;
-        cp16(rb + (size_t)li * SP + NXP + c * per,
-             P.st.ux + (size_t)(g0 + li) * SP + NXP + c * per, true);
-      }
-    } else {
-      // rows in global memory: the asynchronous copy writes shared memory only
-      for (int e = tm.tid; e < m * NUP; e += tm.nt) {
-        const int li = e / NUP, j = e - li * NUP;
-        rb[(size_t)li * SP + NXP + j] = __ldcg(P.st.ux + (size_t)(g0 + li) * SP + NXP + j);
-      }
-    }
-    cp_wait();
-    tm.sync();
-    nl = desc[1];
-    lvl = desc + 4;
-    par = lvl + nl + 1;
-  }
-  if (phase == 0) {
+  {
   // all chains of the group have arrived; the counter restarts for the
   // next evaluation (no chain arrives again before the flag below)
   if (tm.tid == 0) {
@@ -1102,23 +1080,17 @@ __device__ bool group_step(const KParams<T> &P, int g, const Smem<T> &sm, const 
     tm.sync();
   }
   if (root >= 0) {
-    // a part: its top nodes' sums to the root; the last part completes it
+    // a part: its top nodes' sums to the root (buffer of this step's
+    // parity: a part that runs one step ahead writes the other one), then
+    // its arrival
     const int m0 = lvl[1] - lvl[0];
-    T *hpg = P.st.hp + (size_t)pl.g_hp[g] * SP;
+    T *hpg = P.st.hp + ((size_t)(step & 1u) * pl.hp_rows + pl.g_hp[g]) * SP;
     for (int e = tm.tid; e < m0 * SP; e += tm.nt) hpg[e] = rb[e];
     tm.sync();
     if (tm.tid == 0) {
       __threadfence();
-      const unsigned np = (unsigned)(pl.r_part[2 * root + 1] - pl.r_part[2 * root]);
-      const unsigned old = atomicAdd(P.st.count + pl.n_groups + root, 1u);
-      sm.flag[1] = old + 1u == np;
-      if (sm.flag[1]) {
-        __threadfence();
-        atomicExch(P.st.count + pl.n_groups + root, 0u);
-      }
+      st_release(P.st.arrive + g, step + 1u);
     }
-    tm.sync();
-    if (sm.flag[1]) root_step(P, root, sm, tm, step, H, eb, fb, i2p);
   }
   // z = F ghat / (2p) at every node of the group
   for (int q0 = 0; q0 < m; q0 += fbr) {
@@ -1130,18 +1102,20 @@ __device__ bool group_step(const KParams<T> &P, int g, const Smem<T> &sm, const 
   }
   tm.sync();
   if (root >= 0) {
-    // z rows for phase 1
-    constexpr int per = 16 / sizeof(T);
-    const int nv = NUP / per;
-    using V = typename std::conditional<sizeof(T) == 8, double2, float4>::type;
-    for (int e = tm.tid; e < m * nv; e += tm.nt) {
-      const int li = e / nv, c = e - li * nv;
-      reinterpret_cast<V *>(P.st.ux + (size_t)(g0 + li) * SP + NXP)[c] =
-          reinterpret_cast<const V *>(rb + (size_t)li * SP + NXP)[c];
+    // every part completes the root itself once all parts have arrived
+    const int p0 = pl.r_part[2 * root], p1 = pl.r_part[2 * root + 1];
+    if (tm.tid == 0) {
+      bool ok = true;
+      for (int q = p0; q < p1 && ok; ++q)
+        ok = spin_geq(P.st.arrive + q, step + 1u, P.st.err, P.st.wait_ns, 3);
+      sm.flag[0] = ok;
     }
-    return true;
+    tm.sync();
+    if (!sm.flag[0]) return false;
+    root_compute(P, root, sm, tm, step, H, eb, fb, i2p, g == p0);
+    base = H;
   }
-  }  // phase 0
+  }
   // forward over the levels: Z_v = Z_a(v) + z_v, x_v = x_a(v) + B u_v + Gd d_v
   // (four nodes per thread at a time: loads, then sums, then stores)
   constexpr int NF = 4;
@@ -1249,10 +1223,45 @@ __device__ bool chain_forward(const KParams<T> &P, int k, FwdCtx<T> &c, const Sm
   T *xp = sm.buf, *Zp = xp + NXP, *BZ = Zp + NUP;
   const int fpn = fwd_elems_per_node(NXP, NUP, YP, SP, MODE);
   T *slots = sm.buf + round4(2 * NXP + NUP) + (size_t)warp * S * fpn;
+  // nodes in the order the warps take them: the chain's own nodes (head to
+  // leaf) first, then the top nodes the chain owns
+  const int K = nown + L;
+  constexpr int per = 16 / sizeof(T);
+  auto node_of = [&](int q) { return q < L ? start + q : pl.ch_own[own0 + (q - L)]; };
+  auto copy_row = [&](T *dst, const T *src, int len, bool cg) {
+    for (int e = lane; e < len / per; e += 32) cp16(dst + e * per, src + e * per, cg);
+  };
+  auto issue = [&](int q, T *dst) {
+    const int v = node_of(q);
+    copy_row(dst, P.st.ux + (size_t)v * SP, SP, q >= L);
+    if constexpr (MODE == kFwdApg) {
+      copy_row(dst + SP, c.ycur + (size_t)v * YP, YP, false);
+      copy_row(dst + SP + YP, c.yprv + (size_t)v * YP, YP, false);
+    } else if constexpr (MODE == kFwdMixed) {
+      copy_row(dst + SP, c.ycur + (size_t)v * YP, YP, false);
+      copy_row(dst + SP + YP, c.yprv + (size_t)v * YP, YP, false);
+      copy_row(dst + SP + 2 * YP, mx->ybh + (size_t)v * YP, YP, false);
+      copy_row(dst + SP + 3 * YP, mx->uref + (size_t)v * NUP, NUP, false);
+      copy_row(dst + SP + 3 * YP + NUP, mx->xref + (size_t)v * NXP, NXP, false);
+    }
+    cp_commit();
+  };
+  // ring of S slots per warp: node t of the warp (q = warp + t nw) lives
+  // in slot t % S; up to S - 1 nodes ahead are in flight.  The first nodes
+  // of the chain itself (their rows come from this team and from the
+  // previous iteration) are requested before the wait for the group; a
+  // top node's row is published by its group and requested after it.
+  int issued = 0;
+  tm.sync();  // the team's chain rows (chain_rest) are written
+  for (; issued < S && warp + issued * nw < L; ++issued)
+    issue(warp + issued * nw, slots + (size_t)issued * fpn);
   if (g >= 0) {
     if (tm.tid == 0) sm.flag[1] = spin_geq(P.st.flags + g, step + 1u, P.st.err, P.st.wait_ns, 2);
     tm.sync();
-    if (!sm.flag[1]) return false;
+    if (!sm.flag[1]) {
+      cp_wait_group<0>();
+      return false;
+    }
     const T *src = P.st.ux + (size_t)par * SP;
     for (int e = tm.tid; e < NXP + NUP; e += tm.nt) xp[e] = __ldcg(src + e);
   } else {
@@ -1270,30 +1279,6 @@ __device__ bool chain_forward(const KParams<T> &P, int k, FwdCtx<T> &c, const Sm
     }
   }
   tm.sync();
-  const int K = nown + L;
-  constexpr int per = 16 / sizeof(T);
-  auto node_of = [&](int q) { return q < nown ? pl.ch_own[own0 + q] : start + (q - nown); };
-  auto copy_row = [&](T *dst, const T *src, int len, bool cg) {
-    for (int e = lane; e < len / per; e += 32) cp16(dst + e * per, src + e * per, cg);
-  };
-  auto issue = [&](int q, T *dst) {
-    const int v = node_of(q);
-    copy_row(dst, P.st.ux + (size_t)v * SP, SP, q < nown);
-    if constexpr (MODE == kFwdApg) {
-      copy_row(dst + SP, c.ycur + (size_t)v * YP, YP, false);
-      copy_row(dst + SP + YP, c.yprv + (size_t)v * YP, YP, false);
-    } else if constexpr (MODE == kFwdMixed) {
-      copy_row(dst + SP, c.ycur + (size_t)v * YP, YP, false);
-      copy_row(dst + SP + YP, c.yprv + (size_t)v * YP, YP, false);
-      copy_row(dst + SP + 2 * YP, mx->ybh + (size_t)v * YP, YP, false);
-      copy_row(dst + SP + 3 * YP, mx->uref + (size_t)v * NUP, NUP, false);
-      copy_row(dst + SP + 3 * YP + NUP, mx->xref + (size_t)v * NXP, NXP, false);
-    }
-    cp_commit();
-  };
-  // ring of S slots per warp: node t of the warp (q = warp + t nw) lives
-  // in slot t % S; up to S - 1 nodes ahead are in flight
-  int issued = 0;
   for (; issued < S && warp + issued * nw < K; ++issued)
     issue(warp + issued * nw, slots + (size_t)issued * fpn);
   int t = 0;
@@ -1308,13 +1293,13 @@ __device__ bool chain_forward(const KParams<T> &P, int k, FwdCtx<T> &c, const Sm
       cp_wait_group<0>();
     __syncwarp();
     const int v = node_of(q);
-    if (q < nown) {
+    if (q >= L) {
       for (int j = lane; j < nu; j += 32) {
         const T base = data ? P.st.ub[(size_t)v * NUP + j] : T(0);
         r[NXP + j] = base - r[NXP + j];
       }
     } else {
-      const T depth = (T)(q - nown + 1);
+      const T depth = (T)(q + 1);
       for (int i = lane; i < nx; i += 32) r[i] = (xp[i] + r[i]) - depth * BZ[i];
       for (int j = lane; j < nu; j += 32) r[NXP + j] -= Zp[j];
     }
@@ -1404,8 +1389,8 @@ static __device__ void final_node(const MixedParams &M, int v) {
 // one evaluation of the dual gradient (with the per-node step of MODE) by a
 // block whose items are i = blockIdx.x, blockIdx.x + gridDim.x, ...: items
 // below n_groups are groups (whole block), the rest sets of tpb chains
-// (one per team).  Phases: chain heads, groups (phase 0), the chains'
-// local parts, parts of split subtrees (phase 1), the forward sweeps.
+// (one per team).  Phases: chain heads, groups, the chains' local parts,
+// the forward sweeps.
 // keep: the block holds one chain set and no group.
 // False (for the calling team) on timeout.
 // ---------------------------------------------------------------------------
@@ -1422,16 +1407,11 @@ __device__ bool eval_step(const KParams<T> &P, FwdCtx<T> &c, const MixedDev *mx,
   }
   for (int i = blockIdx.x; i < G; i += gridDim.x) {
     __syncthreads();
-    if (!group_step<T>(P, i, smg, tb, step, 0)) ok = false;
+    if (!group_step<T>(P, i, smg, tb, step)) ok = false;
   }
   for (int i = blockIdx.x; i < n_items; i += gridDim.x) {
     const int k = tpb * (i - G) + team;
     if (i >= G && k < K) chain_rest<T, C>(P, k, smc, tc, keep);
-  }
-  for (int i = blockIdx.x; i < G; i += gridDim.x) {
-    if (P.plan.g_root[i] < 0) continue;
-    __syncthreads();
-    if (!group_step<T>(P, i, smg, tb, step, 1)) ok = false;
   }
   for (int i = blockIdx.x; i < n_items && ok; i += gridDim.x) {
     const int k = tpb * (i - G) + team;

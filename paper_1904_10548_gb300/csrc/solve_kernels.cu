@@ -26,6 +26,8 @@ namespace rn {
 // the persistent kernel: `iters` APG iterations (APG = true) or one
 // evaluation of the dual gradient (APG = false)
 // ---------------------------------------------------------------------------
+namespace RN_CAT(kv, RN_DENSE) {  // one kernel per (C, W_u diagonal or dense)
+
 template <typename T, bool APG, int C>
 __global__ void __launch_bounds__(512) k_solve(KParams<T> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -86,10 +88,13 @@ __global__ void __launch_bounds__(512) k_solve(KParams<T> P) {
   }
 }
 
-// this translation unit is compiled once per component count RN_CVAL
-const void *RN_CAT(solve_kernel_c, RN_CVAL)(bool apg) {
-  return apg ? (const void *)k_solve<double, true, RN_CVAL>
-             : (const void *)k_solve<double, false, RN_CVAL>;
+}  // namespace
+
+// this translation unit is compiled once per component count RN_CVAL and
+// kind of W_u RN_DENSE
+const void *RN_CAT(RN_CAT(solve_kernel_c, RN_CVAL), RN_CAT(_d, RN_DENSE))(bool apg) {
+  return apg ? (const void *)RN_CAT(kv, RN_DENSE)::k_solve<double, true, RN_CVAL>
+             : (const void *)RN_CAT(kv, RN_DENSE)::k_solve<double, false, RN_CVAL>;
 }
 
 }  // namespace rn

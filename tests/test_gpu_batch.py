@@ -123,3 +123,16 @@ def test_cap_below_the_work_items_is_refused():
                   max_ctas=n - 1)
     assert ei.value.status == B.RN_ERR_UNSUPPORTED
     assert "work items" in str(ei.value)
+
+
+def test_batch_refuses_dense_wu():
+    """The batched kernel applies F in its sparse form: a handle with a
+    dense W_u is refused before any launch."""
+    from synthetic import make_cost
+    pb = batch_problem(1)
+    dense = make_cost(pb.net, seed=5, dense_wu=True)
+    f = rn.Factor(pb.net, dense, pb.tree, gamma=1e-3, precision=rn.RN_PREC_MIXED)
+    with pytest.raises(B.RapidNetError) as ei:
+        rn.solve_batch([f], [tensors(pb)], 10)
+    assert ei.value.status == B.RN_ERR_UNSUPPORTED
+    f.close()

@@ -71,25 +71,40 @@ def test_mixed_tolerance_stop():
     assert abs(out["iters"] - ref.iters) <= 50, (out["iters"], ref.iters)
 
 
+def spread(a, b):
+    return dict(cost=abs(a["cost"] - b["cost"]) / abs(b["cost"]), u=rel_err(a["u"], b["u"]),
+                y=rel_err(a["y"], b["y"]))
+
+
 @pytest.mark.slow
-def test_mixed_full_size_against_fp64_gpu():
-    """512-scenario tree, bench configuration: after 500 iterations the
-    mixed path's cost is within 1e-3 of the FP64 path's, and its returned
-    primal satisfies the dynamics and couplings.  The two iterate sequences
-    drift apart gradually as the accelerated method amplifies FP32 rounding
-    far from convergence (cost gap measured 1.5e-6, 1.7e-5, 7e-4, 1.05e-3
-    after 200, 500, 1000, 2000 iterations at residual ~1e2), so the
-    comparison is made where a defect would still stand out."""
+@pytest.mark.parametrize("iters", [500, 2000])
+def test_mixed_full_size_against_fp64_gpu(iters):
+    """512-scenario tree, bench configuration, against the FP64 path at the
+    same iteration count.  Far from convergence the accelerated iteration
+    carries any perturbation forward and amplifies it (an FP64 run whose step
+    size differs by one FP32 ulp drifts from the unperturbed one by a growing
+    amount), so the bar is the larger of 1e-3 and twenty times that FP64
+    spread, for the cost, u and y.  The returned primal satisfies the
+    dynamics and couplings, and the mixed path's residual and input-box
+    violation (the primal infeasibility of the reading of the paper's
+    tolerance) are within 10 % of the FP64 path's."""
     pb = problem("barcelona512")
+    d = pb.data
     f64 = rn.Factor(pb.net, pb.cost, pb.tree)
     gamma = f64.info()["gamma"]
-    a = f64.solve(pb.data.x0, pb.data.q, pb.data.demand, pb.data.alpha, max_iters=500)
+    a = f64.solve(d.x0, d.q, d.demand, d.alpha, max_iters=iters)
     f64.close()
+    f64b = rn.Factor(pb.net, pb.cost, pb.tree, gamma=gamma * (1.0 + 2.0 ** -23))
+    e = f64b.solve(d.x0, d.q, d.demand, d.alpha, max_iters=iters)
+    f64b.close()
     mx = rn.Factor(pb.net, pb.cost, pb.tree, gamma=gamma, precision=rn.RN_PREC_MIXED)
-    b = mx.solve(pb.data.x0, pb.data.q, pb.data.demand, pb.data.alpha, max_iters=500)
+    b = mx.solve(d.x0, d.q, d.demand, d.alpha, max_iters=iters)
     mx.close()
-    msg = (f"cost {a['cost']:.6e} vs {b['cost']:.6e}; u {rel_err(b['u'], a['u']):.2e} "
-           f"y {rel_err(b['y'], a['y']):.2e} res {a['primal_res']:.3e} vs {b['primal_res']:.3e}")
-    assert abs(a["cost"] - b["cost"]) <= 1e-3 * abs(a["cost"]), msg
+    env, got = spread(e, a), spread(b, a)
+    msg = f"mixed vs FP64 {got}; FP64 one-ulp spread {env}; res {a['primal_res']:.4g} vs {b['primal_res']:.4g}"
+    for k in ("cost", "u", "y"):
+        assert got[k] <= max(1e-3, 20.0 * env[k]), msg
     scale = max(np.abs(b["x"]).max(), np.abs(b["u"]).max())
     assert infeasibility(pb, b["u"], b["x"]) <= 1e-9 * scale, msg
+    assert abs(b["primal_res"] - a["primal_res"]) <= 0.1 * a["primal_res"], msg
+    assert abs(b["ubox_viol"] - a["ubox_viol"]) <= 0.1 * max(a["ubox_viol"], 1e-6), msg
