@@ -1,10 +1,12 @@
 """Batched mode (one persistent launch over many problems) against solo
 solves and against the FP64 oracle.
 
-Each problem of a batch must give the same result as its solo
-mixed-precision solve (same kernels, same arithmetic order per problem:
-the batch shares only the launch, barriers and the stop decision
-schedule) and meet the mixed-precision bar against the FP64 oracle.
+Each problem of a batch must give the result of its solo mixed-precision
+solve (the same device functions; the batch shares only the launch,
+barriers and the stop decision schedule) and meet the mixed-precision bar
+against the FP64 oracle.  The solo kernel forms a chain's head sums while
+it writes them (the batched one in a separate pass), so the FP32 sums differ
+in order: the two agree to SAME relative, not bit for bit.
 Problems have different networks (nx 6, 16, 63) and uneven trees.
 """
 import numpy as np
@@ -18,6 +20,8 @@ from synthetic.configs import Problem
 from tests.test_gpu_parity import rel_err
 
 pytestmark = pytest.mark.gpu
+
+SAME = 1e-4  # batch against solo: FP32 summation order of the head sums only
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -73,8 +77,8 @@ def test_batch_equals_solo_and_oracle(capped):
         assert o["status"] == B.RN_OK and o["iters"] == iters
         solo = f.solve(pb.data.x0, pb.data.q, pb.data.demand, pb.data.alpha, max_iters=iters)
         for k in ("u", "x", "y"):
-            assert np.array_equal(o[k].cpu().numpy(), solo[k]), (i, k)
-        assert o["cost"] == solo["cost"]
+            assert rel_err(o[k].cpu().numpy(), solo[k]) <= SAME, (i, k, rel_err(o[k].cpu().numpy(), solo[k]))
+        assert abs(o["cost"] - solo["cost"]) <= SAME * abs(solo["cost"])
         P = O.OracleProblem.from_parts(pb.net, pb.cost, pb.tree)
         F = O.factor(P)
         S = O.solve_consts(P, F, pb.data.x0, pb.data.q, pb.data.demand, pb.data.alpha)
@@ -96,7 +100,7 @@ def test_batch_per_problem_stopping():
         solo = f.solve(pb.data.x0, pb.data.q, pb.data.demand, pb.data.alpha, max_iters=3000,
                        tol=tol)
         assert o["iters"] == solo["iters"]
-        assert np.array_equal(o["y"].cpu().numpy(), solo["y"])
+        assert rel_err(o["y"].cpu().numpy(), solo["y"]) <= SAME
         if o["iters"] < 3000:
             assert o["primal_res"] <= tol
     for f in facs:
