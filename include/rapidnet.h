@@ -129,6 +129,14 @@ typedef struct {
                           RN_THETA_SIMPLE theta_nu = 2 / (nu + 2); both from
                           theta_0 = theta_{-1} = 1 and beta_nu = theta_nu
                           (1 / theta_{nu-1} - 1) */
+  int batch_tune;      /* rapidnet_solve_batch, read from the batch's first
+                          handle: 0 (default) times the candidate launch
+                          layouts (team width, teams per block) on a short
+                          run of the first batch of a set of handles, keeps
+                          the fastest for later batches of that set, and
+                          replays the batch as a captured CUDA graph; 1 the
+                          rule-based layout, as a graph; 2 the rule-based
+                          layout launched directly (no graph) */
 } rn_opts;
 
 enum { RN_THETA_EQUALITY = 0, RN_THETA_SIMPLE = 1 };
@@ -254,7 +262,13 @@ typedef struct {
  * (before any launch) when a problem's group of top nodes does not fit the
  * batch's shared-memory layout, when a handle has a dense W_u (the batched
  * kernel applies F in its sparse form only) or when a request asks for the
- * averaged primal iterate. */
+ * averaged primal iterate.  A call runs every problem's preparation, the
+ * batched kernel and the outputs on the stream of f[0] (the other handles'
+ * streams are synchronised first), with one read-back of all problems'
+ * scalars; the library keeps the last batch's work space and CUDA graph per
+ * device and replays the graph when the next call has the same handles,
+ * requests, max_iters and tol.  out->apg_ms is the batched kernel's time;
+ * t_begin_ns and t_end_ns are 0. */
 int rapidnet_solve_batch(rn_factor *const *f, const rn_solve_req *req, int n,
                          int max_iters, double tol);
 

@@ -60,7 +60,7 @@ class rn_opts(ctypes.Structure):
     _fields_ = [("device", c_int), ("stream", c_void_p), ("precision", c_int),
                 ("gamma", c_double), ("power_iters", c_int), ("check_every", c_int),
                 ("refresh_every", c_int), ("max_ctas", c_int), ("block_threads", c_int),
-                ("wait_us", c_int), ("theta_rule", c_int)]
+                ("wait_us", c_int), ("theta_rule", c_int), ("batch_tune", c_int)]
 
 
 class rn_result(ctypes.Structure):
@@ -331,14 +331,15 @@ class Factor:
     def __init__(self, net, cost, tree, precision: int = RN_PREC_FP64, gamma: float = 0.0,
                  device: int = 0, stream=None, power_iters: int = 0, check_every: int = 0,
                  refresh_every: int = 0, max_ctas: int = 0, block_threads: int = 0,
-                 wait_us: int = 0, theta_rule: int = 0):
+                 wait_us: int = 0, theta_rule: int = 0, batch_tune: int = 0):
         self._marshal(net, cost, tree, precision, gamma, device, stream, power_iters,
-                      check_every, refresh_every, max_ctas, block_threads, wait_us, theta_rule)
+                      check_every, refresh_every, max_ctas, block_threads, wait_us, theta_rule,
+                      batch_tune)
         self.h = rapidnet_factor(self.net_c, self.tree_c, self.cost_c, self.opts_c)
 
     def _marshal(self, net, cost, tree, precision, gamma, device, stream, power_iters=0,
                  check_every=0, refresh_every=0, max_ctas=0, block_threads=0, wait_us=0,
-                 theta_rule=0):
+                 theta_rule=0, batch_tune=0):
         nx, nu, nd, ne = net.nx, net.nu, net.nd, net.ne
         self._keep = [
             _f64(net.A, (nx, nx)), _f64(net.B, (nx, nu)), _f64(net.Gd, (nx, nd)),
@@ -357,7 +358,8 @@ class Factor:
                               float(cost.Wx))
         st = None if stream is None else c_void_p(getattr(stream, "cuda_stream", stream))
         self.opts_c = rn_opts(device, st, precision, gamma, power_iters, check_every,
-                              refresh_every, max_ctas, block_threads, wait_us, theta_rule)
+                              refresh_every, max_ctas, block_threads, wait_us, theta_rule,
+                              batch_tune)
         self.nx, self.nu, self.nd, self.ne = nx, nu, nd, ne
         self.n_nodes = int(tree.stage_ptr[-1])
         self.ny = 2 * nx + nu

@@ -154,7 +154,6 @@ __global__ void __launch_bounds__(512) k_batch(BatchDev B) {
         cf.beta = (float)mp.f.st.beta[it];
         cf.beta_n = (float)mp.f.st.beta[it + 1];
         cf.write_out = check;
-        cf.fuse = false;
         cf.avg = false;
         cf.theta = 0.0;
         cf.rbits = rb_local[sl];

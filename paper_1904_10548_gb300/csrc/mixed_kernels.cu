@@ -54,7 +54,6 @@ __global__ void __launch_bounds__(512) k_mixed(MixedParams M) {
   eval_step<double, kFwdPlain, C>(M.d, c64, nullptr, sdc, sdg, tc, tb, step++, keep);
   bool ok = !block_err(bm, P.st.err);
   if (!ok) reason = 3;
-  bool heads_ready = false;  // the previous iteration formed this one's chain-head sums
   for (; it < P.iters && ok; ++it) {
     FwdCtx<float> c;
     float *dcur = (it & 1) ? M.mx.db : M.mx.da;
@@ -68,12 +67,7 @@ __global__ void __launch_bounds__(512) k_mixed(MixedParams M) {
     c.avg = P.st.uavg != nullptr;
     c.theta = P.st.theta[it];
     c.rbits = 0ull;
-    // the forward sweep forms the next iteration's chain-head sums unless a
-    // check (which may stop the launch) or a refresh comes next
-    const bool refresh_next = (it + 1) % M.mx.refresh_every == 0 && it + 1 < P.iters;
-    c.fuse = !check && !refresh_next && it + 1 < P.iters;
-    eval_step<float, kFwdMixed, C>(P, c, &M.mx, sfc, sfg, tc, tb, step++, keep, heads_ready);
-    heads_ready = c.fuse;
+    eval_step<float, kFwdMixed, C>(P, c, &M.mx, sfc, sfg, tc, tb, step++, keep);
     if (block_err(bm, P.st.err)) {
       ok = false;
       reason = 3;

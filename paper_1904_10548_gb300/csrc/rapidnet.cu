@@ -9,9 +9,12 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <vector>
@@ -443,12 +446,33 @@ __global__ void k_gather_mixed_y(NetDev<double> nt, const int *perm, int n, cons
   }
 }
 
+// the same for a batched solve: the last iteration's parity from the
+// problem's info on the device (iterations in info[0])
+__global__ void k_gather_mixed_y_batch(NetDev<double> nt, const int *perm, int n, const double *yb,
+                                       const float *da, const float *db, const int *info,
+                                       double *y) {
+  const float *d = ((info[0] - 1) & 1) ? da : db;
+  const int ny = 2 * nt.nx + nt.nu;
+  for (int v = blockIdx.x; v < n; v += gridDim.x) {
+    const int b = perm[v];
+    for (int e = threadIdx.x; e < ny; e += blockDim.x) {
+      double val = 0.0;
+      if (v != 0) {
+        const int c = e < nt.nx ? e : (e < 2 * nt.nx ? nt.NXP + e - nt.nx : 2 * nt.NXP + e - 2 * nt.nx);
+        val = yb[(size_t)v * nt.YP + c] + (double)d[(size_t)v * nt.YP + c];
+      }
+      y[(size_t)b * ny + e] = val;
+    }
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
 // factor handle
 // ---------------------------------------------------------------------------
 struct rn_factor {
+  unsigned long long serial = 0;  // unique per handle of the process (batch caches)
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -1516,6 +1540,8 @@ extern "C" int rapidnet_factor(const rn_network *net, const rn_tree *tree, const
     set_error("factor: host allocation failed");
     return RN_ERR_NOMEM;
   }
+  static std::atomic<unsigned long long> next_serial{1};
+  f->serial = next_serial.fetch_add(1);
   f->device = opts ? opts->device : 0;
   int rc = factor_impl(net, tree, cost, opts, f.get());
   if (rc) return rc;
@@ -1801,16 +1827,329 @@ extern "C" int rapidnet_dual_gradient_noalloc(rn_factor *f, const double *w, dou
 
 // ---------------------------------------------------------------------------
 // batched solve (many handles, one cooperative launch)
+//
+// A call runs, on the stream of the first handle: every problem's
+// preparation (data terms, x*(0), initial dual), the persistent batched
+// kernel, every problem's outputs and reductions, and one gathering kernel
+// that packs each problem's scalars into a record read back with a single
+// copy.  The whole sequence is captured once into a CUDA graph per set of
+// handles, requests, iteration cap and tolerance, and replayed by later
+// calls with the same arguments.  The launch layout (team width, teams per
+// block) of a set of handles is chosen once by timing the candidates on a
+// short run of the same batch (rn_opts.batch_tune of the first handle).
 // ---------------------------------------------------------------------------
 namespace {
 
-struct BatchWorkspace {
-  unsigned char *dev = nullptr;
-  size_t cap = 0;
-  int device = -1;
+// one problem's scalars after a batched solve
+struct BatchRec {
+  double res_last;      // residual bits of the last check (as a double's bits)
+  double cost[3];       // smooth cost, soft cost, input-box violation
+  int iters, nchk, reason, err;
 };
+
+struct BatchSrc {
+  const int *info;                 // iterations, checks, stop reason
+  const unsigned long long *res;   // residual history
+  const double *scal;              // reductions of k_final_reduce
+  const int *err;                  // the handle's error word (preparation)
+};
+
+__global__ void k_batch_collect(int n, const BatchSrc *src, BatchRec *out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const BatchSrc s = src[i];
+    BatchRec r;
+    r.iters = s.info[0];
+    r.nchk = s.info[1];
+    r.reason = s.info[2];
+    r.err = *s.err;
+    const unsigned long long b = r.nchk > 0 ? s.res[r.nchk - 1] : 0ull;
+    r.res_last = __longlong_as_double((long long)b);
+    r.cost[0] = s.scal[0];
+    r.cost[1] = s.scal[1];
+    r.cost[2] = s.scal[2];
+    out[i] = r;
+  }
+}
+
+// launch layout of the batched kernel for a set of handles
+struct BatchLayout {
+  int tw = 64, tpb = 4, block = 256, maxc = 1, grid = 0, net_f = 0, net_region = 0;
+  int team_bytes = 0;
+  long long items = 0;
+  size_t smem = 0;
+  std::vector<Sizes> szf, szd;
+};
+
+// the layout for teams of tw threads, tpb to a block (tw at least each
+// problem's own team width); RN_OK or the reason the layout does not fit
+int batch_layout(rn_factor *const *fs, int n, int tw, int tpb, BatchLayout *L) {
+  const int dev = fs[0]->device;
+  int rc;
+  L->tw = tw;
+  L->tpb = tpb;
+  L->block = tpb * tw;
+  L->net_f = 0;
+  L->items = 0;
+  L->maxc = 1;
+  for (int i = 0; i < n; ++i) {
+    L->net_f = std::max(L->net_f, fs[i]->net_bytes_f);
+    L->items += fs[i]->plan.n_groups + (fs[i]->plan.n_chains + tpb - 1) / tpb;
+    const int m = std::max(fs[i]->nx, fs[i]->nu);
+    int c = std::max((m + tw - 1) / tw, (fs[i]->nx + 31) / 32);
+    if (c > 8) {
+      set_error("solve_batch: teams of %d threads are too narrow for nx = %d, nu = %d", tw,
+                fs[i]->nx, fs[i]->nu);
+      return RN_ERR_UNSUPPORTED;
+    }
+    c = c <= 1 ? 1 : (c <= 2 ? 2 : (c <= 4 ? 4 : 8));
+    L->maxc = std::max(L->maxc, c);
+  }
+  L->net_region = L->net_f + (int)round16(sizeof(NetDev<double>));
+  int static_smem = 0;
+  RN_CUDA(batch_static_smem(L->maxc, &static_smem));
+  if ((rc = team_budget(dev, (int)std::min<long long>(L->items, 1 << 30), tpb, L->block,
+                        L->net_region, static_smem, &L->team_bytes)))
+    return rc;
+  L->szf.assign(n, Sizes{});
+  L->szd.assign(n, Sizes{});
+  for (int i = 0; i < n; ++i)
+    if ((rc = fit_sizes(fs[i], 4, L->team_bytes, L->net_region, tw, tpb, 2, &L->szf[i])) ||
+        (rc = fit_sizes(fs[i], 8, L->team_bytes, L->net_f, tw, tpb, 0, &L->szd[i])) ||
+        (rc = check_layout(fs[i]->plan, L->szf[i], 0, 0, "solve_batch")) ||
+        (rc = check_layout(fs[i]->plan, L->szd[i], 0, 0, "solve_batch")))
+      return rc;
+  L->smem = kHdrBytes + L->net_region + (size_t)tpb * L->team_bytes;
+  int bps = 0, sms = 0;
+  RN_CUDA(batch_occupancy(L->maxc, L->block, L->smem, &bps));
+  RN_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (bps < 1) {
+    set_error("solve_batch: the batched kernel does not fit on the device");
+    return RN_ERR_UNSUPPORTED;
+  }
+  L->grid = (int)std::min<long long>(L->items, (long long)bps * sms);
+  if (fs[0]->opts.max_ctas > 0) L->grid = std::min(L->grid, fs[0]->opts.max_ctas);
+  return RN_OK;
+}
+
+// the node reductions of one handle (cost, input-box violation) into its
+// scal, without reading them back
+int reduce_nodes_async(rn_factor *f) {
+  ReduceArgs a{f->pd.parent, f->perm, f->prob, f->alpha, f->alpha0, f->wdiag, f->q,
+               f->wdense, f->st.uo, f->st.xo, nullptr, f->W_alpha, 0};
+  k_node_reduce<<<kRedBlocks, 256, 0, f->stream>>>(f->net, a, f->plan.n, f->partial);
+  k_final_reduce<<<1, 32, 0, f->stream>>>(f->partial, kRedBlocks, f->scal);
+  RN_CUDA(cudaGetLastError());
+  return RN_OK;
+}
+
+// a batch prepared for launch: its device workspace (parameters, work
+// items, barrier, error and info words, result records), the pinned host
+// copy of the records and, once captured, the graph
+struct BatchRun {
+  std::vector<unsigned long long> key;
+  BatchLayout L;
+  unsigned char *dev = nullptr;
+  BatchRec *host = nullptr;
+  size_t o_probs = 0, o_ip = 0, o_ic = 0, o_cb = 0, o_bar = 0, o_err = 0, o_info = 0, o_src = 0,
+         o_rec = 0;
+  cudaGraphExec_t exec = nullptr;
+  bool graph = false;  // the sequence replays as a graph
+  ~BatchRun() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (dev) cudaFree(dev);
+    if (host) cudaFreeHost(host);
+  }
+};
+
+// workspace, parameters and work items of a batch (host to device, before
+// any capture)
+int batch_setup(rn_factor *const *fs, const rn_solve_req *req, int n, int max_iters, double tol,
+                BatchRun &R) {
+  const BatchLayout &L = R.L;
+  const int grid = L.grid;
+  const long long items = L.items;
+  std::vector<int> ip, ic, cb(grid + 1);
+  ip.reserve(items);
+  ic.reserve(items);
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < fs[i]->plan.n_groups + (fs[i]->plan.n_chains + L.tpb - 1) / L.tpb; ++k) {
+      ip.push_back(i);
+      ic.push_back(k);
+    }
+  for (int b = 0; b <= grid; ++b) cb[b] = (int)((long long)b * items / grid);
+  for (int b = 0; b < grid; ++b) {
+    int distinct = 0;
+    for (int it = cb[b]; it < cb[b + 1]; ++it)
+      if (it == cb[b] || ip[it] != ip[it - 1]) ++distinct;
+    if (distinct > kBatchMaxDistinct) {
+      set_error("solve_batch: a block would touch %d problems (more than %d); "
+                "too many small problems for this batch size", distinct, kBatchMaxDistinct);
+      return RN_ERR_UNSUPPORTED;
+    }
+  }
+  R.o_probs = 0;
+  R.o_ip = round16(R.o_probs + n * sizeof(MixedParams));
+  R.o_ic = round16(R.o_ip + items * sizeof(int));
+  R.o_cb = round16(R.o_ic + items * sizeof(int));
+  R.o_bar = round16(R.o_cb + (grid + 1) * sizeof(int));
+  R.o_err = round16(R.o_bar + sizeof(unsigned));
+  R.o_info = round16(R.o_err + sizeof(int));
+  R.o_src = round16(R.o_info + 3 * n * sizeof(int));
+  R.o_rec = round16(R.o_src + n * sizeof(BatchSrc));
+  const size_t total = round16(R.o_rec + n * sizeof(BatchRec));
+  void *p = nullptr;
+  cudaError_t e = cudaMalloc(&p, total);
+  if (e != cudaSuccess) {
+    set_error("solve_batch: cudaMalloc of %zu bytes failed: %s", total, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? RN_ERR_NOMEM : RN_ERR_CUDA;
+  }
+  R.dev = static_cast<unsigned char *>(p);
+  e = cudaMallocHost(&p, n * sizeof(BatchRec));
+  if (e != cudaSuccess) {
+    set_error("solve_batch: cudaMallocHost failed: %s", cudaGetErrorString(e));
+    return RN_ERR_NOMEM;
+  }
+  R.host = static_cast<BatchRec *>(p);
+  int *berr = reinterpret_cast<int *>(R.dev + R.o_err);
+  std::vector<MixedParams> probs(n);
+  std::vector<BatchSrc> src(n);
+  const int *binfo = reinterpret_cast<const int *>(R.dev + R.o_info);
+  for (int i = 0; i < n; ++i) {
+    MixedParams &M = probs[i];
+    M = mixed_params(fs[i], max_iters, tol);
+    set_sizes(M.f, L.szf[i]);
+    set_sizes(M.d, L.szd[i]);
+    M.f.st.err = berr;
+    M.d.st.err = berr;
+    src[i] = BatchSrc{binfo + 3 * i, fs[i]->res, fs[i]->scal, fs[i]->err};
+  }
+  RN_CUDA(cudaMemcpy(R.dev + R.o_probs, probs.data(), n * sizeof(MixedParams),
+                     cudaMemcpyHostToDevice));
+  RN_CUDA(cudaMemcpy(R.dev + R.o_ip, ip.data(), items * sizeof(int), cudaMemcpyHostToDevice));
+  RN_CUDA(cudaMemcpy(R.dev + R.o_ic, ic.data(), items * sizeof(int), cudaMemcpyHostToDevice));
+  RN_CUDA(cudaMemcpy(R.dev + R.o_cb, cb.data(), (grid + 1) * sizeof(int), cudaMemcpyHostToDevice));
+  RN_CUDA(cudaMemcpy(R.dev + R.o_src, src.data(), n * sizeof(BatchSrc), cudaMemcpyHostToDevice));
+  (void)req;
+  return RN_OK;
+}
+
+// the device work of a batch on stream bs (every handle's stream set to bs
+// by the caller): preparations, the batched kernel between the timing
+// events of the first handle, outputs, reductions, records and their copy
+// to the pinned host buffer
+int batch_enqueue(rn_factor *const *fs, const rn_solve_req *req, int n, int max_iters,
+                  double tol, BatchRun &R, cudaStream_t bs) {
+  const BatchLayout &L = R.L;
+  int rc;
+  for (int i = 0; i < n; ++i) {
+    rn_factor *f = fs[i];
+    const int ck = (max_iters + f->opts.check_every - 1) / f->opts.check_every + 1;
+    if ((rc = clear_err(f)) || (rc = prepare(f, req[i].x0, req[i].q, req[i].demand, req[i].alpha)))
+      return rc;
+    const int nn = f->plan.n;
+    k_mixed_init<<<node_blocks(nn), 128, 0, bs>>>(f->net, f->perm, nn, req[i].y_warm, f->mx.yb,
+                                                  f->mx.ybh, f->mx.da, f->mx.db, f->st.s,
+                                                  f->stf.s);
+    RN_CUDA(cudaGetLastError());
+    if ((rc = reset_sync(f))) return rc;
+    RN_CUDA(cudaMemsetAsync(f->res, 0, ck * sizeof(unsigned long long), bs));
+  }
+  unsigned char *W = R.dev;
+  int *berr = reinterpret_cast<int *>(W + R.o_err);
+  RN_CUDA(cudaMemsetAsync(W + R.o_bar, 0, sizeof(unsigned), bs));
+  RN_CUDA(cudaMemsetAsync(berr, 0, sizeof(int), bs));
+  RN_CUDA(cudaMemsetAsync(W + R.o_info, 0, 3 * n * sizeof(int), bs));
+  BatchDev B{};
+  B.n_problems = n;
+  B.probs = reinterpret_cast<const MixedParams *>(W + R.o_probs);
+  B.item_prob = reinterpret_cast<const int *>(W + R.o_ip);
+  B.item_sub = reinterpret_cast<const int *>(W + R.o_ic);
+  B.cta_begin = reinterpret_cast<const int *>(W + R.o_cb);
+  B.barrier = reinterpret_cast<unsigned *>(W + R.o_bar);
+  B.err = berr;
+  B.prob_info = reinterpret_cast<int *>(W + R.o_info);
+  B.iters = max_iters;
+  B.check_every = fs[0]->opts.check_every;
+  B.refresh_every = fs[0]->opts.refresh_every;
+  B.wait_ns = fs[0]->st.wait_ns;
+  B.net_bytes = L.net_region;
+  B.net_bytes_f = L.net_f;
+  B.team_bytes = L.team_bytes;
+  B.tpb = L.tpb;
+  B.tol = tol > 0.0 ? tol : 0.0;
+  RN_CUDA(cudaEventRecord(fs[0]->ev0, bs));
+  RN_CUDA(launch_batch(B, L.maxc, L.grid, L.block, L.smem, bs));
+  RN_CUDA(cudaEventRecord(fs[0]->ev1, bs));
+  for (int i = 0; i < n; ++i) {
+    rn_factor *f = fs[i];
+    rn_result *out = req[i].out;
+    const int nn = f->plan.n;
+    // the final dual sits in the delta buffer of the last iteration's
+    // parity, read from the problem's info on the device
+    k_gather<<<node_blocks(nn) + 1, 128, 0, bs>>>(f->net, f->perm, nn, f->st.uo, f->st.xo,
+                                                  nullptr, f->q, f->x0, out->u, out->x, nullptr);
+    k_gather_mixed_y_batch<<<node_blocks(nn) + 1, 128, 0, bs>>>(
+        f->net, f->perm, nn, f->mx.yb, f->mx.da, f->mx.db, B.prob_info + 3 * i, out->y);
+    RN_CUDA(cudaGetLastError());
+    if ((rc = reduce_nodes_async(f))) return rc;
+  }
+  k_batch_collect<<<(n + 127) / 128, 128, 0, bs>>>(
+      n, reinterpret_cast<const BatchSrc *>(W + R.o_src), reinterpret_cast<BatchRec *>(W + R.o_rec));
+  RN_CUDA(cudaGetLastError());
+  RN_CUDA(cudaMemcpyAsync(R.host, W + R.o_rec, n * sizeof(BatchRec), cudaMemcpyDeviceToHost, bs));
+  return RN_OK;
+}
+
+// every handle's stream set to bs for the duration of a batch, restored after
+struct StreamSwap {
+  std::vector<cudaStream_t> saved;
+  rn_factor *const *fs;
+  int n;
+  StreamSwap(rn_factor *const *fs_, int n_, cudaStream_t bs) : fs(fs_), n(n_) {
+    for (int i = 0; i < n; ++i) {
+      saved.push_back(fs[i]->stream);
+      fs[i]->stream = bs;
+    }
+  }
+  ~StreamSwap() {
+    for (int i = 0; i < n; ++i) fs[i]->stream = saved[i];
+  }
+};
+
+// enqueue the batch: by graph (captured on first use, replayed after) or,
+// where the capture fails, directly
+int batch_launch(rn_factor *const *fs, const rn_solve_req *req, int n, int max_iters, double tol,
+                 BatchRun &R, cudaStream_t bs, bool try_graph) {
+  StreamSwap swap(fs, n, bs);
+  if (R.exec) {
+    RN_CUDA(cudaGraphLaunch(R.exec, bs));
+    return RN_OK;
+  }
+  if (try_graph) {
+    cudaGraph_t g = nullptr;
+    RN_CUDA(cudaStreamBeginCapture(bs, cudaStreamCaptureModeThreadLocal));
+    const int rc = batch_enqueue(fs, req, n, max_iters, tol, R, bs);
+    const cudaError_t e = cudaStreamEndCapture(bs, &g);
+    if (rc == RN_OK && e == cudaSuccess && g &&
+        cudaGraphInstantiate(&R.exec, g, 0) == cudaSuccess) {
+      cudaGraphDestroy(g);
+      R.graph = true;
+      clear_error();
+      RN_CUDA(cudaGraphLaunch(R.exec, bs));
+      return RN_OK;
+    }
+    if (g) cudaGraphDestroy(g);
+    R.exec = nullptr;
+    cudaGetLastError();  // the failed capture leaves no sticky error; clear the last one
+    clear_error();
+  }
+  R.graph = false;
+  return batch_enqueue(fs, req, n, max_iters, tol, R, bs);
+}
+
 std::mutex g_batch_mu;
-BatchWorkspace g_batch_ws[kMaxDevices];
+std::unique_ptr<BatchRun> g_batch_run[kMaxDevices];        // the last batch per device
+std::map<std::vector<unsigned long long>, std::pair<int, int>> g_batch_tuned[kMaxDevices];
 
 int batch_impl(rn_factor *const *fs, const rn_solve_req *req, int n, int max_iters, double tol) {
   if (!fs || !req || n < 1) {
@@ -1848,6 +2187,11 @@ int batch_impl(rn_factor *const *fs, const rn_solve_req *req, int n, int max_ite
       set_error("solve_batch: handles on different devices");
       return RN_ERR_INVAL;
     }
+    if (f->opts.check_every != fs[0]->opts.check_every ||
+        f->opts.refresh_every != fs[0]->opts.refresh_every) {
+      set_error("solve_batch: all handles need the same check_every and refresh_every");
+      return RN_ERR_INVAL;
+    }
     for (int j = 0; j < i; ++j)
       if (fs[j] == f) {
         set_error("solve_batch: handle %d appears twice", i);
@@ -1861,193 +2205,112 @@ int batch_impl(rn_factor *const *fs, const rn_solve_req *req, int n, int max_ite
   RN_CUDA(cudaSetDevice(dev));
   cudaStream_t bs = fs[0]->stream;
   int rc;
-  // per-problem preparation on each handle's stream
-  int checks = 0, maxc = 1, tw = 64, net_region = 0, net_f = 0;
-  long long items = 0;
+  // earlier work of every handle on its own stream ends first; buffers
+  // that depend on the iteration cap are sized now (no allocation below)
   for (int i = 0; i < n; ++i) {
     rn_factor *f = fs[i];
+    if (f->stream != bs) RN_CUDA(cudaStreamSynchronize(f->stream));
     const int ck = (max_iters + f->opts.check_every - 1) / f->opts.check_every + 1;
-    checks = std::max(checks, ck);
     if ((rc = ensure_beta(f, max_iters)) || (rc = ensure_res(f, ck))) return rc;
-    if ((rc = clear_err(f)) || (rc = prepare(f, req[i].x0, req[i].q, req[i].demand, req[i].alpha)))
-      return rc;
-    const int nn = f->plan.n;
-    k_mixed_init<<<node_blocks(nn), 128, 0, f->stream>>>(f->net, f->perm, nn, req[i].y_warm,
-                                                         f->mx.yb, f->mx.ybh, f->mx.da,
-                                                         f->mx.db, f->st.s, f->stf.s);
-    RN_CUDA(cudaGetLastError());
-    if ((rc = reset_sync(f))) return rc;
-    RN_CUDA(cudaMemsetAsync(f->res, 0, ck * sizeof(unsigned long long), f->stream));
-    tw = std::max(tw, f->tw);
-    net_f = std::max(net_f, f->net_bytes_f);
   }
-  const int tpb = tw <= 128 ? 4 : 2, block = tpb * tw;
-  for (int i = 0; i < n; ++i) items += fs[i]->plan.n_groups + (fs[i]->plan.n_chains + tpb - 1) / tpb;
-  net_region = net_f + (int)round16(sizeof(NetDev<double>));
-  // each handle's preparation (its x*(0) evaluation) must have finished its waits
-  for (int i = 0; i < n; ++i)
-    if ((rc = check_err(fs[i]))) return rc;
-  for (int i = 0; i < n; ++i) {
-    const int m = std::max(fs[i]->nx, fs[i]->nu);
-    int c = std::max((m + tw - 1) / tw, (fs[i]->nx + 31) / 32);
-    c = c <= 1 ? 1 : (c <= 2 ? 2 : (c <= 4 ? 4 : 8));
-    maxc = std::max(maxc, c);
-  }
-  int static_smem = 0, team_bytes = 0;
-  RN_CUDA(batch_static_smem(maxc, &static_smem));
-  if ((rc = team_budget(dev, (int)std::min<long long>(items, 1 << 30), tpb, block, net_region,
-                        static_smem, &team_bytes)))
-    return rc;
-  std::vector<Sizes> szf(n), szd(n);
-  for (int i = 0; i < n; ++i)
-    if ((rc = fit_sizes(fs[i], 4, team_bytes, net_region, tw, tpb, 2, &szf[i])) ||
-        (rc = fit_sizes(fs[i], 8, team_bytes, net_f, tw, tpb, 0, &szd[i])) ||
-        (rc = check_layout(fs[i]->plan, szf[i], 0, 0, "solve_batch")) ||
-        (rc = check_layout(fs[i]->plan, szd[i], 0, 0, "solve_batch")))
-      return rc;
-  const size_t smem = kHdrBytes + net_region + (size_t)tpb * team_bytes;
-  int bps = 0, sms = 0;
-  RN_CUDA(batch_occupancy(maxc, block, smem, &bps));
-  RN_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  if (bps < 1) {
-    set_error("solve_batch: the batched kernel does not fit on the device");
-    return RN_ERR_UNSUPPORTED;
-  }
-  int grid = (int)std::min<long long>(items, (long long)bps * sms);
-  if (fs[0]->opts.max_ctas > 0) grid = std::min(grid, fs[0]->opts.max_ctas);
-  // work items sorted by problem, contiguous ranges per block
-  std::vector<int> ip, ic, cb(grid + 1);
-  ip.reserve(items);
-  ic.reserve(items);
-  for (int i = 0; i < n; ++i)
-    for (int k = 0; k < fs[i]->plan.n_groups + (fs[i]->plan.n_chains + tpb - 1) / tpb; ++k) {
-      ip.push_back(i);
-      ic.push_back(k);
-    }
-  for (int b = 0; b <= grid; ++b) cb[b] = (int)((long long)b * items / grid);
-  for (int b = 0; b < grid; ++b) {
-    int distinct = 0;
-    for (int it = cb[b]; it < cb[b + 1]; ++it)
-      if (it == cb[b] || ip[it] != ip[it - 1]) ++distinct;
-    if (distinct > kBatchMaxDistinct) {
-      set_error("solve_batch: a block would touch %d problems (more than %d); "
-                "too many small problems for this batch size", distinct, kBatchMaxDistinct);
-      return RN_ERR_UNSUPPORTED;
-    }
-  }
-  // device workspace (kept per device, grown on demand)
-  const size_t o_probs = 0;
-  const size_t o_ip = round16(o_probs + n * sizeof(MixedParams));
-  const size_t o_ic = round16(o_ip + items * sizeof(int));
-  const size_t o_cb = round16(o_ic + items * sizeof(int));
-  const size_t o_bar = round16(o_cb + (grid + 1) * sizeof(int));
-  const size_t o_err = round16(o_bar + sizeof(unsigned));
-  const size_t o_info = round16(o_err + sizeof(int));
-  const size_t total = round16(o_info + 3 * n * sizeof(int));
   std::lock_guard<std::mutex> lock(g_batch_mu);
-  BatchWorkspace &ws = g_batch_ws[dev];
-  if (ws.cap < total) {
-    if (ws.dev) cudaFree(ws.dev);
-    ws.dev = nullptr;
-    ws.cap = 0;
-    void *p = nullptr;
-    cudaError_t e = cudaMalloc(&p, total);
-    if (e != cudaSuccess) {
-      set_error("solve_batch: cudaMalloc of %zu bytes failed: %s", total, cudaGetErrorString(e));
-      return e == cudaErrorMemoryAllocation ? RN_ERR_NOMEM : RN_ERR_CUDA;
-    }
-    ws.dev = static_cast<unsigned char *>(p);
-    ws.cap = total;
-  }
-  unsigned char *W = ws.dev;
-  int *berr = reinterpret_cast<int *>(W + o_err);
-  std::vector<MixedParams> probs(n);
+  // the layout: rule-based, or the fastest of the candidates timed on the
+  // first batch of this set of handles
+  std::vector<unsigned long long> set_key;
+  int tw0 = 64;
   for (int i = 0; i < n; ++i) {
-    MixedParams &M = probs[i];
-    M = mixed_params(fs[i], max_iters, tol);
-    set_sizes(M.f, szf[i]);
-    set_sizes(M.d, szd[i]);
-    M.f.st.err = berr;
-    M.d.st.err = berr;
+    set_key.push_back(fs[i]->serial);
+    tw0 = std::max(tw0, fs[i]->tw);
   }
-  RN_CUDA(cudaMemcpyAsync(W + o_probs, probs.data(), n * sizeof(MixedParams),
-                          cudaMemcpyHostToDevice, bs));
-  RN_CUDA(cudaMemcpyAsync(W + o_ip, ip.data(), items * sizeof(int), cudaMemcpyHostToDevice, bs));
-  RN_CUDA(cudaMemcpyAsync(W + o_ic, ic.data(), items * sizeof(int), cudaMemcpyHostToDevice, bs));
-  RN_CUDA(cudaMemcpyAsync(W + o_cb, cb.data(), (grid + 1) * sizeof(int), cudaMemcpyHostToDevice, bs));
-  RN_CUDA(cudaMemsetAsync(W + o_bar, 0, sizeof(unsigned), bs));
-  RN_CUDA(cudaMemsetAsync(W + o_err, 0, sizeof(int), bs));
-  RN_CUDA(cudaMemsetAsync(W + o_info, 0, 3 * n * sizeof(int), bs));
-  BatchDev B{};
-  B.n_problems = n;
-  B.probs = reinterpret_cast<const MixedParams *>(W + o_probs);
-  B.item_prob = reinterpret_cast<const int *>(W + o_ip);
-  B.item_sub = reinterpret_cast<const int *>(W + o_ic);
-  B.cta_begin = reinterpret_cast<const int *>(W + o_cb);
-  B.barrier = reinterpret_cast<unsigned *>(W + o_bar);
-  B.err = berr;
-  B.prob_info = reinterpret_cast<int *>(W + o_info);
-  B.iters = max_iters;
-  B.check_every = fs[0]->opts.check_every;
-  for (int i = 1; i < n; ++i)
-    if (fs[i]->opts.check_every != B.check_every) {
-      set_error("solve_batch: all handles need the same check_every");
-      return RN_ERR_INVAL;
+  const int tpb0 = tw0 <= 128 ? 4 : 2;
+  std::pair<int, int> choice{tw0, tpb0};
+  auto &tuned = g_batch_tuned[dev];
+  if (fs[0]->opts.batch_tune == 0) {
+    auto it = tuned.find(set_key);
+    if (it != tuned.end()) {
+      choice = it->second;
+    } else {
+      std::vector<std::pair<int, int>> cand{{tw0, tpb0}};
+      if (tpb0 == 4) cand.push_back({tw0, 2});
+      if (2 * tw0 <= 256) cand.push_back({2 * tw0, 2});
+      const int titers = std::min(max_iters, 30);
+      float best = 0.f;
+      for (const auto &c : cand) {
+        BatchRun T;
+        if (batch_layout(fs, n, c.first, c.second, &T.L) != RN_OK) continue;
+        if ((rc = batch_setup(fs, req, n, titers, 0.0, T))) return rc;
+        if ((rc = batch_launch(fs, req, n, titers, 0.0, T, bs, false))) return rc;
+        RN_CUDA(cudaStreamSynchronize(bs));
+        float ms = 0.f;
+        RN_CUDA(cudaEventElapsedTime(&ms, fs[0]->ev0, fs[0]->ev1));
+        if (best == 0.f || ms < best) {
+          best = ms;
+          choice = c;
+        }
+      }
+      clear_error();
+      tuned[set_key] = choice;
     }
-  B.refresh_every = fs[0]->opts.refresh_every;
-  B.wait_ns = fs[0]->st.wait_ns;
-  B.net_bytes = net_region;
-  B.net_bytes_f = net_f;
-  B.team_bytes = team_bytes;
-  B.tpb = tpb;
-  B.tol = tol > 0.0 ? tol : 0.0;
-  RN_CUDA(cudaEventRecord(fs[0]->ev0, bs));
-  RN_CUDA(launch_batch(B, maxc, grid, block, smem, bs));
-  RN_CUDA(cudaEventRecord(fs[0]->ev1, bs));
-  std::vector<int> info(3 * n);
-  RN_CUDA(cudaMemcpyAsync(info.data(), W + o_info, 3 * n * sizeof(int), cudaMemcpyDeviceToHost, bs));
+  }
+  // the prepared batch (and its graph) of the same arguments, or a new one
+  std::vector<unsigned long long> key = set_key;
+  unsigned long long tb;
+  std::memcpy(&tb, &tol, sizeof tb);
+  key.insert(key.end(), {(unsigned long long)n, (unsigned long long)max_iters, tb,
+                         (unsigned long long)choice.first, (unsigned long long)choice.second});
+  for (int i = 0; i < n; ++i) {
+    const rn_solve_req &r = req[i];
+    for (const void *p : {(const void *)r.x0, (const void *)r.q, (const void *)r.demand,
+                          (const void *)r.alpha, (const void *)r.y_warm, (const void *)r.out->u,
+                          (const void *)r.out->x, (const void *)r.out->y,
+                          (const void *)fs[i]->beta, (const void *)fs[i]->res})
+      key.push_back((unsigned long long)(uintptr_t)p);
+  }
+  std::unique_ptr<BatchRun> &run = g_batch_run[dev];
+  if (!run || run->key != key) {
+    run.reset(new BatchRun());
+    run->key = key;
+    if ((rc = batch_layout(fs, n, choice.first, choice.second, &run->L)) ||
+        (rc = batch_setup(fs, req, n, max_iters, tol, *run))) {
+      run.reset();
+      return rc;
+    }
+  }
+  if ((rc = batch_launch(fs, req, n, max_iters, tol, *run, bs, fs[0]->opts.batch_tune != 2))) {
+    run.reset();
+    return rc;
+  }
   RN_CUDA(cudaStreamSynchronize(bs));
   float ms = 0.f;
-  RN_CUDA(cudaEventElapsedTime(&ms, fs[0]->ev0, fs[0]->ev1));
-  // errors of any problem (shared wait error words)
+  if (cudaEventElapsedTime(&ms, fs[0]->ev0, fs[0]->ev1) != cudaSuccess) {
+    ms = NAN;
+    cudaGetLastError();
+  }
+  const int berr_host = [&] {
+    int e = 0;
+    for (int i = 0; i < n; ++i) e = e ? e : run->host[i].err;
+    return e;
+  }();
   int any_err = 0;
-  RN_CUDA(cudaMemcpy(&any_err, berr, sizeof(int), cudaMemcpyDeviceToHost));
-  if (any_err) return timeout_error("solve_batch: ", any_err, B.wait_ns);
+  RN_CUDA(cudaMemcpy(&any_err, run->dev + run->o_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (berr_host) return timeout_error("solve_batch (preparation): ", berr_host, fs[0]->st.wait_ns);
+  if (any_err) return timeout_error("solve_batch: ", any_err, fs[0]->st.wait_ns);
   int status = RN_OK;
   for (int i = 0; i < n; ++i) {
     rn_factor *f = fs[i];
     rn_result *out = req[i].out;
-    const int iters = info[3 * i], nchk = info[3 * i + 1], reason = info[3 * i + 2];
-    const int nn = f->plan.n;
-    const float *dfin = ((iters - 1) & 1) ? f->mx.da : f->mx.db;
-    k_gather<<<node_blocks(nn) + 1, 128, 0, f->stream>>>(f->net, f->perm, nn, f->st.uo, f->st.xo,
-                                                         nullptr, f->q, f->x0, out->u, out->x,
-                                                         nullptr);
-    k_gather_mixed_y<<<node_blocks(nn) + 1, 128, 0, f->stream>>>(f->net, f->perm, nn, f->mx.yb,
-                                                                 dfin, out->y);
-    RN_CUDA(cudaGetLastError());
-    double red[3];
-    if ((rc = reduce_nodes(f, 0, nullptr, red))) return rc;
-    std::vector<unsigned long long> hist(std::max(1, nchk));
-    if (nchk > 0)
-      RN_CUDA(cudaMemcpy(hist.data(), f->res, nchk * sizeof(unsigned long long),
-                         cudaMemcpyDeviceToHost));
-    double last = NAN;
-    if (nchk > 0) {
-      std::memcpy(&last, &hist[nchk - 1], sizeof last);
-      last *= 1.0 / f->gamma;
-    }
-    out->iters = iters;
-    out->n_checks = nchk;
-    out->primal_res = last;
-    out->cost = red[0] + red[1];
-    out->ubox_viol = red[2];
+    const BatchRec &r = run->host[i];
+    out->iters = r.iters;
+    out->n_checks = r.nchk;
+    out->primal_res = r.nchk > 0 ? r.res_last * (1.0 / f->gamma) : NAN;
+    out->cost = r.cost[0] + r.cost[1];
+    out->ubox_viol = r.cost[2];
     out->gap = NAN;
     out->gamma = f->gamma;
     out->apg_ms = ms;
     out->t_begin_ns = out->t_end_ns = 0;
-    if (reason == 2) status = RN_ERR_DIVERGED;
-    else if (tol > 0.0 && reason != 1 && status == RN_OK) status = RN_NOT_CONVERGED;
+    if (r.reason == 2) status = RN_ERR_DIVERGED;
+    else if (tol > 0.0 && r.reason != 1 && status == RN_OK) status = RN_NOT_CONVERGED;
   }
   if (status == RN_ERR_DIVERGED) set_error("solve_batch: a residual became non-finite");
   return status;

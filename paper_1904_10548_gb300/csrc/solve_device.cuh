@@ -438,7 +438,6 @@ struct FwdCtx {
   T *yprv;
   T beta, beta_n;
   bool write_out;
-  bool fuse;                 // (mixed) form the next iteration's chain-head sums
   bool avg;                  // update the averaged primal with weight theta
   double theta;
   unsigned long long rbits;  // running max of |y+ - w| (abs_bits of T)
@@ -525,21 +524,11 @@ __device__ void prox_node_warp(const KParams<T> &P, const NetDev<T> &nt, int v, 
 // is evaluated on d = y+ - yb: the clamp decision compares ybh + dw with
 // the edges, the value is dw - edge (or -ybh when the component leaves its
 // edge), so the small increments of a small step gamma survive in FP32.
-// Chain-head sums of the next iteration, formed while the dual update
-// writes the backward input s of a chain's nodes: per lane the sums over
-// its nodes of (w1 + w2), of (q + 1) (w1 + w2) (q the node's position from
-// the head) and of w3 for the components it owns.
-template <int MAXC>
-struct HeadAcc {
-  float lam[MAXC], Lam[MAXC], g3[8];
-};
-
 template <int MAXC>
 __device__ void prox_node_warp_mixed(const KParams<float> &P, const NetDev<float> &nt,
                                      const MixedDev &mx, int v, const float *Uq, const float *Xq,
                                      const float *dc, const float *dp, const float *bh,
-                                     const float *ur, const float *xr, FwdCtx<float> &c,
-                                     HeadAcc<MAXC> *ha, float wq) {
+                                     const float *ur, const float *xr, FwdCtx<float> &c) {
   const int lane = threadIdx.x & 31;
   const float g = (float)P.gamma;
   float *dpg = c.yprv + (size_t)v * nt.YP;
@@ -590,19 +579,11 @@ __device__ void prox_node_warp_mixed(const KParams<float> &P, const NetDev<float
       c.rbits = r > c.rbits ? r : c.rbits;
       dpg[i] = d1;
       dpg[nt.NXP + i] = d2;
-      const float s1 = (d1 + c.beta_n * (d1 - a1[cc])) + (d2 + c.beta_n * (d2 - a2[cc]));
-      srow[i] = s1;
-      if (ha) {
-        ha->lam[cc] += s1;
-        ha->Lam[cc] = __fmaf_rn(wq, s1, ha->Lam[cc]);
-      }
+      srow[i] = (d1 + c.beta_n * (d1 - a1[cc])) + (d2 + c.beta_n * (d2 - a2[cc]));
       if (c.write_out) swrow[i] = w1[cc] + w2[cc];
     }
   }
-#pragma unroll
-  for (int jj = 0; jj < 8; ++jj) {
-    const int j = lane + 32 * jj;
-    if (j >= nt.nu) break;
+  for (int j = lane; j < nt.nu; j += 32) {
     const float a3 = dc[2 * nt.NXP + j];
     const float w3 = a3 + c.beta * (a3 - dp[2 * nt.NXP + j]);
     const float h3 = bh[2 * nt.NXP + j];
@@ -617,9 +598,7 @@ __device__ void prox_node_warp_mixed(const KParams<float> &P, const NetDev<float
     const unsigned long long r = abs_bits(d3 - w3);
     c.rbits = r > c.rbits ? r : c.rbits;
     dpg[2 * nt.NXP + j] = d3;
-    const float s3 = d3 + c.beta_n * (d3 - a3);
-    srow[nt.NXP + j] = s3;
-    if (ha) ha->g3[jj] += s3;
+    srow[nt.NXP + j] = d3 + c.beta_n * (d3 - a3);
     if (c.write_out) swrow[nt.NXP + j] = w3;
   }
 }
@@ -1243,16 +1222,6 @@ __device__ bool chain_forward(const KParams<T> &P, int k, FwdCtx<T> &c, const Sm
   const int lane = tm.lane(), warp = tm.warp(), nw = tm.nwarps(), S = P.fslots;
   T *xp = sm.buf, *Zp = xp + NXP, *BZ = Zp + NUP;
   const int fpn = fwd_elems_per_node(NXP, NUP, YP, SP, MODE);
-  // (mixed) the next iteration's head sums are formed here (chains below a
-  // group only: nobody reads the head sums of a chain below the root)
-  const bool fuse = MODE == kFwdMixed && c.fuse && g >= 0;
-  HeadAcc<C> ha;
-  if constexpr (MODE == kFwdMixed) {
-#pragma unroll
-    for (int cc = 0; cc < C; ++cc) ha.lam[cc] = ha.Lam[cc] = 0.f;
-#pragma unroll
-    for (int jj = 0; jj < 8; ++jj) ha.g3[jj] = 0.f;
-  }
   T *slots = sm.buf + round4(2 * NXP + NUP) + (size_t)warp * S * fpn;
   // nodes in the order the warps take them: the chain's own nodes (head to
   // leaf) first, then the top nodes the chain owns
@@ -1339,8 +1308,7 @@ __device__ bool chain_forward(const KParams<T> &P, int k, FwdCtx<T> &c, const Sm
       prox_node_warp<T, C>(P, nt, v, r + NXP, r, r + SP, r + SP + YP, c);
     } else if constexpr (MODE == kFwdMixed) {
       prox_node_warp_mixed<C>(P, nt, *mx, v, r + NXP, r, r + SP, r + SP + YP, r + SP + 2 * YP,
-                              r + SP + 3 * YP, r + SP + 3 * YP + NUP, c,
-                              fuse && q < L ? &ha : nullptr, (float)(q + 1));
+                              r + SP + 3 * YP, r + SP + 3 * YP + NUP, c);
     } else {
       for (int j = lane; j < nu; j += 32) {
         const T val = r[NXP + j];
@@ -1361,56 +1329,6 @@ __device__ bool chain_forward(const KParams<T> &P, int k, FwdCtx<T> &c, const Sm
     }
   }
   tm.sync();
-  if constexpr (MODE == kFwdMixed) {
-    if (fuse) {
-      // the next iteration's chain-head sums (as chain_head forms them from
-      // the rows just written): per-warp partials combined in warp order,
-      // then (lambda_h | ghat_h = sum w3 + B' sum_q lambda_q) to up[k] and
-      // one arrival at the group's counter
-      const int W = 2 * NXP + NUP;
-      T *red = sm.buf + round4(2 * NXP + NUP);
-#pragma unroll
-      for (int cc = 0; cc < C; ++cc) {
-        const int i = lane + 32 * cc;
-        if (i < nx) {
-          red[(size_t)warp * W + i] = ha.lam[cc];
-          red[(size_t)warp * W + NXP + i] = ha.Lam[cc];
-        }
-      }
-#pragma unroll
-      for (int jj = 0; jj < 8; ++jj) {
-        const int j = lane + 32 * jj;
-        if (j < nu) red[(size_t)warp * W + 2 * NXP + j] = ha.g3[jj];
-      }
-      tm.sync();
-      T *vec = xp;  // (x_p | Z_p | B Z_p) are not needed any more
-      T *out = P.st.up + (size_t)k * SP;
-      for (int i = tm.tid; i < nx; i += tm.nt) {
-        T lam = T(0), Lam = T(0);
-        for (int w = 0; w < nw; ++w) {
-          lam += red[(size_t)w * W + i];
-          Lam += red[(size_t)w * W + NXP + i];
-        }
-        out[i] = lam;
-        vec[i] = Lam;
-      }
-      tm.sync();
-      const int *Bc_ptr = nt.Bc_ptr, *Bc_idx = nt.Bc_idx;
-      const T *Bc_val = nt.Bc_val;
-      for (int j = tm.tid; j < nu; j += tm.nt) {
-        T g3 = T(0);
-        for (int w = 0; w < nw; ++w) g3 += red[(size_t)w * W + 2 * NXP + j];
-        Slice<T, 2> bc;
-        bc.load(Bc_ptr, Bc_idx, Bc_val, j);
-        out[NXP + j] = bc.dot(g3, [&](int t) { return vec[t]; }, Bc_idx, Bc_val);
-      }
-      tm.sync();
-      if (tm.tid == 0) {
-        __threadfence();
-        atomicAdd(P.st.count + g, 1u);
-      }
-    }
-  }
   return true;
 }
 
@@ -1479,14 +1397,11 @@ static __device__ void final_node(const MixedParams &M, int v) {
 template <typename T, int MODE, int C>
 __device__ bool eval_step(const KParams<T> &P, FwdCtx<T> &c, const MixedDev *mx,
                           const Smem<T> &smc, const Smem<T> &smg, const Team &tc,
-                          const Team &tb, unsigned step, bool keep, bool heads_ready = false) {
+                          const Team &tb, unsigned step, bool keep) {
   const int G = P.plan.n_groups, K = P.plan.n_chains, tpb = P.tpb;
   const int n_items = G + (K + tpb - 1) / tpb, team = team_index(tpb);
   bool ok = true;
-  // heads_ready: the previous iteration's forward sweep formed and
-  // published the chain-head sums (and chain_head's rows are not kept)
-  if (heads_ready) keep = false;
-  for (int i = blockIdx.x; i < n_items && !heads_ready; i += gridDim.x) {
+  for (int i = blockIdx.x; i < n_items; i += gridDim.x) {
     const int k = tpb * (i - G) + team;
     if (i >= G && k < K) chain_head<T, C>(P, k, smc, tc);
   }

@@ -49,7 +49,6 @@ __global__ void __launch_bounds__(512) k_solve(KParams<T> P) {
     c.beta_n = APG ? (T)P.st.beta[it + 1] : T(0);
     const bool check = APG && (((it + 1) % P.check_every) == 0 || it + 1 == P.iters);
     c.write_out = !APG || check;
-    c.fuse = false;
     c.avg = APG && P.st.uavg != nullptr;
     c.theta = APG ? P.st.theta[it] : 0.0;
     c.rbits = 0ull;
