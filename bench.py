@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--batch-iters", type=int, default=2000)
     ap.add_argument("--serve-iters", type=int, default=2000)
     ap.add_argument("--loop-hours", type=int, default=168)
+    ap.add_argument("--tree-paths", type=int, default=10000)
+    ap.add_argument("--tree-oracle-paths", type=int, default=2000)
     ap.add_argument("--loop-iters", type=int, default=500)
     ap.add_argument("--mode-tol", type=float, default=10.0,
                     help="stopping tolerance of the batched and served solves (and of the "
@@ -528,6 +530,47 @@ def run_closed_loop(rn, hours, max_iters):
             "final_residual_median": float(np.median(out.residual)), "precision": "mixed"}
 
 
+def run_scenario_tree(rn, S, oracle_S):
+    """Scenario-tree construction (paper §6.2: 10^4 Monte-Carlo price paths
+    reduced into a tree) with the 512-scenario shape [8,4,4,2,2,1,...],
+    N = 24, on the GPU; the oracle (numpy, one thread) on a smaller sample
+    of the same kind for scale."""
+    import numpy as np
+    from synthetic import make_price_paths
+    br = [8, 4, 4, 2, 2] + [1] * 19
+    paths = make_price_paths(S, 24, 1, seed=6)
+    rn.scenario_tree(paths[:2000], br)  # warm-up (module load, allocations)
+    t0 = time.perf_counter()
+    t = rn.scenario_tree(paths, br)
+    gpu_s = time.perf_counter() - t0
+    # the selection steps stream the S x S distance matrix once per choice
+    # at the root: 8 choices x S^2 x 8 bytes
+    root_bytes = 8 * S * S * 8
+    out = {"paths": S, "stages": 24, "branching": "[8,4,4,2,2,1,...]",
+           "nodes": int(t["n_nodes"]), "leaves": int(np.diff(t["stage_ptr"])[-1]),
+           "gpu_s": gpu_s, "root_selection_bytes": root_bytes}
+    if oracle_S > 0:
+        code = (f"import sys, time, numpy as np; sys.path.insert(0, {ROOT!r}); "
+                "from synthetic import make_price_paths; "
+                "from oracle.scenario_tree import build_tree; "
+                f"P = make_price_paths({oracle_S}, 24, 1, seed=6); "
+                "t = time.perf_counter(); "
+                f"build_tree(P, np.full({oracle_S}, 1.0 / {oracle_S}), {br!r}); "
+                "print(time.perf_counter() - t)")
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
+                   CUDA_VISIBLE_DEVICES="")
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+        if r.returncode == 0:
+            cpu_s = float(r.stdout.strip().splitlines()[-1])
+            t2 = rn.scenario_tree(paths[:oracle_S], br)
+            t0 = time.perf_counter()
+            rn.scenario_tree(paths[:oracle_S], br)
+            out["oracle_sample"] = {"paths": oracle_S, "cpu_s": cpu_s, "cores": 1,
+                                    "gpu_s": time.perf_counter() - t0,
+                                    "nodes": int(t2["n_nodes"])}
+    return out
+
+
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
@@ -662,6 +705,7 @@ def main():
         modes["serving"] = run_serving(rn, args.serve_seconds, args.serve_rate,
                                        args.serve_iters, args.mode_tol)
         modes["closed_loop"] = run_closed_loop(rn, args.loop_hours, args.loop_iters)
+        modes["scenario_tree"] = run_scenario_tree(rn, args.tree_paths, args.tree_oracle_paths)
 
     # roofline of the dominant kernel (the persistent APG launch)
     values, flops = node_counts(net)

@@ -369,6 +369,40 @@ int rapidnet_server_stats(rn_server *s, rn_server_stats *st);
 /* Finishes the queued requests, then frees every slot. */
 void rapidnet_server_destroy(rn_server *s);
 
+/* ---------------------------------------------------------------------
+ * Scenario tree from sampled paths (paper §2.3 and §6.2: Monte-Carlo
+ * scenarios reduced into a tree; the paper cites Heitsch and Römisch).
+ * The tree is built forward: every node of stage t holds a bundle of the
+ * paths (the root all of them); its min(branching[t], bundle size)
+ * children are representatives chosen by fast forward selection on the
+ * distance between the paths' remaining parts (stages t+1 .. N,
+ * Euclidean over stages and dimensions), one at a time, each minimising
+ * sum_j p_j min(m_j, d(j, u)) with m_j the distance of path j to the
+ * nearest representative chosen so far (lowest index on ties); every path
+ * goes to its nearest representative (first chosen on ties).  A child
+ * carries its representative's value at its stage and the probability of
+ * its paths.  Distances, selection and assignment run on the GPU in FP64.
+ * ------------------------------------------------------------------- */
+typedef struct {
+  int max_nodes;     /* capacity of anc, prob, rep (and value / dim) */
+  int n_nodes;       /* filled: nodes of the tree, breadth first */
+  int *stage_ptr;    /* N + 2: nodes of stage t are [stage_ptr[t], stage_ptr[t+1]) */
+  int *anc;          /* ancestor of each node, anc[0] = -1 */
+  double *prob;      /* probability of reaching each node */
+  double *value;     /* n_nodes * dim: the node's value (row 0 zero) */
+  int *rep;          /* the path each node represents (-1 at the root) */
+  int *leaf_of;      /* S: the leaf of every path */
+} rn_tree_out;
+
+/* paths: host, S * N * dim row-major (path s, stage t + 1, component);
+ * prob: S, adding up to 1 (NULL: uniform); branching: N entries >= 1.
+ * Output arrays are host memory allocated by the caller.  Returns RN_OK,
+ * RN_ERR_INVAL (bad sizes, probabilities, non-finite values, or more nodes
+ * than max_nodes), RN_ERR_NOMEM or RN_ERR_CUDA.  Work space on the device:
+ * S * S doubles for the distance matrix plus O(S * N * dim). */
+int rapidnet_scenario_tree(const double *paths, const double *prob, int S, int N, int dim,
+                           const int *branching, int device, rn_tree_out *out);
+
 /* Description of the last failure on the calling thread ("" if none). */
 const char *rapidnet_last_error(void);
 

@@ -92,6 +92,11 @@ class rn_server_stats(ctypes.Structure):
                 ("p50_s", c_double), ("p99_s", c_double), ("mean_s", c_double)]
 
 
+class rn_tree_out(ctypes.Structure):
+    _fields_ = [("max_nodes", c_int), ("n_nodes", c_int), ("stage_ptr", PI), ("anc", PI),
+                ("prob", PD), ("value", PD), ("rep", PI), ("leaf_of", PI)]
+
+
 class rn_factor_info(ctypes.Structure):
     _fields_ = [("nx", c_int), ("nu", c_int), ("nd", c_int), ("ne", c_int), ("N", c_int),
                 ("n_nodes", c_int), ("n_chains", c_int), ("n_top", c_int),
@@ -123,6 +128,8 @@ EXPORTS = {
                                      POINTER(c_double)]),
     "rapidnet_server_stats": (c_int, [c_void_p, POINTER(rn_server_stats)]),
     "rapidnet_server_destroy": (None, [c_void_p]),
+    "rapidnet_scenario_tree": (c_int, [PD, PD, c_int, c_int, c_int, PI, c_int,
+                                       POINTER(rn_tree_out)]),
     "rapidnet_last_error": (ctypes.c_char_p, []),
 }
 
@@ -293,6 +300,36 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def scenario_tree(paths, branching, prob=None, device: int = 0) -> dict:
+    """rapidnet_scenario_tree: paths (S, N, dim) host array, branching (N,);
+    returns the tree (stage_ptr, anc, prob, value, rep, leaf_of)."""
+    P = _f64(paths)
+    if P.ndim == 2:
+        P = P[:, :, None]
+    S, N, dim = P.shape
+    br = np.ascontiguousarray(branching, dtype=np.int32)
+    if br.shape != (N,):
+        raise ValueError("branching needs one entry per stage")
+    cap, level = 1, 1
+    for b in br:
+        level *= int(max(b, 1))
+        cap += min(level, S)
+    stage_ptr = np.zeros(N + 2, dtype=np.int32)
+    anc = np.zeros(cap, dtype=np.int32)
+    prb = np.zeros(cap)
+    value = np.zeros((cap, dim))
+    rep = np.zeros(cap, dtype=np.int32)
+    leaf = np.zeros(S, dtype=np.int32)
+    out = rn_tree_out(cap, 0, stage_ptr.ctypes.data_as(PI), anc.ctypes.data_as(PI), _pd(prb),
+                      _pd(value), rep.ctypes.data_as(PI), leaf.ctypes.data_as(PI))
+    p = None if prob is None else _f64(prob, (S,))
+    _check(load().rapidnet_scenario_tree(_pd(P), None if p is None else _pd(p), S, N, dim,
+                                         br.ctypes.data_as(PI), device, ctypes.byref(out)))
+    n = out.n_nodes
+    return dict(n_nodes=n, stage_ptr=stage_ptr, anc=anc[:n], prob=prb[:n], value=value[:n],
+                rep=rep[:n], leaf_of=leaf)
 
 
 def rapidnet_dual_gradient_noalloc(h, w, u, x) -> int:

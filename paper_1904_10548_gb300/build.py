@@ -28,8 +28,8 @@ SOURCES += [(k, f"{os.path.splitext(k)[0]}_c{c}_d{d}.o", [f"-DRN_CVAL={c}", f"-D
             for k in ("mixed_kernels.cu", "solve_kernels.cu") for d in (0, 1)
             for c in (8, 4, 2, 1)]
 SOURCES += [(s, os.path.splitext(s)[0] + ".o", []) for s in
-            ["rapidnet.cu", "dispatch.cu", "server.cpp", "plan.cpp", "factor_check.cpp",
-             "layout.cpp"]]
+            ["rapidnet.cu", "dispatch.cu", "scenario_tree.cu", "server.cpp", "plan.cpp",
+             "factor_check.cpp", "layout.cpp"]]
 
 
 def _nvcc() -> str:

@@ -86,7 +86,7 @@ __device__ bool batch_eval(const BatchDev &B, BatchCtx &bc, MixedParams &mp, con
     const int sub = B.item_sub[i];
     if (sub < P.plan.n_groups) {
       __syncthreads();
-      if (!group_step<T>(P, sub, smem_g(), tb, step)) ok = false;
+      if (!group_step<T>(P, sub, smem_g(), tb, step, 0)) ok = false;
     }
   }
   for (int i = i0; i < i1; ++i) {
@@ -95,6 +95,19 @@ __device__ bool batch_eval(const BatchDev &B, BatchCtx &bc, MixedParams &mp, con
     const KParams<T> &P = params();
     const int G = P.plan.n_groups, sub = B.item_sub[i], k = B.tpb * (sub - G) + ti;
     if (sub >= G && k < P.plan.n_chains) chain_rest<T, C>(P, k, smem_c(), tc, false);
+  }
+  // parts of split subtrees complete their root once every part of it has
+  // arrived: a block may hold several parts, so no part waits before the
+  // block has done the first half of all of its groups
+  for (int i = i0; i < i1; ++i) {
+    if (!use(i)) continue;
+    load_problem(B, B.item_prob[i], bc, mp, bm);
+    const KParams<T> &P = params();
+    const int sub = B.item_sub[i];
+    if (sub < P.plan.n_groups && P.plan.g_root[sub] >= 0) {
+      __syncthreads();
+      if (!group_step<T>(P, sub, smem_g(), tb, step, 1)) ok = false;
+    }
   }
   for (int i = i0; i < i1; ++i) {
     if (!use(i)) continue;

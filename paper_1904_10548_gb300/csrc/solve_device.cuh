@@ -876,11 +876,16 @@ __device__ void root_compute(const KParams<T> &P, int root, const Smem<T> &sm, c
 // publishes the sums at its top nodes in hp and its arrival, applies F to
 // its rows, waits until every part of the root has arrived, completes the
 // root node itself (root_compute; every part does, so no part waits for
-// another's result) and rolls down from it.  False on timeout.
+// another's result) and rolls down from it.  phase -1 does all of this in
+// one call (a block with one work item); a block with several items (the
+// batched kernel) calls phase 0 (up to the arrival, z rows left in ux) for
+// all its groups before phase 1 (the wait, the root and the roll-down), so
+// that no part waits for a part that its own block has still to start.
+// False on timeout.
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ bool group_step(const KParams<T> &P, int g, const Smem<T> &sm, const Team &tm,
-                           unsigned step) {
+                           unsigned step, int phase = -1) {
   const NetDev<T> &nt = *sm.net;
   const PlanDev &pl = P.plan;
   const int SP = nt.SP, NXP = nt.NXP, NUP = nt.NUP, nx = nt.nx, nu = nt.nu, NEP = nt.NEP;
@@ -902,7 +907,47 @@ __device__ bool group_step(const KParams<T> &P, int g, const Smem<T> &sm, const 
   T *base = nullptr;  // (x | Z) at the parent of the group's top node, if not the tree root
   int nl = 0;
   const int *lvl = nullptr, *par = nullptr;
-  {
+  const int p0 = root >= 0 ? pl.r_part[2 * root] : 0, p1 = root >= 0 ? pl.r_part[2 * root + 1] : 0;
+  // every part waits until all parts of its root have arrived (bounded)
+  auto wait_parts = [&]() {
+    if (tm.tid == 0) {
+      bool ok = true;
+      for (int q = p0; q < p1 && ok; ++q)
+        ok = spin_geq(P.st.arrive + q, step + 1u, P.st.err, P.st.wait_ns, 3);
+      sm.flag[0] = ok;
+    }
+    tm.sync();
+    return sm.flag[0] != 0;
+  };
+  if (phase == 1) {
+    // second half of a part (a block that holds several items): the
+    // descriptor and the z rows the first half left in ux, then the root
+    if (root < 0) return true;
+    if (!wait_parts()) return false;
+    for (int e = tm.tid; e < dn / 4; e += tm.nt) cp16(desc + 4 * e, pl.g_desc + d0 + 4 * e, false);
+    constexpr int per = 16 / sizeof(T);
+    const int nv = NUP / per;
+    if (m <= gcap) {
+      for (int e = tm.tid; e < m * nv; e += tm.nt) {
+        const int li = e / nv, c = e - li * nv;
+        cp16(rb + (size_t)li * SP + NXP + c * per,
+             P.st.ux + (size_t)(g0 + li) * SP + NXP + c * per, true);
+      }
+    } else {
+      // rows in global memory: the asynchronous copy writes shared memory only
+      for (int e = tm.tid; e < m * NUP; e += tm.nt) {
+        const int li = e / NUP, j = e - li * NUP;
+        rb[(size_t)li * SP + NXP + j] = __ldcg(P.st.ux + (size_t)(g0 + li) * SP + NXP + j);
+      }
+    }
+    cp_wait();
+    tm.sync();
+    nl = desc[1];
+    lvl = desc + 4;
+    par = lvl + nl + 1;
+    root_compute(P, root, sm, tm, step, H, eb, fb, i2p, g == p0);
+    base = H;
+  } else {
   // all chains of the group have arrived; the counter restarts for the
   // next evaluation (no chain arrives again before the flag below)
   if (tm.tid == 0) {
@@ -1102,16 +1147,20 @@ __device__ bool group_step(const KParams<T> &P, int g, const Smem<T> &sm, const 
   }
   tm.sync();
   if (root >= 0) {
-    // every part completes the root itself once all parts have arrived
-    const int p0 = pl.r_part[2 * root], p1 = pl.r_part[2 * root + 1];
-    if (tm.tid == 0) {
-      bool ok = true;
-      for (int q = p0; q < p1 && ok; ++q)
-        ok = spin_geq(P.st.arrive + q, step + 1u, P.st.err, P.st.wait_ns, 3);
-      sm.flag[0] = ok;
+    if (phase == 0) {
+      // first half of a part: leave the z rows in ux for the second half
+      constexpr int per = 16 / sizeof(T);
+      const int nv = NUP / per;
+      using V = typename std::conditional<sizeof(T) == 8, double2, float4>::type;
+      for (int e = tm.tid; e < m * nv; e += tm.nt) {
+        const int li = e / nv, c = e - li * nv;
+        reinterpret_cast<V *>(P.st.ux + (size_t)(g0 + li) * SP + NXP)[c] =
+            reinterpret_cast<const V *>(rb + (size_t)li * SP + NXP)[c];
+      }
+      return true;
     }
-    tm.sync();
-    if (!sm.flag[0]) return false;
+    // every part completes the root itself once all parts have arrived
+    if (!wait_parts()) return false;
     root_compute(P, root, sm, tm, step, H, eb, fb, i2p, g == p0);
     base = H;
   }

@@ -17,14 +17,17 @@ with the same dimensions and structure:
 * tree: a branching vector per stage, Dirichlet splits of probability;
 * demand: positive daily sinusoid times (1 + 0.1 N(0,1)) per node;
 * price: lognormal(log 0.1, 0.3) per node and hour, multiplied by a
-  per-pump energy coefficient (valves cost nothing to operate).
+  per-pump energy coefficient (valves cost nothing to operate);
+* sampled price paths (AR(1) log-price deviations with a daily profile)
+  for the scenario-tree construction.
 """
 from .network import Cost, Network, make_cost, make_network
 from .tree import Tree, make_tree, random_branching
 from .data import SolveData, make_data
 from .configs import CONFIGS, Problem, make_problem
+from .paths import make_price_paths
 
 __all__ = [
     "Cost", "Network", "make_cost", "make_network", "Tree", "make_tree", "random_branching",
-    "SolveData", "make_data", "CONFIGS", "Problem", "make_problem",
+    "SolveData", "make_data", "CONFIGS", "Problem", "make_problem", "make_price_paths",
 ]

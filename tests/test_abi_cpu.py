@@ -47,7 +47,7 @@ def test_ctypes_layouts_match_header(tmp_path):
     """Compile a C program against the header and compare sizeof/offsetof."""
     structs = {"rn_network": B.rn_network, "rn_tree": B.rn_tree, "rn_cost": B.rn_cost,
                "rn_opts": B.rn_opts, "rn_result": B.rn_result,
-               "rn_factor_info": B.rn_factor_info}
+               "rn_factor_info": B.rn_factor_info, "rn_tree_out": B.rn_tree_out}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rapidnet.h"',
              'int main(void) {']
     for s, cls in structs.items():

@@ -13,7 +13,7 @@ import pytest
 import oracle as O
 import paper_1904_10548_gb300 as rn
 from paper_1904_10548_gb300 import _binding as B
-from synthetic import make_cost, make_data, make_network, random_branching
+from synthetic import make_cost, make_data, make_network, make_tree, random_branching
 from synthetic.configs import Problem
 from tests.test_gpu_parity import rel_err
 
@@ -162,3 +162,37 @@ def test_batch_layouts_and_graph_replay_agree():
         for a, b in zip(outs[tune], outs[2]):
             for k in ("u", "x", "y"):
                 assert np.array_equal(a[k], b[k]), (tune, k)
+
+
+def test_batch_with_split_subtrees_in_shared_blocks():
+    """A tree whose stage-1 subtrees are split into parts (85 top nodes
+    each), batched with small problems on a grid capped so that blocks
+    hold several work items, parts of one root among them: the batched
+    kernel runs the parts in two halves (no part waits for a part its own
+    block has not started) and still equals the solo solve, which runs them
+    in one."""
+    net = make_network(10, 18, 12, 3, seed=61)
+    tree = make_tree([2, 4, 4, 4, 2] + [1] * 4, seed=62)
+    split = Problem(net=net, cost=make_cost(net, seed=61), tree=tree,
+                    data=make_data(net, tree, seed=63))
+    pbs = [batch_problem(0), split, batch_problem(1)]
+    facs = [rn.Factor(pb.net, pb.cost, pb.tree, power_iters=50, precision=rn.RN_PREC_MIXED)
+            for pb in pbs]
+    items = [f.info()["grid_ctas"] for f in facs]
+    assert facs[1].info()["n_top"] > 2 * 24  # the stage-1 subtrees are split
+    for f in facs:
+        f.close()
+    # the batch takes the first handle's cap (which must cover that handle's
+    # own work items); about four items to a block
+    cap = max(items[0], sum(items) // 4)
+    assert cap < sum(items) // 2
+    facs = [rn.Factor(pb.net, pb.cost, pb.tree, power_iters=50, precision=rn.RN_PREC_MIXED,
+                      max_ctas=cap if i == 0 else 0) for i, pb in enumerate(pbs)]
+    outs = rn.solve_batch(facs, [tensors(pb) for pb in pbs], 60)
+    for pb, f, o in zip(pbs, facs, outs):
+        assert o["iters"] == 60
+        solo = f.solve(pb.data.x0, pb.data.q, pb.data.demand, pb.data.alpha, max_iters=60)
+        for k in ("u", "x", "y"):
+            assert np.array_equal(o[k].cpu().numpy(), solo[k]), k
+    for f in facs:
+        f.close()
