@@ -267,7 +267,8 @@ typedef struct {
  * streams are synchronised first), with one read-back of all problems'
  * scalars; the library keeps the last batch's work space and CUDA graph per
  * device and replays the graph when the next call has the same handles,
- * requests, max_iters and tol.  out->apg_ms is the batched kernel's time;
+ * requests, max_iters and tol.  out->apg_ms is the device time of the whole
+ * sequence (preparations, batched kernel, outputs);
  * t_begin_ns and t_end_ns are 0. */
 int rapidnet_solve_batch(rn_factor *const *f, const rn_solve_req *req, int n,
                          int max_iters, double tol);

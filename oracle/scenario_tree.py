@@ -17,8 +17,14 @@ representatives one at a time, each the candidate that minimises the
 probability-weighted distance of the bundle's paths to the nearest chosen
 one:
     z(u) = sum_j p_j min(m_j, d(j, u)),   m_j = min over chosen c of d(j, c)
-(m_j = +inf before the first choice), ties to the lowest path index.
-Everything here is FP64 and follows those definitions literally.
+(m_j = +inf before the first choice), ties to the lowest path index.  A
+tie is a value within TIE (relative) of the smallest: such ties are real
+(in one dimension the weighted median of an even number of paths is an
+interval, and near the end of the horizon the remaining parts are short),
+and two sides that add the same terms in different orders must take the
+same decision on them.  The assignment of paths to representatives breaks
+ties the same way.  Everything here is FP64 and follows those definitions
+literally.
 """
 from __future__ import annotations
 
@@ -49,6 +55,16 @@ def tail_distances(paths: np.ndarray, idx: np.ndarray, t: int) -> np.ndarray:
     return np.sqrt(d2)
 
 
+TIE = 1e-12  # values within TIE (relative) of the smallest count as ties
+
+
+def first_within_tie(values) -> int:
+    """Lowest index whose value is within TIE of the smallest value."""
+    v = np.asarray(values, float)
+    lo = v.min()
+    return int(np.flatnonzero(v <= lo + TIE * abs(lo))[0])
+
+
 def fast_forward_selection(D: np.ndarray, p: np.ndarray, K: int) -> list:
     """Indices (into D's rows) of K representatives chosen greedily."""
     M = D.shape[0]
@@ -56,13 +72,11 @@ def fast_forward_selection(D: np.ndarray, p: np.ndarray, K: int) -> list:
     m = np.full(M, np.inf)
     chosen: list = []
     for _ in range(K):
-        best, best_z = -1, np.inf
+        z = np.full(M, np.inf)
         for u in range(M):
-            if u in chosen:
-                continue
-            z = float(np.sum(p * np.minimum(m, D[:, u])))
-            if z < best_z:
-                best, best_z = u, z
+            if u not in chosen:
+                z[u] = float(np.sum(p * np.minimum(m, D[:, u])))
+        best = first_within_tie(z)
         chosen.append(best)
         m = np.minimum(m, D[:, best])
     return chosen
@@ -86,7 +100,7 @@ def build_tree(paths: np.ndarray, prob: np.ndarray, branching) -> ReducedTree:
             D = tail_distances(paths, idx, t)
             sel = fast_forward_selection(D, prob[idx], branching[t])
             # every path to its nearest representative (first chosen on ties)
-            owner = np.argmin(D[:, sel], axis=1)
+            owner = np.array([first_within_tie(D[a, sel]) for a in range(len(idx))])
             for c, s in enumerate(sel):
                 members = idx[owner == c]
                 anc.append(parent)

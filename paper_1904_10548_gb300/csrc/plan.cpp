@@ -208,7 +208,9 @@ int build_plan(const rn_tree *t, Plan &p, int max_groups) {
   }
   p.n_roots = (int)root_orig.size();
   p.r_hp.push_back(hp_rows);
-  p.hp_rows = hp_rows;
+  // one more row per root after the children's sums: a copy of the root's
+  // own backward input, taken by its first part before it arrives
+  p.hp_rows = hp_rows + p.n_roots;
   for (int b1 : root_orig) {
     p.perm[next] = b1;
     p.iperm[b1] = next;

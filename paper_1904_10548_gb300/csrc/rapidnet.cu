@@ -2077,9 +2077,7 @@ int batch_enqueue(rn_factor *const *fs, const rn_solve_req *req, int n, int max_
   B.team_bytes = L.team_bytes;
   B.tpb = L.tpb;
   B.tol = tol > 0.0 ? tol : 0.0;
-  RN_CUDA(cudaEventRecord(fs[0]->ev0, bs));
   RN_CUDA(launch_batch(B, L.maxc, L.grid, L.block, L.smem, bs));
-  RN_CUDA(cudaEventRecord(fs[0]->ev1, bs));
   for (int i = 0; i < n; ++i) {
     rn_factor *f = fs[i];
     rn_result *out = req[i].out;
@@ -2121,30 +2119,30 @@ struct StreamSwap {
 int batch_launch(rn_factor *const *fs, const rn_solve_req *req, int n, int max_iters, double tol,
                  BatchRun &R, cudaStream_t bs, bool try_graph) {
   StreamSwap swap(fs, n, bs);
-  if (R.exec) {
-    RN_CUDA(cudaGraphLaunch(R.exec, bs));
-    return RN_OK;
-  }
-  if (try_graph) {
+  // the first handle's events bracket the whole sequence on the device
+  if (!R.exec && try_graph) {
     cudaGraph_t g = nullptr;
     RN_CUDA(cudaStreamBeginCapture(bs, cudaStreamCaptureModeThreadLocal));
     const int rc = batch_enqueue(fs, req, n, max_iters, tol, R, bs);
     const cudaError_t e = cudaStreamEndCapture(bs, &g);
-    if (rc == RN_OK && e == cudaSuccess && g &&
-        cudaGraphInstantiate(&R.exec, g, 0) == cudaSuccess) {
-      cudaGraphDestroy(g);
+    if (rc == RN_OK && e == cudaSuccess && g && cudaGraphInstantiate(&R.exec, g, 0) == cudaSuccess) {
       R.graph = true;
-      clear_error();
-      RN_CUDA(cudaGraphLaunch(R.exec, bs));
-      return RN_OK;
+    } else {
+      R.exec = nullptr;
+      cudaGetLastError();  // the failed capture leaves no sticky error; clear the last one
     }
     if (g) cudaGraphDestroy(g);
-    R.exec = nullptr;
-    cudaGetLastError();  // the failed capture leaves no sticky error; clear the last one
     clear_error();
   }
-  R.graph = false;
-  return batch_enqueue(fs, req, n, max_iters, tol, R, bs);
+  RN_CUDA(cudaEventRecord(fs[0]->ev0, bs));
+  if (R.exec) {
+    RN_CUDA(cudaGraphLaunch(R.exec, bs));
+  } else {
+    R.graph = false;
+    if (const int rc = batch_enqueue(fs, req, n, max_iters, tol, R, bs)) return rc;
+  }
+  RN_CUDA(cudaEventRecord(fs[0]->ev1, bs));
+  return RN_OK;
 }
 
 std::mutex g_batch_mu;

@@ -56,7 +56,8 @@ struct Plan {
   // per group its root (-1 unless the group is a part of a split stage-1
   // subtree) and the first hp row of its top nodes' sums; roots: internal
   // node r_node[r], parts [r_part[2r], r_part[2r+1]), the sums of its
-  // children in hp rows [r_hp[r], r_hp[r+1])
+  // children in hp rows [r_hp[r], r_hp[r+1]); hp row r_hp[n_roots] + r
+  // holds root r's own backward input (hp_rows counts both kinds)
   std::vector<int> g_root, g_hp, r_node, r_part, r_hp;
   // per group the top nodes with chain children: ccn[g_ccn[g] .. g_ccn[g+1])
   std::vector<int> g_ccn, ccn;

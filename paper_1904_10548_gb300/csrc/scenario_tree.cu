@@ -10,8 +10,9 @@
 //   d(i, j) = || x_i[t:] - x_j[t:] ||  (Euclidean over stages and dimensions)
 //   z(u)    = sum_j p_j min(m_j, d(j, u)),  m_j = min over chosen c of d(j, c)
 // one representative at a time, the one with the smallest z (lowest index
-// on ties); every path of the bundle then goes to its nearest
-// representative (first chosen on ties).  Per bundle on the GPU:
+// on ties, a tie being a value within 1e-12 relative of the smallest);
+// every path of the bundle then goes to its nearest representative (first
+// chosen on ties).  Per bundle on the GPU:
 //   k_tail_dist   the bundle's distance matrix (FP64, tiles of 32 x 32 pairs,
 //                 the tails staged through shared memory);
 //   k_ffs_z       z for every candidate: one warp per candidate reads one
@@ -88,41 +89,42 @@ __global__ void k_ffs_z(const double *D, int M, const double *p, const double *m
   }
 }
 
-// the candidate with the smallest z (lowest index on ties) becomes choice k
+// values within kTie (relative) of the smallest count as ties: they are real
+// (in one dimension the median of an even number of paths is an interval),
+// and sums added in different orders must still take the same decision
+constexpr double kTie = 1e-12;
+
+// the lowest candidate whose z is within kTie of the smallest becomes
+// choice k (one block: the smallest value, then the first index within it)
 __global__ void k_ffs_pick(const double *z, int M, int k, int *chosen, int *sel) {
-  __shared__ double bz[32];
-  __shared__ int bi[32];
-  double best = INFINITY;
-  int bidx = M;
+  __shared__ double red[32];
+  __shared__ int ired[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double lo = INFINITY;
+  for (int u = threadIdx.x; u < M; u += blockDim.x) lo = fmin(lo, z[u]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+  if (lane == 0) red[w] = lo;
+  __syncthreads();
+  lo = red[0];
+  for (int q = 1; q < nw; ++q) lo = fmin(lo, red[q]);
+  const double thr = lo + kTie * fabs(lo);
+  int first = M;
   for (int u = threadIdx.x; u < M; u += blockDim.x)
-    if (z[u] < best) {  // increasing u per thread: the first minimum is kept
-      best = z[u];
-      bidx = u;
+    if (z[u] <= thr) {
+      first = u;
+      break;
     }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-    const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
-    if (ob < best || (ob == best && oi < bidx)) {
-      best = ob;
-      bidx = oi;
-    }
-  }
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0) {
-    bz[w] = best;
-    bi[w] = bidx;
-  }
+  for (int o = 16; o > 0; o >>= 1) first = min(first, __shfl_xor_sync(0xffffffffu, first, o));
+  if (lane == 0) ired[w] = first;
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int q = 1; q < (int)(blockDim.x >> 5); ++q)
-      if (bz[q] < best || (bz[q] == best && bi[q] < bidx)) {
-        best = bz[q];
-        bidx = bi[q];
-      }
-    if (bidx >= M) bidx = 0;  // all chosen (not reached: k < M)
-    sel[k] = bidx;
-    chosen[bidx] = 1;
+    for (int q = 1; q < nw; ++q) first = min(first, ired[q]);
+    first = min(first, ired[0]);
+    if (first >= M) first = 0;  // every candidate chosen (not reached: k < M)
+    sel[k] = first;
+    chosen[first] = 1;
   }
 }
 
@@ -133,18 +135,18 @@ __global__ void k_ffs_update(const double *D, int M, const int *sel, int k, doub
     m[j] = fmin(m[j], row[j]);
 }
 
-// owner[j] = the first chosen representative nearest to path j
+// owner[j] = the first chosen representative within kTie of the nearest
 __global__ void k_assign(const double *D, int M, const int *sel, int K, int *owner) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
     double best = INFINITY;
+    for (int c = 0; c < K; ++c) best = fmin(best, D[(size_t)j * M + sel[c]]);
+    const double thr = best + kTie * best;
     int o = 0;
-    for (int c = 0; c < K; ++c) {
-      const double d = D[(size_t)j * M + sel[c]];
-      if (d < best) {
-        best = d;
+    for (int c = 0; c < K; ++c)
+      if (D[(size_t)j * M + sel[c]] <= thr) {
         o = c;
+        break;
       }
-    }
     owner[j] = o;
   }
 }

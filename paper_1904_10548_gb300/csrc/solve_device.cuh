@@ -826,8 +826,12 @@ __device__ void root_compute(const KParams<T> &P, int root, const Smem<T> &sm, c
   const int v = pl.r_node[root], q0 = pl.r_hp[root], np = pl.r_hp[root + 1] - q0;
   const bool data = !P.linear;
   T *Rr = W, *Hp = W + SP;
-  stage_span(Rr, P.st.s + (size_t)v * SP, SP, tm, true);
-  stage_span(Hp, P.st.hp + ((size_t)(step & 1u) * pl.hp_rows + q0) * SP, np * SP, tm, true);
+  // the root's own row from the copy its first part took before arriving:
+  // the chain that owns the root may already have written the next
+  // iteration's row into s by the time a late part gets here
+  const T *hpb = P.st.hp + (size_t)(step & 1u) * pl.hp_rows * SP;
+  stage_span(Rr, hpb + (size_t)(pl.r_hp[pl.n_roots] + root) * SP, SP, tm, true);
+  stage_span(Hp, hpb + (size_t)q0 * SP, np * SP, tm, true);
   if (tm.tid == 0) i2p[0] = P.st.inv2p[v];
   cp_wait();
   tm.sync();
@@ -1129,8 +1133,15 @@ __device__ bool group_step(const KParams<T> &P, int g, const Smem<T> &sm, const 
     // parity: a part that runs one step ahead writes the other one), then
     // its arrival
     const int m0 = lvl[1] - lvl[0];
-    T *hpg = P.st.hp + ((size_t)(step & 1u) * pl.hp_rows + pl.g_hp[g]) * SP;
+    T *hpb = P.st.hp + (size_t)(step & 1u) * pl.hp_rows * SP;
+    T *hpg = hpb + (size_t)pl.g_hp[g] * SP;
     for (int e = tm.tid; e < m0 * SP; e += tm.nt) hpg[e] = rb[e];
+    if (g == p0) {
+      // the first part copies the root's own row while no chain can write it
+      const T *src = P.st.s + (size_t)pl.r_node[root] * SP;
+      T *dst = hpb + (size_t)(pl.r_hp[pl.n_roots] + root) * SP;
+      for (int e = tm.tid; e < SP; e += tm.nt) dst[e] = __ldcg(src + e);
+    }
     tm.sync();
     if (tm.tid == 0) {
       __threadfence();

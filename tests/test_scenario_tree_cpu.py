@@ -87,3 +87,18 @@ def test_tree_invariants(branching):
             v, t = T.anc[v], t - 1
     for v in range(1, n):
         assert T.leaf_of[T.rep[v]] >= 0
+
+
+def test_ties_go_to_the_lowest_index():
+    """In one dimension the median of an even number of equally likely paths
+    is an interval: both middle paths give the same z (up to rounding), and
+    the lower index is chosen; a path midway between two representatives
+    goes to the one chosen first."""
+    from oracle.scenario_tree import first_within_tie
+    x = np.array([0.0, 1.0, 2.0, 3.0])
+    P = x[:, None, None]
+    D = tail_distances(P, np.arange(4), 0)
+    p = np.full(4, 0.25)
+    assert fast_forward_selection(D, p, 1) == [1]
+    assert first_within_tie([3.0, 1.0 + 1e-15, 1.0, 2.0]) == 1
+    assert first_within_tie([3.0, 1.0 + 1e-9, 1.0, 2.0]) == 2
