@@ -263,6 +263,7 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 KERNEL_SOURCES = ["paper_1904_10548_gb300/csrc/kernels.cuh",
                   "paper_1904_10548_gb300/csrc/solve_device.cuh",
+                  "paper_1904_10548_gb300/csrc/dense_f.cuh",
                   "paper_1904_10548_gb300/csrc/solve_kernels.cu",
                   "paper_1904_10548_gb300/csrc/mixed_kernels.cu"]
 

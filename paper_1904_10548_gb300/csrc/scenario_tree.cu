@@ -12,16 +12,23 @@
 // one representative at a time, the one with the smallest z (lowest index
 // on ties, a tie being a value within 1e-12 relative of the smallest);
 // every path of the bundle then goes to its nearest representative (first
-// chosen on ties).  Per bundle on the GPU:
-//   k_tail_dist   the bundle's distance matrix (FP64, tiles of 32 x 32 pairs,
-//                 the tails staged through shared memory);
-//   k_ffs_z       z for every candidate: one warp per candidate reads one
-//                 row of the matrix (it is symmetric) with the weights and
-//                 the current minima: the matrix streams from HBM once per
-//                 choice, the bound of this step;
-//   k_ffs_pick    the smallest z (one block), marks the choice;
-//   k_ffs_update  m_j = min(m_j, d(j, chosen));
-//   k_assign      each path's nearest representative.
+// chosen on ties).
+//
+// The bundles of a stage partition the paths, so a stage is processed with
+// one set of launches over all its bundles: the paths in bundle order
+// (pos[], offsets boff[]), every bundle's distance matrix at doff[] in one
+// array (sum of M_b^2 <= S^2 doubles).
+//   k_tail_dist  the distance matrices (FP64, tiles of 32 x 32 pairs from a
+//                tile table, the tails staged through shared memory);
+//   k_ffs_z      z for every candidate of every bundle still choosing: one
+//                warp per candidate reads one row of its bundle's matrix (it
+//                is symmetric) with the weights and the current minima: the
+//                matrices stream from HBM once per choice, the bound of this
+//                step;
+//   k_ffs_pick   one block per bundle: the smallest z, then the first
+//                candidate within the tie tolerance;
+//   k_ffs_update m_j = min(m_j, d(j, chosen));
+//   k_assign     each path's nearest representative.
 // The host keeps the bundles (index lists) and writes the tree in
 // breadth-first order.
 #include <cuda_runtime.h>
@@ -35,19 +42,36 @@
 namespace {
 
 constexpr int kTile = 32;
+// values within kTie (relative) of the smallest count as ties: they are real
+// (in one dimension the median of an even number of paths is an interval),
+// and sums added in different orders must still take the same decision
+constexpr double kTie = 1e-12;
 
-// D[a][b] = || X[idx[a], t0:] - X[idx[b], t0:] || for a bundle of M paths;
-// X is S x R row-major (R = N dim), the tail is columns [c0, R)
-__global__ void k_tail_dist(const double *X, int R, const int *idx, int M, int c0, double *D) {
+// one stage's bundles on the device
+struct StageDev {
+  const int *pos;        // S: path of each position, bundle by bundle
+  const int *boff;       // B + 1: first position of each bundle
+  const long long *doff; // B: first entry of each bundle's distance matrix
+  const int *bundle_of;  // S: bundle of each position
+  const int *K;          // B: representatives the bundle chooses
+  int B;
+};
+
+// D_b[a][c] = || X[pos[a], c0:] - X[pos[c], c0:] || for the pairs of one
+// 32 x 32 tile (tile table: bundle, tile row, tile column); X is S x R
+__global__ void k_tail_dist(const double *X, int R, StageDev sd, const int4 *tiles, int c0,
+                            double *D) {
   __shared__ double A[kTile][kTile + 1], Bt[kTile][kTile + 1];
-  const int a0 = blockIdx.y * kTile, b0 = blockIdx.x * kTile;
+  const int4 tl = tiles[blockIdx.x];
+  const int b = tl.x, first = sd.boff[b], M = sd.boff[b + 1] - first;
+  const int a0 = tl.y * kTile, b0 = tl.z * kTile;
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8 threads
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   for (int c = c0; c < R; c += kTile) {
     for (int r = ty; r < kTile; r += 8) {
-      const int a = a0 + r, b = b0 + r, col = c + tx;
-      A[r][tx] = (a < M && col < R) ? X[(size_t)idx[a] * R + col] : 0.0;
-      Bt[r][tx] = (b < M && col < R) ? X[(size_t)idx[b] * R + col] : 0.0;
+      const int a = a0 + r, e = b0 + r, col = c + tx;
+      A[r][tx] = (a < M && col < R) ? X[(size_t)sd.pos[first + a] * R + col] : 0.0;
+      Bt[r][tx] = (e < M && col < R) ? X[(size_t)sd.pos[first + e] * R + col] : 0.0;
     }
     __syncthreads();
     const int kmax = min(kTile, R - c);
@@ -61,10 +85,11 @@ __global__ void k_tail_dist(const double *X, int R, const int *idx, int M, int c
     }
     __syncthreads();
   }
+  double *Db = D + sd.doff[b];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    const int a = a0 + ty + 8 * q, b = b0 + tx;
-    if (a < M && b < M) D[(size_t)a * M + b] = sqrt(acc[q]);
+    const int a = a0 + ty + 8 * q, e = b0 + tx;
+    if (a < M && e < M) Db[(size_t)a * M + e] = sqrt(acc[q]);
   }
 }
 
@@ -74,34 +99,36 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-// z[u] = sum_j p_j min(m_j, D[u][j]) for every candidate u not yet chosen
-// (a chosen one gets +inf); one warp per candidate
-__global__ void k_ffs_z(const double *D, int M, const double *p, const double *m,
-                        const int *chosen, double *z) {
+// choice k: z[u] = sum_j p_j min(m_j, D_b[u][j]) for every position u of a
+// bundle with k < K_b (a chosen one gets +inf); one warp per position
+__global__ void k_ffs_z(const double *D, StageDev sd, int S, int k, const double *p,
+                        const double *m, const int *chosen, double *z) {
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
-  for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < M; u += warps) {
-    const double *row = D + (size_t)u * M;
+  for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < S; u += warps) {
+    const int b = sd.bundle_of[u];
+    if (k >= sd.K[b]) continue;
+    const int first = sd.boff[b], M = sd.boff[b + 1] - first, a = u - first;
+    const double *row = D + sd.doff[b] + (size_t)a * M;
+    const double *pb = p + first, *mb = m + first;
     double acc = 0.0;
-    for (int j = lane; j < M; j += 32) acc += p[j] * fmin(m[j], __ldcs(row + j));
+    for (int j = lane; j < M; j += 32) acc += pb[j] * fmin(mb[j], __ldcs(row + j));
     acc = warp_sum_d(acc);
     if (lane == 0) z[u] = chosen[u] ? INFINITY : acc;
   }
 }
 
-// values within kTie (relative) of the smallest count as ties: they are real
-// (in one dimension the median of an even number of paths is an interval),
-// and sums added in different orders must still take the same decision
-constexpr double kTie = 1e-12;
-
-// the lowest candidate whose z is within kTie of the smallest becomes
-// choice k (one block: the smallest value, then the first index within it)
-__global__ void k_ffs_pick(const double *z, int M, int k, int *chosen, int *sel) {
+// one block per bundle with k < K_b: the first candidate within kTie of the
+// smallest z becomes choice k (sel[b * kmax + k], a position in the bundle)
+__global__ void k_ffs_pick(const double *z, StageDev sd, int k, int kmax, int *chosen, int *sel) {
   __shared__ double red[32];
   __shared__ int ired[32];
+  const int b = blockIdx.x;
+  if (k >= sd.K[b]) return;
+  const int first = sd.boff[b], M = sd.boff[b + 1] - first;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   double lo = INFINITY;
-  for (int u = threadIdx.x; u < M; u += blockDim.x) lo = fmin(lo, z[u]);
+  for (int a = threadIdx.x; a < M; a += blockDim.x) lo = fmin(lo, z[first + a]);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
   if (lane == 0) red[w] = lo;
@@ -109,41 +136,48 @@ __global__ void k_ffs_pick(const double *z, int M, int k, int *chosen, int *sel)
   lo = red[0];
   for (int q = 1; q < nw; ++q) lo = fmin(lo, red[q]);
   const double thr = lo + kTie * fabs(lo);
-  int first = M;
-  for (int u = threadIdx.x; u < M; u += blockDim.x)
-    if (z[u] <= thr) {
-      first = u;
+  int fa = M;
+  for (int a = threadIdx.x; a < M; a += blockDim.x)
+    if (z[first + a] <= thr) {
+      fa = a;
       break;
     }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) first = min(first, __shfl_xor_sync(0xffffffffu, first, o));
-  if (lane == 0) ired[w] = first;
+  for (int o = 16; o > 0; o >>= 1) fa = min(fa, __shfl_xor_sync(0xffffffffu, fa, o));
+  if (lane == 0) ired[w] = fa;
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int q = 1; q < nw; ++q) first = min(first, ired[q]);
-    first = min(first, ired[0]);
-    if (first >= M) first = 0;  // every candidate chosen (not reached: k < M)
-    sel[k] = first;
-    chosen[first] = 1;
+    for (int q = 0; q < nw; ++q) fa = min(fa, ired[q]);
+    if (fa >= M) fa = 0;  // every candidate chosen (not reached: k < K_b <= M)
+    sel[b * kmax + k] = fa;
+    chosen[first + fa] = 1;
   }
 }
 
-// m_j = min(m_j, D[sel[k]][j])
-__global__ void k_ffs_update(const double *D, int M, const int *sel, int k, double *m) {
-  const double *row = D + (size_t)sel[k] * M;
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x)
-    m[j] = fmin(m[j], row[j]);
+// choice k: m_j = min(m_j, D_b[sel_b][j]) for the positions of bundles with k < K_b
+__global__ void k_ffs_update(const double *D, StageDev sd, int S, int k, int kmax,
+                             const int *sel, double *m) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < S; j += gridDim.x * blockDim.x) {
+    const int b = sd.bundle_of[j];
+    if (k >= sd.K[b]) continue;
+    const int first = sd.boff[b], M = sd.boff[b + 1] - first;
+    m[j] = fmin(m[j], D[sd.doff[b] + (size_t)sel[b * kmax + k] * M + (j - first)]);
+  }
 }
 
 // owner[j] = the first chosen representative within kTie of the nearest
-__global__ void k_assign(const double *D, int M, const int *sel, int K, int *owner) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
+__global__ void k_assign(const double *D, StageDev sd, int S, int kmax, const int *sel,
+                         int *owner) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < S; j += gridDim.x * blockDim.x) {
+    const int b = sd.bundle_of[j], K = sd.K[b];
+    const int first = sd.boff[b], M = sd.boff[b + 1] - first, a = j - first;
+    const double *Db = D + sd.doff[b] + (size_t)a * M;
     double best = INFINITY;
-    for (int c = 0; c < K; ++c) best = fmin(best, D[(size_t)j * M + sel[c]]);
+    for (int c = 0; c < K; ++c) best = fmin(best, Db[sel[b * kmax + c]]);
     const double thr = best + kTie * best;
     int o = 0;
     for (int c = 0; c < K; ++c)
-      if (D[(size_t)j * M + sel[c]] <= thr) {
+      if (Db[sel[b * kmax + c]] <= thr) {
         o = c;
         break;
       }
@@ -199,19 +233,26 @@ extern "C" int rapidnet_scenario_tree(const double *paths, const double *prob, i
       rn::set_error("scenario_tree: a path value is not finite");
       return RN_ERR_INVAL;
     }
-  int maxb = 1;
-  for (int t = 0; t < N; ++t) maxb = std::max(maxb, branching[t]);
   int rc = RN_OK;
   double *dX = nullptr, *dD = nullptr, *dp = nullptr, *dm = nullptr, *dz = nullptr;
-  int *didx = nullptr, *dch = nullptr, *dsel = nullptr, *down = nullptr;
+  int *dpos = nullptr, *dboff = nullptr, *dbof = nullptr, *dK = nullptr, *dch = nullptr;
+  int *dsel = nullptr, *down = nullptr;
+  long long *ddoff = nullptr;
+  int4 *dtiles = nullptr;
+  size_t tiles_cap = 0;
   cudaStream_t st = nullptr;
-  // breadth-first output; bundles of the current stage's nodes
+  // breadth-first output; the bundles of the current stage's nodes
   std::vector<std::vector<int>> bundles(1), next;
-  std::vector<int> anc{-1}, rep{-1}, sel(maxb), owner(S);
-  std::vector<double> pr{1.0}, val((size_t)dim, 0.0), pb, minit(S, INFINITY);
-  std::vector<int> stage_ptr{0, 1};
+  std::vector<int> anc{-1}, rep{-1}, stage_ptr{0, 1};
+  std::vector<double> pr{1.0}, val((size_t)dim, 0.0);
+  std::vector<int> pos(S), boff, bof(S), Kb, sel, owner(S);
+  std::vector<long long> doff;
+  std::vector<int4> tiles;
+  std::vector<double> pb(S), minit(S, INFINITY);
   bundles[0].resize(S);
   for (int s = 0; s < S; ++s) bundles[0][s] = s;
+  int maxb = 1;
+  for (int t = 0; t < N; ++t) maxb = std::max(maxb, branching[t]);
   ST_CUDA(cudaSetDevice(device));
   ST_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
   ST_CUDA(cudaMalloc(&dX, (size_t)S * R * sizeof(double)));
@@ -219,45 +260,82 @@ extern "C" int rapidnet_scenario_tree(const double *paths, const double *prob, i
   ST_CUDA(cudaMalloc(&dp, (size_t)S * sizeof(double)));
   ST_CUDA(cudaMalloc(&dm, (size_t)S * sizeof(double)));
   ST_CUDA(cudaMalloc(&dz, (size_t)S * sizeof(double)));
-  ST_CUDA(cudaMalloc(&didx, (size_t)S * sizeof(int)));
+  ST_CUDA(cudaMalloc(&dpos, (size_t)S * sizeof(int)));
+  ST_CUDA(cudaMalloc(&dboff, (size_t)(S + 1) * sizeof(int)));
+  ST_CUDA(cudaMalloc(&dbof, (size_t)S * sizeof(int)));
+  ST_CUDA(cudaMalloc(&dK, (size_t)S * sizeof(int)));
+  ST_CUDA(cudaMalloc(&ddoff, (size_t)S * sizeof(long long)));
   ST_CUDA(cudaMalloc(&dch, (size_t)S * sizeof(int)));
-  ST_CUDA(cudaMalloc(&dsel, (size_t)maxb * sizeof(int)));
+  ST_CUDA(cudaMalloc(&dsel, (size_t)S * maxb * sizeof(int)));
   ST_CUDA(cudaMalloc(&down, (size_t)S * sizeof(int)));
   ST_CUDA(cudaMemcpyAsync(dX, paths, (size_t)S * R * sizeof(double), cudaMemcpyHostToDevice, st));
   for (int t = 0; t < N; ++t) {
-    next.clear();
-    for (size_t off = 0; off < bundles.size(); ++off) {
-      const std::vector<int> &idx = bundles[off];
-      const int parent = stage_ptr[t] + (int)off, M = (int)idx.size();
-      const int K = std::min(branching[t], M);
-      pb.resize(M);
-      for (int a = 0; a < M; ++a) pb[a] = p[idx[a]];
-      ST_CUDA(cudaMemcpyAsync(didx, idx.data(), M * sizeof(int), cudaMemcpyHostToDevice, st));
-      ST_CUDA(cudaMemcpyAsync(dp, pb.data(), M * sizeof(double), cudaMemcpyHostToDevice, st));
-      ST_CUDA(cudaMemcpyAsync(dm, minit.data(), M * sizeof(double), cudaMemcpyHostToDevice, st));
-      ST_CUDA(cudaMemsetAsync(dch, 0, M * sizeof(int), st));
-      const int tiles = (M + kTile - 1) / kTile;
-      k_tail_dist<<<dim3(tiles, tiles), dim3(32, 8), 0, st>>>(dX, R, didx, M, t * dim, dD);
-      const int zblocks = std::min(4096, (M + 7) / 8);
-      for (int k = 0; k < K; ++k) {
-        k_ffs_z<<<zblocks, 256, 0, st>>>(dD, M, dp, dm, dch, dz);
-        k_ffs_pick<<<1, 1024, 0, st>>>(dz, M, k, dch, dsel);
-        k_ffs_update<<<std::min(1024, (M + 255) / 256), 256, 0, st>>>(dD, M, dsel, k, dm);
+    // the stage's bundles in order: positions, offsets, matrices, tiles
+    const int B = (int)bundles.size(), kmax = branching[t];
+    boff.assign(B + 1, 0);
+    doff.assign(B, 0);
+    Kb.assign(B, 0);
+    tiles.clear();
+    long long dsum = 0;
+    for (int b = 0; b < B; ++b) {
+      const int M = (int)bundles[b].size(), f = boff[b];
+      boff[b + 1] = f + M;
+      doff[b] = dsum;
+      dsum += (long long)M * M;
+      Kb[b] = std::min(kmax, M);
+      for (int a = 0; a < M; ++a) {
+        pos[f + a] = bundles[b][a];
+        bof[f + a] = b;
+        pb[f + a] = p[bundles[b][a]];
       }
-      k_assign<<<std::min(1024, (M + 255) / 256), 256, 0, st>>>(dD, M, dsel, K, down);
-      ST_CUDA(cudaGetLastError());
-      ST_CUDA(cudaMemcpyAsync(sel.data(), dsel, K * sizeof(int), cudaMemcpyDeviceToHost, st));
-      ST_CUDA(cudaMemcpyAsync(owner.data(), down, M * sizeof(int), cudaMemcpyDeviceToHost, st));
-      ST_CUDA(cudaStreamSynchronize(st));
-      for (int c = 0; c < K; ++c) {
+      const int nt = (M + kTile - 1) / kTile;
+      for (int i = 0; i < nt; ++i)
+        for (int j = 0; j < nt; ++j) tiles.push_back(make_int4(b, i, j, 0));
+    }
+    if (tiles.size() > tiles_cap) {
+      if (dtiles) cudaFree(dtiles);
+      dtiles = nullptr;
+      tiles_cap = tiles.size();
+      ST_CUDA(cudaMalloc(&dtiles, tiles_cap * sizeof(int4)));
+    }
+    ST_CUDA(cudaMemcpyAsync(dpos, pos.data(), S * sizeof(int), cudaMemcpyHostToDevice, st));
+    ST_CUDA(cudaMemcpyAsync(dboff, boff.data(), (B + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+    ST_CUDA(cudaMemcpyAsync(dbof, bof.data(), S * sizeof(int), cudaMemcpyHostToDevice, st));
+    ST_CUDA(cudaMemcpyAsync(dK, Kb.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+    ST_CUDA(cudaMemcpyAsync(ddoff, doff.data(), B * sizeof(long long), cudaMemcpyHostToDevice, st));
+    ST_CUDA(cudaMemcpyAsync(dp, pb.data(), S * sizeof(double), cudaMemcpyHostToDevice, st));
+    ST_CUDA(cudaMemcpyAsync(dm, minit.data(), S * sizeof(double), cudaMemcpyHostToDevice, st));
+    ST_CUDA(cudaMemcpyAsync(dtiles, tiles.data(), tiles.size() * sizeof(int4),
+                            cudaMemcpyHostToDevice, st));
+    ST_CUDA(cudaMemsetAsync(dch, 0, S * sizeof(int), st));
+    const StageDev sd{dpos, dboff, ddoff, dbof, dK, B};
+    k_tail_dist<<<(unsigned)tiles.size(), dim3(32, 8), 0, st>>>(dX, R, sd, dtiles, t * dim, dD);
+    const int zblocks = std::min(8192, (S + 7) / 8), eblocks = std::min(2048, (S + 255) / 256);
+    for (int k = 0; k < kmax; ++k) {
+      k_ffs_z<<<zblocks, 256, 0, st>>>(dD, sd, S, k, dp, dm, dch, dz);
+      k_ffs_pick<<<B, 1024, 0, st>>>(dz, sd, k, kmax, dch, dsel);
+      k_ffs_update<<<eblocks, 256, 0, st>>>(dD, sd, S, k, kmax, dsel, dm);
+    }
+    k_assign<<<eblocks, 256, 0, st>>>(dD, sd, S, kmax, dsel, down);
+    ST_CUDA(cudaGetLastError());
+    sel.resize((size_t)B * kmax);
+    ST_CUDA(cudaMemcpyAsync(sel.data(), dsel, (size_t)B * kmax * sizeof(int),
+                            cudaMemcpyDeviceToHost, st));
+    ST_CUDA(cudaMemcpyAsync(owner.data(), down, S * sizeof(int), cudaMemcpyDeviceToHost, st));
+    ST_CUDA(cudaStreamSynchronize(st));
+    // the children, bundle by bundle in the order of their choices
+    next.clear();
+    for (int b = 0; b < B; ++b) {
+      const int f = boff[b], M = boff[b + 1] - f, parent = stage_ptr[t] + b;
+      for (int c = 0; c < Kb[b]; ++c) {
         std::vector<int> members;
         double mass = 0.0;
         for (int a = 0; a < M; ++a)
-          if (owner[a] == c) {
-            members.push_back(idx[a]);
-            mass += p[idx[a]];
+          if (owner[f + a] == c) {
+            members.push_back(pos[f + a]);
+            mass += p[pos[f + a]];
           }
-        const int r = idx[sel[c]];
+        const int r = pos[f + sel[(size_t)b * kmax + c]];
         anc.push_back(parent);
         pr.push_back(mass);
         rep.push_back(r);
@@ -284,8 +362,9 @@ extern "C" int rapidnet_scenario_tree(const double *paths, const double *prob, i
     for (int s : bundles[off]) out->leaf_of[s] = stage_ptr[N] + (int)off;
 done:
   if (st) cudaStreamSynchronize(st);
-  for (void *q : {(void *)dX, (void *)dD, (void *)dp, (void *)dm, (void *)dz, (void *)didx,
-                  (void *)dch, (void *)dsel, (void *)down})
+  for (void *q : {(void *)dX, (void *)dD, (void *)dp, (void *)dm, (void *)dz, (void *)dpos,
+                  (void *)dboff, (void *)dbof, (void *)dK, (void *)ddoff, (void *)dch,
+                  (void *)dsel, (void *)down, (void *)dtiles})
     if (q) cudaFree(q);
   if (st) cudaStreamDestroy(st);
   return rc;
