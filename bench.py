@@ -28,6 +28,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "dual-APG iters/s & solve time to 1e-4 residual @512 scen; serving p50/p99"
+MODES = ("fp64_path", "batched", "serving", "closed_loop", "scenario_tree", "dense_wu")
 CONFIG_NAME = "barcelona512"
 WORKLOAD = ("barcelona512: synthetic Barcelona-sized network (63 tanks, 114 flows, 88 demand "
             "sectors, 17 mixing nodes, A = I), N = 24, branching [8,4,4,2,2,1,...], "
@@ -50,7 +51,9 @@ def parse():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-modes", action="store_true",
-                    help="skip the FP64-path, batched and serving sections")
+                    help="skip every section after the headline solve")
+    ap.add_argument("--modes", default=",".join(MODES),
+                    help="comma-separated sections to run after the headline solve")
     ap.add_argument("--batch-problems", type=int, default=256)
     ap.add_argument("--batch-iters", type=int, default=2000)
     ap.add_argument("--serve-iters", type=int, default=2000)
@@ -531,6 +534,34 @@ def run_closed_loop(rn, hours, max_iters):
             "final_residual_median": float(np.median(out.residual)), "precision": "mixed"}
 
 
+def run_dense_wu(rn, iters):
+    """The benchmark tree with a dense symmetric positive definite W_u: F is
+    a dense matrix, applied with FMAs in the FP64 steps and on the tensor
+    cores (TF32 head/tail split) in the FP32 steps of the mixed path."""
+    import numpy as np
+    from synthetic import make_cost, make_problem
+    pb = make_problem(CONFIG_NAME)
+    cost = make_cost(pb.net, seed=1, dense_wu=True)
+    d = pb.data
+    rel = lambda a, b: float(np.abs(a - b).max() / np.abs(b).max())
+    out = {"workload": "barcelona512 with a dense SPD W_u", "iters": iters}
+    f64 = rn.Factor(pb.net, cost, pb.tree, precision=rn.RN_PREC_FP64, power_iters=100)
+    gamma = f64.info()["gamma"]
+    f64.solve(d.x0, d.q, d.demand, d.alpha, max_iters=20)
+    a = f64.solve(d.x0, d.q, d.demand, d.alpha, max_iters=iters)
+    f64.close()
+    mx = rn.Factor(pb.net, cost, pb.tree, precision=rn.RN_PREC_MIXED, gamma=gamma)
+    mx.solve(d.x0, d.q, d.demand, d.alpha, max_iters=20)
+    b = mx.solve(d.x0, d.q, d.demand, d.alpha, max_iters=iters)
+    mx.close()
+    out.update(fp64_us_per_iter=a["apg_ms"] * 1e3 / iters,
+               mixed_us_per_iter=b["apg_ms"] * 1e3 / iters,
+               mixed_vs_fp64={"cost_rel": abs(a["cost"] - b["cost"]) / abs(a["cost"]),
+                              "u_rel": rel(b["u"], a["u"]), "y_rel": rel(b["y"], a["y"])},
+               tensor_cores="mma.sync m16n8k8 TF32, head/tail split (FP32 steps)")
+    return out
+
+
 def run_scenario_tree(rn, S, oracle_S):
     """Scenario-tree construction (paper §6.2: 10^4 Monte-Carlo price paths
     reduced into a tree) with the 512-scenario shape [8,4,4,2,2,1,...],
@@ -700,13 +731,23 @@ def main():
         accuracy = accuracy_vs_fp64(rn, pb, (x0, q, dem, alp), info["gamma"], args.iters)
 
     modes = {}
-    if not args.no_modes and world == 1:
+    want = set() if args.no_modes or world > 1 else set(args.modes.split(",")) - {""}
+    unknown = want - set(MODES)
+    if unknown:
+        raise SystemExit(f"unknown --modes entries {sorted(unknown)}; known: {list(MODES)}")
+    if "fp64_path" in want:
         modes["fp64_path"] = run_fp64_path(rn, pb, (x0, q, dem, alp, u, x, y), info["gamma"])
+    if "batched" in want:
         modes["batched"] = run_batched(rn, args.batch_problems, args.batch_iters, args.mode_tol)
+    if "serving" in want:
         modes["serving"] = run_serving(rn, args.serve_seconds, args.serve_rate,
                                        args.serve_iters, args.mode_tol)
+    if "closed_loop" in want:
         modes["closed_loop"] = run_closed_loop(rn, args.loop_hours, args.loop_iters)
+    if "scenario_tree" in want:
         modes["scenario_tree"] = run_scenario_tree(rn, args.tree_paths, args.tree_oracle_paths)
+    if "dense_wu" in want:
+        modes["dense_wu"] = run_dense_wu(rn, 300)
 
     # roofline of the dominant kernel (the persistent APG launch)
     values, flops = node_counts(net)

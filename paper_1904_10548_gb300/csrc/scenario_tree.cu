@@ -19,12 +19,13 @@
 // (pos[], offsets boff[]), every bundle's distance matrix at doff[] in one
 // array (sum of M_b^2 <= S^2 doubles).
 //   k_tail_dist  the distance matrices (FP64, tiles of 32 x 32 pairs from a
-//                tile table, the tails staged through shared memory);
-//   k_ffs_z      z for every candidate of every bundle still choosing: one
-//                warp per candidate reads one row of its bundle's matrix (it
-//                is symmetric) with the weights and the current minima: the
-//                matrices stream from HBM once per choice, the bound of this
-//                step;
+//                tile table of the upper triangle, each tile written with
+//                its mirror; the tails staged through shared memory);
+//   k_ffs_z      z for every candidate of every bundle still choosing: a
+//                warp reads the rows of four candidates of its bundle's
+//                matrix (it is symmetric) with the weights and the current
+//                minima: the matrices stream from HBM once per choice, the
+//                bound of this step;
 //   k_ffs_pick   one block per bundle: the smallest z, then the first
 //                candidate within the tie tolerance;
 //   k_ffs_update m_j = min(m_j, d(j, chosen));
@@ -58,7 +59,9 @@ struct StageDev {
 };
 
 // D_b[a][c] = || X[pos[a], c0:] - X[pos[c], c0:] || for the pairs of one
-// 32 x 32 tile (tile table: bundle, tile row, tile column); X is S x R
+// 32 x 32 tile and its mirror (tile table: bundle, tile row, tile column,
+// row <= column); X is S x R.  The differences are squared exactly alike
+// either way round, so D_b is symmetric bit for bit.
 __global__ void k_tail_dist(const double *X, int R, StageDev sd, const int4 *tiles, int c0,
                             double *D) {
   __shared__ double A[kTile][kTile + 1], Bt[kTile][kTile + 1];
@@ -85,11 +88,22 @@ __global__ void k_tail_dist(const double *X, int R, StageDev sd, const int4 *til
     }
     __syncthreads();
   }
+  // the tile, then (off the diagonal) its mirror: the table holds the tiles
+  // with tile row <= tile column only, D being symmetric
   double *Db = D + sd.doff[b];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    const int a = a0 + ty + 8 * q, e = b0 + tx;
-    if (a < M && e < M) Db[(size_t)a * M + e] = sqrt(acc[q]);
+    const int r = ty + 8 * q, a = a0 + r, e = b0 + tx;
+    const double d = sqrt(acc[q]);
+    if (a < M && e < M) Db[(size_t)a * M + e] = d;
+    A[r][tx] = d;
+  }
+  if (tl.y == tl.z) return;
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int r = ty + 8 * q, e = b0 + r, a = a0 + tx;
+    if (e < M && a < M) Db[(size_t)e * M + a] = A[tx][r];
   }
 }
 
@@ -99,22 +113,53 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
+constexpr int kZRows = 4;  // candidates per warp in k_ffs_z
+
 // choice k: z[u] = sum_j p_j min(m_j, D_b[u][j]) for every position u of a
-// bundle with k < K_b (a chosen one gets +inf); one warp per position
+// bundle with k < K_b (a chosen one gets +inf).  One warp takes kZRows
+// consecutive positions: when they share a bundle it streams their rows
+// together, reading p and m once for all of them.
 __global__ void k_ffs_z(const double *D, StageDev sd, int S, int k, const double *p,
                         const double *m, const int *chosen, double *z) {
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
-  for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < S; u += warps) {
-    const int b = sd.bundle_of[u];
-    if (k >= sd.K[b]) continue;
-    const int first = sd.boff[b], M = sd.boff[b + 1] - first, a = u - first;
-    const double *row = D + sd.doff[b] + (size_t)a * M;
-    const double *pb = p + first, *mb = m + first;
-    double acc = 0.0;
-    for (int j = lane; j < M; j += 32) acc += pb[j] * fmin(mb[j], __ldcs(row + j));
-    acc = warp_sum_d(acc);
-    if (lane == 0) z[u] = chosen[u] ? INFINITY : acc;
+  const int groups = (S + kZRows - 1) / kZRows;
+  for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < groups; g += warps) {
+    const int u0 = g * kZRows, u1 = min(u0 + kZRows, S);
+    const int b0 = sd.bundle_of[u0];
+    if (u1 - u0 == kZRows && sd.bundle_of[u1 - 1] == b0) {
+      if (k >= sd.K[b0]) continue;
+      const int first = sd.boff[b0], M = sd.boff[b0 + 1] - first;
+      const double *row = D + sd.doff[b0] + (size_t)(u0 - first) * M;
+      const double *pb = p + first, *mb = m + first;
+      double acc[kZRows];
+#pragma unroll
+      for (int r = 0; r < kZRows; ++r) acc[r] = 0.0;
+#pragma unroll 2
+      for (int j = lane; j < M; j += 32) {
+        const double pj = pb[j], mj = mb[j];
+#pragma unroll
+        for (int r = 0; r < kZRows; ++r)
+          acc[r] += pj * fmin(mj, __ldcs(row + (size_t)r * M + j));
+      }
+#pragma unroll
+      for (int r = 0; r < kZRows; ++r) {
+        const double v = warp_sum_d(acc[r]);
+        if (lane == 0) z[u0 + r] = chosen[u0 + r] ? INFINITY : v;
+      }
+      continue;
+    }
+    for (int u = u0; u < u1; ++u) {
+      const int b = sd.bundle_of[u];
+      if (k >= sd.K[b]) continue;
+      const int first = sd.boff[b], M = sd.boff[b + 1] - first;
+      const double *row = D + sd.doff[b] + (size_t)(u - first) * M;
+      const double *pb = p + first, *mb = m + first;
+      double acc = 0.0;
+      for (int j = lane; j < M; j += 32) acc += pb[j] * fmin(mb[j], __ldcs(row + j));
+      acc = warp_sum_d(acc);
+      if (lane == 0) z[u] = chosen[u] ? INFINITY : acc;
+    }
   }
 }
 
@@ -290,7 +335,7 @@ extern "C" int rapidnet_scenario_tree(const double *paths, const double *prob, i
       }
       const int nt = (M + kTile - 1) / kTile;
       for (int i = 0; i < nt; ++i)
-        for (int j = 0; j < nt; ++j) tiles.push_back(make_int4(b, i, j, 0));
+        for (int j = i; j < nt; ++j) tiles.push_back(make_int4(b, i, j, 0));
     }
     if (tiles.size() > tiles_cap) {
       if (dtiles) cudaFree(dtiles);
@@ -310,7 +355,7 @@ extern "C" int rapidnet_scenario_tree(const double *paths, const double *prob, i
     ST_CUDA(cudaMemsetAsync(dch, 0, S * sizeof(int), st));
     const StageDev sd{dpos, dboff, ddoff, dbof, dK, B};
     k_tail_dist<<<(unsigned)tiles.size(), dim3(32, 8), 0, st>>>(dX, R, sd, dtiles, t * dim, dD);
-    const int zblocks = std::min(8192, (S + 7) / 8), eblocks = std::min(2048, (S + 255) / 256);
+    const int zblocks = std::min(8192, (S + 8 * kZRows - 1) / (8 * kZRows)), eblocks = std::min(2048, (S + 255) / 256);
     for (int k = 0; k < kmax; ++k) {
       k_ffs_z<<<zblocks, 256, 0, st>>>(dD, sd, S, k, dp, dm, dch, dz);
       k_ffs_pick<<<B, 1024, 0, st>>>(dz, sd, k, kmax, dch, dsel);
