@@ -28,7 +28,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "dual-APG iters/s & solve time to 1e-4 residual @512 scen; serving p50/p99"
-MODES = ("fp64_path", "batched", "serving", "closed_loop", "scenario_tree", "dense_wu")
+MODES = ("fp64_path", "batched", "serving", "closed_loop", "scenario_tree", "dense_wu",
+         "per_node")
 CONFIG_NAME = "barcelona512"
 WORKLOAD = ("barcelona512: synthetic Barcelona-sized network (63 tanks, 114 flows, 88 demand "
             "sectors, 17 mixing nodes, A = I), N = 24, branching [8,4,4,2,2,1,...], "
@@ -61,6 +62,8 @@ def parse():
     ap.add_argument("--tree-paths", type=int, default=10000)
     ap.add_argument("--tree-oracle-paths", type=int, default=2000)
     ap.add_argument("--loop-iters", type=int, default=500)
+    ap.add_argument("--pn-iters", type=int, default=200,
+                    help="APG iterations of the timed per-node FP32 solve")
     ap.add_argument("--mode-tol", type=float, default=10.0,
                     help="stopping tolerance of the batched and served solves (and of the "
                          "FP64 solves they are compared with)")
@@ -534,6 +537,51 @@ def run_closed_loop(rn, hours, max_iters):
             "final_residual_median": float(np.median(out.residual)), "precision": "mixed"}
 
 
+def run_per_node(rn, gamma, iters32, iters64):
+    """The per-node factor form (paper §4.4 general recursion; §5.2 streams
+    per-node matrices): barcelona512, Phi_nu and K_nu streamed from HBM at
+    every iteration.  Algorithmic bytes per node and iteration: the 1,491
+    vector values of the shared form plus the 2 nu^2 matrix entries, in the
+    iteration's precision.  FP32 against FP64 of the same form at the same
+    iteration count for the error; the factor step (host, FP64) timed."""
+    import numpy as np
+    from synthetic import make_problem
+    pb = make_problem(CONFIG_NAME)
+    d = pb.data
+    nu, n = pb.net.nu, int(pb.tree.stage_ptr[-1]) - 1
+    hbm_peak, hbm_src = load_peaks()
+    rel = lambda a, b: float(np.abs(a - b).max() / np.abs(b).max())
+    out = {"workload": WORKLOAD.split(":")[0] + " (A = I), per-node matrices", "nodes": n}
+    res = {}
+    for prec, iters, bpv in ((rn.RN_PREC_FP32, iters32, 4), (rn.RN_PREC_FP64, iters64, 8)):
+        t0 = time.perf_counter()
+        f = rn.Factor(pb.net, pb.cost, pb.tree, gamma=gamma, precision=prec,
+                      factor_form=rn.RN_FACTOR_PER_NODE)
+        factor_s = time.perf_counter() - t0
+        info = f.info()
+        f.solve(d.x0, d.q, d.demand, d.alpha, max_iters=10)
+        r = f.solve(d.x0, d.q, d.demand, d.alpha, max_iters=iters)
+        acc = f.solve(d.x0, d.q, d.demand, d.alpha, max_iters=iters64)
+        f.close()
+        us = r["apg_ms"] * 1e3 / iters
+        bytes_it = (1491 + 2 * nu * nu) * bpv * n
+        gbs = bytes_it / (us * 1e-6) / 1e9
+        key = "fp32" if prec == rn.RN_PREC_FP32 else "fp64"
+        res[key] = acc
+        out[key] = {"iters": iters, "us_per_iter": us, "iters_per_s": 1e6 / us,
+                    "algorithmic_bytes_per_iter": bytes_it, "achieved_gbs": gbs,
+                    "frac_hbm": gbs / hbm_peak, "peak_source": f"{hbm_src} copy bandwidth",
+                    "factor_step_s": factor_s, "grid_ctas": info["grid_ctas"],
+                    "block_threads": info["block_threads"],
+                    "device_bytes": info["device_bytes"]}
+    out["fp32_vs_fp64"] = {"iters": iters64, "cost_rel": abs(res["fp32"]["cost"] - res["fp64"]["cost"])
+                           / abs(res["fp64"]["cost"]),
+                           "u_rel": rel(res["fp32"]["u"], res["fp64"]["u"]),
+                           "x_rel": rel(res["fp32"]["x"], res["fp64"]["x"]),
+                           "y_rel": rel(res["fp32"]["y"], res["fp64"]["y"])}
+    return out
+
+
 def run_dense_wu(rn, iters):
     """The benchmark tree with a dense symmetric positive definite W_u: F is
     a dense matrix, applied with FMAs in the FP64 steps and on the tensor
@@ -748,6 +796,8 @@ def main():
         modes["scenario_tree"] = run_scenario_tree(rn, args.tree_paths, args.tree_oracle_paths)
     if "dense_wu" in want:
         modes["dense_wu"] = run_dense_wu(rn, 300)
+    if "per_node" in want:
+        modes["per_node"] = run_per_node(rn, info["gamma"], args.pn_iters, 40)
 
     # roofline of the dominant kernel (the persistent APG launch)
     values, flops = node_counts(net)

@@ -49,15 +49,34 @@ typedef enum {
 
 typedef enum {
   RN_PREC_FP64 = 0,       /* every step of the iteration in FP64 */
-  RN_PREC_MIXED = 1       /* FP32 iteration around an FP64 reference point */
+  RN_PREC_MIXED = 1,      /* FP32 iteration around an FP64 reference point
+                             (shared-operator form only) */
+  RN_PREC_FP32 = 2        /* every step of the iteration in FP32, the factor
+                             step in FP64 (per-node form only) */
 } rn_precision;
+
+/* Form of the dual gradient (rn_opts.factor_form), paper §4.4:
+ *   RN_FACTOR_SHARED   the recursion collapsed onto one operator
+ *                      F = W^-1 - W^-1 E'(E W^-1 E')^-1 E W^-1 shared by all
+ *                      nodes, evaluated as subtree and path sums (needs
+ *                      A = I; the default where it applies);
+ *   RN_FACTOR_PER_NODE the general recursion with one matrix pair
+ *                      (Phi_nu, K_nu) per node from the factor step,
+ *                      streamed from device memory at every evaluation;
+ *                      any A, nx and nu up to 1024, precision RN_PREC_FP64
+ *                      or RN_PREC_FP32; no batched or served solves, no
+ *                      duality gap, no allocation-free entry point;
+ *   RN_FACTOR_AUTO (0) the shared form, or the per-node form for A != I or
+ *                      RN_PREC_FP32. */
+enum { RN_FACTOR_AUTO = 0, RN_FACTOR_SHARED = 1, RN_FACTOR_PER_NODE = 2 };
 
 /* Water network, paper §2.1 (eqs. dynamics, input-disturbance-coupling,
  * state-constraints, input-constraints).  Shapes: A nx*nx, B nx*nu,
  * Gd nx*nd, E ne*nu, Ed ne*nd; xmin, xmax, xs: nx; umin, umax: nu.
- * ne may be 0 (then E, Ed may be NULL).  The library requires A = I (the
- * exact discretisation of the tank mass balance, eq. tank-dynamics);
- * other A give RN_ERR_UNSUPPORTED. */
+ * ne may be 0 (then E, Ed may be NULL).  A = I (the exact discretisation
+ * of the tank mass balance, eq. tank-dynamics) is what the shared-operator
+ * form handles; any other A takes the per-node form (RN_FACTOR_AUTO) or
+ * gives RN_ERR_UNSUPPORTED (RN_FACTOR_SHARED). */
 typedef struct {
   int nx, nu, nd, ne;
   const double *A, *B, *Gd, *E, *Ed;
@@ -137,6 +156,8 @@ typedef struct {
                           replays the batch as a captured CUDA graph; 1 the
                           rule-based layout, as a graph; 2 the rule-based
                           layout launched directly (no graph) */
+  int factor_form;     /* RN_FACTOR_AUTO (0), RN_FACTOR_SHARED or
+                          RN_FACTOR_PER_NODE */
 } rn_opts;
 
 enum { RN_THETA_EQUALITY = 0, RN_THETA_SIMPLE = 1 };
@@ -197,6 +218,7 @@ typedef struct {
   long long noalloc_bytes; /* scratch that rapidnet_dual_gradient_noalloc
                               needs for this handle's tree (compare with
                               RN_NOALLOC_SCRATCH_BYTES) */
+  int factor_form;         /* RN_FACTOR_SHARED or RN_FACTOR_PER_NODE */
 } rn_factor_info;
 
 /* Factor step (paper Table 2 Engine::factorStep, §4.4): validates the
@@ -209,15 +231,34 @@ typedef struct {
  * (Q = 2 p W_u + sum of the children's P, Phi = L (L' Q L)^-1 L', L a
  * basis of ker E) in FP64 at the first node of stages 1, N/2 and N, and
  * returns RN_ERR_RANK if 2 p Phi differs from the shared operator F by more
- * than 1e-8 relative (E W_u^-1 E' too ill-conditioned).  Returns
- * RN_ERR_UNSUPPORTED, before any launch, for A != I,
+ * than 1e-8 relative (E W_u^-1 E' too ill-conditioned).  The shared form
+ * returns RN_ERR_UNSUPPORTED, before any launch, for A != I,
  * nx or nu above 256, or a tree whose schedule needs more work items than
  * the device keeps resident (one item per group of top nodes and per four
  * chains), a group larger than the shared-memory capacity, or a dense W_u
- * with chain teams narrower than nu / 2 threads (block_threads). */
+ * with chain teams narrower than nu / 2 threads (block_threads); with
+ * RN_FACTOR_AUTO and RN_PREC_FP64 such a refusal is followed by the
+ * per-node form.
+ * The per-node form (RN_FACTOR_PER_NODE; RN_FACTOR_AUTO for A != I or
+ * RN_PREC_FP32) runs the general recursion at every node on the host in
+ * FP64 (one worker thread per core), uploads Phi_nu and K_nu in the
+ * iteration's precision (rows padded to 16 bytes: 2 nu^2 values per node,
+ * 1.1 GB in FP32 for 10^4 nodes of nu = 114) and (I - Phi_nu Q_nu) E' in
+ * FP64, and estimates L by power iteration in the iteration's precision.
+ * It returns RN_ERR_INVAL where L' Q L is not positive definite at some
+ * node, RN_ERR_UNSUPPORTED for nx or nu above 1024 or RN_PREC_MIXED. */
 int rapidnet_factor(const rn_network *net, const rn_tree *tree,
                     const rn_cost *cost, const rn_opts *opts,
                     rn_factor **out);
+
+/* The per-node matrices of the general recursion (paper §4.4) as the
+ * per-node form's factor step computes them, in FP64 on the host, with no
+ * device work: Phi (n_nodes*nu*nu), K (n_nodes*nu*nu) and Mc (n_nodes*nu*ne,
+ * may be NULL) = (I - Phi_nu Q_nu) E', row-major per node, root rows zero.
+ * Caller-allocated host arrays.  RN_OK, RN_ERR_INVAL, RN_ERR_RANK. */
+int rapidnet_pernode_matrices(const rn_network *net, const rn_tree *tree,
+                              const rn_cost *cost, double *Phi, double *K,
+                              double *Mc);
 void rapidnet_factor_free(rn_factor *f);
 int rapidnet_factor_info(const rn_factor *f, rn_factor_info *info);
 

@@ -30,6 +30,10 @@ RN_ERR_DIVERGED = -7
 RN_PREC_FP64 = 0
 RN_NOALLOC_SCRATCH_BYTES = 8 << 20  # rapidnet.h
 RN_PREC_MIXED = 1
+RN_PREC_FP32 = 2
+RN_FACTOR_AUTO = 0
+RN_FACTOR_SHARED = 1
+RN_FACTOR_PER_NODE = 2
 RN_THETA_EQUALITY = 0
 RN_THETA_SIMPLE = 1
 
@@ -60,7 +64,8 @@ class rn_opts(ctypes.Structure):
     _fields_ = [("device", c_int), ("stream", c_void_p), ("precision", c_int),
                 ("gamma", c_double), ("power_iters", c_int), ("check_every", c_int),
                 ("refresh_every", c_int), ("max_ctas", c_int), ("block_threads", c_int),
-                ("wait_us", c_int), ("theta_rule", c_int), ("batch_tune", c_int)]
+                ("wait_us", c_int), ("theta_rule", c_int), ("batch_tune", c_int),
+                ("factor_form", c_int)]
 
 
 class rn_result(ctypes.Structure):
@@ -102,7 +107,8 @@ class rn_factor_info(ctypes.Structure):
                 ("n_nodes", c_int), ("n_chains", c_int), ("n_top", c_int),
                 ("grid_ctas", c_int), ("block_threads", c_int), ("L", c_double),
                 ("gamma", c_double), ("precision", c_int), ("device_bytes", c_longlong),
-                ("collapse_dev", c_double), ("noalloc_bytes", c_longlong)]
+                ("collapse_dev", c_double), ("noalloc_bytes", c_longlong),
+                ("factor_form", c_int)]
 
 
 EXPORTS = {
@@ -130,6 +136,8 @@ EXPORTS = {
     "rapidnet_server_destroy": (None, [c_void_p]),
     "rapidnet_scenario_tree": (c_int, [PD, PD, c_int, c_int, c_int, PI, c_int,
                                        POINTER(rn_tree_out)]),
+    "rapidnet_pernode_matrices": (c_int, [POINTER(rn_network), POINTER(rn_tree),
+                                          POINTER(rn_cost), PD, PD, PD]),
     "rapidnet_last_error": (ctypes.c_char_p, []),
 }
 
@@ -302,6 +310,22 @@ class Server:
             pass
 
 
+def pernode_matrices(net, cost, tree) -> dict:
+    """rapidnet_pernode_matrices: the per-node matrices of the general
+    recursion as the per-node form's factor step computes them (FP64, on the
+    host, no device work): Phi, K (n_nodes, nu, nu) and Mc (n_nodes, nu, ne)."""
+    spec = Factor.__new__(Factor)
+    Factor._marshal(spec, net, cost, tree, RN_PREC_FP64, 0.0, 0, None)
+    n, nu, ne = spec.n_nodes, spec.nu, spec.ne
+    Phi = np.zeros((n, nu, nu))
+    K = np.zeros((n, nu, nu))
+    Mc = np.zeros((n, nu, max(ne, 1)))
+    _check(load().rapidnet_pernode_matrices(ctypes.byref(spec.net_c), ctypes.byref(spec.tree_c),
+                                            ctypes.byref(spec.cost_c), _pd(Phi), _pd(K),
+                                            _pd(Mc)))
+    return {"Phi": Phi, "K": K, "Mc": Mc[:, :, :ne]}
+
+
 def scenario_tree(paths, branching, prob=None, device: int = 0) -> dict:
     """rapidnet_scenario_tree: paths (S, N, dim) host array, branching (N,);
     returns the tree (stage_ptr, anc, prob, value, rep, leaf_of)."""
@@ -368,15 +392,16 @@ class Factor:
     def __init__(self, net, cost, tree, precision: int = RN_PREC_FP64, gamma: float = 0.0,
                  device: int = 0, stream=None, power_iters: int = 0, check_every: int = 0,
                  refresh_every: int = 0, max_ctas: int = 0, block_threads: int = 0,
-                 wait_us: int = 0, theta_rule: int = 0, batch_tune: int = 0):
+                 wait_us: int = 0, theta_rule: int = 0, batch_tune: int = 0,
+                 factor_form: int = RN_FACTOR_AUTO):
         self._marshal(net, cost, tree, precision, gamma, device, stream, power_iters,
                       check_every, refresh_every, max_ctas, block_threads, wait_us, theta_rule,
-                      batch_tune)
+                      batch_tune, factor_form)
         self.h = rapidnet_factor(self.net_c, self.tree_c, self.cost_c, self.opts_c)
 
     def _marshal(self, net, cost, tree, precision, gamma, device, stream, power_iters=0,
                  check_every=0, refresh_every=0, max_ctas=0, block_threads=0, wait_us=0,
-                 theta_rule=0, batch_tune=0):
+                 theta_rule=0, batch_tune=0, factor_form=RN_FACTOR_AUTO):
         nx, nu, nd, ne = net.nx, net.nu, net.nd, net.ne
         self._keep = [
             _f64(net.A, (nx, nx)), _f64(net.B, (nx, nu)), _f64(net.Gd, (nx, nd)),
@@ -396,7 +421,7 @@ class Factor:
         st = None if stream is None else c_void_p(getattr(stream, "cuda_stream", stream))
         self.opts_c = rn_opts(device, st, precision, gamma, power_iters, check_every,
                               refresh_every, max_ctas, block_threads, wait_us, theta_rule,
-                              batch_tune)
+                              batch_tune, factor_form)
         self.nx, self.nu, self.nd, self.ne = nx, nu, nd, ne
         self.n_nodes = int(tree.stage_ptr[-1])
         self.ny = 2 * nx + nu

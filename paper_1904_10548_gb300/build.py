@@ -28,8 +28,8 @@ SOURCES += [(k, f"{os.path.splitext(k)[0]}_c{c}_d{d}.o", [f"-DRN_CVAL={c}", f"-D
             for k in ("mixed_kernels.cu", "solve_kernels.cu") for d in (0, 1)
             for c in (8, 4, 2, 1)]
 SOURCES += [(s, os.path.splitext(s)[0] + ".o", []) for s in
-            ["rapidnet.cu", "dispatch.cu", "scenario_tree.cu", "server.cpp", "plan.cpp",
-             "factor_check.cpp", "layout.cpp"]]
+            ["pernode.cu", "rapidnet.cu", "dispatch.cu", "scenario_tree.cu", "server.cpp",
+             "plan.cpp", "factor_check.cpp", "layout.cpp", "pernode_factor.cpp"]]
 
 
 def _nvcc() -> str:
@@ -64,7 +64,7 @@ def build(verbose: bool = False) -> str:
         objs = list(ex.map(lambda s: _compile(s, verbose), SOURCES))
     newest = max(os.path.getmtime(o) for o in objs)
     if not os.path.exists(LIB) or os.path.getmtime(LIB) < newest:
-        cmd = [_nvcc(), *ARCH, "-shared", "-o", LIB + ".tmp", *objs]
+        cmd = [_nvcc(), *ARCH, "-shared", "-o", LIB + ".tmp", *objs, "-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -1,0 +1,1638 @@
+// Per-node factor form of the dual gradient: kernels and host driver.
+//
+// Paper §4.4 evaluates x*(w) by a Riccati-type recursion with one set of
+// matrices per node, and §5.2 runs its products stage by stage as batched
+// matrix-vector products.  This form keeps one (Phi_nu, K_nu) pair per node
+// (from the factor step in pernode_factor.cpp) and streams both from
+// device memory at every evaluation:
+//   backward (stage N .. 1):
+//     lambda_nu = w1 + w2 + A' sum_c lambda_c
+//     g_nu      = c0_nu + w3 + B' lambda_nu + sum_c r_c
+//     m_nu      = mc_nu - Phi_nu g_nu
+//     r_nu      = -2 p_nu W_u m_nu
+//   forward (stage 1 .. N):
+//     u_nu = m_nu + K_nu u_a(nu),  x_nu = A x_a(nu) + B u_nu + Gd d_nu
+// followed at every node by the dual update of eqs. apg:1 / apg:2.  Unlike
+// the shared-operator kernels it needs neither A = I nor the collapse of
+// the per-node factors, and it is bound by the stream of 2 nu^2 matrix
+// entries per node and iteration.
+//
+// One persistent cooperative launch runs all iterations.  A block is a set
+// of teams (four warps each); every team owns whole chains (the path below
+// a node with a single leaf under it) and some top nodes (two or more
+// leaves below), and walks a fixed list of work items per iteration: its
+// chains leaf to head, the top nodes stage by stage up, then down, then its
+// chains head to leaf.  Grid barriers separate the stages of the top nodes
+// only; a chain needs no synchronisation beyond its team.  The matrices of
+// the team's items arrive in order through a ring of shared-memory slots
+// filled by bulk copies (cp.async.bulk, completion on an mbarrier per
+// slot), issued as far ahead as the ring allows, independent of the data:
+// the copy engine streams the next rows while the warps work on the
+// current ones.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <thread>
+#include <vector>
+
+#include "pernode.h"
+
+namespace rn {
+namespace {
+
+__device__ __forceinline__ unsigned long long pn_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void team_sync(int team, int nt) {
+  asm volatile("bar.sync %0, %1;" ::"r"(team + 1), "r"(nt) : "memory");
+}
+
+template <typename T>
+__device__ __forceinline__ T wsum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long res_bits(double d) {
+  return (unsigned long long)__double_as_longlong(fabs(d));
+}
+
+// mbarrier and bulk copy (PTX ISA: mbarrier.*, cp.async.bulk)
+__device__ __forceinline__ void mb_init(unsigned long long *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mb_expect_tx(unsigned long long *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mb_try_wait(unsigned long long *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes,
+                                         unsigned long long *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Ring of matrix chunks of one team.  Chunk i is rows [c rpc, (c+1) rpc)
+// of the matrix of the team's item (i / nch) mod n_items, c = i mod nch,
+// in slot i mod slots; its mbarrier completes phase (i / slots) mod 2.
+template <typename T>
+struct Ring {
+  const PnParams<T> *P;
+  T *slot0;
+  unsigned long long *bar;
+  const int *items;  // the team's items of one iteration
+  int n_items;
+  long long issued, cons, limit;
+  __device__ void issue_one(int tid) {
+    if (tid == 0) {
+      const long long i = issued;
+      const int c = (int)(i % P->nch);
+      const int item = items[(int)((i / P->nch) % n_items)];
+      const int v = item & kPnNodeMask;
+      const int rows = min(P->rpc, P->nu - c * P->rpc);
+      const unsigned bytes = (unsigned)(rows * P->ldm * (int)sizeof(T));
+      const T *src = ((item & kPnK) ? P->K : P->Phi) + (size_t)v * P->mstride +
+                     (size_t)c * P->rpc * P->ldm;
+      const int s = (int)(i % P->slots);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mb_expect_tx(bar + s, bytes);
+      bulk_g2s(slot0 + (size_t)s * P->slot_elems, src, bytes, bar + s);
+    }
+    ++issued;
+  }
+  // wait for chunk `cons` (every thread of the team); false on timeout
+  // (after an error elsewhere it returns false at once: the launch is
+  // being abandoned, and the drain at the end waits for what is in flight)
+  __device__ bool wait(long long i, bool drain = false) const {
+    unsigned long long *b = bar + (int)(i % P->slots);
+    const unsigned par = (unsigned)((i / P->slots) & 1);
+    if (mb_try_wait(b, par)) return true;
+    if (!drain && *(volatile int *)P->err != 0) return false;
+    // a copy of device memory completes by itself: the drain waits for it
+    // whatever the handle's wait bound (up to 2 s)
+    const long long limit = drain ? 2000000000LL : P->wait_ns;
+    const unsigned long long t0 = pn_ns();
+    while (!mb_try_wait(b, par))
+      if ((long long)(pn_ns() - t0) > limit) return false;
+    return true;
+  }
+  __device__ const T *slot(long long i) const {
+    return slot0 + (size_t)(i % P->slots) * P->slot_elems;
+  }
+};
+
+// out[i] = base[i] + sgn * (M_i . vec) for the nu rows of the team's current
+// item, chunk by chunk out of the ring; vec (smem) is zero beyond nu
+template <typename T>
+__device__ void ring_matvec(Ring<T> &R, const T *vec, const T *base, T sgn, T *out, T *gout,
+                            int team, int tid, int nt) {
+  const PnParams<T> &P = *R.P;
+  constexpr int VW = 16 / sizeof(T);
+  using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  for (int c = 0; c < P.nch; ++c) {
+    if (!R.wait(R.cons)) {
+      if (tid == 0) atomicCAS(P.err, 0, 5);
+      R.limit = R.issued;  // no further copies into a ring that is being abandoned
+    }
+    const T *S = R.slot(R.cons);
+    const int r0 = c * P.rpc, rows = min(P.rpc, P.nu - r0);
+    for (int rr = warp; rr < rows; rr += nw) {
+      const T *row = S + (size_t)rr * P.ldm;
+      T acc = T(0);
+      for (int k = lane * VW; k < P.ldm; k += 32 * VW) {
+        const V a = *reinterpret_cast<const V *>(row + k);
+        const V b = *reinterpret_cast<const V *>(vec + k);
+        if constexpr (sizeof(T) == 4) {
+          acc = fmaf(a.x, b.x, acc);
+          acc = fmaf(a.y, b.y, acc);
+          acc = fmaf(a.z, b.z, acc);
+          acc = fmaf(a.w, b.w, acc);
+        } else {
+          acc = fma(a.x, b.x, acc);
+          acc = fma(a.y, b.y, acc);
+        }
+      }
+      acc = wsum(acc);
+      if (lane == 0) {
+        const int i = r0 + rr;
+        const T val = (base ? base[i] : T(0)) + sgn * acc;
+        out[i] = val;
+        if (gout) gout[i] = val;
+      }
+    }
+    team_sync(team, nt);
+    ++R.cons;
+    if (R.issued < R.limit) R.issue_one(tid);
+  }
+}
+
+// sum over a compressed row
+template <typename T>
+__device__ __forceinline__ T csr_dot(const int *p, const int *ix, const T *val, int row,
+                                     const T *x) {
+  T s = T(0);
+  for (int e = p[row]; e < p[row + 1]; ++e) s = fma(val[e], x[ix[e]], s);
+  return s;
+}
+
+template <typename T>
+__device__ __forceinline__ T clampv(T v, T lo, T hi) {
+  return v < lo ? lo : (v > hi ? hi : v);
+}
+
+// grid barrier of the persistent launch (all blocks resident); false on
+// timeout or an error raised elsewhere
+__device__ bool grid_barrier(unsigned *bar, unsigned target, int *err, long long wait_ns) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    __threadfence();
+    atomicAdd(bar, 1u);
+    const unsigned long long t0 = pn_ns();
+    while (true) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+      if (v >= target) break;
+      if (*(volatile int *)err != 0) {
+        ok = 0;
+        break;
+      }
+      if ((long long)(pn_ns() - t0) > wait_ns) {
+        atomicCAS(err, 0, 4);
+        ok = 0;
+        break;
+      }
+    }
+    if (ok && *(volatile int *)err != 0) ok = 0;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// the persistent kernel: P.iters APG iterations (P.apg = 1) or one
+// evaluation of x*(w) with w = ya (P.apg = 0)
+// ---------------------------------------------------------------------------
+template <typename T>
+struct TeamVec {
+  T *sl, *sr, *lamb, *rr, *g, *mv;  // backward: child sums, own sums, g, m
+  T *xa, *ua, *x, *u;               // forward: parent values, own values
+  T *red;                           // 2 * 32 reduction slots
+};
+
+template <typename T>
+__device__ void backward_item(const PnParams<T> &P, Ring<T> &R, TeamVec<T> &V, int item,
+                              const T *ycur, const T *yprv, T beta, int team, int tid, int nt) {
+  const int v = item & kPnNodeMask;
+  const int nx = P.nx, nu = P.nu, NXP = P.NXP, NUP = P.NUP;
+  if (item & kPnTop) {
+    const int c0 = P.cbeg[v], c1 = P.cend[v];
+    for (int i = tid; i < nx; i += nt) {
+      T s = T(0);
+      for (int c = c0; c < c1; ++c) s += __ldcg(P.lam + (size_t)c * NXP + i);
+      V.sl[i] = s;
+    }
+    for (int j = tid; j < nu; j += nt) {
+      T s = T(0);
+      for (int c = c0; c < c1; ++c) s += __ldcg(P.r + (size_t)c * NUP + j);
+      V.sr[j] = s;
+    }
+  } else if (item & kPnFirst) {  // a leaf
+    for (int i = tid; i < nx; i += nt) V.sl[i] = T(0);
+    for (int j = tid; j < nu; j += nt) V.sr[j] = T(0);
+  }
+  team_sync(team, nt);
+  const bool publish = (item & (kPnTop | kPnLast)) != 0;
+  const T *yc = ycur + (size_t)v * P.YP, *yp = yprv + (size_t)v * P.YP;
+  for (int i = tid; i < nx; i += nt) {
+    const T a1 = yc[i], a2 = yc[NXP + i];
+    const T w1 = a1 + beta * (a1 - yp[i]), w2 = a2 + beta * (a2 - yp[NXP + i]);
+    const T l = (w1 + w2) + csr_dot(P.Atp, P.Ati, P.Atv, i, V.sl);
+    V.lamb[i] = l;
+    if (publish) P.lam[(size_t)v * NXP + i] = l;
+  }
+  team_sync(team, nt);
+  for (int j = tid; j < nu; j += nt) {
+    const T a3 = yc[2 * NXP + j];
+    const T w3 = a3 + beta * (a3 - yp[2 * NXP + j]);
+    const T c = P.c0 ? P.c0[(size_t)v * NUP + j] : T(0);
+    V.g[j] = (c + w3) + csr_dot(P.Btp, P.Bti, P.Btv, j, V.lamb) + V.sr[j];
+  }
+  team_sync(team, nt);
+  // m = mc - Phi g (the matrix streams through the ring)
+  ring_matvec(R, V.g, P.mc ? P.mc + (size_t)v * NUP : (const T *)nullptr, T(-1), V.mv,
+              P.m + (size_t)v * NUP, team, tid, nt);
+  const T w2p = T(-2.0 * P.prob[v]);
+  for (int j = tid; j < nu; j += nt) {
+    const T rv = w2p * csr_dot(P.Wp, P.Wi, P.Wv, j, V.mv);
+    V.rr[j] = rv;
+    if (publish) P.r[(size_t)v * NUP + j] = rv;
+  }
+  // this node's sums are its parent's child sums when the chain goes on
+  T *t = V.sl;
+  V.sl = V.lamb;
+  V.lamb = t;
+  t = V.sr;
+  V.sr = V.rr;
+  V.rr = t;
+}
+
+template <typename T>
+__device__ void forward_item(const PnParams<T> &P, Ring<T> &R, TeamVec<T> &V, int item,
+                             const T *ycur, T *yprv, T beta, bool write_out, double theta,
+                             unsigned long long &rbits, int team, int tid, int nt) {
+  const int v = item & kPnNodeMask;
+  const int nx = P.nx, nu = P.nu, NXP = P.NXP, NUP = P.NUP;
+  if (item & (kPnTop | kPnFirst)) {
+    const int a = P.anc[v];
+    if (a == 0) {
+      for (int i = tid; i < nx; i += nt) V.xa[i] = P.x0 ? P.x0[i] : T(0);
+      for (int j = tid; j < nu; j += nt) V.ua[j] = P.q ? P.q[j] : T(0);
+    } else {
+      for (int i = tid; i < nx; i += nt) V.xa[i] = __ldcg(P.xo + (size_t)a * NXP + i);
+      for (int j = tid; j < nu; j += nt) V.ua[j] = __ldcg(P.uo + (size_t)a * NUP + j);
+    }
+  }
+  team_sync(team, nt);
+  // u = m + K u_a
+  const bool top = (item & kPnTop) != 0;
+  const bool store = top || write_out || !P.apg;
+  ring_matvec(R, V.ua, P.m + (size_t)v * NUP, T(1), V.u,
+              store ? P.uo + (size_t)v * NUP : (T *)nullptr, team, tid, nt);
+  for (int i = tid; i < nx; i += nt) {
+    const T gd = P.gd ? P.gd[(size_t)v * NXP + i] : T(0);
+    const T xv = (gd + csr_dot(P.Ap, P.Ai, P.Av, i, V.xa)) + csr_dot(P.Bp, P.Bi, P.Bv, i, V.u);
+    V.x[i] = xv;
+    if (store) P.xo[(size_t)v * NXP + i] = xv;
+  }
+  if (P.uavg) {
+    for (int i = tid; i < nx; i += nt) {
+      double *xa = P.xavg + (size_t)v * NXP + i;
+      *xa = (1.0 - theta) * *xa + theta * (double)V.x[i];
+    }
+    for (int j = tid; j < nu; j += nt) {
+      double *ua = P.uavg + (size_t)v * NUP + j;
+      *ua = (1.0 - theta) * *ua + theta * (double)V.u[j];
+    }
+  }
+  if (P.apg) {
+    // y+ = prox_{gamma g*}(w + gamma H x): distance-to-set prox of the soft
+    // state terms (§4.3) through the Moreau decomposition (§4.2), box
+    // projection on the input block
+    const T g = (T)P.gamma, ig = (T)P.invgamma;
+    const T *yc = ycur + (size_t)v * P.YP;
+    T *yn = yprv + (size_t)v * P.YP;  // y^{nu-1} is read here before it is replaced
+    T n1 = T(0), n2 = T(0);
+    for (int i = tid; i < nx; i += nt) {
+      const T a1 = yc[i], a2 = yc[NXP + i];
+      const T w1 = a1 + beta * (a1 - yn[i]), w2 = a2 + beta * (a2 - yn[NXP + i]);
+      const T v1 = V.x[i] + w1 * ig, v2 = V.x[i] + w2 * ig;
+      const T e1 = v1 - clampv(v1, P.xmin[i], P.xmax[i]);
+      const T e2 = fmin(v2 - P.xs[i], T(0));
+      n1 += e1 * e1;
+      n2 += e2 * e2;
+    }
+    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    n1 = wsum(n1);
+    n2 = wsum(n2);
+    if (lane == 0) {
+      V.red[warp] = n1;
+      V.red[32 + warp] = n2;
+    }
+    team_sync(team, nt);
+    n1 = T(0);
+    n2 = T(0);
+    for (int w = 0; w < nw; ++w) {
+      n1 += V.red[w];
+      n2 += V.red[32 + w];
+    }
+    const T s1 = n1 > T(0) ? fmin(g, P.Wx / sqrt(n1)) : T(0);
+    const T s2 = n2 > T(0) ? fmin(g, P.Ws / sqrt(n2)) : T(0);
+    for (int i = tid; i < nx; i += nt) {
+      const T a1 = yc[i], a2 = yc[NXP + i];
+      const T w1 = a1 + beta * (a1 - yn[i]), w2 = a2 + beta * (a2 - yn[NXP + i]);
+      const T v1 = V.x[i] + w1 * ig, v2 = V.x[i] + w2 * ig;
+      const T y1 = (v1 - clampv(v1, P.xmin[i], P.xmax[i])) * s1;
+      const T y2 = fmin(v2 - P.xs[i], T(0)) * s2;
+      const unsigned long long b1 = res_bits((double)(y1 - w1)), b2 = res_bits((double)(y2 - w2));
+      rbits = max(rbits, max(b1, b2));
+      yn[i] = y1;
+      yn[NXP + i] = y2;
+    }
+    for (int j = tid; j < nu; j += nt) {
+      const T a3 = yc[2 * NXP + j];
+      const T w3 = a3 + beta * (a3 - yn[2 * NXP + j]);
+      const T v3 = V.u[j] + w3 * ig;
+      const T y3 = g * (v3 - clampv(v3, P.umin[j], P.umax[j]));
+      rbits = max(rbits, res_bits((double)(y3 - w3)));
+      yn[2 * NXP + j] = y3;
+    }
+  }
+  T *t = V.xa;
+  V.xa = V.x;
+  V.x = t;
+  t = V.ua;
+  V.ua = V.u;
+  V.u = t;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512, 1) k_pn_solve(PnParams<T> P) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int nt = P.team_threads, team = threadIdx.x / nt, tid = threadIdx.x % nt;
+  const int gteam = blockIdx.x * P.teams + team;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const unsigned long long t = pn_ns();
+    memcpy(P.info + 4, &t, sizeof t);
+  }
+  const size_t mb_bytes = ((size_t)P.teams * 8 * 8 + 127) & ~(size_t)127;  // up to 8 slots
+  const size_t ring_bytes = ((size_t)P.slots * P.slot_elems * sizeof(T) + 127) & ~(size_t)127;
+  const size_t vec_bytes = ((size_t)P.vec_elems * sizeof(T) + 127) & ~(size_t)127;
+  unsigned char *base = smem + mb_bytes + (size_t)team * (ring_bytes + vec_bytes);
+  unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem) + team * P.slots;
+  T *vec = reinterpret_cast<T *>(base + ring_bytes);
+  for (int e = tid; e < P.vec_elems; e += nt) vec[e] = T(0);
+  if (tid == 0) {
+    for (int s = 0; s < P.slots; ++s) mb_init(bars + s, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  TeamVec<T> V;
+  {
+    T *p = vec;
+    V.sl = p; p += P.NXP;
+    V.lamb = p; p += P.NXP;
+    V.sr = p; p += P.NUP;
+    V.rr = p; p += P.NUP;
+    V.g = p; p += P.NUP;
+    V.mv = p; p += P.NUP;
+    V.red = p;
+    V.xa = V.sl;  // the forward reuses the backward's region
+    V.x = V.lamb;
+    V.ua = V.sr;
+    V.u = V.rr;
+  }
+  const int *seg = P.seg + (size_t)gteam * (P.n_seg + 1);
+  Ring<T> R;
+  R.P = &P;
+  R.slot0 = reinterpret_cast<T *>(base);
+  R.bar = bars;
+  R.items = P.items + seg[0];
+  R.n_items = seg[P.n_seg] - seg[0];
+  R.issued = R.cons = 0;
+  R.limit = R.n_items > 0 ? (long long)R.n_items * P.nch * (P.apg ? P.iters : 1) : 0;
+  for (int s = 0; s < P.slots && R.issued < R.limit; ++s) R.issue_one(tid);
+  unsigned nbar = 0;
+  int it = 0, ci = 0, reason = 0;  // reason: 0 max iters, 1 converged, 2 non-finite, 3 wait
+  bool pend = false;
+  const int TT = P.t_top;
+  const int n_it = P.apg ? P.iters : 1;
+  for (; it < n_it; ++it) {
+    const T *ycur = (it & 1) ? P.yb : P.ya;
+    T *yprv = P.apg ? ((it & 1) ? P.ya : P.yb) : P.ya;
+    const T beta = P.apg ? (T)P.beta[it] : T(0);
+    const double theta = P.apg ? P.theta[it] : 1.0;
+    const bool check = P.apg && (((it + 1) % P.check_every) == 0 || it + 1 == P.iters);
+    const bool wout = !P.apg || check;
+    unsigned long long rbits = 0ull;
+    // chains, leaf to head
+    for (int k = seg[0]; k < seg[1]; ++k)
+      backward_item(P, R, V, P.items[k], ycur, yprv, beta, team, tid, nt);
+    if (!grid_barrier(P.bar, ++nbar * gridDim.x, P.err, P.wait_ns)) {
+      reason = 3;
+      break;
+    }
+    if (pend) {  // the check of the previous iteration, now that every block added to it
+      pend = false;
+      const double rv =
+          __longlong_as_double((long long)__ldcg(P.res + ci - 1)) * P.invgamma;
+      if (!(rv <= 1.7976931348623157e308)) {
+        reason = 2;
+        break;
+      }
+      if (P.tol > 0.0 && rv <= P.tol) {
+        reason = 1;
+        break;
+      }
+    }
+    bool ok = true;
+    // top nodes, stage T .. 1 (a node and its forward step have the same team)
+    for (int s = 1; s <= TT && ok; ++s) {
+      for (int k = seg[s]; k < seg[s + 1]; ++k)
+        backward_item(P, R, V, P.items[k], ycur, yprv, beta, team, tid, nt);
+      if (s < TT) ok = grid_barrier(P.bar, ++nbar * gridDim.x, P.err, P.wait_ns);
+    }
+    // top nodes, stage 1 .. T
+    for (int s = TT + 1; s <= 2 * TT && ok; ++s) {
+      for (int k = seg[s]; k < seg[s + 1]; ++k)
+        forward_item(P, R, V, P.items[k], ycur, yprv, beta, wout, theta, rbits, team, tid, nt);
+      ok = grid_barrier(P.bar, ++nbar * gridDim.x, P.err, P.wait_ns);
+    }
+    if (!ok) {
+      reason = 3;
+      break;
+    }
+    // chains, head to leaf
+    for (int k = seg[2 * TT + 1]; k < seg[2 * TT + 2]; ++k)
+      forward_item(P, R, V, P.items[k], ycur, yprv, beta, wout, theta, rbits, team, tid, nt);
+    if (check) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long b = __shfl_xor_sync(0xffffffffu, rbits, o);
+        rbits = b > rbits ? b : rbits;
+      }
+      if ((tid & 31) == 0 && rbits) atomicMax(P.res + ci, rbits);
+      ++ci;
+      pend = true;
+    }
+  }
+  if (reason == 0 && pend) {
+    if (grid_barrier(P.bar, ++nbar * gridDim.x, P.err, P.wait_ns)) {
+      const double rv =
+          __longlong_as_double((long long)__ldcg(P.res + ci - 1)) * P.invgamma;
+      if (!(rv <= 1.7976931348623157e308))
+        reason = 2;
+      else if (P.tol > 0.0 && rv <= P.tol)
+        reason = 1;
+    } else {
+      reason = 3;
+    }
+  }
+  // no bulk copy may still be writing into this block's memory when it ends
+  for (long long i = R.cons; i < R.issued; ++i) R.wait(i, true);
+  __syncthreads();
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    P.info[0] = P.apg ? it : 1;
+    P.info[1] = ci;
+    P.info[2] = reason;
+    const unsigned long long t = pn_ns();
+    memcpy(P.info + 6, &t, sizeof t);
+  }
+}
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// kernels around the persistent launch (one block or warp per node)
+// ---------------------------------------------------------------------------
+struct PnPrepArgs {
+  const double *prob, *demand, *alpha, *alpha0;  // demand n x nd, alpha n x nu
+  const int *Gp, *Gi;                            // Gd rows
+  const double *Gv;
+  const double *Mc, *Sd;                         // n x nu x ne, ne x nd
+  double W_alpha;
+  int nx, nu, nd, ne, n, NXP, NUP;
+};
+
+// c0 = p W_alpha (alpha0 + alpha), gd = Gd d, mc = Mc (Sd d) per node
+// (FP64, stored in T); the root row is zero
+template <typename T>
+__global__ void k_pn_prep(PnPrepArgs a, T *c0, T *mc, T *gd) {
+  extern __shared__ double sv[];  // ne
+  for (int v = blockIdx.x; v < a.n; v += gridDim.x) {
+    const double *d = a.demand + (size_t)v * a.nd;
+    __syncthreads();
+    for (int e = threadIdx.x; e < a.ne; e += blockDim.x) {
+      double s = 0.0;
+      for (int k = 0; k < a.nd; ++k) s += a.Sd[(size_t)e * a.nd + k] * d[k];
+      sv[e] = s;
+    }
+    __syncthreads();
+    const bool root = v == 0;
+    for (int j = threadIdx.x; j < a.NUP; j += blockDim.x) {
+      double cv = 0.0, mv = 0.0;
+      if (!root && j < a.nu) {
+        cv = a.prob[v] * a.W_alpha * (a.alpha0[j] + a.alpha[(size_t)v * a.nu + j]);
+        const double *row = a.Mc + ((size_t)v * a.nu + j) * a.ne;
+        for (int e = 0; e < a.ne; ++e) mv += row[e] * sv[e];
+      }
+      c0[(size_t)v * a.NUP + j] = (T)cv;
+      mc[(size_t)v * a.NUP + j] = (T)mv;
+    }
+    for (int i = threadIdx.x; i < a.NXP; i += blockDim.x) {
+      double gv = 0.0;
+      if (!root && i < a.nx)
+        for (int e = a.Gp[i]; e < a.Gp[i + 1]; ++e) gv += a.Gv[e] * d[a.Gi[e]];
+      gd[(size_t)v * a.NXP + i] = (T)gv;
+    }
+  }
+}
+
+// y^0 = y^{-1} = src (n x (2nx + nu) doubles, row 0 ignored) or 0, in the
+// padded layout; also the T copies of x0 and q
+template <typename T>
+__global__ void k_pn_init(int n, int nx, int nu, int NXP, int YP, const double *src, T *ya,
+                          T *yb, const double *x0, const double *q, T *x0t, T *qt) {
+  const int ny = 2 * nx + nu;
+  for (int v = blockIdx.x; v < n; v += gridDim.x)
+    for (int e = threadIdx.x; e < YP; e += blockDim.x) {
+      int k = -1;
+      if (e < nx) k = e;
+      else if (e >= NXP && e < NXP + nx) k = nx + (e - NXP);
+      else if (e >= 2 * NXP && e < 2 * NXP + nu) k = 2 * nx + (e - 2 * NXP);
+      const T val = (v > 0 && k >= 0 && src) ? (T)src[(size_t)v * ny + k] : T(0);
+      ya[(size_t)v * YP + e] = val;
+      yb[(size_t)v * YP + e] = val;
+    }
+  if (blockIdx.x == 0 && x0t) {
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) x0t[i] = (T)x0[i];
+    for (int j = threadIdx.x; j < nu; j += blockDim.x) qt[j] = (T)q[j];
+  }
+}
+
+// outputs in the caller's layout (doubles): u, x (root rows q, x0), y
+// (root row 0); any of them may be null
+template <typename T>
+__global__ void k_pn_gather(int n, int nx, int nu, int NXP, int NUP, int YP, const T *uo,
+                            const T *xo, const T *y, const double *q, const double *x0,
+                            double *u, double *x, double *yout) {
+  const int ny = 2 * nx + nu;
+  for (int v = blockIdx.x; v < n; v += gridDim.x) {
+    if (u)
+      for (int j = threadIdx.x; j < nu; j += blockDim.x)
+        u[(size_t)v * nu + j] = v == 0 ? q[j] : (double)uo[(size_t)v * NUP + j];
+    if (x)
+      for (int i = threadIdx.x; i < nx; i += blockDim.x)
+        x[(size_t)v * nx + i] = v == 0 ? x0[i] : (double)xo[(size_t)v * NXP + i];
+    if (yout)
+      for (int k = threadIdx.x; k < ny; k += blockDim.x) {
+        const int e = k < nx ? k : (k < 2 * nx ? NXP + (k - nx) : 2 * NXP + (k - 2 * nx));
+        yout[(size_t)v * ny + k] = v == 0 ? 0.0 : (double)y[(size_t)v * YP + e];
+      }
+  }
+}
+
+template <typename T>
+__global__ void k_pn_gather_avg(int n, int nx, int nu, int NXP, int NUP, const double *ua,
+                                const double *xa, const double *q, const double *x0, double *u,
+                                double *x) {
+  for (int v = blockIdx.x; v < n; v += gridDim.x) {
+    for (int j = threadIdx.x; j < nu; j += blockDim.x)
+      u[(size_t)v * nu + j] = v == 0 ? q[j] : ua[(size_t)v * NUP + j];
+    for (int i = threadIdx.x; i < nx; i += blockDim.x)
+      x[(size_t)v * nx + i] = v == 0 ? x0[i] : xa[(size_t)v * NXP + i];
+  }
+}
+
+__device__ __forceinline__ double pn_splitmix_unit(unsigned long long i) {
+  // SplitMix64 (Steele, Lea, Flood 2014) from seed 0, top 53 bits
+  unsigned long long z = (i + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+}
+
+// power iteration start: 1 + SplitMix64 over the non-root dual entries in
+// node order
+template <typename T>
+__global__ void k_pn_power_start(int n, int nx, int nu, int NXP, int YP, T *ya) {
+  const int ny = 2 * nx + nu;
+  for (int v = blockIdx.x + 1; v < n; v += gridDim.x)
+    for (int k = threadIdx.x; k < ny; k += blockDim.x) {
+      const int e = k < nx ? k : (k < 2 * nx ? NXP + (k - nx) : 2 * NXP + (k - 2 * nx));
+      ya[(size_t)v * YP + e] = (T)(1.0 + pn_splitmix_unit((unsigned long long)(v - 1) * ny + k));
+    }
+}
+
+// per-block partial sums of |H x|^2 = sum 2 |x_nu|^2 + |u_nu|^2
+template <typename T>
+__global__ void k_pn_norm2(int n, int nx, int nu, int NXP, int NUP, const T *uo, const T *xo,
+                           double *partial) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (int v = blockIdx.x + 1; v < n; v += gridDim.x) {
+    for (int j = threadIdx.x; j < nu; j += blockDim.x) {
+      const double a = uo[(size_t)v * NUP + j];
+      acc += a * a;
+    }
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+      const double a = xo[(size_t)v * NXP + i];
+      acc += 2.0 * a * a;
+    }
+  }
+  acc = wsum(acc);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    partial[blockIdx.x] = t;
+  }
+}
+
+// v = -H x / |H x| as the next input (the partial sums of every block
+// are added up again by each block)
+template <typename T>
+__global__ void k_pn_power_scale(int n, int nx, int nu, int NXP, int NUP, int YP, const T *uo,
+                                 const T *xo, const double *partial, int nparts, T *ya,
+                                 double *norm2) {
+  __shared__ double inv;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int b = 0; b < nparts; ++b) t += partial[b];
+    inv = 1.0 / sqrt(t);
+    if (blockIdx.x == 0) *norm2 = t;
+  }
+  __syncthreads();
+  for (int v = blockIdx.x + 1; v < n; v += gridDim.x) {
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+      const T a = (T)(-(double)xo[(size_t)v * NXP + i] * inv);
+      ya[(size_t)v * YP + i] = a;
+      ya[(size_t)v * YP + NXP + i] = a;
+    }
+    for (int j = threadIdx.x; j < nu; j += blockDim.x)
+      ya[(size_t)v * YP + 2 * NXP + j] = (T)(-(double)uo[(size_t)v * NUP + j] * inv);
+  }
+}
+
+struct PnCostArgs {
+  const int *anc;
+  const double *prob, *alpha, *alpha0, *xmin, *xmax, *xs, *umin, *umax;
+  const int *Wp, *Wi;
+  const double *Wv;
+  const double *u, *x;  // caller layout, root rows q, x0
+  double W_alpha, Wx, Ws;
+  int n, nx, nu;
+};
+
+// per-block partials: smooth cost, soft cost, max input-box violation (one
+// warp per node, FP64)
+__global__ void k_pn_cost(PnCostArgs a, double *partial) {
+  __shared__ double sh[3][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double sm = 0.0, so = 0.0, vb = 0.0;
+  for (int v = 1 + blockIdx.x * nw + warp; v < a.n; v += gridDim.x * nw) {
+    const double *u = a.u + (size_t)v * a.nu, *ua = a.u + (size_t)a.anc[v] * a.nu;
+    const double *x = a.x + (size_t)v * a.nx;
+    const double p = a.prob[v];
+    double lin = 0.0, quad = 0.0, dx = 0.0, ds = 0.0;
+    for (int j = lane; j < a.nu; j += 32) {
+      lin += p * a.W_alpha * (a.alpha0[j] + a.alpha[(size_t)v * a.nu + j]) * u[j];
+      double wd = 0.0;
+      for (int e = a.Wp[j]; e < a.Wp[j + 1]; ++e) wd += a.Wv[e] * (u[a.Wi[e]] - ua[a.Wi[e]]);
+      quad += (u[j] - ua[j]) * wd;
+      vb = fmax(vb, fmax(a.umin[j] - u[j], u[j] - a.umax[j]));
+    }
+    for (int i = lane; i < a.nx; i += 32) {
+      const double e1 = x[i] - fmin(fmax(x[i], a.xmin[i]), a.xmax[i]);
+      const double e2 = fmin(x[i] - a.xs[i], 0.0);
+      dx += e1 * e1;
+      ds += e2 * e2;
+    }
+    lin = wsum(lin);
+    quad = wsum(quad);
+    dx = wsum(dx);
+    ds = wsum(ds);
+    if (lane == 0) {
+      sm += lin + p * quad;
+      so += a.Wx * sqrt(dx) + a.Ws * sqrt(ds);
+    }
+  }
+  vb = fmax(vb, 0.0);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) vb = fmax(vb, __shfl_xor_sync(0xffffffffu, vb, o));
+  if (lane == 0) {
+    sh[0][warp] = sm;
+    sh[1][warp] = so;
+    sh[2][warp] = vb;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int w = 0; w < nw; ++w) {
+      s0 += sh[0][w];
+      s1 += sh[1][w];
+      s2 = fmax(s2, sh[2][w]);
+    }
+    partial[3 * blockIdx.x] = s0;
+    partial[3 * blockIdx.x + 1] = s1;
+    partial[3 * blockIdx.x + 2] = s2;
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host driver
+// ---------------------------------------------------------------------------
+struct PnFactor {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool fp32 = false;
+  int nx = 0, nu = 0, nd = 0, ne = 0, n = 0, N = 0, NXP = 0, NUP = 0, YP = 0, ldm = 0;
+  long long mstride = 0;
+  double W_alpha = 0.0, Wx = 0.0, Ws = 0.0;
+  int theta_rule = 0, check_every = 10;
+  double gamma = 0.0, L = 0.0;
+  long long wait_ns = 0;
+  std::vector<void *> allocs;
+  long long bytes = 0;
+  // tree and operators
+  int *anc = nullptr, *cbeg = nullptr, *cend = nullptr;
+  double *prob = nullptr;
+  int *Ap = nullptr, *Ai = nullptr, *Atp = nullptr, *Ati = nullptr, *Bp = nullptr, *Bi = nullptr;
+  int *Btp = nullptr, *Bti = nullptr, *Wp = nullptr, *Wi = nullptr, *Gp = nullptr, *Gi = nullptr;
+  void *Av = nullptr, *Atv = nullptr, *Bv = nullptr, *Btv = nullptr, *Wv = nullptr;
+  double *Wv64 = nullptr, *Gv = nullptr;
+  void *xmin = nullptr, *xmax = nullptr, *xs = nullptr, *umin = nullptr, *umax = nullptr;
+  double *bnd64 = nullptr;  // xmin, xmax, xs (nx each), umin, umax (nu each)
+  double *alpha0 = nullptr;
+  void *Phi = nullptr, *K = nullptr;
+  double *Mc = nullptr, *Sd = nullptr;
+  // per solve
+  void *c0 = nullptr, *mc = nullptr, *gd = nullptr, *x0t = nullptr, *qt = nullptr;
+  double *x0 = nullptr, *q = nullptr, *alpha = nullptr;  // copies of the last data
+  void *ya = nullptr, *yb = nullptr, *m = nullptr, *lam = nullptr, *r = nullptr;
+  void *uo = nullptr, *xo = nullptr;
+  double *uavg = nullptr, *xavg = nullptr;
+  double *beta = nullptr;
+  int beta_cap = 0;
+  unsigned long long *res = nullptr;
+  int res_cap = 0;
+  unsigned *bar = nullptr;
+  int *err = nullptr, *info = nullptr;
+  double *partial = nullptr, *norm2 = nullptr;
+  bool have_data = false;
+  // schedule and launch layout
+  int *items = nullptr, *seg = nullptr;
+  int n_seg = 0, t_top = 0, n_chains = 0, n_top = 0;
+  int grid = 0, block = 0, team_threads = 128, teams = 4;
+  int rpc = 0, nch = 0, slots = 0, slot_elems = 0, vec_elems = 0;
+  size_t smem = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  ~PnFactor() {
+    cudaSetDevice(device);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    for (void *p : allocs) cudaFree(p);
+  }
+};
+
+namespace {
+
+constexpr int kPnParts = 304;  // blocks of the reductions
+
+#define PN_CUDA(call)                                                       \
+  do {                                                                      \
+    cudaError_t e_ = (call);                                                \
+    if (e_ != cudaSuccess) {                                                \
+      set_error("per-node path: %s failed: %s", #call, cudaGetErrorString(e_)); \
+      return e_ == cudaErrorMemoryAllocation ? RN_ERR_NOMEM : RN_ERR_CUDA;  \
+    }                                                                       \
+  } while (0)
+
+template <typename U>
+int pn_alloc(PnFactor *f, U **p, size_t count) {
+  void *q = nullptr;
+  PN_CUDA(cudaMalloc(&q, std::max<size_t>(1, count) * sizeof(U)));
+  f->allocs.push_back(q);
+  f->bytes += (long long)(std::max<size_t>(1, count) * sizeof(U));
+  *p = static_cast<U *>(q);
+  return RN_OK;
+}
+
+template <typename U>
+int pn_upload(PnFactor *f, U **p, const std::vector<U> &h) {
+  int rc = pn_alloc(f, p, h.size());
+  if (rc) return rc;
+  if (!h.empty())
+    PN_CUDA(cudaMemcpyAsync(*p, h.data(), h.size() * sizeof(U), cudaMemcpyHostToDevice, f->stream));
+  return RN_OK;
+}
+
+// a vector of T (float or double) from doubles, uploaded
+template <typename T>
+int pn_upload_t(PnFactor *f, void **p, const double *src, size_t count) {
+  std::vector<T> h(src, src + count);
+  T *d = nullptr;
+  int rc = pn_upload(f, &d, h);
+  *p = d;
+  return rc;
+}
+
+int pn_upload_csr(PnFactor *f, const Csr &c, int **p, int **i, void **v, bool fp32,
+                  double **v64 = nullptr) {
+  int rc;
+  if ((rc = pn_upload(f, p, c.ptr)) || (rc = pn_upload(f, i, c.idx))) return rc;
+  rc = fp32 ? pn_upload_t<float>(f, v, c.val.data(), c.val.size())
+            : pn_upload_t<double>(f, v, c.val.data(), c.val.size());
+  if (rc) return rc;
+  if (v64) rc = pn_upload(f, v64, c.val);
+  return rc;
+}
+
+template <typename T>
+PnParams<T> pn_params(const PnFactor *f) {
+  PnParams<T> P{};
+  P.nx = f->nx;
+  P.nu = f->nu;
+  P.n = f->n;
+  P.NXP = f->NXP;
+  P.NUP = f->NUP;
+  P.YP = f->YP;
+  P.ldm = f->ldm;
+  P.mstride = f->mstride;
+  P.anc = f->anc;
+  P.cbeg = f->cbeg;
+  P.cend = f->cend;
+  P.prob = f->prob;
+  P.Ap = f->Ap;
+  P.Ai = f->Ai;
+  P.Atp = f->Atp;
+  P.Ati = f->Ati;
+  P.Bp = f->Bp;
+  P.Bi = f->Bi;
+  P.Btp = f->Btp;
+  P.Bti = f->Bti;
+  P.Wp = f->Wp;
+  P.Wi = f->Wi;
+  P.Av = static_cast<const T *>(f->Av);
+  P.Atv = static_cast<const T *>(f->Atv);
+  P.Bv = static_cast<const T *>(f->Bv);
+  P.Btv = static_cast<const T *>(f->Btv);
+  P.Wv = static_cast<const T *>(f->Wv);
+  P.xmin = static_cast<const T *>(f->xmin);
+  P.xmax = static_cast<const T *>(f->xmax);
+  P.xs = static_cast<const T *>(f->xs);
+  P.umin = static_cast<const T *>(f->umin);
+  P.umax = static_cast<const T *>(f->umax);
+  P.Wx = (T)f->Wx;
+  P.Ws = (T)f->Ws;
+  P.Phi = static_cast<const T *>(f->Phi);
+  P.K = static_cast<const T *>(f->K);
+  P.ya = static_cast<T *>(f->ya);
+  P.yb = static_cast<T *>(f->yb);
+  P.m = static_cast<T *>(f->m);
+  P.lam = static_cast<T *>(f->lam);
+  P.r = static_cast<T *>(f->r);
+  P.uo = static_cast<T *>(f->uo);
+  P.xo = static_cast<T *>(f->xo);
+  P.bar = f->bar;
+  P.err = f->err;
+  P.info = f->info;
+  P.wait_ns = f->wait_ns;
+  P.gamma = f->gamma;
+  P.invgamma = f->gamma > 0.0 ? 1.0 / f->gamma : 0.0;
+  P.items = f->items;
+  P.seg = f->seg;
+  P.n_seg = f->n_seg;
+  P.t_top = f->t_top;
+  P.team_threads = f->team_threads;
+  P.teams = f->teams;
+  P.rpc = f->rpc;
+  P.nch = f->nch;
+  P.slots = f->slots;
+  P.slot_elems = f->slot_elems;
+  P.vec_elems = f->vec_elems;
+  return P;
+}
+
+template <typename T>
+int pn_launch(PnFactor *f, PnParams<T> &P) {
+  PN_CUDA(cudaMemsetAsync(f->bar, 0, sizeof(unsigned), f->stream));
+  void *args[] = {&P};
+  PN_CUDA(cudaLaunchCooperativeKernel((const void *)k_pn_solve<T>, f->grid, f->block, args,
+                                      f->smem, f->stream));
+  return RN_OK;
+}
+
+int pn_check_err(PnFactor *f) {
+  int e = 0;
+  PN_CUDA(cudaMemcpyAsync(&e, f->err, sizeof(int), cudaMemcpyDeviceToHost, f->stream));
+  PN_CUDA(cudaStreamSynchronize(f->stream));
+  if (e) {
+    PN_CUDA(cudaMemsetAsync(f->err, 0, sizeof(int), f->stream));
+    set_error("per-node path: a device-side wait gave up after %.3g s (%s)", f->wait_ns * 1e-9,
+              e == 4 ? "grid barrier" : "matrix copy");
+    return RN_ERR_TIMEOUT;
+  }
+  return RN_OK;
+}
+
+// one evaluation of x*(w), w in ya; `linear` drops every data term
+template <typename T>
+int pn_eval(PnFactor *f, bool linear) {
+  PnParams<T> P = pn_params<T>(f);
+  P.apg = 0;
+  P.iters = 1;
+  P.check_every = 1;
+  if (!linear) {
+    P.c0 = static_cast<const T *>(f->c0);
+    P.mc = static_cast<const T *>(f->mc);
+    P.gd = static_cast<const T *>(f->gd);
+    P.x0 = static_cast<const T *>(f->x0t);
+    P.q = static_cast<const T *>(f->qt);
+  }
+  return pn_launch<T>(f, P);
+}
+
+template <typename T>
+int pn_power(PnFactor *f, int iters, double *L) {
+  const int nb = std::max(1, std::min(f->n - 1, 4096));
+  k_pn_power_start<T><<<nb, 128, 0, f->stream>>>(f->n, f->nx, f->nu, f->NXP, f->YP,
+                                                static_cast<T *>(f->ya));
+  PN_CUDA(cudaGetLastError());
+  for (int k = 0; k < iters; ++k) {
+    int rc = pn_eval<T>(f, true);
+    if (rc) return rc;
+    k_pn_norm2<T><<<kPnParts, 256, 0, f->stream>>>(f->n, f->nx, f->nu, f->NXP, f->NUP,
+                                                   static_cast<const T *>(f->uo),
+                                                   static_cast<const T *>(f->xo), f->partial);
+    k_pn_power_scale<T><<<nb, 128, 0, f->stream>>>(
+        f->n, f->nx, f->nu, f->NXP, f->NUP, f->YP, static_cast<const T *>(f->uo),
+        static_cast<const T *>(f->xo), f->partial, kPnParts, static_cast<T *>(f->ya), f->norm2);
+    PN_CUDA(cudaGetLastError());
+  }
+  double n2 = 0.0;
+  PN_CUDA(cudaMemcpyAsync(&n2, f->norm2, sizeof(double), cudaMemcpyDeviceToHost, f->stream));
+  int rc = pn_check_err(f);
+  if (rc) return rc;
+  *L = std::sqrt(n2);
+  return RN_OK;
+}
+
+}  // namespace
+
+int pn_validate(const rn_network *net, const rn_tree *tree, const rn_cost *cost) {
+  if (!net || !tree || !cost) {
+    set_error("network, tree or cost is NULL");
+    return RN_ERR_INVAL;
+  }
+  if (std::max(net->nx, net->nu) > kPnMaxDim) {
+    set_error("per-node path: nx, nu <= %d", kPnMaxDim);
+    return RN_ERR_UNSUPPORTED;
+  }
+  Plan p;
+  return build_plan(tree, p);  // the tree's structure (see rn_tree)
+}
+
+namespace {
+
+// Work lists of the teams (see PnParams): chains by longest-first onto the
+// least loaded team (teams taken in an order that visits every block before
+// a second team of any block), top nodes of a stage one per team in the
+// same order.
+int pn_schedule(PnFactor *f, const rn_tree *tree, int n_teams) {
+  const int n = tree->n_nodes, N = tree->N;
+  std::vector<int> stage(n), cbeg(n, 0), cend(n, 0), nleaf(n, 0);
+  for (int t = 0; t <= N; ++t)
+    for (int v = tree->stage_ptr[t]; v < tree->stage_ptr[t + 1]; ++v) stage[v] = t;
+  for (int v = 1; v < n; ++v) {
+    const int a = tree->anc[v];
+    if (cend[a] == 0) cbeg[a] = v;
+    cend[a] = v + 1;
+  }
+  for (int v = n - 1; v >= 1; --v) {
+    if (cend[v] == 0) nleaf[v] = 1;
+    nleaf[tree->anc[v]] += nleaf[v];
+  }
+  std::vector<char> top(n, 0);
+  int t_top = 0;
+  for (int v = 1; v < n; ++v)
+    if (nleaf[v] >= 2) {
+      top[v] = 1;
+      t_top = std::max(t_top, stage[v]);
+    }
+  // chains: head (parent is the root or a top node) down to the leaf
+  std::vector<std::vector<int>> chains;
+  for (int v = 1; v < n; ++v)
+    if (!top[v] && (tree->anc[v] == 0 || top[tree->anc[v]])) {
+      std::vector<int> c{v};
+      int u = v;
+      while (cend[u] > 0) {
+        u = cbeg[u];
+        c.push_back(u);
+      }
+      chains.push_back(std::move(c));
+    }
+  const int grid = std::max(1, n_teams / f->teams);
+  std::vector<int> ord(n_teams);
+  for (int k = 0; k < n_teams; ++k) ord[k] = (k % grid) * f->teams + (k / grid);
+  std::vector<int> corder(chains.size());
+  std::iota(corder.begin(), corder.end(), 0);
+  std::stable_sort(corder.begin(), corder.end(),
+                   [&](int a, int b) { return chains[a].size() > chains[b].size(); });
+  std::vector<long long> load(n_teams, 0);
+  std::vector<std::vector<int>> team_chains(n_teams);
+  {
+    // least loaded team, ties to the earliest in the spread order
+    std::vector<std::pair<long long, int>> heap;
+    for (int k = 0; k < n_teams; ++k) heap.push_back({0, k});
+    auto cmp = [](const std::pair<long long, int> &a, const std::pair<long long, int> &b) {
+      return a.first != b.first ? a.first > b.first : a.second > b.second;
+    };
+    std::make_heap(heap.begin(), heap.end(), cmp);
+    for (int c : corder) {
+      std::pop_heap(heap.begin(), heap.end(), cmp);
+      auto h = heap.back();
+      heap.pop_back();
+      team_chains[ord[h.second]].push_back(c);
+      h.first += (long long)chains[c].size();
+      heap.push_back(h);
+      std::push_heap(heap.begin(), heap.end(), cmp);
+    }
+  }
+  std::vector<std::vector<std::vector<int>>> team_top(n_teams,
+                                                      std::vector<std::vector<int>>(t_top + 1));
+  for (int t = 1; t <= t_top; ++t) {
+    int j = 0;
+    for (int v = tree->stage_ptr[t]; v < tree->stage_ptr[t + 1]; ++v)
+      if (top[v]) team_top[ord[j++ % n_teams]][t].push_back(v);
+  }
+  const int n_seg = 2 * t_top + 2;
+  std::vector<int> items, seg;
+  for (int tm = 0; tm < n_teams; ++tm) {
+    seg.push_back((int)items.size());
+    for (int c : team_chains[tm]) {  // chain backward: leaf to head
+      const auto &ch = chains[c];
+      for (int q = (int)ch.size() - 1; q >= 0; --q) {
+        int it = ch[q];
+        if (q == (int)ch.size() - 1) it |= kPnFirst;
+        if (q == 0) it |= kPnLast;
+        items.push_back(it);
+      }
+    }
+    for (int t = t_top; t >= 1; --t) {
+      seg.push_back((int)items.size());
+      for (int v : team_top[tm][t]) items.push_back(v | kPnTop);
+    }
+    for (int t = 1; t <= t_top; ++t) {
+      seg.push_back((int)items.size());
+      for (int v : team_top[tm][t]) items.push_back(v | kPnTop | kPnK);
+    }
+    seg.push_back((int)items.size());
+    for (int c : team_chains[tm]) {  // chain forward: head to leaf
+      const auto &ch = chains[c];
+      for (int q = 0; q < (int)ch.size(); ++q) {
+        int it = ch[q] | kPnK;
+        if (q == 0) it |= kPnFirst;
+        if (q == (int)ch.size() - 1) it |= kPnLast;
+        items.push_back(it);
+      }
+    }
+  }
+  seg.push_back((int)items.size());
+  // seg holds n_teams * (n_seg + 1) entries: each team's n_seg + 1 offsets
+  // (its last offset is the next team's first)
+  std::vector<int> segs;
+  for (int tm = 0; tm < n_teams; ++tm)
+    for (int s = 0; s <= n_seg; ++s) segs.push_back(seg[(size_t)tm * n_seg + s]);
+  int rc;
+  if ((rc = pn_upload(f, &f->items, items)) || (rc = pn_upload(f, &f->seg, segs))) return rc;
+  if ((rc = pn_upload(f, &f->cbeg, cbeg)) || (rc = pn_upload(f, &f->cend, cend))) return rc;
+  f->n_seg = n_seg;
+  f->t_top = t_top;
+  f->n_chains = (int)chains.size();
+  int ntop = 0;
+  for (int v = 1; v < n; ++v) ntop += top[v];
+  f->n_top = ntop;
+  return RN_OK;
+}
+
+// widest work of one phase: chains, or the top nodes of one stage
+int pn_width(const rn_tree *tree) {
+  const int n = tree->n_nodes;
+  std::vector<int> nleaf(n, 0), nch(n, 0);
+  for (int v = 1; v < n; ++v) ++nch[tree->anc[v]];
+  for (int v = n - 1; v >= 1; --v) {
+    if (nch[v] == 0) nleaf[v] = 1;
+    nleaf[tree->anc[v]] += nleaf[v];
+  }
+  int w = 1;
+  for (int t = 1; t <= tree->N; ++t) {
+    int k = 0;
+    for (int v = tree->stage_ptr[t]; v < tree->stage_ptr[t + 1]; ++v) k += nleaf[v] >= 2;
+    w = std::max(w, k);
+  }
+  return std::max(w, nleaf[0]);
+}
+
+template <typename T>
+struct PnMatSink {
+  T *Phi, *K;
+  double *Mc;
+  int nu, ne, ldm;
+  static void put(void *ctx, int v, const double *P, const double *Kv, const double *M) {
+    PnMatSink *s = static_cast<PnMatSink *>(ctx);
+    const size_t ms = (size_t)s->nu * s->ldm;
+    for (int i = 0; i < s->nu; ++i)
+      for (int j = 0; j < s->nu; ++j) {
+        s->Phi[(size_t)v * ms + (size_t)i * s->ldm + j] = (T)P[(size_t)i * s->nu + j];
+        s->K[(size_t)v * ms + (size_t)i * s->ldm + j] = (T)Kv[(size_t)i * s->nu + j];
+      }
+    if (s->ne > 0)
+      std::copy(M, M + (size_t)s->nu * s->ne, s->Mc + (size_t)v * s->nu * s->ne);
+  }
+};
+
+template <typename T>
+int pn_matrices(PnFactor *f, const rn_network *net, const rn_tree *tree, const rn_cost *cost) {
+  const size_t ms = (size_t)f->nu * f->ldm;
+  std::vector<T> hP((size_t)f->n * ms, T(0)), hK((size_t)f->n * ms, T(0));
+  std::vector<double> hM((size_t)f->n * f->nu * std::max(1, f->ne), 0.0), Sd;
+  PnMatSink<T> sink{hP.data(), hK.data(), hM.data(), f->nu, f->ne, f->ldm};
+  const int threads = (int)std::max(1u, std::thread::hardware_concurrency());
+  int rc = pn_factor_host(net, tree, cost, threads, &PnMatSink<T>::put, &sink, &Sd);
+  if (rc) return rc;
+  T *dP = nullptr, *dK = nullptr;
+  if ((rc = pn_upload(f, &dP, hP)) || (rc = pn_upload(f, &dK, hK)) ||
+      (rc = pn_upload(f, &f->Mc, hM)) || (rc = pn_upload(f, &f->Sd, Sd)))
+    return rc;
+  f->Phi = dP;
+  f->K = dK;
+  // the host copies go when this returns: the uploads must be done
+  PN_CUDA(cudaStreamSynchronize(f->stream));
+  return RN_OK;
+}
+
+// launch layout: teams of team_threads threads, a ring of matrix chunks per
+// team in the shared memory left after its vectors
+int pn_layout(PnFactor *f, int max_ctas, int width) {
+  const int sz = f->fp32 ? 4 : 8;
+  int sms = 0, optin = 0;
+  PN_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, f->device));
+  PN_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, f->device));
+  const size_t avail = (size_t)optin - 1024;  // static shared memory of the kernel
+  f->vec_elems = 2 * f->NXP + 4 * f->NUP + 64;
+  const size_t vec_bytes = ((size_t)f->vec_elems * sz + 127) & ~(size_t)127;
+  const size_t rowb = (size_t)f->ldm * sz;
+  for (int teams = 4; teams >= 1; teams /= 2) {
+    const size_t mb = ((size_t)teams * 8 * 8 + 127) & ~(size_t)127;
+    if (avail < mb + teams * vec_bytes) continue;
+    const size_t per = ((avail - mb) / teams - vec_bytes) & ~(size_t)127;
+    const int max_rows = (int)(per / rowb);
+    if (max_rows < 2) continue;
+    const int rpc0 = std::max(1, max_rows / 4);
+    f->nch = (f->nu + rpc0 - 1) / rpc0;
+    f->rpc = (f->nu + f->nch - 1) / f->nch;
+    f->slots = std::min(8, max_rows / f->rpc);
+    f->slot_elems = f->rpc * f->ldm;
+    f->teams = teams;
+    f->block = teams * f->team_threads;
+    f->smem = mb + teams * ((((size_t)f->slots * f->slot_elems * sz + 127) & ~(size_t)127) +
+                            vec_bytes);
+    const void *k = f->fp32 ? (const void *)k_pn_solve<float> : (const void *)k_pn_solve<double>;
+    PN_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f->smem));
+    int occ = 0;
+    PN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, f->block, f->smem));
+    if (occ < 1) continue;
+    int grid = std::min(sms * occ, (width + teams - 1) / teams);
+    if (max_ctas > 0) grid = std::min(grid, max_ctas);
+    f->grid = std::max(1, grid);
+    return RN_OK;
+  }
+  set_error("per-node path: nu = %d does not fit the shared memory of a block", f->nu);
+  return RN_ERR_UNSUPPORTED;
+}
+
+}  // namespace
+
+void pn_destroy(PnFactor *f) { delete f; }
+
+int pn_create(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
+              const PnOptions &o, PnFactor **out) {
+  *out = nullptr;
+  int rc = pn_validate(net, tree, cost);
+  if (rc) return rc;
+  std::unique_ptr<PnFactor> f(new (std::nothrow) PnFactor());
+  if (!f) {
+    set_error("per-node path: host allocation failed");
+    return RN_ERR_NOMEM;
+  }
+  PnFactor *F = f.get();
+  F->device = o.device;
+  F->stream = o.stream;
+  F->fp32 = o.fp32;
+  F->nx = net->nx;
+  F->nu = net->nu;
+  F->nd = net->nd;
+  F->ne = net->ne;
+  F->n = tree->n_nodes;
+  F->N = tree->N;
+  F->NXP = (F->nx + 3) & ~3;
+  F->NUP = (F->nu + 3) & ~3;
+  F->YP = 2 * F->NXP + F->NUP;
+  F->ldm = F->fp32 ? ((F->nu + 3) & ~3) : ((F->nu + 1) & ~1);
+  F->mstride = (long long)F->nu * F->ldm;
+  F->W_alpha = cost->W_alpha;
+  F->Wx = cost->Wx;
+  F->Ws = cost->Ws;
+  F->theta_rule = o.theta_rule;
+  F->check_every = o.check_every;
+  F->wait_ns = o.wait_ns;
+  PN_CUDA(cudaSetDevice(F->device));
+  PN_CUDA(cudaEventCreate(&F->ev0));
+  PN_CUDA(cudaEventCreate(&F->ev1));
+  if ((rc = pn_layout(F, o.max_ctas, pn_width(tree)))) return rc;
+  if ((rc = pn_schedule(F, tree, F->grid * F->teams))) return rc;
+  const int nx = F->nx, nu = F->nu, n = F->n;
+  // tree, operators, bounds
+  {
+    std::vector<int> anc(tree->anc, tree->anc + n);
+    anc[0] = 0;
+    std::vector<double> prob(tree->prob, tree->prob + n);
+    if ((rc = pn_upload(F, &F->anc, anc)) || (rc = pn_upload(F, &F->prob, prob))) return rc;
+  }
+  const Csr Ar = dense_to_csr(net->A, nx, nx), At = dense_to_csc(net->A, nx, nx);
+  const Csr Br = dense_to_csr(net->B, nx, nu), Bt = dense_to_csc(net->B, nx, nu);
+  const Csr Wr = dense_to_csr(cost->Wu, nu, nu), Gr = dense_to_csr(net->Gd, nx, F->nd);
+  if ((rc = pn_upload_csr(F, Ar, &F->Ap, &F->Ai, &F->Av, F->fp32)) ||
+      (rc = pn_upload_csr(F, At, &F->Atp, &F->Ati, &F->Atv, F->fp32)) ||
+      (rc = pn_upload_csr(F, Br, &F->Bp, &F->Bi, &F->Bv, F->fp32)) ||
+      (rc = pn_upload_csr(F, Bt, &F->Btp, &F->Bti, &F->Btv, F->fp32)) ||
+      (rc = pn_upload_csr(F, Wr, &F->Wp, &F->Wi, &F->Wv, F->fp32, &F->Wv64)) ||
+      (rc = pn_upload(F, &F->Gp, Gr.ptr)) || (rc = pn_upload(F, &F->Gi, Gr.idx)) ||
+      (rc = pn_upload(F, &F->Gv, Gr.val)))
+    return rc;
+  {
+    std::vector<double> b;
+    b.insert(b.end(), net->xmin, net->xmin + nx);
+    b.insert(b.end(), net->xmax, net->xmax + nx);
+    b.insert(b.end(), net->xs, net->xs + nx);
+    b.insert(b.end(), net->umin, net->umin + nu);
+    b.insert(b.end(), net->umax, net->umax + nu);
+    if ((rc = pn_upload(F, &F->bnd64, b))) return rc;
+    auto up = [&](void **p, const double *s, int k) {
+      return F->fp32 ? pn_upload_t<float>(F, p, s, k) : pn_upload_t<double>(F, p, s, k);
+    };
+    if ((rc = up(&F->xmin, net->xmin, nx)) || (rc = up(&F->xmax, net->xmax, nx)) ||
+        (rc = up(&F->xs, net->xs, nx)) || (rc = up(&F->umin, net->umin, nu)) ||
+        (rc = up(&F->umax, net->umax, nu)))
+      return rc;
+    std::vector<double> a0(cost->alpha0, cost->alpha0 + nu);
+    if ((rc = pn_upload(F, &F->alpha0, a0))) return rc;
+  }
+  // the per-node matrices (general recursion, FP64 on the host)
+  rc = F->fp32 ? pn_matrices<float>(F, net, tree, cost) : pn_matrices<double>(F, net, tree, cost);
+  if (rc) return rc;
+  // state and per-solve buffers
+  const int sz = F->fp32 ? 4 : 8;
+  auto talloc = [&](void **p, size_t count) -> int {
+    if (F->fp32) {
+      float *q = nullptr;
+      int r2 = pn_alloc(F, &q, count);
+      *p = q;
+      return r2;
+    }
+    double *q = nullptr;
+    int r2 = pn_alloc(F, &q, count);
+    *p = q;
+    return r2;
+  };
+  (void)sz;
+  if ((rc = talloc(&F->c0, (size_t)n * F->NUP)) || (rc = talloc(&F->mc, (size_t)n * F->NUP)) ||
+      (rc = talloc(&F->gd, (size_t)n * F->NXP)) || (rc = talloc(&F->x0t, F->NXP)) ||
+      (rc = talloc(&F->qt, F->NUP)) || (rc = talloc(&F->ya, (size_t)n * F->YP)) ||
+      (rc = talloc(&F->yb, (size_t)n * F->YP)) || (rc = talloc(&F->m, (size_t)n * F->NUP)) ||
+      (rc = talloc(&F->lam, (size_t)n * F->NXP)) || (rc = talloc(&F->r, (size_t)n * F->NUP)) ||
+      (rc = talloc(&F->uo, (size_t)n * F->NUP)) || (rc = talloc(&F->xo, (size_t)n * F->NXP)) ||
+      (rc = pn_alloc(F, &F->x0, nx)) || (rc = pn_alloc(F, &F->q, nu)) ||
+      (rc = pn_alloc(F, &F->alpha, (size_t)n * nu)) || (rc = pn_alloc(F, &F->bar, 1)) ||
+      (rc = pn_alloc(F, &F->err, 1)) || (rc = pn_alloc(F, &F->info, 8)) ||
+      (rc = pn_alloc(F, &F->partial, 3 * kPnParts)) || (rc = pn_alloc(F, &F->norm2, 1)))
+    return rc;
+  PN_CUDA(cudaMemsetAsync(F->err, 0, sizeof(int), F->stream));
+  PN_CUDA(cudaMemsetAsync(F->uo, 0, (size_t)n * F->NUP * (F->fp32 ? 4 : 8), F->stream));
+  PN_CUDA(cudaMemsetAsync(F->xo, 0, (size_t)n * F->NXP * (F->fp32 ? 4 : 8), F->stream));
+  // step size: gamma = 1 / (1.01 L), L by power iteration on the dual Hessian
+  if (o.gamma > 0.0) {
+    F->gamma = o.gamma;
+  } else {
+    rc = F->fp32 ? pn_power<float>(F, o.power_iters, &F->L)
+                 : pn_power<double>(F, o.power_iters, &F->L);
+    if (rc) return rc;
+    if (!(F->L > 0.0) || !std::isfinite(F->L)) {
+      set_error("per-node path: power iteration gave L = %g", F->L);
+      return RN_ERR_INVAL;
+    }
+    F->gamma = 1.0 / (1.01 * F->L);
+  }
+  PN_CUDA(cudaStreamSynchronize(F->stream));
+  *out = f.release();
+  return RN_OK;
+}
+
+namespace {
+
+int pn_beta(PnFactor *f, int iters) {
+  if (iters + 1 <= f->beta_cap) return RN_OK;
+  const int cap = std::max(iters + 1, 2 * f->beta_cap);
+  // beta_nu = theta_nu (1 / theta_{nu-1} - 1) from theta_0 = theta_{-1} = 1
+  // (paper §4.3: the equality rule, or theta_nu = 2 / (nu + 2))
+  std::vector<double> b(2 * (size_t)cap);
+  double th = 1.0, prev = 1.0;
+  for (int k = 0; k < cap; ++k) {
+    b[k] = th * (1.0 / prev - 1.0);
+    b[cap + k] = th;
+    const double t2 = th * th;
+    const double nt = f->theta_rule == RN_THETA_SIMPLE ? 2.0 / (k + 3)
+                                                       : 0.5 * (std::sqrt(t2 * t2 + 4.0 * t2) - t2);
+    prev = th;
+    th = nt;
+  }
+  double *d = nullptr;
+  int rc = pn_upload(f, &d, b);
+  if (rc) return rc;
+  f->beta = d;
+  f->beta_cap = cap;
+  return RN_OK;
+}
+
+int pn_res(PnFactor *f, int checks) {
+  if (checks <= f->res_cap) return RN_OK;
+  const int cap = std::max(checks, 2 * f->res_cap);
+  int rc = pn_alloc(f, &f->res, cap);
+  if (rc) return rc;
+  f->res_cap = cap;
+  return RN_OK;
+}
+
+// per-solve constants from device inputs
+template <typename T>
+int pn_prepare_t(PnFactor *f, const double *x0, const double *q, const double *demand,
+                 const double *alpha) {
+  PN_CUDA(cudaMemcpyAsync(f->x0, x0, f->nx * sizeof(double), cudaMemcpyDeviceToDevice, f->stream));
+  PN_CUDA(cudaMemcpyAsync(f->q, q, f->nu * sizeof(double), cudaMemcpyDeviceToDevice, f->stream));
+  PN_CUDA(cudaMemcpyAsync(f->alpha, alpha, (size_t)f->n * f->nu * sizeof(double),
+                          cudaMemcpyDeviceToDevice, f->stream));
+  PnPrepArgs a{f->prob, demand, f->alpha, f->alpha0, f->Gp, f->Gi, f->Gv, f->Mc, f->Sd,
+               f->W_alpha, f->nx, f->nu, f->nd, f->ne, f->n, f->NXP, f->NUP};
+  const int nb = std::max(1, std::min(f->n, 4096));
+  k_pn_prep<T><<<nb, 128, std::max(1, f->ne) * sizeof(double), f->stream>>>(
+      a, static_cast<T *>(f->c0), static_cast<T *>(f->mc), static_cast<T *>(f->gd));
+  PN_CUDA(cudaGetLastError());
+  f->have_data = true;
+  return RN_OK;
+}
+
+int pn_prepare(PnFactor *f, const double *x0, const double *q, const double *demand,
+               const double *alpha) {
+  return f->fp32 ? pn_prepare_t<float>(f, x0, q, demand, alpha)
+                 : pn_prepare_t<double>(f, x0, q, demand, alpha);
+}
+
+template <typename T>
+int pn_init(PnFactor *f, const double *src) {
+  const int nb = std::max(1, std::min(f->n, 4096));
+  k_pn_init<T><<<nb, 128, 0, f->stream>>>(f->n, f->nx, f->nu, f->NXP, f->YP, src,
+                                          static_cast<T *>(f->ya), static_cast<T *>(f->yb),
+                                          f->x0, f->q, static_cast<T *>(f->x0t),
+                                          static_cast<T *>(f->qt));
+  PN_CUDA(cudaGetLastError());
+  return RN_OK;
+}
+
+template <typename T>
+int pn_gather(PnFactor *f, const T *yfin, double *u, double *x, double *y) {
+  const int nb = std::max(1, std::min(f->n, 4096));
+  k_pn_gather<T><<<nb, 128, 0, f->stream>>>(f->n, f->nx, f->nu, f->NXP, f->NUP, f->YP,
+                                            static_cast<const T *>(f->uo),
+                                            static_cast<const T *>(f->xo), yfin, f->q, f->x0, u,
+                                            x, y);
+  PN_CUDA(cudaGetLastError());
+  return RN_OK;
+}
+
+int pn_cost(PnFactor *f, const double *u, const double *x, double out[3]) {
+  PnCostArgs a{f->anc, f->prob, f->alpha, f->alpha0, f->bnd64, f->bnd64 + f->nx,
+               f->bnd64 + 2 * f->nx, f->bnd64 + 3 * f->nx, f->bnd64 + 3 * f->nx + f->nu,
+               f->Wp, f->Wi, f->Wv64, u, x, f->W_alpha, f->Wx, f->Ws, f->n, f->nx, f->nu};
+  k_pn_cost<<<kPnParts, 256, 0, f->stream>>>(a, f->partial);
+  PN_CUDA(cudaGetLastError());
+  std::vector<double> h(3 * kPnParts);
+  PN_CUDA(cudaMemcpyAsync(h.data(), f->partial, h.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                          f->stream));
+  PN_CUDA(cudaStreamSynchronize(f->stream));
+  out[0] = out[1] = out[2] = 0.0;
+  for (int b = 0; b < kPnParts; ++b) {
+    out[0] += h[3 * b];
+    out[1] += h[3 * b + 1];
+    out[2] = std::max(out[2], h[3 * b + 2]);
+  }
+  return RN_OK;
+}
+
+template <typename T>
+int pn_solve_t(PnFactor *f, const double *x0, const double *q, const double *demand,
+               const double *alpha, int max_iters, double tol, const double *y_warm,
+               rn_result *out) {
+  const bool avg = out->u_avg != nullptr;
+  const int checks = (max_iters + f->check_every - 1) / f->check_every + 1;
+  int rc;
+  if ((rc = pn_beta(f, max_iters)) || (rc = pn_res(f, checks))) return rc;
+  if ((rc = pn_prepare_t<T>(f, x0, q, demand, alpha)) || (rc = pn_init<T>(f, y_warm))) return rc;
+  PN_CUDA(cudaMemsetAsync(f->res, 0, checks * sizeof(unsigned long long), f->stream));
+  PN_CUDA(cudaMemsetAsync(f->err, 0, sizeof(int), f->stream));
+  if (avg) {
+    if (!f->uavg && ((rc = pn_alloc(f, &f->uavg, (size_t)f->n * f->NUP)) ||
+                     (rc = pn_alloc(f, &f->xavg, (size_t)f->n * f->NXP))))
+      return rc;
+    PN_CUDA(cudaMemsetAsync(f->uavg, 0, (size_t)f->n * f->NUP * sizeof(double), f->stream));
+    PN_CUDA(cudaMemsetAsync(f->xavg, 0, (size_t)f->n * f->NXP * sizeof(double), f->stream));
+  }
+  PnParams<T> P = pn_params<T>(f);
+  P.apg = 1;
+  P.iters = max_iters;
+  P.check_every = f->check_every;
+  P.tol = tol > 0.0 ? tol : 0.0;
+  P.c0 = static_cast<const T *>(f->c0);
+  P.mc = static_cast<const T *>(f->mc);
+  P.gd = static_cast<const T *>(f->gd);
+  P.x0 = static_cast<const T *>(f->x0t);
+  P.q = static_cast<const T *>(f->qt);
+  P.uavg = avg ? f->uavg : nullptr;
+  P.xavg = avg ? f->xavg : nullptr;
+  P.beta = f->beta;
+  P.theta = f->beta + f->beta_cap;
+  P.res = f->res;
+  PN_CUDA(cudaEventRecord(f->ev0, f->stream));
+  if ((rc = pn_launch<T>(f, P))) return rc;
+  PN_CUDA(cudaEventRecord(f->ev1, f->stream));
+  int info[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  PN_CUDA(cudaMemcpyAsync(info, f->info, sizeof info, cudaMemcpyDeviceToHost, f->stream));
+  if ((rc = pn_check_err(f))) return rc;
+  const int iters = info[0], nchk = info[1], reason = info[2];
+  {
+    unsigned long long st[2];
+    std::memcpy(st, info + 4, sizeof st);
+    out->t_begin_ns = (long long)st[0];
+    out->t_end_ns = (long long)st[1];
+  }
+  float ms = 0.f;
+  PN_CUDA(cudaEventElapsedTime(&ms, f->ev0, f->ev1));
+  out->apg_ms = ms;
+  // y^{iters} was written into the buffer that held y^{iters-2}
+  const T *yfin = static_cast<const T *>(((iters - 1) & 1) ? f->ya : f->yb);
+  if ((rc = pn_gather<T>(f, yfin, out->u, out->x, out->y))) return rc;
+  if (avg) {
+    const int nb = std::max(1, std::min(f->n, 4096));
+    k_pn_gather_avg<T><<<nb, 128, 0, f->stream>>>(f->n, f->nx, f->nu, f->NXP, f->NUP, f->uavg,
+                                                  f->xavg, f->q, f->x0, out->u_avg, out->x_avg);
+    PN_CUDA(cudaGetLastError());
+  }
+  std::vector<unsigned long long> hist(std::max(1, nchk));
+  if (nchk > 0)
+    PN_CUDA(cudaMemcpyAsync(hist.data(), f->res, nchk * sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, f->stream));
+  double red[3];
+  if ((rc = pn_cost(f, out->u, out->x, red))) return rc;
+  out->cost = red[0] + red[1];
+  out->ubox_viol = red[2];
+  out->iters = iters;
+  out->n_checks = nchk;
+  out->gamma = f->gamma;
+  std::vector<double> rh(std::max(1, nchk));
+  for (int i = 0; i < nchk; ++i) {
+    double d;
+    std::memcpy(&d, &hist[i], sizeof d);
+    rh[i] = d / f->gamma;
+  }
+  out->primal_res = nchk > 0 ? rh[nchk - 1] : NAN;
+  if (out->res_hist && out->res_hist_len > 0 && nchk > 0)
+    PN_CUDA(cudaMemcpyAsync(out->res_hist, rh.data(),
+                            std::min(out->res_hist_len, nchk) * sizeof(double),
+                            cudaMemcpyHostToDevice, f->stream));
+  out->gap = NAN;
+  PN_CUDA(cudaStreamSynchronize(f->stream));
+  if (reason == 2) {
+    set_error("the residual became non-finite after %d iterations", iters);
+    return RN_ERR_DIVERGED;
+  }
+  if (reason == 3) {
+    set_error("per-node path: a device-side wait gave up after %.3g s", f->wait_ns * 1e-9);
+    return RN_ERR_TIMEOUT;
+  }
+  if (tol > 0.0 && reason != 1) return RN_NOT_CONVERGED;
+  return RN_OK;
+}
+
+}  // namespace
+
+int pn_solve_device(PnFactor *f, const double *x0, const double *q, const double *demand,
+                    const double *alpha, int max_iters, double tol, const double *y_warm,
+                    rn_result *out) {
+  if (out->compute_gap) {
+    set_error("solve: the per-node factor form does not evaluate the duality gap");
+    return RN_ERR_UNSUPPORTED;
+  }
+  PN_CUDA(cudaSetDevice(f->device));
+  return f->fp32 ? pn_solve_t<float>(f, x0, q, demand, alpha, max_iters, tol, y_warm, out)
+                 : pn_solve_t<double>(f, x0, q, demand, alpha, max_iters, tol, y_warm, out);
+}
+
+namespace {
+template <typename T>
+int pn_dual_gradient_t(PnFactor *f, const double *w, double *u, double *x) {
+  int rc;
+  if ((rc = pn_init<T>(f, w))) return rc;
+  PN_CUDA(cudaMemsetAsync(f->err, 0, sizeof(int), f->stream));
+  if ((rc = pn_eval<T>(f, false))) return rc;
+  if ((rc = pn_gather<T>(f, nullptr, u, x, nullptr))) return rc;
+  return pn_check_err(f);
+}
+}  // namespace
+
+int pn_dual_gradient_device(PnFactor *f, const double *x0, const double *q,
+                            const double *demand, const double *alpha, const double *w,
+                            double *u, double *x) {
+  PN_CUDA(cudaSetDevice(f->device));
+  int rc;
+  if (x0 || q || demand || alpha) {
+    if (!(x0 && q && demand && alpha)) {
+      set_error("dual_gradient: give all of x0, q, demand, alpha or none");
+      return RN_ERR_INVAL;
+    }
+    if ((rc = pn_prepare(f, x0, q, demand, alpha))) return rc;
+  } else if (!f->have_data) {
+    set_error("dual_gradient: no data yet (give x0, q, demand, alpha)");
+    return RN_ERR_INVAL;
+  }
+  return f->fp32 ? pn_dual_gradient_t<float>(f, w, u, x)
+                 : pn_dual_gradient_t<double>(f, w, u, x);
+}
+
+void pn_info(const PnFactor *f, rn_factor_info *info) {
+  info->grid_ctas = f->grid;
+  info->block_threads = f->block;
+  info->L = f->L;
+  info->gamma = f->gamma;
+  info->device_bytes = f->bytes;
+  info->n_chains = f->n_chains;
+  info->n_top = f->n_top;
+}
+
+double pn_gamma(const PnFactor *f) { return f->gamma; }
+
+}  // namespace rn

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "kernels.cuh"
+#include "pernode.h"
 #include "rn_internal.h"
 
 using namespace rn;
@@ -525,8 +526,11 @@ struct rn_factor {
   // averaged primal iterate (internal rows) and its host staging
   double *uavg = nullptr, *xavg = nullptr, *io_uavg = nullptr, *io_xavg = nullptr;
   int io_hist_cap = 0;
+  // the per-node form (null for the shared-operator form)
+  rn::PnFactor *pn = nullptr;
 
   ~rn_factor() {
+    if (pn) rn::pn_destroy(pn);
     if (device >= 0) cudaSetDevice(device);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
@@ -779,7 +783,14 @@ std::vector<float> dense_f_fragments(const std::vector<double> &F, int nu) {
   return out;
 }
 
-int validate_network(const rn_network *net, const rn_cost *cost) {
+bool is_identity(const double *A, int nx) {
+  for (int i = 0; i < nx; ++i)
+    for (int j = 0; j < nx; ++j)
+      if (A[(size_t)i * nx + j] != (i == j ? 1.0 : 0.0)) return false;
+  return true;
+}
+
+int validate_network(const rn_network *net, const rn_cost *cost, bool shared = true) {
   if (!net || !cost) {
     set_error("network or cost is NULL");
     return RN_ERR_INVAL;
@@ -838,12 +849,11 @@ int validate_network(const rn_network *net, const rn_cost *cost) {
       return RN_ERR_INVAL;
     }
   }
-  for (int i = 0; i < nx; ++i)
-    for (int j = 0; j < nx; ++j)
-      if (net->A[(size_t)i * nx + j] != (i == j ? 1.0 : 0.0)) {
-        set_error("network: the library handles A = I only (tank mass balance)");
-        return RN_ERR_UNSUPPORTED;
-      }
+  if (!shared) return RN_OK;
+  if (!is_identity(net->A, nx)) {
+    set_error("network: the shared-operator form handles A = I only (tank mass balance)");
+    return RN_ERR_UNSUPPORTED;
+  }
   if (std::max(nx, nu) > 256) {
     set_error("network: the library handles nx, nu <= 256");
     return RN_ERR_UNSUPPORTED;
@@ -1290,6 +1300,74 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
   return RN_OK;
 }
 
+// The per-node form (paper §4.4, general recursion): the checks every form
+// shares, the staging buffers of the host entry point, then the handle of
+// pernode.cu, which holds everything else.
+int pernode_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
+                 const rn_opts *opts, rn_factor *f) {
+  int rc = validate_network(net, cost, false);
+  if (rc) return rc;
+  if ((rc = pn_validate(net, tree, cost))) return rc;
+  if ((rc = build_plan(tree, f->plan))) return rc;  // sizes of the host staging
+  f->opts = opts ? *opts : rn_opts{};
+  if (f->opts.precision == RN_PREC_MIXED) {
+    set_error("precision RN_PREC_MIXED needs the shared-operator form (A = I); the per-node "
+              "form runs RN_PREC_FP64 or RN_PREC_FP32");
+    return RN_ERR_UNSUPPORTED;
+  }
+  if (f->opts.precision != RN_PREC_FP64 && f->opts.precision != RN_PREC_FP32) {
+    set_error("precision must be RN_PREC_FP64, RN_PREC_MIXED or RN_PREC_FP32");
+    return RN_ERR_INVAL;
+  }
+  if (f->opts.power_iters <= 0) f->opts.power_iters = 200;
+  if (f->opts.check_every <= 0) f->opts.check_every = 10;
+  if (f->opts.theta_rule != RN_THETA_EQUALITY && f->opts.theta_rule != RN_THETA_SIMPLE) {
+    set_error("theta_rule must be RN_THETA_EQUALITY or RN_THETA_SIMPLE");
+    return RN_ERR_INVAL;
+  }
+  if (f->opts.wait_us < 0) {
+    set_error("wait_us must be >= 0");
+    return RN_ERR_INVAL;
+  }
+  f->device = f->opts.device;
+  RN_CUDA(cudaSetDevice(f->device));
+  if (f->opts.stream) {
+    f->stream = static_cast<cudaStream_t>(f->opts.stream);
+  } else {
+    RN_CUDA(cudaStreamCreateWithFlags(&f->stream, cudaStreamNonBlocking));
+    f->own_stream = true;
+  }
+  f->nx = net->nx;
+  f->nu = net->nu;
+  f->nd = net->nd;
+  f->ne = net->ne;
+  f->NXP = ceil4(f->nx);
+  f->NUP = ceil4(f->nu);
+  f->SP = f->NXP + f->NUP;
+  f->YP = 2 * f->NXP + f->NUP;
+  f->W_alpha = cost->W_alpha;
+  f->Ws = cost->Ws;
+  f->Wx = cost->Wx;
+  const int n = f->plan.n;
+  if ((rc = dalloc(f, &f->x0, f->nx)) || (rc = dalloc(f, &f->q, f->nu)) ||
+      (rc = dalloc(f, &f->demand, (size_t)n * f->nd)) ||
+      (rc = dalloc(f, &f->alpha, (size_t)n * f->nu)))
+    return rc;
+  PnOptions o;
+  o.device = f->device;
+  o.stream = f->stream;
+  o.fp32 = f->opts.precision == RN_PREC_FP32;
+  o.gamma = f->opts.gamma > 0.0 ? f->opts.gamma : 0.0;
+  o.power_iters = f->opts.power_iters;
+  o.check_every = f->opts.check_every;
+  o.theta_rule = f->opts.theta_rule;
+  o.max_ctas = f->opts.max_ctas;
+  o.wait_ns = f->opts.wait_us > 0 ? 1000LL * f->opts.wait_us : kWaitNs;
+  if ((rc = pn_create(net, tree, cost, o, &f->pn))) return rc;
+  f->gamma = pn_gamma(f->pn);
+  return RN_OK;
+}
+
 int ensure_beta(rn_factor *f, int iters) {
   if (iters + 1 <= f->beta_cap) return RN_OK;
   int cap = std::max(iters + 1, 2 * f->beta_cap);
@@ -1392,6 +1470,7 @@ int solve_device_impl(rn_factor *f, const double *x0, const double *q, const dou
     return RN_ERR_INVAL;
   }
   const bool avg = out->u_avg != nullptr;
+  if (f->pn) return pn_solve_device(f->pn, x0, q, demand, alpha, max_iters, tol, y_warm, out);
   RN_CUDA(cudaSetDevice(f->device));
   const int n = f->plan.n;
   const int checks = (max_iters + f->opts.check_every - 1) / f->opts.check_every + 1;
@@ -1543,7 +1622,33 @@ extern "C" int rapidnet_factor(const rn_network *net, const rn_tree *tree, const
   static std::atomic<unsigned long long> next_serial{1};
   f->serial = next_serial.fetch_add(1);
   f->device = opts ? opts->device : 0;
-  int rc = factor_impl(net, tree, cost, opts, f.get());
+  const int form = opts ? opts->factor_form : RN_FACTOR_AUTO;
+  const int prec = opts ? opts->precision : RN_PREC_FP64;
+  if (form != RN_FACTOR_AUTO && form != RN_FACTOR_SHARED && form != RN_FACTOR_PER_NODE) {
+    set_error("factor_form must be RN_FACTOR_AUTO, RN_FACTOR_SHARED or RN_FACTOR_PER_NODE");
+    return RN_ERR_INVAL;
+  }
+  bool per_node = form == RN_FACTOR_PER_NODE;
+  if (form == RN_FACTOR_AUTO && net && net->A && net->nx > 0)
+    per_node = prec == RN_PREC_FP32 || !is_identity(net->A, net->nx);
+  int rc = per_node ? pernode_impl(net, tree, cost, opts, f.get())
+                    : factor_impl(net, tree, cost, opts, f.get());
+  if (rc == RN_ERR_UNSUPPORTED && form == RN_FACTOR_AUTO && !per_node &&
+      prec == RN_PREC_FP64) {
+    // outside what the shared-operator form lays out: the per-node form
+    const std::string why = rapidnet_last_error();
+    f.reset(new (std::nothrow) rn_factor());
+    if (!f) {
+      set_error("factor: host allocation failed");
+      return RN_ERR_NOMEM;
+    }
+    f->serial = next_serial.fetch_add(1);
+    f->device = opts ? opts->device : 0;
+    clear_error();
+    rc = pernode_impl(net, tree, cost, opts, f.get());
+    if (rc == RN_ERR_UNSUPPORTED) set_error("%s; per-node form: %s", why.c_str(),
+                                            rapidnet_last_error());
+  }
   if (rc) return rc;
   *out = f.release();
   return RN_OK;
@@ -1575,6 +1680,14 @@ extern "C" int rapidnet_factor_info(const rn_factor *f, rn_factor_info *info) {
   size_t need_d = 0, need_w = 0;
   noalloc_need(f, &need_d, &need_w);
   info->noalloc_bytes = (long long)(8 * (need_d + (need_w + 1) / 2));
+  info->factor_form = RN_FACTOR_SHARED;
+  if (f->pn) {
+    pn_info(f->pn, info);
+    info->device_bytes += f->bytes;
+    info->collapse_dev = 0.0;
+    info->noalloc_bytes = 0;
+    info->factor_form = RN_FACTOR_PER_NODE;
+  }
   return RN_OK;
 }
 
@@ -1679,6 +1792,7 @@ extern "C" int rapidnet_dual_gradient_device(rn_factor *f, const double *x0, con
     set_error("dual_gradient: NULL argument");
     return RN_ERR_INVAL;
   }
+  if (f->pn) return pn_dual_gradient_device(f->pn, x0, q, demand, alpha, w, u, x);
   RN_CUDA(cudaSetDevice(f->device));
   int rc;
   if (x0 || q || demand || alpha) {
@@ -1758,6 +1872,11 @@ extern "C" int rapidnet_dual_gradient_noalloc(rn_factor *f, const double *w, dou
   if (!f || !w || !u || !x) {
     set_error("dual_gradient_noalloc: NULL argument");
     return RN_ERR_INVAL;
+  }
+  if (f->pn) {
+    set_error("dual_gradient_noalloc: a handle of the per-node form has no allocation-free "
+              "entry point");
+    return RN_ERR_UNSUPPORTED;
   }
   if (!f->have_data) {
     set_error("dual_gradient_noalloc: no data yet (run a solve or "

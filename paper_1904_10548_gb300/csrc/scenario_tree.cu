@@ -22,7 +22,7 @@
 //                tile table of the upper triangle, each tile written with
 //                its mirror; the tails staged through shared memory);
 //   k_ffs_z      z for every candidate of every bundle still choosing: a
-//                warp reads the rows of four candidates of its bundle's
+//                block reads the rows of four candidates of its bundle's
 //                matrix (it is symmetric) with the weights and the current
 //                minima: the matrices stream from HBM once per choice, the
 //                bound of this step;
@@ -113,53 +113,65 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-constexpr int kZRows = 4;  // candidates per warp in k_ffs_z
+constexpr int kZRows = 4, kZThreads = 256;  // candidates and threads per block of k_ffs_z
 
 // choice k: z[u] = sum_j p_j min(m_j, D_b[u][j]) for every position u of a
-// bundle with k < K_b (a chosen one gets +inf).  One warp takes kZRows
-// consecutive positions: when they share a bundle it streams their rows
-// together, reading p and m once for all of them.
-__global__ void k_ffs_z(const double *D, StageDev sd, int S, int k, const double *p,
-                        const double *m, const int *chosen, double *z) {
-  const int lane = threadIdx.x & 31;
-  const int warps = (gridDim.x * blockDim.x) >> 5;
+// bundle with k < K_b (a chosen one gets +inf).  One block takes kZRows
+// consecutive positions and splits the columns over its threads: when the
+// positions share a bundle their rows stream together, with p and m read
+// once for all of them.
+__global__ void __launch_bounds__(kZThreads)
+    k_ffs_z(const double *D, StageDev sd, int S, int k, const double *p, const double *m,
+            const int *chosen, double *z) {
+  __shared__ double red[kZThreads / 32][kZRows];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int groups = (S + kZRows - 1) / kZRows;
-  for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < groups; g += warps) {
-    const int u0 = g * kZRows, u1 = min(u0 + kZRows, S);
+  for (int g = blockIdx.x; g < groups; g += gridDim.x) {
+    const int u0 = g * kZRows, nr = min(kZRows, S - u0);
     const int b0 = sd.bundle_of[u0];
-    if (u1 - u0 == kZRows && sd.bundle_of[u1 - 1] == b0) {
-      if (k >= sd.K[b0]) continue;
+    const bool one = sd.bundle_of[u0 + nr - 1] == b0;  // bundles are contiguous
+    if (one && k >= sd.K[b0]) continue;                 // the same for the whole block
+    double acc[kZRows];
+#pragma unroll
+    for (int r = 0; r < kZRows; ++r) acc[r] = 0.0;
+    if (one) {
       const int first = sd.boff[b0], M = sd.boff[b0 + 1] - first;
       const double *row = D + sd.doff[b0] + (size_t)(u0 - first) * M;
       const double *pb = p + first, *mb = m + first;
-      double acc[kZRows];
-#pragma unroll
-      for (int r = 0; r < kZRows; ++r) acc[r] = 0.0;
-#pragma unroll 2
-      for (int j = lane; j < M; j += 32) {
+      for (int j = threadIdx.x; j < M; j += kZThreads) {
         const double pj = pb[j], mj = mb[j];
 #pragma unroll
         for (int r = 0; r < kZRows; ++r)
-          acc[r] += pj * fmin(mj, __ldcs(row + (size_t)r * M + j));
+          if (r < nr) acc[r] += pj * fmin(mj, __ldcs(row + (size_t)r * M + j));
       }
+    } else {
 #pragma unroll
       for (int r = 0; r < kZRows; ++r) {
-        const double v = warp_sum_d(acc[r]);
-        if (lane == 0) z[u0 + r] = chosen[u0 + r] ? INFINITY : v;
+        const int u = u0 + r;
+        if (r >= nr) continue;
+        const int b = sd.bundle_of[u];
+        if (k >= sd.K[b]) continue;
+        const int first = sd.boff[b], M = sd.boff[b + 1] - first;
+        const double *row = D + sd.doff[b] + (size_t)(u - first) * M;
+        for (int j = threadIdx.x; j < M; j += kZThreads)
+          acc[r] += p[first + j] * fmin(m[first + j], __ldcs(row + j));
       }
-      continue;
     }
-    for (int u = u0; u < u1; ++u) {
-      const int b = sd.bundle_of[u];
-      if (k >= sd.K[b]) continue;
-      const int first = sd.boff[b], M = sd.boff[b + 1] - first;
-      const double *row = D + sd.doff[b] + (size_t)(u - first) * M;
-      const double *pb = p + first, *mb = m + first;
-      double acc = 0.0;
-      for (int j = lane; j < M; j += 32) acc += pb[j] * fmin(mb[j], __ldcs(row + j));
-      acc = warp_sum_d(acc);
-      if (lane == 0) z[u] = chosen[u] ? INFINITY : acc;
+#pragma unroll
+    for (int r = 0; r < kZRows; ++r) {
+      const double v = warp_sum_d(acc[r]);
+      if (lane == 0) red[w][r] = v;
     }
+    __syncthreads();
+    if (threadIdx.x < nr) {
+      const int u = u0 + threadIdx.x;
+      if (k < sd.K[sd.bundle_of[u]]) {
+        double v = 0.0;
+        for (int q = 0; q < kZThreads / 32; ++q) v += red[q][threadIdx.x];
+        z[u] = chosen[u] ? INFINITY : v;
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -355,9 +367,9 @@ extern "C" int rapidnet_scenario_tree(const double *paths, const double *prob, i
     ST_CUDA(cudaMemsetAsync(dch, 0, S * sizeof(int), st));
     const StageDev sd{dpos, dboff, ddoff, dbof, dK, B};
     k_tail_dist<<<(unsigned)tiles.size(), dim3(32, 8), 0, st>>>(dX, R, sd, dtiles, t * dim, dD);
-    const int zblocks = std::min(8192, (S + 8 * kZRows - 1) / (8 * kZRows)), eblocks = std::min(2048, (S + 255) / 256);
+    const int zblocks = std::min(1 << 16, (S + kZRows - 1) / kZRows), eblocks = std::min(2048, (S + 255) / 256);
     for (int k = 0; k < kmax; ++k) {
-      k_ffs_z<<<zblocks, 256, 0, st>>>(dD, sd, S, k, dp, dm, dch, dz);
+      k_ffs_z<<<zblocks, kZThreads, 0, st>>>(dD, sd, S, k, dp, dm, dch, dz);
       k_ffs_pick<<<B, 1024, 0, st>>>(dz, sd, k, kmax, dch, dsel);
       k_ffs_update<<<eblocks, 256, 0, st>>>(dD, sd, S, k, kmax, dsel, dm);
     }

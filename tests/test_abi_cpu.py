@@ -87,10 +87,16 @@ def _factor_status(net, cost, tree):
 
 def test_validation_errors_before_cuda(lib):
     pb = make_problem("tiny")
-    # A != I is outside what the library handles
+    # A != I is outside what the shared-operator form handles (the default
+    # form then is the per-node one, tests/test_pernode_cpu.py)
     net = make_problem("tiny").net
     net.A = np.eye(net.nx) * 1.01
-    assert _factor_status(net, pb.cost, pb.tree) == B.RN_ERR_UNSUPPORTED
+    try:
+        rn.Factor(net, pb.cost, pb.tree, gamma=1.0, factor_form=rn.RN_FACTOR_SHARED).close()
+        status = B.RN_OK
+    except B.RapidNetError as e:
+        status = e.status
+    assert status == B.RN_ERR_UNSUPPORTED
     assert "A = I" in rn.rapidnet_last_error()
     # a dense symmetric positive definite Wu passes validation (the next step
     # needs a device: RN_ERR_CUDA without one); an indefinite or
