@@ -98,9 +98,22 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
       : "memory");
 }
 
-// Ring of matrix chunks of one team.  Chunk i is rows [c rpc, (c+1) rpc)
-// of the matrix of the team's item (i / nch) mod n_items, c = i mod nch,
-// in slot i mod slots; its mbarrier completes phase (i / slots) mod 2.
+// 16-byte copies global -> shared (L2 only) in commit groups
+__device__ __forceinline__ void cp16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Ring of matrix chunks of one team.  A node's matrix is stored as nch
+// column blocks of qw 16-byte units (the last one narrower), each block nu
+// rows in row-major order; chunk i is block c = i mod nch of the matrix of
+// the team's item (i / nch) mod n_items, in slot i mod slots; its mbarrier
+// completes phase (i / slots) mod 2.
 template <typename T>
 struct Ring {
   const PnParams<T> *P;
@@ -109,88 +122,128 @@ struct Ring {
   const int *items;  // the team's items of one iteration
   int n_items;
   long long issued, cons, limit;
+  // incremental positions (no 64-bit division on the way): slot and phase
+  // parity of the next chunk to consume and to issue, the issued chunk's
+  // block within its matrix; thread 0 also keeps the item of the chunks
+  // being issued, the next one (loaded ahead) and its index
+  int cslot, islot, ic;
+  unsigned cpar;
+  int icur, inext, iidx;
   __device__ void issue_one(int tid) {
     if (tid == 0) {
-      const long long i = issued;
-      const int c = (int)(i % P->nch);
-      const int item = items[(int)((i / P->nch) % n_items)];
-      const int v = item & kPnNodeMask;
-      const int rows = min(P->rpc, P->nu - c * P->rpc);
-      const unsigned bytes = (unsigned)(rows * P->ldm * (int)sizeof(T));
-      const T *src = ((item & kPnK) ? P->K : P->Phi) + (size_t)v * P->mstride +
-                     (size_t)c * P->rpc * P->ldm;
-      const int s = (int)(i % P->slots);
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mb_expect_tx(bar + s, bytes);
-      bulk_g2s(slot0 + (size_t)s * P->slot_elems, src, bytes, bar + s);
+      constexpr int VW = 16 / sizeof(T);
+      if (ic == 0 && issued > 0) {  // the next item; the one after it is loaded ahead
+        iidx = iidx + 1 == n_items ? 0 : iidx + 1;
+        icur = inext;
+        inext = items[iidx + 1 == n_items ? 0 : iidx + 1];
+      }
+      const int v = icur & kPnNodeMask;
+      const int w = min(P->qw, P->ldm / VW - ic * P->qw);  // 16-byte units of this block
+      const unsigned bytes = (unsigned)(P->nu * w * 16);
+      const T *src = ((icur & kPnK) ? P->K : P->Phi) + (size_t)v * P->mstride +
+                     (size_t)P->nu * ic * P->qw * VW;
+      // the slot's previous chunk was read by the team before the barrier
+      // that precedes this call: the reads are complete, and the copy that
+      // overwrites them is ordered after them (as a consumer release before
+      // a producer's refill)
+      mb_expect_tx(bar + islot, bytes);
+      bulk_g2s(slot0 + (size_t)islot * P->slot_elems, src, bytes, bar + islot);
     }
     ++issued;
+    if (++ic == P->nch) ic = 0;
+    if (++islot == P->slots) islot = 0;
   }
-  // wait for chunk `cons` (every thread of the team); false on timeout
-  // (after an error elsewhere it returns false at once: the launch is
-  // being abandoned, and the drain at the end waits for what is in flight)
-  __device__ bool wait(long long i, bool drain = false) const {
-    unsigned long long *b = bar + (int)(i % P->slots);
-    const unsigned par = (unsigned)((i / P->slots) & 1);
-    if (mb_try_wait(b, par)) return true;
+  // wait for the next chunk to consume (every thread of the team); false on
+  // timeout (after an error elsewhere it returns false at once: the launch
+  // is being abandoned, and the drain at the end waits for what is in flight)
+  __device__ bool wait(bool drain = false) const {
+    unsigned long long *b = bar + cslot;
+    if (mb_try_wait(b, cpar)) return true;
     if (!drain && *(volatile int *)P->err != 0) return false;
     // a copy of device memory completes by itself: the drain waits for it
     // whatever the handle's wait bound (up to 2 s)
-    const long long limit = drain ? 2000000000LL : P->wait_ns;
+    const long long lim = drain ? 2000000000LL : P->wait_ns;
     const unsigned long long t0 = pn_ns();
-    while (!mb_try_wait(b, par))
-      if ((long long)(pn_ns() - t0) > limit) return false;
+    while (!mb_try_wait(b, cpar))
+      if ((long long)(pn_ns() - t0) > lim) return false;
     return true;
   }
-  __device__ const T *slot(long long i) const {
-    return slot0 + (size_t)(i % P->slots) * P->slot_elems;
+  __device__ const T *slot() const { return slot0 + (size_t)cslot * P->slot_elems; }
+  __device__ void consumed() {
+    ++cons;
+    if (++cslot == P->slots) {
+      cslot = 0;
+      cpar ^= 1u;
+    }
   }
 };
 
 // out[i] = base[i] + sgn * (M_i . vec) for the nu rows of the team's current
-// item, chunk by chunk out of the ring; vec (smem) is zero beyond nu
-template <typename T>
+// item, block of columns by block out of the ring; vec (smem) is zero
+// beyond nu.  Thread t owns rows t, t + nt, ... and keeps their sums in
+// registers over the blocks: no reduction between threads.  A block's row
+// pitch is an odd number of 16-byte units (but for the last block), so the
+// 8 threads of a shared-memory phase read 8 distinct bank groups; vec is
+// read by all threads at once (broadcast).
+template <typename T, int MR>  // MR: rows per thread (nu <= 128 MR)
 __device__ void ring_matvec(Ring<T> &R, const T *vec, const T *base, T sgn, T *out, T *gout,
-                            int team, int tid, int nt) {
+                            bool base_pending, int team, int tid, int nt) {
   const PnParams<T> &P = *R.P;
   constexpr int VW = 16 / sizeof(T);
   using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
-  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  const V *vq = reinterpret_cast<const V *>(vec);
+  T acc[MR], acc2[MR];
+#pragma unroll
+  for (int r = 0; r < MR; ++r) acc[r] = acc2[r] = T(0);
+  const int nqt = P.ldm / VW;
   for (int c = 0; c < P.nch; ++c) {
-    if (!R.wait(R.cons)) {
+    if (!R.wait()) {
       if (tid == 0) atomicCAS(P.err, 0, 5);
       R.limit = R.issued;  // no further copies into a ring that is being abandoned
     }
-    const T *S = R.slot(R.cons);
-    const int r0 = c * P.rpc, rows = min(P.rpc, P.nu - r0);
-    for (int rr = warp; rr < rows; rr += nw) {
-      const T *row = S + (size_t)rr * P.ldm;
-      T acc = T(0);
-      for (int k = lane * VW; k < P.ldm; k += 32 * VW) {
-        const V a = *reinterpret_cast<const V *>(row + k);
-        const V b = *reinterpret_cast<const V *>(vec + k);
-        if constexpr (sizeof(T) == 4) {
-          acc = fmaf(a.x, b.x, acc);
-          acc = fmaf(a.y, b.y, acc);
-          acc = fmaf(a.z, b.z, acc);
-          acc = fmaf(a.w, b.w, acc);
-        } else {
-          acc = fma(a.x, b.x, acc);
-          acc = fma(a.y, b.y, acc);
+    const V *S = reinterpret_cast<const V *>(R.slot());
+    const int q0 = c * P.qw, w = min(P.qw, nqt - q0);
+#pragma unroll
+    for (int r = 0; r < MR; ++r) {
+      const int i = tid + r * nt;
+      if (i < P.nu) {
+        const V *row = S + (size_t)i * w;
+        T a0 = acc[r], a1 = acc2[r];
+        for (int k = 0; k < w; ++k) {
+          const V a = row[k], b = vq[q0 + k];
+          if constexpr (sizeof(T) == 4) {
+            a0 = fmaf(a.x, b.x, a0);
+            a1 = fmaf(a.y, b.y, a1);
+            a0 = fmaf(a.z, b.z, a0);
+            a1 = fmaf(a.w, b.w, a1);
+          } else {
+            a0 = fma(a.x, b.x, a0);
+            a1 = fma(a.y, b.y, a1);
+          }
         }
-      }
-      acc = wsum(acc);
-      if (lane == 0) {
-        const int i = r0 + rr;
-        const T val = (base ? base[i] : T(0)) + sgn * acc;
-        out[i] = val;
-        if (gout) gout[i] = val;
+        acc[r] = a0;
+        acc2[r] = a1;
       }
     }
-    team_sync(team, nt);
-    ++R.cons;
+    team_sync(team, nt);  // the slot is free again
+    R.consumed();
     if (R.issued < R.limit) R.issue_one(tid);
   }
+  // a base row still in flight (the second newest copy group) lands first
+  if (base_pending) {
+    cp_wait<1>();
+    team_sync(team, nt);
+  }
+#pragma unroll
+  for (int r = 0; r < MR; ++r) {
+    const int i = tid + r * nt;
+    if (i < P.nu) {
+      const T val = (base ? base[i] : T(0)) + sgn * (acc[r] + acc2[r]);
+      out[i] = val;
+      if (gout) gout[i] = val;
+    }
+  }
+  team_sync(team, nt);
 }
 
 // sum over a compressed row
@@ -248,11 +301,42 @@ struct TeamVec {
   T *sl, *sr, *lamb, *rr, *g, *mv;  // backward: child sums, own sums, g, m
   T *xa, *ua, *x, *u;               // forward: parent values, own values
   T *red;                           // 2 * 32 reduction slots
+  T *pf, *mb;                       // prefetched rows: 3 buffers of P.vb, 2 m rows of vup
+  int vup;
 };
 
+// The rows an item reads besides its matrix, copied ahead into shared
+// memory (one copy group per thread): y^nu and y^{nu-1} of the node, then
+// c0 and mc (backward) or Gd d (forward).  Buffer layout: yc (YP) | yp (YP)
+// | b1 (max(NUP, NXP)) | b2 (NUP).
 template <typename T>
+__device__ void prefetch_item(const PnParams<T> &P, int item, const T *ycur, const T *yprv,
+                              T *dst, int tid, int nt) {
+  constexpr int per = 16 / sizeof(T);
+  const int v = item & kPnNodeMask;
+  const bool fw = (item & kPnK) != 0;
+  const int YP = P.YP;
+  const T *b1 = fw ? (P.gd ? P.gd + (size_t)v * P.NXP : nullptr)
+                   : (P.c0 ? P.c0 + (size_t)v * P.NUP : nullptr);
+  const T *b2 = (!fw && P.mc) ? P.mc + (size_t)v * P.NUP : nullptr;
+  const int uY = YP / per, u1 = b1 ? (fw ? P.NXP : P.NUP) / per : 0, u2 = b2 ? P.NUP / per : 0;
+  const T *yc = ycur + (size_t)v * YP, *yp = yprv + (size_t)v * YP;
+  for (int e = tid; e < 2 * uY + u1 + u2; e += nt) {
+    if (e < uY)
+      cp16(dst + e * per, yc + e * per);
+    else if (e < 2 * uY)
+      cp16(dst + YP + (e - uY) * per, yp + (e - uY) * per);
+    else if (e < 2 * uY + u1)
+      cp16(dst + 2 * YP + (e - 2 * uY) * per, b1 + (e - 2 * uY) * per);
+    else
+      cp16(dst + 2 * YP + P.b1 + (e - 2 * uY - u1) * per, b2 + (e - 2 * uY - u1) * per);
+  }
+  cp_commit();
+}
+
+template <typename T, int MR>
 __device__ void backward_item(const PnParams<T> &P, Ring<T> &R, TeamVec<T> &V, int item,
-                              const T *ycur, const T *yprv, T beta, int team, int tid, int nt) {
+                              const T *pf, T beta, int team, int tid, int nt) {
   const int v = item & kPnNodeMask;
   const int nx = P.nx, nu = P.nu, NXP = P.NXP, NUP = P.NUP;
   if (item & kPnTop) {
@@ -273,7 +357,8 @@ __device__ void backward_item(const PnParams<T> &P, Ring<T> &R, TeamVec<T> &V, i
   }
   team_sync(team, nt);
   const bool publish = (item & (kPnTop | kPnLast)) != 0;
-  const T *yc = ycur + (size_t)v * P.YP, *yp = yprv + (size_t)v * P.YP;
+  const T *yc = pf, *yp = pf + P.YP;  // prefetched rows (see prefetch_item)
+  const T *c0 = P.c0 ? pf + 2 * P.YP : nullptr, *mc = P.mc ? pf + 2 * P.YP + P.b1 : nullptr;
   for (int i = tid; i < nx; i += nt) {
     const T a1 = yc[i], a2 = yc[NXP + i];
     const T w1 = a1 + beta * (a1 - yp[i]), w2 = a2 + beta * (a2 - yp[NXP + i]);
@@ -285,13 +370,12 @@ __device__ void backward_item(const PnParams<T> &P, Ring<T> &R, TeamVec<T> &V, i
   for (int j = tid; j < nu; j += nt) {
     const T a3 = yc[2 * NXP + j];
     const T w3 = a3 + beta * (a3 - yp[2 * NXP + j]);
-    const T c = P.c0 ? P.c0[(size_t)v * NUP + j] : T(0);
+    const T c = c0 ? c0[j] : T(0);
     V.g[j] = (c + w3) + csr_dot(P.Btp, P.Bti, P.Btv, j, V.lamb) + V.sr[j];
   }
   team_sync(team, nt);
   // m = mc - Phi g (the matrix streams through the ring)
-  ring_matvec(R, V.g, P.mc ? P.mc + (size_t)v * NUP : (const T *)nullptr, T(-1), V.mv,
-              P.m + (size_t)v * NUP, team, tid, nt);
+  ring_matvec<T, MR>(R, V.g, mc, T(-1), V.mv, P.m + (size_t)v * NUP, false, team, tid, nt);
   const T w2p = T(-2.0 * P.prob[v]);
   for (int j = tid; j < nu; j += nt) {
     const T rv = w2p * csr_dot(P.Wp, P.Wi, P.Wv, j, V.mv);
@@ -307,10 +391,10 @@ __device__ void backward_item(const PnParams<T> &P, Ring<T> &R, TeamVec<T> &V, i
   V.rr = t;
 }
 
-template <typename T>
+template <typename T, int MR>
 __device__ void forward_item(const PnParams<T> &P, Ring<T> &R, TeamVec<T> &V, int item,
-                             const T *ycur, T *yprv, T beta, bool write_out, double theta,
-                             unsigned long long &rbits, int team, int tid, int nt) {
+                             const T *pf, const T *mrow, T *yprv, T beta, bool write_out,
+                             double theta, unsigned long long &rbits, int team, int tid, int nt) {
   const int v = item & kPnNodeMask;
   const int nx = P.nx, nu = P.nu, NXP = P.NXP, NUP = P.NUP;
   if (item & (kPnTop | kPnFirst)) {
@@ -327,10 +411,11 @@ __device__ void forward_item(const PnParams<T> &P, Ring<T> &R, TeamVec<T> &V, in
   // u = m + K u_a
   const bool top = (item & kPnTop) != 0;
   const bool store = top || write_out || !P.apg;
-  ring_matvec(R, V.ua, P.m + (size_t)v * NUP, T(1), V.u,
-              store ? P.uo + (size_t)v * NUP : (T *)nullptr, team, tid, nt);
+  ring_matvec<T, MR>(R, V.ua, mrow, T(1), V.u, store ? P.uo + (size_t)v * NUP : (T *)nullptr, true,
+              team, tid, nt);
+  const T *gdr = P.gd ? pf + 2 * P.YP : nullptr;
   for (int i = tid; i < nx; i += nt) {
-    const T gd = P.gd ? P.gd[(size_t)v * NXP + i] : T(0);
+    const T gd = gdr ? gdr[i] : T(0);
     const T xv = (gd + csr_dot(P.Ap, P.Ai, P.Av, i, V.xa)) + csr_dot(P.Bp, P.Bi, P.Bv, i, V.u);
     V.x[i] = xv;
     if (store) P.xo[(size_t)v * NXP + i] = xv;
@@ -350,12 +435,12 @@ __device__ void forward_item(const PnParams<T> &P, Ring<T> &R, TeamVec<T> &V, in
     // state terms (§4.3) through the Moreau decomposition (§4.2), box
     // projection on the input block
     const T g = (T)P.gamma, ig = (T)P.invgamma;
-    const T *yc = ycur + (size_t)v * P.YP;
-    T *yn = yprv + (size_t)v * P.YP;  // y^{nu-1} is read here before it is replaced
+    const T *yc = pf, *yo = pf + P.YP;  // y^nu, y^{nu-1} (prefetched)
+    T *yn = yprv + (size_t)v * P.YP;   // y^{nu+1} replaces y^{nu-1}
     T n1 = T(0), n2 = T(0);
     for (int i = tid; i < nx; i += nt) {
       const T a1 = yc[i], a2 = yc[NXP + i];
-      const T w1 = a1 + beta * (a1 - yn[i]), w2 = a2 + beta * (a2 - yn[NXP + i]);
+      const T w1 = a1 + beta * (a1 - yo[i]), w2 = a2 + beta * (a2 - yo[NXP + i]);
       const T v1 = V.x[i] + w1 * ig, v2 = V.x[i] + w2 * ig;
       const T e1 = v1 - clampv(v1, P.xmin[i], P.xmax[i]);
       const T e2 = fmin(v2 - P.xs[i], T(0));
@@ -380,7 +465,7 @@ __device__ void forward_item(const PnParams<T> &P, Ring<T> &R, TeamVec<T> &V, in
     const T s2 = n2 > T(0) ? fmin(g, P.Ws / sqrt(n2)) : T(0);
     for (int i = tid; i < nx; i += nt) {
       const T a1 = yc[i], a2 = yc[NXP + i];
-      const T w1 = a1 + beta * (a1 - yn[i]), w2 = a2 + beta * (a2 - yn[NXP + i]);
+      const T w1 = a1 + beta * (a1 - yo[i]), w2 = a2 + beta * (a2 - yo[NXP + i]);
       const T v1 = V.x[i] + w1 * ig, v2 = V.x[i] + w2 * ig;
       const T y1 = (v1 - clampv(v1, P.xmin[i], P.xmax[i])) * s1;
       const T y2 = fmin(v2 - P.xs[i], T(0)) * s2;
@@ -391,7 +476,7 @@ __device__ void forward_item(const PnParams<T> &P, Ring<T> &R, TeamVec<T> &V, in
     }
     for (int j = tid; j < nu; j += nt) {
       const T a3 = yc[2 * NXP + j];
-      const T w3 = a3 + beta * (a3 - yn[2 * NXP + j]);
+      const T w3 = a3 + beta * (a3 - yo[2 * NXP + j]);
       const T v3 = V.u[j] + w3 * ig;
       const T y3 = g * (v3 - clampv(v3, P.umin[j], P.umax[j]));
       rbits = max(rbits, res_bits((double)(y3 - w3)));
@@ -406,7 +491,7 @@ __device__ void forward_item(const PnParams<T> &P, Ring<T> &R, TeamVec<T> &V, in
   V.u = t;
 }
 
-template <typename T>
+template <typename T, int MR>
 __global__ void __launch_bounds__(512, 1) k_pn_solve(PnParams<T> P) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int nt = P.team_threads, team = threadIdx.x / nt, tid = threadIdx.x % nt;
@@ -432,11 +517,16 @@ __global__ void __launch_bounds__(512, 1) k_pn_solve(PnParams<T> P) {
     T *p = vec;
     V.sl = p; p += P.NXP;
     V.lamb = p; p += P.NXP;
-    V.sr = p; p += P.NUP;
-    V.rr = p; p += P.NUP;
-    V.g = p; p += P.NUP;
-    V.mv = p; p += P.NUP;
-    V.red = p;
+    // vectors of nu read against a matrix row span the row pitch ldm
+    const int vup = (max(P.NUP, P.ldm) + 3) & ~3;
+    V.sr = p; p += vup;
+    V.rr = p; p += vup;
+    V.g = p; p += vup;
+    V.mv = p; p += vup;
+    V.red = p; p += 64;
+    V.pf = p; p += 3 * P.vb;
+    V.mb = p;
+    V.vup = vup;
     V.xa = V.sl;  // the forward reuses the backward's region
     V.x = V.lamb;
     V.ua = V.sr;
@@ -450,7 +540,14 @@ __global__ void __launch_bounds__(512, 1) k_pn_solve(PnParams<T> P) {
   R.items = P.items + seg[0];
   R.n_items = seg[P.n_seg] - seg[0];
   R.issued = R.cons = 0;
+  R.cslot = R.islot = R.ic = 0;
+  R.cpar = 0u;
   R.limit = R.n_items > 0 ? (long long)R.n_items * P.nch * (P.apg ? P.iters : 1) : 0;
+  if (tid == 0 && R.n_items > 0) {
+    R.iidx = 0;
+    R.icur = R.items[0];
+    R.inext = R.items[R.n_items > 1 ? 1 : 0];
+  }
   for (int s = 0; s < P.slots && R.issued < R.limit; ++s) R.issue_one(tid);
   unsigned nbar = 0;
   int it = 0, ci = 0, reason = 0;  // reason: 0 max iters, 1 converged, 2 non-finite, 3 wait
@@ -465,9 +562,45 @@ __global__ void __launch_bounds__(512, 1) k_pn_solve(PnParams<T> P) {
     const bool check = P.apg && (((it + 1) % P.check_every) == 0 || it + 1 == P.iters);
     const bool wout = !P.apg || check;
     unsigned long long rbits = 0ull;
+    // one item: the rows of the next item are requested before this one's
+    // wait (three row buffers, two m buffers, in item order; nothing is
+    // requested across the end of an iteration, whose last item may write
+    // rows the next one reads)
+    const int k0 = seg[0], kend = seg[P.n_seg];
+    // items k and k + 1 in registers, k + 2 on its way (called for k = k0, k0 + 1, ...)
+    int ia = k0 < kend ? P.items[k0] : 0, ib = k0 + 1 < kend ? P.items[k0 + 1] : 0;
+    auto run_item = [&](int k) {
+      const int item = ia, next = ib, kk = k - k0;
+      ia = ib;
+      ib = k + 2 < kend ? P.items[k + 2] : 0;
+      const bool fw = (item & kPnK) != 0;
+      T *pfk = V.pf + (kk % 3) * P.vb;
+      if (kk == 0) {
+        team_sync(team, nt);  // the rows the previous iteration wrote
+        prefetch_item(P, item, ycur, yprv, pfk, tid, nt);
+      }
+      T *mrow = V.mb + (kk & 1) * V.vup;
+      if (fw) {  // m of this node, written by its backward step
+        constexpr int per = 16 / sizeof(T);
+        const T *src = P.m + (size_t)(item & kPnNodeMask) * P.NUP;
+        for (int e = tid; e < P.NUP / per; e += nt) cp16(mrow + e * per, src + e * per);
+        cp_commit();
+      }
+      if (k + 1 < kend)
+        prefetch_item(P, next, ycur, yprv, V.pf + ((kk + 1) % 3) * P.vb, tid, nt);
+      else
+        cp_commit();
+      if (fw) {
+        cp_wait<2>();
+        forward_item<T, MR>(P, R, V, item, pfk, mrow, yprv, beta, wout, theta, rbits, team, tid,
+                            nt);
+      } else {
+        cp_wait<1>();
+        backward_item<T, MR>(P, R, V, item, pfk, beta, team, tid, nt);
+      }
+    };
     // chains, leaf to head
-    for (int k = seg[0]; k < seg[1]; ++k)
-      backward_item(P, R, V, P.items[k], ycur, yprv, beta, team, tid, nt);
+    for (int k = seg[0]; k < seg[1]; ++k) run_item(k);
     if (!grid_barrier(P.bar, ++nbar * gridDim.x, P.err, P.wait_ns)) {
       reason = 3;
       break;
@@ -488,14 +621,12 @@ __global__ void __launch_bounds__(512, 1) k_pn_solve(PnParams<T> P) {
     bool ok = true;
     // top nodes, stage T .. 1 (a node and its forward step have the same team)
     for (int s = 1; s <= TT && ok; ++s) {
-      for (int k = seg[s]; k < seg[s + 1]; ++k)
-        backward_item(P, R, V, P.items[k], ycur, yprv, beta, team, tid, nt);
+      for (int k = seg[s]; k < seg[s + 1]; ++k) run_item(k);
       if (s < TT) ok = grid_barrier(P.bar, ++nbar * gridDim.x, P.err, P.wait_ns);
     }
     // top nodes, stage 1 .. T
     for (int s = TT + 1; s <= 2 * TT && ok; ++s) {
-      for (int k = seg[s]; k < seg[s + 1]; ++k)
-        forward_item(P, R, V, P.items[k], ycur, yprv, beta, wout, theta, rbits, team, tid, nt);
+      for (int k = seg[s]; k < seg[s + 1]; ++k) run_item(k);
       ok = grid_barrier(P.bar, ++nbar * gridDim.x, P.err, P.wait_ns);
     }
     if (!ok) {
@@ -503,8 +634,7 @@ __global__ void __launch_bounds__(512, 1) k_pn_solve(PnParams<T> P) {
       break;
     }
     // chains, head to leaf
-    for (int k = seg[2 * TT + 1]; k < seg[2 * TT + 2]; ++k)
-      forward_item(P, R, V, P.items[k], ycur, yprv, beta, wout, theta, rbits, team, tid, nt);
+    for (int k = seg[2 * TT + 1]; k < seg[2 * TT + 2]; ++k) run_item(k);
     if (check) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -528,8 +658,12 @@ __global__ void __launch_bounds__(512, 1) k_pn_solve(PnParams<T> P) {
       reason = 3;
     }
   }
-  // no bulk copy may still be writing into this block's memory when it ends
-  for (long long i = R.cons; i < R.issued; ++i) R.wait(i, true);
+  // no copy may still be writing into this block's memory when it ends
+  cp_wait<0>();
+  while (R.cons < R.issued) {
+    R.wait(true);
+    R.consumed();
+  }
   __syncthreads();
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     P.info[0] = P.apg ? it : 1;
@@ -828,7 +962,7 @@ struct PnFactor {
   int *items = nullptr, *seg = nullptr;
   int n_seg = 0, t_top = 0, n_chains = 0, n_top = 0;
   int grid = 0, block = 0, team_threads = 128, teams = 4;
-  int rpc = 0, nch = 0, slots = 0, slot_elems = 0, vec_elems = 0;
+  int qw = 0, nch = 0, slots = 0, slot_elems = 0, vec_elems = 0, b1 = 0, vb = 0;
   size_t smem = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 
@@ -951,20 +1085,35 @@ PnParams<T> pn_params(const PnFactor *f) {
   P.t_top = f->t_top;
   P.team_threads = f->team_threads;
   P.teams = f->teams;
-  P.rpc = f->rpc;
+  P.qw = f->qw;
   P.nch = f->nch;
   P.slots = f->slots;
   P.slot_elems = f->slot_elems;
   P.vec_elems = f->vec_elems;
+  P.b1 = f->b1;
+  P.vb = f->vb;
   return P;
+}
+
+// the instantiation for the handle's precision and rows per thread
+const void *pn_kernel(bool fp32, int mr) {
+  if (fp32)
+    return mr <= 1 ? (const void *)k_pn_solve<float, 1>
+         : mr <= 2 ? (const void *)k_pn_solve<float, 2>
+         : mr <= 4 ? (const void *)k_pn_solve<float, 4>
+                   : (const void *)k_pn_solve<float, 8>;
+  return mr <= 1 ? (const void *)k_pn_solve<double, 1>
+       : mr <= 2 ? (const void *)k_pn_solve<double, 2>
+       : mr <= 4 ? (const void *)k_pn_solve<double, 4>
+                 : (const void *)k_pn_solve<double, 8>;
 }
 
 template <typename T>
 int pn_launch(PnFactor *f, PnParams<T> &P) {
   PN_CUDA(cudaMemsetAsync(f->bar, 0, sizeof(unsigned), f->stream));
   void *args[] = {&P};
-  PN_CUDA(cudaLaunchCooperativeKernel((const void *)k_pn_solve<T>, f->grid, f->block, args,
-                                      f->smem, f->stream));
+  PN_CUDA(cudaLaunchCooperativeKernel(pn_kernel(f->fp32, (f->nu + 127) / 128), f->grid, f->block,
+                                      args, f->smem, f->stream));
   return RN_OK;
 }
 
@@ -1179,19 +1328,27 @@ int pn_width(const rn_tree *tree) {
   return std::max(w, nleaf[0]);
 }
 
+// the matrices in the layout of the ring: column blocks of qw 16-byte units
+// (the last block narrower), each block nu rows, row-major; padding zero
 template <typename T>
 struct PnMatSink {
   T *Phi, *K;
   double *Mc;
-  int nu, ne, ldm;
+  int nu, ne, ldm, qw;
   static void put(void *ctx, int v, const double *P, const double *Kv, const double *M) {
     PnMatSink *s = static_cast<PnMatSink *>(ctx);
+    constexpr int VW = 16 / sizeof(T);
     const size_t ms = (size_t)s->nu * s->ldm;
-    for (int i = 0; i < s->nu; ++i)
-      for (int j = 0; j < s->nu; ++j) {
-        s->Phi[(size_t)v * ms + (size_t)i * s->ldm + j] = (T)P[(size_t)i * s->nu + j];
-        s->K[(size_t)v * ms + (size_t)i * s->ldm + j] = (T)Kv[(size_t)i * s->nu + j];
+    const int cw = s->qw * VW;  // columns of a full block
+    for (int j = 0; j < s->nu; ++j) {
+      const int b = j / cw, wb = std::min(cw, s->ldm - b * cw), jj = j - b * cw;
+      const size_t col = (size_t)s->nu * b * cw + jj;
+      for (int i = 0; i < s->nu; ++i) {
+        const size_t o = (size_t)v * ms + col + (size_t)i * wb;
+        s->Phi[o] = (T)P[(size_t)i * s->nu + j];
+        s->K[o] = (T)Kv[(size_t)i * s->nu + j];
       }
+    }
     if (s->ne > 0)
       std::copy(M, M + (size_t)s->nu * s->ne, s->Mc + (size_t)v * s->nu * s->ne);
   }
@@ -1202,7 +1359,7 @@ int pn_matrices(PnFactor *f, const rn_network *net, const rn_tree *tree, const r
   const size_t ms = (size_t)f->nu * f->ldm;
   std::vector<T> hP((size_t)f->n * ms, T(0)), hK((size_t)f->n * ms, T(0));
   std::vector<double> hM((size_t)f->n * f->nu * std::max(1, f->ne), 0.0), Sd;
-  PnMatSink<T> sink{hP.data(), hK.data(), hM.data(), f->nu, f->ne, f->ldm};
+  PnMatSink<T> sink{hP.data(), hK.data(), hM.data(), f->nu, f->ne, f->ldm, f->qw};
   const int threads = (int)std::max(1u, std::thread::hardware_concurrency());
   int rc = pn_factor_host(net, tree, cost, threads, &PnMatSink<T>::put, &sink, &Sd);
   if (rc) return rc;
@@ -1225,25 +1382,31 @@ int pn_layout(PnFactor *f, int max_ctas, int width) {
   PN_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, f->device));
   PN_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, f->device));
   const size_t avail = (size_t)optin - 1024;  // static shared memory of the kernel
-  f->vec_elems = 2 * f->NXP + 4 * f->NUP + 64;
+  const int vup = (std::max(f->NUP, f->ldm) + 3) & ~3;
+  f->b1 = std::max(f->NUP, f->NXP);
+  f->vb = 2 * f->YP + f->b1 + f->NUP;
+  f->vec_elems = 2 * f->NXP + 4 * vup + 64 + 3 * f->vb + 2 * vup;
   const size_t vec_bytes = ((size_t)f->vec_elems * sz + 127) & ~(size_t)127;
-  const size_t rowb = (size_t)f->ldm * sz;
+  const size_t colb = (size_t)f->nu * 16;  // bytes of one 16-byte column unit of a matrix
+  const int nq = f->ldm / (16 / sz);
   for (int teams = 4; teams >= 1; teams /= 2) {
     const size_t mb = ((size_t)teams * 8 * 8 + 127) & ~(size_t)127;
     if (avail < mb + teams * vec_bytes) continue;
     const size_t per = ((avail - mb) / teams - vec_bytes) & ~(size_t)127;
-    const int max_rows = (int)(per / rowb);
-    if (max_rows < 2) continue;
-    const int rpc0 = std::max(1, max_rows / 4);
-    f->nch = (f->nu + rpc0 - 1) / rpc0;
-    f->rpc = (f->nu + f->nch - 1) / f->nch;
-    f->slots = std::min(8, max_rows / f->rpc);
-    f->slot_elems = f->rpc * f->ldm;
+    const int max_units = (int)(per / colb);  // column units the ring holds
+    if (max_units < 2) continue;
+    // blocks of an odd number of units, four slots where they fit
+    int qw = std::max(1, std::min(nq, max_units / 4));
+    if (qw % 2 == 0) qw = std::max(1, qw - 1);
+    f->qw = qw;
+    f->nch = (nq + qw - 1) / qw;
+    f->slots = std::min(8, max_units / qw);
+    f->slot_elems = (int)((size_t)f->nu * qw * (16 / sz));
     f->teams = teams;
     f->block = teams * f->team_threads;
     f->smem = mb + teams * ((((size_t)f->slots * f->slot_elems * sz + 127) & ~(size_t)127) +
                             vec_bytes);
-    const void *k = f->fp32 ? (const void *)k_pn_solve<float> : (const void *)k_pn_solve<double>;
+    const void *k = pn_kernel(f->fp32, (f->nu + 127) / 128);
     PN_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f->smem));
     int occ = 0;
     PN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, f->block, f->smem));
@@ -1284,7 +1447,11 @@ int pn_create(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
   F->NXP = (F->nx + 3) & ~3;
   F->NUP = (F->nu + 3) & ~3;
   F->YP = 2 * F->NXP + F->NUP;
-  F->ldm = F->fp32 ? ((F->nu + 3) & ~3) : ((F->nu + 1) & ~1);
+  // columns padded to 16 bytes
+  {
+    const int vw = F->fp32 ? 4 : 2;
+    F->ldm = (F->nu + vw - 1) / vw * vw;
+  }
   F->mstride = (long long)F->nu * F->ldm;
   F->W_alpha = cost->W_alpha;
   F->Wx = cost->Wx;

@@ -35,6 +35,7 @@ constexpr int kPnK = 1 << 26;      // the item streams K (forward), else Phi (ba
 constexpr int kPnFirst = 1 << 27;  // first node of a chain in this sweep (leaf / head)
 constexpr int kPnLast = 1 << 28;   // last node of a chain in this sweep (head / leaf)
 constexpr int kPnTop = 1 << 29;    // a node with two or more leaves below it
+constexpr int kPnWarps = 4;        // warps of a team
 
 template <typename T>
 struct PnParams {
@@ -66,8 +67,11 @@ struct PnParams {
   const int *items, *seg;
   int n_seg, t_top;
   int team_threads, teams;
-  // matrix ring of every team: slots of slot_elems T, chunks of rpc rows
-  int rpc, nch, slots, slot_elems, vec_elems;
+  // matrix ring of every team: slots of slot_elems T; a matrix is nch
+  // column blocks of qw 16-byte units (ldm columns in all)
+  int qw, nch, slots, slot_elems, vec_elems;
+  // prefetched rows of an item: yc | yp | b1 (max(NUP, NXP)) | b2 (NUP), vb in all
+  int b1, vb;
 };
 
 // A handle of the per-node form (owned by an rn_factor).
