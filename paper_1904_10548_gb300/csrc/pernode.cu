@@ -290,6 +290,31 @@ __device__ bool grid_barrier(unsigned *bar, unsigned target, int *err, long long
   return ok != 0;
 }
 
+// the flag of another team's node reached `target` (bounded spin by one
+// thread; the caller's team barrier then orders the team's reads after it)
+__device__ bool wait_flag(const unsigned *f, unsigned target, int *err, long long wait_ns) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
+  if (v >= target) return true;
+  const unsigned long long t0 = pn_ns();
+  while (true) {
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
+    if (v >= target) return true;
+    if (*(volatile int *)err != 0) return false;
+    if ((long long)(pn_ns() - t0) > wait_ns) {
+      atomicCAS(err, 0, 6);
+      return false;
+    }
+  }
+}
+
+// publish a node's results of iteration `stamp - 1` (after the team barrier
+// that follows their stores)
+__device__ __forceinline__ void set_flag(unsigned *f, unsigned stamp) {
+  __threadfence();
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(f), "r"(stamp) : "memory");
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -336,11 +361,15 @@ __device__ void prefetch_item(const PnParams<T> &P, int item, const T *ycur, con
 
 template <typename T, int MR>
 __device__ void backward_item(const PnParams<T> &P, Ring<T> &R, TeamVec<T> &V, int item,
-                              const T *pf, T beta, int team, int tid, int nt) {
+                              const T *pf, T beta, unsigned stamp, int team, int tid, int nt) {
   const int v = item & kPnNodeMask;
   const int nx = P.nx, nu = P.nu, NXP = P.NXP, NUP = P.NUP;
   if (item & kPnTop) {
     const int c0 = P.cbeg[v], c1 = P.cend[v];
+    // the children's sums of this iteration (other teams)
+    if (tid == 0)
+      for (int c = c0; c < c1; ++c) wait_flag(P.nflag + c, stamp, P.err, P.wait_ns);
+    team_sync(team, nt);
     for (int i = tid; i < nx; i += nt) {
       T s = T(0);
       for (int c = c0; c < c1; ++c) s += __ldcg(P.lam + (size_t)c * NXP + i);
@@ -382,6 +411,10 @@ __device__ void backward_item(const PnParams<T> &P, Ring<T> &R, TeamVec<T> &V, i
     V.rr[j] = rv;
     if (publish) P.r[(size_t)v * NUP + j] = rv;
   }
+  if (publish) {  // a chain head's or top node's sums, for its parent
+    team_sync(team, nt);
+    if (tid == 0) set_flag(P.nflag + v, stamp);
+  }
   // this node's sums are its parent's child sums when the chain goes on
   T *t = V.sl;
   V.sl = V.lamb;
@@ -394,7 +427,8 @@ __device__ void backward_item(const PnParams<T> &P, Ring<T> &R, TeamVec<T> &V, i
 template <typename T, int MR>
 __device__ void forward_item(const PnParams<T> &P, Ring<T> &R, TeamVec<T> &V, int item,
                              const T *pf, const T *mrow, T *yprv, T beta, bool write_out,
-                             double theta, unsigned long long &rbits, int team, int tid, int nt) {
+                             double theta, unsigned long long &rbits, unsigned stamp, int team,
+                             int tid, int nt) {
   const int v = item & kPnNodeMask;
   const int nx = P.nx, nu = P.nu, NXP = P.NXP, NUP = P.NUP;
   if (item & (kPnTop | kPnFirst)) {
@@ -403,6 +437,9 @@ __device__ void forward_item(const PnParams<T> &P, Ring<T> &R, TeamVec<T> &V, in
       for (int i = tid; i < nx; i += nt) V.xa[i] = P.x0 ? P.x0[i] : T(0);
       for (int j = tid; j < nu; j += nt) V.ua[j] = P.q ? P.q[j] : T(0);
     } else {
+      // the parent's values of this iteration (another team)
+      if (tid == 0) wait_flag(P.nflag + P.n + a, stamp, P.err, P.wait_ns);
+      team_sync(team, nt);
       for (int i = tid; i < nx; i += nt) V.xa[i] = __ldcg(P.xo + (size_t)a * NXP + i);
       for (int j = tid; j < nu; j += nt) V.ua[j] = __ldcg(P.uo + (size_t)a * NUP + j);
     }
@@ -483,6 +520,10 @@ __device__ void forward_item(const PnParams<T> &P, Ring<T> &R, TeamVec<T> &V, in
       yn[2 * NXP + j] = y3;
     }
   }
+  if (top) {  // a top node's values, for its children
+    team_sync(team, nt);
+    if (tid == 0) set_flag(P.nflag + P.n + v, stamp);
+  }
   T *t = V.xa;
   V.xa = V.x;
   V.x = t;
@@ -561,6 +602,7 @@ __global__ void __launch_bounds__(512, 1) k_pn_solve(PnParams<T> P) {
     const double theta = P.apg ? P.theta[it] : 1.0;
     const bool check = P.apg && (((it + 1) % P.check_every) == 0 || it + 1 == P.iters);
     const bool wout = !P.apg || check;
+    const unsigned stamp = (unsigned)it + 1u;  // flags of this iteration's results
     unsigned long long rbits = 0ull;
     // one item: the rows of the next item are requested before this one's
     // wait (three row buffers, two m buffers, in item order; nothing is
@@ -592,20 +634,20 @@ __global__ void __launch_bounds__(512, 1) k_pn_solve(PnParams<T> P) {
         cp_commit();
       if (fw) {
         cp_wait<2>();
-        forward_item<T, MR>(P, R, V, item, pfk, mrow, yprv, beta, wout, theta, rbits, team, tid,
-                            nt);
+        forward_item<T, MR>(P, R, V, item, pfk, mrow, yprv, beta, wout, theta, rbits, stamp, team,
+                            tid, nt);
       } else {
         cp_wait<1>();
-        backward_item<T, MR>(P, R, V, item, pfk, beta, team, tid, nt);
+        backward_item<T, MR>(P, R, V, item, pfk, beta, stamp, team, tid, nt);
       }
     };
     // chains, leaf to head
     for (int k = seg[0]; k < seg[1]; ++k) run_item(k);
-    if (!grid_barrier(P.bar, ++nbar * gridDim.x, P.err, P.wait_ns)) {
-      reason = 3;
-      break;
-    }
-    if (pend) {  // the check of the previous iteration, now that every block added to it
+    if (pend) {  // the check of the previous iteration, once every block has added to it
+      if (!grid_barrier(P.bar, ++nbar * gridDim.x, P.err, P.wait_ns)) {
+        reason = 3;
+        break;
+      }
       pend = false;
       const double rv =
           __longlong_as_double((long long)__ldcg(P.res + ci - 1)) * P.invgamma;
@@ -618,21 +660,13 @@ __global__ void __launch_bounds__(512, 1) k_pn_solve(PnParams<T> P) {
         break;
       }
     }
-    bool ok = true;
-    // top nodes, stage T .. 1 (a node and its forward step have the same team)
-    for (int s = 1; s <= TT && ok; ++s) {
-      for (int k = seg[s]; k < seg[s + 1]; ++k) run_item(k);
-      if (s < TT) ok = grid_barrier(P.bar, ++nbar * gridDim.x, P.err, P.wait_ns);
-    }
-    // top nodes, stage 1 .. T
-    for (int s = TT + 1; s <= 2 * TT && ok; ++s) {
-      for (int k = seg[s]; k < seg[s + 1]; ++k) run_item(k);
-      ok = grid_barrier(P.bar, ++nbar * gridDim.x, P.err, P.wait_ns);
-    }
-    if (!ok) {
-      reason = 3;
-      break;
-    }
+    // top nodes, stage T .. 1, then 1 .. T: every item waits for the flags
+    // of the nodes it reads (children going up, the parent going down),
+    // which earlier stages of other teams set; a node and its forward step
+    // have the same team
+    // (a wait that gave up has set the error word: the launch ends at the
+    // next residual check, where every block sees it)
+    for (int k = seg[1]; k < seg[2 * TT + 1]; ++k) run_item(k);
     // chains, head to leaf
     for (int k = seg[2 * TT + 1]; k < seg[2 * TT + 2]; ++k) run_item(k);
     if (check) {
@@ -954,7 +988,7 @@ struct PnFactor {
   int beta_cap = 0;
   unsigned long long *res = nullptr;
   int res_cap = 0;
-  unsigned *bar = nullptr;
+  unsigned *bar = nullptr, *nflag = nullptr;
   int *err = nullptr, *info = nullptr;
   double *partial = nullptr, *norm2 = nullptr;
   bool have_data = false;
@@ -1074,6 +1108,7 @@ PnParams<T> pn_params(const PnFactor *f) {
   P.uo = static_cast<T *>(f->uo);
   P.xo = static_cast<T *>(f->xo);
   P.bar = f->bar;
+  P.nflag = f->nflag;
   P.err = f->err;
   P.info = f->info;
   P.wait_ns = f->wait_ns;
@@ -1111,6 +1146,7 @@ const void *pn_kernel(bool fp32, int mr) {
 template <typename T>
 int pn_launch(PnFactor *f, PnParams<T> &P) {
   PN_CUDA(cudaMemsetAsync(f->bar, 0, sizeof(unsigned), f->stream));
+  PN_CUDA(cudaMemsetAsync(f->nflag, 0, 2 * (size_t)f->n * sizeof(unsigned), f->stream));
   void *args[] = {&P};
   PN_CUDA(cudaLaunchCooperativeKernel(pn_kernel(f->fp32, (f->nu + 127) / 128), f->grid, f->block,
                                       args, f->smem, f->stream));
@@ -1526,7 +1562,7 @@ int pn_create(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
       (rc = talloc(&F->lam, (size_t)n * F->NXP)) || (rc = talloc(&F->r, (size_t)n * F->NUP)) ||
       (rc = talloc(&F->uo, (size_t)n * F->NUP)) || (rc = talloc(&F->xo, (size_t)n * F->NXP)) ||
       (rc = pn_alloc(F, &F->x0, nx)) || (rc = pn_alloc(F, &F->q, nu)) ||
-      (rc = pn_alloc(F, &F->alpha, (size_t)n * nu)) || (rc = pn_alloc(F, &F->bar, 1)) ||
+      (rc = pn_alloc(F, &F->alpha, (size_t)n * nu)) || (rc = pn_alloc(F, &F->bar, 1)) || (rc = pn_alloc(F, &F->nflag, 2 * (size_t)n)) ||
       (rc = pn_alloc(F, &F->err, 1)) || (rc = pn_alloc(F, &F->info, 8)) ||
       (rc = pn_alloc(F, &F->partial, 3 * kPnParts)) || (rc = pn_alloc(F, &F->norm2, 1)))
     return rc;

@@ -56,7 +56,9 @@ struct PnParams {
   double *uavg, *xavg;         // averaged primal (nullable), NUP / NXP per node
   const double *beta, *theta;  // APG sequences
   unsigned long long *res;     // per check: max |y+ - w| as ordered bits
-  unsigned *bar;               // grid barrier counter
+  unsigned *bar;               // grid barrier counter (residual checks)
+  unsigned *nflag;             // per node: backward sums [0, n), forward values [n, 2n)
+                               // published for iteration k (value k + 1)
   int *err, *info;             // error word; info: iters, checks, reason, -, stamps
   long long wait_ns;
   double gamma, invgamma, tol;
