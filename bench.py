@@ -274,25 +274,29 @@ KERNEL_SOURCES = ["paper_1904_10548_gb300/csrc/kernels.cuh",
                   "paper_1904_10548_gb300/csrc/mixed_kernels.cu"]
 
 
-def kernel_source_hash() -> str:
+PERNODE_SOURCES = ["paper_1904_10548_gb300/csrc/pernode.h",
+                   "paper_1904_10548_gb300/csrc/pernode.cu"]
+
+
+def kernel_source_hash(sources=None) -> str:
     import hashlib
     h = hashlib.sha256()
-    for rel in KERNEL_SOURCES:
+    for rel in sources or KERNEL_SOURCES:
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def measured_traffic(kind: str):
-    """Per-iteration DRAM bytes of the persistent kernel from
-    profiles/traffic.json, or None when the sources changed since."""
+def measured_traffic(kind: str, sources=None):
+    """Per-iteration DRAM bytes of a persistent kernel from
+    profiles/traffic.json, or None when its sources changed since."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f).get(kind)
     except (OSError, ValueError):
         return None
-    if not d or d.get("source_hash") != kernel_source_hash():
+    if not d or d.get("source_hash") != kernel_source_hash(sources):
         return None
     return d["dram_bytes_per_iter"]
 
@@ -571,6 +575,7 @@ def run_per_node(rn, gamma, iters32, iters64):
         out[key] = {"iters": iters, "us_per_iter": us, "iters_per_s": 1e6 / us,
                     "algorithmic_bytes_per_iter": bytes_it, "achieved_gbs": gbs,
                     "frac_hbm": gbs / hbm_peak, "peak_source": f"{hbm_src} copy bandwidth",
+                    "traffic_per_iter": measured_traffic(f"k_pn_{key}", PERNODE_SOURCES),
                     "factor_step_s": factor_s, "grid_ctas": info["grid_ctas"],
                     "block_threads": info["block_threads"],
                     "device_bytes": info["device_bytes"]}

@@ -313,3 +313,29 @@ def test_refusals_of_the_per_node_form():
         fac.dual_gradient_noalloc(w, u, x)
     assert ei.value.status == B.RN_ERR_UNSUPPORTED
     fac.close()
+
+
+def test_flag_wait_that_runs_out_reports_timeout_and_the_handle_recovers():
+    """A top node waits for its children's flags, which other teams set
+    only after their whole chain: with a 1 us bound the wait runs out, the
+    error word ends the launch at the next residual check, and the call
+    returns RN_ERR_TIMEOUT.  Nothing is withheld or faulted; a handle with
+    the default bound then solves normally."""
+    kind = "barcelona32_A"
+    pb = problem(kind)
+    P, F, S = oracle_for(kind, pb)
+    gamma = O.step_size(O.power_iteration(P, F, 100))
+    d = pb.data
+    bad = rn.Factor(pb.net, pb.cost, pb.tree, gamma=gamma, factor_form=PN, wait_us=1)
+    for _ in range(2):
+        with pytest.raises(B.RapidNetError) as ei:
+            bad.solve(d.x0, d.q, d.demand, d.alpha, max_iters=50)
+        assert ei.value.status == B.RN_ERR_TIMEOUT
+        assert "gave up" in str(ei.value)
+    bad.close()
+    ref = O.apg(P, F, S, 100, gamma)
+    good = rn.Factor(pb.net, pb.cost, pb.tree, gamma=gamma, factor_form=PN)
+    out = good.solve(d.x0, d.q, d.demand, d.alpha, max_iters=100)
+    good.close()
+    for k in "uxy":
+        assert rel_err(out[k], getattr(ref, k)) <= 1e-6, k
