@@ -76,6 +76,11 @@ def problem(kind):
         net = make_network(160, 300, 200, 40, seed=17)
         tree = make_tree([3, 2, 1, 1, 1, 1], seed=18)
         pb = Problem(net=net, cost=make_cost(net, seed=17), tree=tree, data=make_data(net, tree, 19))
+    elif base == "widest":
+        # six to eight rows per thread; one team per block (its vectors fill the shared memory)
+        net = make_network(400, 720, 500, 100, seed=20)
+        tree = make_tree([2, 2, 1, 1], seed=21)
+        pb = Problem(net=net, cost=make_cost(net, seed=20), tree=tree, data=make_data(net, tree, 22))
     else:
         raise KeyError(kind)
     if kind.endswith("_A"):
@@ -115,7 +120,7 @@ def dual_gradient(fac, pb, w, data=True):
 
 
 DG_KINDS = ["tiny_A", "barcelona32_A", "uneven0_A", "uneven1_A", "single_A", "ne0_A", "bushy_A",
-            "dense_A", "tiny", "wide_A"]
+            "dense_A", "tiny", "wide_A", "widest_A"]
 
 
 @pytest.mark.parametrize("kind", DG_KINDS)
@@ -139,7 +144,7 @@ def test_dual_gradient_matches_oracle(kind):
     fac.close()
 
 
-@pytest.mark.parametrize("kind", ["tiny_A", "barcelona32_A", "dense_A"])
+@pytest.mark.parametrize("kind", ["tiny_A", "barcelona32_A", "dense_A", "widest_A"])
 def test_fp32_dual_gradient_matches_oracle(kind):
     pb = problem(kind)
     P, F, S = oracle_for(kind, pb)
