@@ -546,8 +546,10 @@ def run_per_node(rn, gamma, iters32, iters64):
     per-node matrices): barcelona512, Phi_nu and K_nu streamed from HBM at
     every iteration.  Algorithmic bytes per node and iteration: the 1,491
     vector values of the shared form plus the 2 nu^2 matrix entries, in the
-    iteration's precision.  FP32 against FP64 of the same form at the same
-    iteration count for the error; the factor step (host, FP64) timed."""
+    iteration's precision; the mixed precision adds one FP64 evaluation
+    (the same bytes at 8 B) per refresh of its base, every 20 iterations.
+    FP32 and mixed against FP64 of the same form at the same iteration
+    count for the error; the factor step (host, FP64) timed."""
     import numpy as np
     from synthetic import make_problem
     pb = make_problem(CONFIG_NAME)
@@ -557,7 +559,11 @@ def run_per_node(rn, gamma, iters32, iters64):
     rel = lambda a, b: float(np.abs(a - b).max() / np.abs(b).max())
     out = {"workload": WORKLOAD.split(":")[0] + " (A = I), per-node matrices", "nodes": n}
     res = {}
-    for prec, iters, bpv in ((rn.RN_PREC_FP32, iters32, 4), (rn.RN_PREC_FP64, iters64, 8)):
+    per_val = (1491 + 2 * nu * nu) * n
+    for key, prec, iters, bytes_it in (("fp32", rn.RN_PREC_FP32, iters32, per_val * 4),
+                                       ("fp64", rn.RN_PREC_FP64, iters64, per_val * 8),
+                                       ("mixed", rn.RN_PREC_MIXED, iters32,
+                                        per_val * 4 + per_val * 8 / 20)):
         t0 = time.perf_counter()
         f = rn.Factor(pb.net, pb.cost, pb.tree, gamma=gamma, precision=prec,
                       factor_form=rn.RN_FACTOR_PER_NODE)
@@ -568,22 +574,23 @@ def run_per_node(rn, gamma, iters32, iters64):
         acc = f.solve(d.x0, d.q, d.demand, d.alpha, max_iters=iters64)
         f.close()
         us = r["apg_ms"] * 1e3 / iters
-        bytes_it = (1491 + 2 * nu * nu) * bpv * n
         gbs = bytes_it / (us * 1e-6) / 1e9
-        key = "fp32" if prec == rn.RN_PREC_FP32 else "fp64"
         res[key] = acc
         out[key] = {"iters": iters, "us_per_iter": us, "iters_per_s": 1e6 / us,
                     "algorithmic_bytes_per_iter": bytes_it, "achieved_gbs": gbs,
                     "frac_hbm": gbs / hbm_peak, "peak_source": f"{hbm_src} copy bandwidth",
-                    "traffic_per_iter": measured_traffic(f"k_pn_{key}", PERNODE_SOURCES),
+                    "traffic_per_iter": (measured_traffic(f"k_pn_{key}", PERNODE_SOURCES)
+                                         if key != "mixed" else None),
                     "factor_step_s": factor_s, "grid_ctas": info["grid_ctas"],
                     "block_threads": info["block_threads"],
                     "device_bytes": info["device_bytes"]}
-    out["fp32_vs_fp64"] = {"iters": iters64, "cost_rel": abs(res["fp32"]["cost"] - res["fp64"]["cost"])
-                           / abs(res["fp64"]["cost"]),
-                           "u_rel": rel(res["fp32"]["u"], res["fp64"]["u"]),
-                           "x_rel": rel(res["fp32"]["x"], res["fp64"]["x"]),
-                           "y_rel": rel(res["fp32"]["y"], res["fp64"]["y"])}
+    for key in ("fp32", "mixed"):
+        out[f"{key}_vs_fp64"] = {"iters": iters64,
+                                 "cost_rel": abs(res[key]["cost"] - res["fp64"]["cost"])
+                                 / abs(res["fp64"]["cost"]),
+                                 "u_rel": rel(res[key]["u"], res["fp64"]["u"]),
+                                 "x_rel": rel(res[key]["x"], res["fp64"]["x"]),
+                                 "y_rel": rel(res[key]["y"], res["fp64"]["y"])}
     return out
 
 

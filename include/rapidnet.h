@@ -49,8 +49,7 @@ typedef enum {
 
 typedef enum {
   RN_PREC_FP64 = 0,       /* every step of the iteration in FP64 */
-  RN_PREC_MIXED = 1,      /* FP32 iteration around an FP64 reference point
-                             (shared-operator form only) */
+  RN_PREC_MIXED = 1,      /* FP32 iteration around an FP64 reference point */
   RN_PREC_FP32 = 2        /* every step of the iteration in FP32, the factor
                              step in FP64 (per-node form only) */
 } rn_precision;
@@ -63,9 +62,11 @@ typedef enum {
  *   RN_FACTOR_PER_NODE the general recursion with one matrix pair
  *                      (Phi_nu, K_nu) per node from the factor step,
  *                      streamed from device memory at every evaluation;
- *                      any A, nx and nu up to 1024, precision RN_PREC_FP64
- *                      or RN_PREC_FP32; no batched or served solves, no
- *                      duality gap, no allocation-free entry point;
+ *                      any A, nx and nu up to 1024, every precision
+ *                      (RN_PREC_MIXED: FP32 matrices for the iterations and
+ *                      an FP64 copy for the reference point, both on the
+ *                      device); no batched or served solves, no duality
+ *                      gap, no allocation-free entry point;
  *   RN_FACTOR_AUTO (0) the shared form, or the per-node form for A != I or
  *                      RN_PREC_FP32. */
 enum { RN_FACTOR_AUTO = 0, RN_FACTOR_SHARED = 1, RN_FACTOR_PER_NODE = 2 };
@@ -244,9 +245,12 @@ typedef struct {
  * FP64 (one worker thread per core), uploads Phi_nu and K_nu in the
  * iteration's precision (rows padded to 16 bytes: 2 nu^2 values per node,
  * 1.1 GB in FP32 for 10^4 nodes of nu = 114) and (I - Phi_nu Q_nu) E' in
- * FP64, and estimates L by power iteration in the iteration's precision.
+ * FP64, and estimates L by power iteration in the iteration's precision
+ * (FP64 with RN_PREC_MIXED).
+ * With RN_PREC_MIXED it holds both an FP32 and an FP64 set (the FP64 one
+ * evaluates x*(yb) at every refresh and the final primal).
  * It returns RN_ERR_INVAL where L' Q L is not positive definite at some
- * node, RN_ERR_UNSUPPORTED for nx or nu above 1024 or RN_PREC_MIXED. */
+ * node, RN_ERR_UNSUPPORTED for nx or nu above 1024. */
 int rapidnet_factor(const rn_network *net, const rn_tree *tree,
                     const rn_cost *cost, const rn_opts *opts,
                     rn_factor **out);

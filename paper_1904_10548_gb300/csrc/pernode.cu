@@ -341,6 +341,26 @@ __device__ void prefetch_item(const PnParams<T> &P, int item, const T *ycur, con
   const int v = item & kPnNodeMask;
   const bool fw = (item & kPnK) != 0;
   const int YP = P.YP;
+  if (P.delta && fw) {  // the base rows of the delta form: ybh (YP) | xref (NXP) | uref (NUP)
+    const T *yc = ycur + (size_t)v * YP, *yp = yprv + (size_t)v * YP;
+    const T *bh = P.ybh + (size_t)v * YP, *xr = P.xref + (size_t)v * P.NXP,
+            *ur = P.uref + (size_t)v * P.NUP;
+    const int uY = YP / per, uX = P.NXP / per, uU = P.NUP / per;
+    for (int e = tid; e < 3 * uY + uX + uU; e += nt) {
+      if (e < uY)
+        cp16(dst + e * per, yc + e * per);
+      else if (e < 2 * uY)
+        cp16(dst + YP + (e - uY) * per, yp + (e - uY) * per);
+      else if (e < 3 * uY)
+        cp16(dst + 2 * YP + (e - 2 * uY) * per, bh + (e - 2 * uY) * per);
+      else if (e < 3 * uY + uX)
+        cp16(dst + 3 * YP + (e - 3 * uY) * per, xr + (e - 3 * uY) * per);
+      else
+        cp16(dst + 3 * YP + P.NXP + (e - 3 * uY - uX) * per, ur + (e - 3 * uY - uX) * per);
+    }
+    cp_commit();
+    return;
+  }
   const T *b1 = fw ? (P.gd ? P.gd + (size_t)v * P.NXP : nullptr)
                    : (P.c0 ? P.c0 + (size_t)v * P.NUP : nullptr);
   const T *b2 = (!fw && P.mc) ? P.mc + (size_t)v * P.NUP : nullptr;
@@ -424,6 +444,83 @@ __device__ void backward_item(const PnParams<T> &P, Ring<T> &R, TeamVec<T> &V, i
   V.rr = t;
 }
 
+// The dual update in delta form (RN_PREC_MIXED): with h = fl32(yb), the
+// delta dw of w and x = xref + x_lin(dw), the clamp of w = h + dw onto
+// gamma (box - x) decides, and the new delta d+ = y+ - h is formed from
+// small terms (dw - edge, or -h) so that the increments of a small step
+// survive in FP32:
+//   g = t - h with t = w - clamp(w, gamma (lo - x), gamma (hi - x)),
+//   d+ = g, or h (q - 1) + g q when the ball |t| <= W is active
+//   (q = W / |t|), and d+ = dw - edge, or -h, on the input block.
+template <typename T>
+__device__ void delta_prox(const PnParams<T> &P, TeamVec<T> &V, int v, const T *pf, T *yprv,
+                           T beta, bool write_out, unsigned long long &rbits, int team, int tid,
+                           int nt) {
+  const int nx = P.nx, nu = P.nu, NXP = P.NXP, YP = P.YP;
+  const T g = (T)P.gamma;
+  const T *dc = pf, *dp = pf + YP, *bh = pf + 2 * YP, *xr = pf + 3 * YP, *ur = xr + NXP;
+  T *dn = yprv + (size_t)v * YP;
+  T *sw = (write_out && P.swy) ? P.swy + (size_t)v * YP : nullptr;
+  T n1 = T(0), n2 = T(0);
+  for (int i = tid; i < nx; i += nt) {
+    const T w1 = dc[i] + beta * (dc[i] - dp[i]), w2 = dc[NXP + i] + beta * (dc[NXP + i] - dp[NXP + i]);
+    const T h1 = bh[i], h2 = bh[NXP + i];
+    const T x = xr[i] + V.x[i];
+    const T lo = g * (P.xmin[i] - x), hi = g * (P.xmax[i] - x), wa = h1 + w1;
+    const T g1 = wa > hi ? w1 - hi : (wa < lo ? w1 - lo : -h1);
+    const T sa = g * (P.xs[i] - x);
+    const T g2 = (h2 + w2) < sa ? w2 - sa : -h2;
+    const T t1 = h1 + g1, t2 = h2 + g2;
+    n1 += t1 * t1;
+    n2 += t2 * t2;
+  }
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  n1 = wsum(n1);
+  n2 = wsum(n2);
+  if (lane == 0) {
+    V.red[warp] = n1;
+    V.red[32 + warp] = n2;
+  }
+  team_sync(team, nt);
+  n1 = T(0);
+  n2 = T(0);
+  for (int w = 0; w < nw; ++w) {
+    n1 += V.red[w];
+    n2 += V.red[32 + w];
+  }
+  const T q1 = n1 > T(0) ? P.Wx / sqrt(n1) : T(1);
+  const T q2 = n2 > T(0) ? P.Ws / sqrt(n2) : T(1);
+  for (int i = tid; i < nx; i += nt) {
+    const T w1 = dc[i] + beta * (dc[i] - dp[i]), w2 = dc[NXP + i] + beta * (dc[NXP + i] - dp[NXP + i]);
+    const T h1 = bh[i], h2 = bh[NXP + i];
+    const T x = xr[i] + V.x[i];
+    const T lo = g * (P.xmin[i] - x), hi = g * (P.xmax[i] - x), wa = h1 + w1;
+    const T g1 = wa > hi ? w1 - hi : (wa < lo ? w1 - lo : -h1);
+    const T sa = g * (P.xs[i] - x);
+    const T g2 = (h2 + w2) < sa ? w2 - sa : -h2;
+    const T d1 = q1 < T(1) ? fma(h1, q1 - T(1), g1 * q1) : g1;
+    const T d2 = q2 < T(1) ? fma(h2, q2 - T(1), g2 * q2) : g2;
+    rbits = max(rbits, max(res_bits((double)(d1 - w1)), res_bits((double)(d2 - w2))));
+    dn[i] = d1;
+    dn[NXP + i] = d2;
+    if (sw) {
+      sw[i] = w1;
+      sw[NXP + i] = w2;
+    }
+  }
+  for (int j = tid; j < nu; j += nt) {
+    const T a3 = dc[2 * NXP + j];
+    const T w3 = a3 + beta * (a3 - dp[2 * NXP + j]);
+    const T h3 = bh[2 * NXP + j];
+    const T u = ur[j] + V.u[j];
+    const T lo = g * (P.umin[j] - u), hi = g * (P.umax[j] - u), wa = h3 + w3;
+    const T d3 = wa > hi ? w3 - hi : (wa < lo ? w3 - lo : -h3);
+    rbits = max(rbits, res_bits((double)(d3 - w3)));
+    dn[2 * NXP + j] = d3;
+    if (sw) sw[2 * NXP + j] = w3;
+  }
+}
+
 template <typename T, int MR>
 __device__ void forward_item(const PnParams<T> &P, Ring<T> &R, TeamVec<T> &V, int item,
                              const T *pf, const T *mrow, T *yprv, T beta, bool write_out,
@@ -457,17 +554,20 @@ __device__ void forward_item(const PnParams<T> &P, Ring<T> &R, TeamVec<T> &V, in
     V.x[i] = xv;
     if (store) P.xo[(size_t)v * NXP + i] = xv;
   }
-  if (P.uavg) {
+  if (P.uavg) {  // (the delta form adds x*(yb))
+    const T *xr = P.delta ? pf + 3 * P.YP : nullptr, *ur = P.delta ? xr + NXP : nullptr;
     for (int i = tid; i < nx; i += nt) {
       double *xa = P.xavg + (size_t)v * NXP + i;
-      *xa = (1.0 - theta) * *xa + theta * (double)V.x[i];
+      *xa = (1.0 - theta) * *xa + theta * (double)(V.x[i] + (xr ? xr[i] : T(0)));
     }
     for (int j = tid; j < nu; j += nt) {
       double *ua = P.uavg + (size_t)v * NUP + j;
-      *ua = (1.0 - theta) * *ua + theta * (double)V.u[j];
+      *ua = (1.0 - theta) * *ua + theta * (double)(V.u[j] + (ur ? ur[j] : T(0)));
     }
   }
-  if (P.apg) {
+  if (P.apg && P.delta) {
+    delta_prox(P, V, v, pf, yprv, beta, write_out, rbits, team, tid, nt);
+  } else if (P.apg) {
     // y+ = prox_{gamma g*}(w + gamma H x): distance-to-set prox of the soft
     // state terms (§4.3) through the Moreau decomposition (§4.2), box
     // projection on the input block
@@ -596,11 +696,13 @@ __global__ void __launch_bounds__(512, 1) k_pn_solve(PnParams<T> P) {
   const int TT = P.t_top;
   const int n_it = P.apg ? P.iters : 1;
   for (; it < n_it; ++it) {
-    const T *ycur = (it & 1) ? P.yb : P.ya;
-    T *yprv = P.apg ? ((it & 1) ? P.ya : P.yb) : P.ya;
-    const T beta = P.apg ? (T)P.beta[it] : T(0);
-    const double theta = P.apg ? P.theta[it] : 1.0;
-    const bool check = P.apg && (((it + 1) % P.check_every) == 0 || it + 1 == P.iters);
+    const int git = P.it0 + it;  // iteration of the solve
+    const T *ycur = (git & 1) ? P.yb : P.ya;
+    T *yprv = P.apg ? ((git & 1) ? P.ya : P.yb) : P.ya;
+    const T beta = P.apg ? (T)P.beta[git] : T(0);
+    const double theta = P.apg ? P.theta[git] : 1.0;
+    const bool check =
+        P.apg && (((git + 1) % P.check_every) == 0 || git + 1 == P.iters_total);
     const bool wout = !P.apg || check;
     const unsigned stamp = (unsigned)it + 1u;  // flags of this iteration's results
     unsigned long long rbits = 0ull;
@@ -999,8 +1101,16 @@ struct PnFactor {
   int qw = 0, nch = 0, slots = 0, slot_elems = 0, vec_elems = 0, b1 = 0, vb = 0;
   size_t smem = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // RN_PREC_MIXED: this FP32 handle iterates on the delta d = y - yb; the
+  // FP64 twin evaluates x*(yb) at every refresh and the final x*(w)
+  bool mixed = false;
+  int refresh_every = 20;
+  PnFactor *twin = nullptr;
+  double *ybase = nullptr;                              // yb, n x YP
+  float *ybh = nullptr, *uref = nullptr, *xref = nullptr, *swy = nullptr;
 
   ~PnFactor() {
+    delete twin;
     cudaSetDevice(device);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
@@ -1172,6 +1282,8 @@ int pn_eval(PnFactor *f, bool linear) {
   PnParams<T> P = pn_params<T>(f);
   P.apg = 0;
   P.iters = 1;
+  P.it0 = 0;
+  P.iters_total = 1;
   P.check_every = 1;
   if (!linear) {
     P.c0 = static_cast<const T *>(f->c0);
@@ -1420,6 +1532,8 @@ int pn_layout(PnFactor *f, int max_ctas, int width) {
   const size_t avail = (size_t)optin - 1024;  // static shared memory of the kernel
   const int vup = (std::max(f->NUP, f->ldm) + 3) & ~3;
   f->b1 = std::max(f->NUP, f->NXP);
+  // the delta form's forward rows: ybh | xref | uref after y and y_prev
+  if (f->mixed) f->b1 = std::max(f->b1, f->YP + f->NXP + f->NUP);
   f->vb = 2 * f->YP + f->b1 + f->NUP;
   f->vec_elems = 2 * f->NXP + 4 * vup + 64 + 3 * f->vb + 2 * vup;
   const size_t vec_bytes = ((size_t)f->vec_elems * sz + 127) & ~(size_t)127;
@@ -1475,7 +1589,17 @@ int pn_create(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
   PnFactor *F = f.get();
   F->device = o.device;
   F->stream = o.stream;
-  F->fp32 = o.fp32;
+  F->fp32 = o.fp32 || o.mixed;
+  F->mixed = o.mixed;
+  F->refresh_every = std::max(1, o.refresh_every);
+  PnOptions o2 = o;  // the FP64 twin of a mixed handle: its step size serves both
+  if (o.mixed) {
+    o2.mixed = false;
+    o2.fp32 = false;
+    PnFactor *tw = nullptr;
+    if ((rc = pn_create(net, tree, cost, o2, &tw))) return rc;
+    F->twin = tw;
+  }
   F->nx = net->nx;
   F->nu = net->nu;
   F->nd = net->nd;
@@ -1568,11 +1692,20 @@ int pn_create(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
       (rc = pn_alloc(F, &F->err, 1)) || (rc = pn_alloc(F, &F->info, 8)) ||
       (rc = pn_alloc(F, &F->partial, 3 * kPnParts)) || (rc = pn_alloc(F, &F->norm2, 1)))
     return rc;
+  if (F->mixed &&
+      ((rc = pn_alloc(F, &F->ybase, (size_t)n * F->YP)) || (rc = pn_alloc(F, &F->ybh, (size_t)n * F->YP)) ||
+       (rc = pn_alloc(F, &F->uref, (size_t)n * F->NUP)) ||
+       (rc = pn_alloc(F, &F->xref, (size_t)n * F->NXP)) ||
+       (rc = pn_alloc(F, &F->swy, (size_t)n * F->YP))))
+    return rc;
   PN_CUDA(cudaMemsetAsync(F->err, 0, sizeof(int), F->stream));
   PN_CUDA(cudaMemsetAsync(F->uo, 0, (size_t)n * F->NUP * (F->fp32 ? 4 : 8), F->stream));
   PN_CUDA(cudaMemsetAsync(F->xo, 0, (size_t)n * F->NXP * (F->fp32 ? 4 : 8), F->stream));
   // step size: gamma = 1 / (1.01 L), L by power iteration on the dual Hessian
-  if (o.gamma > 0.0) {
+  if (F->twin) {
+    F->gamma = F->twin->gamma;
+    F->L = F->twin->L;
+  } else if (o.gamma > 0.0) {
     F->gamma = o.gamma;
   } else {
     rc = F->fp32 ? pn_power<float>(F, o.power_iters, &F->L)
@@ -1710,6 +1843,8 @@ int pn_solve_t(PnFactor *f, const double *x0, const double *q, const double *dem
   PnParams<T> P = pn_params<T>(f);
   P.apg = 1;
   P.iters = max_iters;
+  P.it0 = 0;
+  P.iters_total = max_iters;
   P.check_every = f->check_every;
   P.tol = tol > 0.0 ? tol : 0.0;
   P.c0 = static_cast<const T *>(f->c0);
@@ -1785,6 +1920,229 @@ int pn_solve_t(PnFactor *f, const double *x0, const double *q, const double *dem
 
 }  // namespace
 
+namespace {
+
+// ---------------------------------------------------------------------------
+// RN_PREC_MIXED on the per-node form: FP32 iterations on the delta d = y - yb
+// (linear evaluations of the FP32 matrices, x*(w) = x*(yb) + x_lin(dw), the
+// dual update in delta form), the FP64 twin evaluating x*(yb) at the start
+// and after every refresh (yb += d every refresh_every iterations), and the
+// final x*(w) in FP64 (the same scheme as the shared-operator mixed kernel)
+// ---------------------------------------------------------------------------
+// yb = y_warm (padded, FP64) or 0, ybh = fl32(yb), d = 0 in both buffers
+__global__ void k_pnm_init(int n, int nx, int nu, int NXP, int YP, const double *src,
+                           double *yb, float *ybh, float *da, float *db) {
+  const int ny = 2 * nx + nu;
+  for (int v = blockIdx.x; v < n; v += gridDim.x)
+    for (int e = threadIdx.x; e < YP; e += blockDim.x) {
+      int k = -1;
+      if (e < nx) k = e;
+      else if (e >= NXP && e < NXP + nx) k = nx + (e - NXP);
+      else if (e >= 2 * NXP && e < 2 * NXP + nu) k = 2 * nx + (e - 2 * NXP);
+      const double val = (v > 0 && k >= 0 && src) ? src[(size_t)v * ny + k] : 0.0;
+      const size_t o = (size_t)v * YP + e;
+      yb[o] = val;
+      ybh[o] = (float)val;
+      da[o] = 0.f;
+      db[o] = 0.f;
+    }
+}
+
+// refresh: yb += dnew (FP64), ybh = fl32(yb), dold -= dnew, dnew = 0; the
+// next iteration's w then starts from the same value relative to the new base
+__global__ void k_pnm_refresh(size_t count, double *yb, float *ybh, float *dnew, float *dold) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const double y = yb[e] + (double)dnew[e];
+    yb[e] = y;
+    ybh[e] = (float)y;
+    dold[e] -= dnew[e];
+    dnew[e] = 0.f;
+  }
+}
+
+__global__ void k_pnm_to32(size_t cu, size_t cx, const double *uo, const double *xo, float *uref,
+                           float *xref) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < cu + cx;
+       e += (size_t)gridDim.x * blockDim.x) {
+    if (e < cu) uref[e] = (float)uo[e];
+    else xref[e - cu] = (float)xo[e - cu];
+  }
+}
+
+// out = yb + delta (FP64), padded layout
+__global__ void k_pnm_add(size_t count, const double *yb, const float *dlt, double *out) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count;
+       e += (size_t)gridDim.x * blockDim.x)
+    out[e] = yb[e] + (double)dlt[e];
+}
+
+int pnm_grid(size_t count) { return (int)std::max<size_t>(1, std::min<size_t>((count + 255) / 256, 4096)); }
+
+// x*(w) in FP64 on the twin for w = yb (+ delta, if given): its uo/xo
+int pnm_eval64(PnFactor *f, const float *dlt) {
+  PnFactor *T64 = f->twin;
+  const size_t cnt = (size_t)f->n * f->YP;
+  if (dlt) {
+    k_pnm_add<<<pnm_grid(cnt), 256, 0, f->stream>>>(cnt, f->ybase, dlt,
+                                                   static_cast<double *>(T64->ya));
+  } else {
+    PN_CUDA(cudaMemcpyAsync(T64->ya, f->ybase, cnt * sizeof(double), cudaMemcpyDeviceToDevice,
+                            f->stream));
+  }
+  PN_CUDA(cudaGetLastError());
+  return pn_eval<double>(T64, false);
+}
+
+int pnm_refs(PnFactor *f) {
+  PnFactor *T64 = f->twin;
+  const size_t cu = (size_t)f->n * f->NUP, cx = (size_t)f->n * f->NXP;
+  k_pnm_to32<<<pnm_grid(cu + cx), 256, 0, f->stream>>>(cu, cx, static_cast<double *>(T64->uo),
+                                                       static_cast<double *>(T64->xo), f->uref,
+                                                       f->xref);
+  PN_CUDA(cudaGetLastError());
+  return RN_OK;
+}
+
+int pn_solve_mixed(PnFactor *f, const double *x0, const double *q, const double *demand,
+                   const double *alpha, int max_iters, double tol, const double *y_warm,
+                   rn_result *out) {
+  PnFactor *T64 = f->twin;
+  const bool avg = out->u_avg != nullptr;
+  const int n = f->n;
+  const int checks = (max_iters + f->check_every - 1) / f->check_every + 1;
+  int rc;
+  if ((rc = pn_beta(f, max_iters)) || (rc = pn_res(f, checks))) return rc;
+  // the twin's data terms, and its FP64 copies of x0 and q
+  if ((rc = pn_prepare_t<double>(T64, x0, q, demand, alpha)) || (rc = pn_init<double>(T64, nullptr)))
+    return rc;
+  PN_CUDA(cudaMemsetAsync(f->res, 0, checks * sizeof(unsigned long long), f->stream));
+  PN_CUDA(cudaMemsetAsync(f->err, 0, sizeof(int), f->stream));
+  PN_CUDA(cudaMemsetAsync(T64->err, 0, sizeof(int), f->stream));
+  if (avg) {
+    if (!f->uavg && ((rc = pn_alloc(f, &f->uavg, (size_t)n * f->NUP)) ||
+                     (rc = pn_alloc(f, &f->xavg, (size_t)n * f->NXP))))
+      return rc;
+    PN_CUDA(cudaMemsetAsync(f->uavg, 0, (size_t)n * f->NUP * sizeof(double), f->stream));
+    PN_CUDA(cudaMemsetAsync(f->xavg, 0, (size_t)n * f->NXP * sizeof(double), f->stream));
+  }
+  const int nb = std::max(1, std::min(n, 4096));
+  PN_CUDA(cudaEventRecord(f->ev0, f->stream));
+  k_pnm_init<<<nb, 128, 0, f->stream>>>(n, f->nx, f->nu, f->NXP, f->YP, y_warm, f->ybase, f->ybh,
+                                        static_cast<float *>(f->ya), static_cast<float *>(f->yb));
+  PN_CUDA(cudaGetLastError());
+  if ((rc = pnm_eval64(f, nullptr)) || (rc = pnm_refs(f))) return rc;
+  int done = 0, nchk = 0, reason = 0;
+  unsigned long long t_begin = 0, t_end = 0;
+  while (done < max_iters) {
+    const int len = std::min(f->refresh_every, max_iters - done);
+    PnParams<float> P = pn_params<float>(f);
+    P.apg = 1;
+    P.delta = 1;
+    P.it0 = done;
+    P.iters = len;
+    P.iters_total = max_iters;
+    P.check_every = f->check_every;
+    P.tol = tol > 0.0 ? tol : 0.0;
+    P.ybh = f->ybh;
+    P.uref = f->uref;
+    P.xref = f->xref;
+    P.swy = f->swy;
+    P.uavg = avg ? f->uavg : nullptr;
+    P.xavg = avg ? f->xavg : nullptr;
+    P.beta = f->beta;
+    P.theta = f->beta + f->beta_cap;
+    P.res = f->res + nchk;
+    if ((rc = pn_launch<float>(f, P))) return rc;
+    int info[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    PN_CUDA(cudaMemcpyAsync(info, f->info, sizeof info, cudaMemcpyDeviceToHost, f->stream));
+    if ((rc = pn_check_err(f))) return rc;
+    {
+      unsigned long long st[2];
+      std::memcpy(st, info + 4, sizeof st);
+      if (done == 0) t_begin = st[0];
+      t_end = st[1];
+    }
+    done += info[0];
+    nchk += info[1];
+    reason = info[2];
+    if (reason != 0) break;
+    if (done < max_iters) {
+      // y^done sits in the buffer that iteration done - 1 wrote
+      float *dnew = static_cast<float *>(((done - 1) & 1) ? f->ya : f->yb);
+      float *dold = static_cast<float *>(((done - 1) & 1) ? f->yb : f->ya);
+      const size_t cnt = (size_t)n * f->YP;
+      k_pnm_refresh<<<pnm_grid(cnt), 256, 0, f->stream>>>(cnt, f->ybase, f->ybh, dnew, dold);
+      PN_CUDA(cudaGetLastError());
+      if ((rc = pnm_eval64(f, nullptr)) || (rc = pnm_refs(f))) return rc;
+    }
+  }
+  // the primal of the last iteration, x*(yb + dw), in FP64
+  if ((rc = pnm_eval64(f, f->swy))) return rc;
+  PN_CUDA(cudaEventRecord(f->ev1, f->stream));
+  if ((rc = pn_check_err(T64))) return rc;
+  float ms = 0.f;
+  PN_CUDA(cudaEventElapsedTime(&ms, f->ev0, f->ev1));
+  out->apg_ms = ms;
+  out->t_begin_ns = (long long)t_begin;
+  out->t_end_ns = (long long)t_end;
+  // outputs: (u, x) of the FP64 evaluation, y = yb + d^done
+  if ((rc = pn_gather<double>(T64, nullptr, out->u, out->x, nullptr))) return rc;
+  {
+    const float *dfin = static_cast<const float *>(((done - 1) & 1) ? f->ya : f->yb);
+    const size_t cnt = (size_t)n * f->YP;
+    double *yfull = static_cast<double *>(T64->yb);  // scratch of the twin
+    k_pnm_add<<<pnm_grid(cnt), 256, 0, f->stream>>>(cnt, f->ybase, dfin, yfull);
+    PN_CUDA(cudaGetLastError());
+    k_pn_gather<double><<<nb, 128, 0, f->stream>>>(n, f->nx, f->nu, f->NXP, f->NUP, f->YP, nullptr,
+                                                   nullptr, yfull, T64->q, T64->x0, nullptr,
+                                                   nullptr, out->y);
+    PN_CUDA(cudaGetLastError());
+  }
+  if (avg) {
+    k_pn_gather_avg<float><<<nb, 128, 0, f->stream>>>(n, f->nx, f->nu, f->NXP, f->NUP, f->uavg,
+                                                      f->xavg, T64->q, T64->x0, out->u_avg,
+                                                      out->x_avg);
+    PN_CUDA(cudaGetLastError());
+  }
+  std::vector<unsigned long long> hist(std::max(1, nchk));
+  if (nchk > 0)
+    PN_CUDA(cudaMemcpyAsync(hist.data(), f->res, nchk * sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, f->stream));
+  double red[3];
+  if ((rc = pn_cost(T64, out->u, out->x, red))) return rc;
+  out->cost = red[0] + red[1];
+  out->ubox_viol = red[2];
+  out->iters = done;
+  out->n_checks = nchk;
+  out->gamma = f->gamma;
+  std::vector<double> rh(std::max(1, nchk));
+  for (int i = 0; i < nchk; ++i) {
+    double d;
+    std::memcpy(&d, &hist[i], sizeof d);
+    rh[i] = d / f->gamma;
+  }
+  out->primal_res = nchk > 0 ? rh[nchk - 1] : NAN;
+  if (out->res_hist && out->res_hist_len > 0 && nchk > 0)
+    PN_CUDA(cudaMemcpyAsync(out->res_hist, rh.data(),
+                            std::min(out->res_hist_len, nchk) * sizeof(double),
+                            cudaMemcpyHostToDevice, f->stream));
+  out->gap = NAN;
+  PN_CUDA(cudaStreamSynchronize(f->stream));
+  if (reason == 2) {
+    set_error("the residual became non-finite after %d iterations", done);
+    return RN_ERR_DIVERGED;
+  }
+  if (reason == 3) {
+    set_error("per-node path: a device-side wait gave up after %.3g s", f->wait_ns * 1e-9);
+    return RN_ERR_TIMEOUT;
+  }
+  if (tol > 0.0 && reason != 1) return RN_NOT_CONVERGED;
+  return RN_OK;
+}
+
+}  // namespace
+
 int pn_solve_device(PnFactor *f, const double *x0, const double *q, const double *demand,
                     const double *alpha, int max_iters, double tol, const double *y_warm,
                     rn_result *out) {
@@ -1793,6 +2151,7 @@ int pn_solve_device(PnFactor *f, const double *x0, const double *q, const double
     return RN_ERR_UNSUPPORTED;
   }
   PN_CUDA(cudaSetDevice(f->device));
+  if (f->mixed) return pn_solve_mixed(f, x0, q, demand, alpha, max_iters, tol, y_warm, out);
   return f->fp32 ? pn_solve_t<float>(f, x0, q, demand, alpha, max_iters, tol, y_warm, out)
                  : pn_solve_t<double>(f, x0, q, demand, alpha, max_iters, tol, y_warm, out);
 }
@@ -1812,6 +2171,7 @@ int pn_dual_gradient_t(PnFactor *f, const double *w, double *u, double *x) {
 int pn_dual_gradient_device(PnFactor *f, const double *x0, const double *q,
                             const double *demand, const double *alpha, const double *w,
                             double *u, double *x) {
+  if (f->mixed) return pn_dual_gradient_device(f->twin, x0, q, demand, alpha, w, u, x);
   PN_CUDA(cudaSetDevice(f->device));
   int rc;
   if (x0 || q || demand || alpha) {
@@ -1833,7 +2193,7 @@ void pn_info(const PnFactor *f, rn_factor_info *info) {
   info->block_threads = f->block;
   info->L = f->L;
   info->gamma = f->gamma;
-  info->device_bytes = f->bytes;
+  info->device_bytes = f->bytes + (f->twin ? f->twin->bytes : 0);
   info->n_chains = f->n_chains;
   info->n_top = f->n_top;
 }

@@ -63,6 +63,15 @@ struct PnParams {
   long long wait_ns;
   double gamma, invgamma, tol;
   int iters, check_every, apg;
+  // iterations [it0, it0 + iters) of a solve of iters_total iterations
+  // (the APG sequences, the ping-pong of y and the checks count from 0)
+  int it0, iters_total;
+  // delta form (RN_PREC_MIXED, FP32 handle): y holds the FP32 delta d from
+  // the FP64 base yb; the evaluation is linear and x*(w) = x*(yb) + x_lin(dw)
+  // with ybh = fl32(yb), uref/xref = x*(yb); swy receives dw at the checks
+  int delta;
+  const T *ybh, *uref, *xref;
+  T *swy;
   // schedule: per team its items, cut into 2 T + 2 segments (chain
   // backward, top backward stage T .. 1, top forward stage 1 .. T, chain
   // forward) at seg[team * (n_seg + 1) + s]
@@ -82,8 +91,10 @@ struct PnOptions {
   int device = 0;
   cudaStream_t stream = nullptr;
   bool fp32 = false;         // matrices and iteration in FP32 (else FP64)
+  bool mixed = false;        // RN_PREC_MIXED: FP32 delta iterations around an FP64
+                             // base, with an FP64 twin handle for the base
   double gamma = 0.0;        // 0: power iteration
-  int power_iters = 200, check_every = 10, theta_rule = 0, max_ctas = 0;
+  int power_iters = 200, check_every = 10, theta_rule = 0, max_ctas = 0, refresh_every = 20;
   long long wait_ns = 0;
 };
 int pn_create(const rn_network *net, const rn_tree *tree, const rn_cost *cost,

@@ -1310,17 +1310,14 @@ int pernode_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost
   if ((rc = pn_validate(net, tree, cost))) return rc;
   if ((rc = build_plan(tree, f->plan))) return rc;  // sizes of the host staging
   f->opts = opts ? *opts : rn_opts{};
-  if (f->opts.precision == RN_PREC_MIXED) {
-    set_error("precision RN_PREC_MIXED needs the shared-operator form (A = I); the per-node "
-              "form runs RN_PREC_FP64 or RN_PREC_FP32");
-    return RN_ERR_UNSUPPORTED;
-  }
-  if (f->opts.precision != RN_PREC_FP64 && f->opts.precision != RN_PREC_FP32) {
+  if (f->opts.precision != RN_PREC_FP64 && f->opts.precision != RN_PREC_FP32 &&
+      f->opts.precision != RN_PREC_MIXED) {
     set_error("precision must be RN_PREC_FP64, RN_PREC_MIXED or RN_PREC_FP32");
     return RN_ERR_INVAL;
   }
   if (f->opts.power_iters <= 0) f->opts.power_iters = 200;
   if (f->opts.check_every <= 0) f->opts.check_every = 10;
+  if (f->opts.refresh_every <= 0) f->opts.refresh_every = 20;
   if (f->opts.theta_rule != RN_THETA_EQUALITY && f->opts.theta_rule != RN_THETA_SIMPLE) {
     set_error("theta_rule must be RN_THETA_EQUALITY or RN_THETA_SIMPLE");
     return RN_ERR_INVAL;
@@ -1357,6 +1354,8 @@ int pernode_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost
   o.device = f->device;
   o.stream = f->stream;
   o.fp32 = f->opts.precision == RN_PREC_FP32;
+  o.mixed = f->opts.precision == RN_PREC_MIXED;
+  o.refresh_every = f->opts.refresh_every;
   o.gamma = f->opts.gamma > 0.0 ? f->opts.gamma : 0.0;
   o.power_iters = f->opts.power_iters;
   o.check_every = f->opts.check_every;
@@ -2285,6 +2284,10 @@ int batch_impl(rn_factor *const *fs, const rn_solve_req *req, int n, int max_ite
         !r.out->y) {
       set_error("solve_batch: NULL handle or argument in request %d", i);
       return RN_ERR_INVAL;
+    }
+    if (f->pn) {
+      set_error("solve_batch: handle %d is of the per-node form (solve it alone)", i);
+      return RN_ERR_UNSUPPORTED;
     }
     if (f->opts.precision != RN_PREC_MIXED) {
       set_error("solve_batch: handle %d is not RN_PREC_MIXED", i);

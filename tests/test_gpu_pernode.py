@@ -344,3 +344,75 @@ def test_flag_wait_that_runs_out_reports_timeout_and_the_handle_recovers():
     good.close()
     for k in "uxy":
         assert rel_err(out[k], getattr(ref, k)) <= 1e-6, k
+
+
+@pytest.mark.parametrize("kind,iters,refresh", [("tiny_A", 500, 20), ("barcelona32_A", 300, 20),
+                                                ("uneven1_A", 300, 7), ("dense_A", 300, 20)])
+def test_mixed_precision_matches_oracle(kind, iters, refresh):
+    """RN_PREC_MIXED on the per-node form: FP32 iterations on the delta from
+    an FP64 base refreshed every `refresh` iterations (7: the refreshes fall
+    between the residual checks), the final primal in FP64.  Cost, u, y and
+    the averaged u against the FP64 oracle at the same iteration count,
+    within the larger of 1e-3 and twice the spread of two FP64 per-node
+    solves whose step sizes differ by one FP32 ulp: some of these problems
+    amplify any perturbation (barcelona32 with this A: 6e-3 in y after 300
+    iterations for that one-ulp change, the mixed solve 3e-3; on the others
+    the mixed solve lands near 1e-5 and plain FP32 near 1e-4).  The primal
+    satisfies the dynamics to FP64 rounding."""
+    pb = problem(kind)
+    P, F, S = oracle_for(kind, pb)
+    gamma = O.step_size(O.power_iteration(P, F, 100))
+    ref = O.apg(P, F, S, iters, gamma, average=True)
+    fac = rn.Factor(pb.net, pb.cost, pb.tree, gamma=gamma, factor_form=PN,
+                    precision=rn.RN_PREC_MIXED, refresh_every=refresh)
+    assert fac.info()["factor_form"] == PN
+    out = fac.solve(pb.data.x0, pb.data.q, pb.data.demand, pb.data.alpha, max_iters=iters,
+                    res_hist_len=1000, average=True)
+    fac.close()
+    f64 = rn.Factor(pb.net, pb.cost, pb.tree, gamma=gamma * (1.0 + 2.0 ** -23), factor_form=PN)
+    e = f64.solve(pb.data.x0, pb.data.q, pb.data.demand, pb.data.alpha, max_iters=iters)
+    f64.close()
+    assert out["status"] == B.RN_OK and out["iters"] == iters
+    assert out["n_checks"] == iters // 10
+    cost = O.primal_cost(P, S, ref.u, ref.x)
+    bar = {k: max(1e-3, 2 * rel_err(e[k], getattr(ref, k))) for k in "uy"}
+    bar["cost"] = max(1e-3, 2 * abs(e["cost"] - cost) / abs(cost))
+    for k in "uy":
+        assert rel_err(out[k], getattr(ref, k)) <= bar[k], (k, bar)
+    assert abs(out["cost"] - cost) <= bar["cost"] * abs(cost)
+    net, d, anc = pb.net, pb.data, np.asarray(pb.tree.anc)
+    A = np.asarray(net.A).reshape(net.nx, net.nx)
+    Bm = np.asarray(net.B).reshape(net.nx, net.nu)
+    Gd = np.asarray(net.Gd).reshape(net.nx, net.nd)
+    x, u = out["x"], out["u"]
+    dyn = x[1:] - (x[anc[1:]] @ A.T + u[1:] @ Bm.T + np.asarray(d.demand)[1:] @ Gd.T)
+    assert np.abs(dyn).max() <= 1e-9 * np.abs(x).max()
+    assert rel_err(out["u_avg"], ref.u_avg) <= bar["u"]
+
+
+def test_mixed_precision_full_size_against_fp64():
+    """barcelona512 (A = I): the per-node mixed solve after 200 iterations
+    against the per-node FP64 solve.  As for the shared form, the bar is the
+    larger of 1e-3 and twenty times the spread between two FP64 solves whose
+    step sizes differ by one FP32 ulp (far from convergence the accelerated
+    iteration amplifies any perturbation), for the cost, u and y."""
+    pb = make_problem("barcelona512")
+    d = pb.data
+    runs = []
+    for prec, scale in ((rn.RN_PREC_FP64, 1.0), (rn.RN_PREC_FP64, 1.0 + 2.0 ** -23),
+                        (rn.RN_PREC_MIXED, 1.0)):
+        if not runs:
+            f = rn.Factor(pb.net, pb.cost, pb.tree, factor_form=PN)
+            gamma = f.info()["gamma"]
+        else:
+            f = rn.Factor(pb.net, pb.cost, pb.tree, gamma=gamma * scale, factor_form=PN,
+                          precision=prec)
+        runs.append(f.solve(d.x0, d.q, d.demand, d.alpha, max_iters=200))
+        f.close()
+    a, e, b = runs
+    assert b["status"] == B.RN_OK and b["iters"] == 200
+    spread = {k: rel_err(e[k], a[k]) for k in "uy"}
+    spread["cost"] = abs(e["cost"] - a["cost"]) / abs(a["cost"])
+    for k in "uy":
+        assert rel_err(b[k], a[k]) <= max(1e-3, 20 * spread[k]), (k, spread)
+    assert abs(b["cost"] - a["cost"]) <= max(1e-3, 20 * spread["cost"]) * abs(a["cost"])

@@ -97,11 +97,10 @@ def test_form_selection_before_any_device_work():
     # the shared-operator form needs A = I
     assert _status(pb, factor_form=rn.RN_FACTOR_SHARED) == B.RN_ERR_UNSUPPORTED
     assert "A = I" in rn.rapidnet_last_error()
-    # RN_PREC_MIXED runs on the shared operator only
-    assert _status(pb, factor_form=rn.RN_FACTOR_PER_NODE,
-                   precision=rn.RN_PREC_MIXED) == B.RN_ERR_UNSUPPORTED
-    assert "RN_PREC_MIXED" in rn.rapidnet_last_error()
-    assert _status(pb, precision=rn.RN_PREC_MIXED) == B.RN_ERR_UNSUPPORTED
+    # every precision on the per-node form (the next step needs a device)
+    for prec in (rn.RN_PREC_MIXED, rn.RN_PREC_FP32, rn.RN_PREC_FP64):
+        assert _status(pb, factor_form=rn.RN_FACTOR_PER_NODE, precision=prec) in (
+            B.RN_OK, B.RN_ERR_CUDA)
     # RN_PREC_FP32 on the shared form is not a precision it has
     pb_i = make_problem("tiny")
     assert _status(pb_i, factor_form=rn.RN_FACTOR_SHARED,
