@@ -541,13 +541,17 @@ def run_closed_loop(rn, hours, max_iters):
             "final_residual_median": float(np.median(out.residual)), "precision": "mixed"}
 
 
+MIXED_REFRESH = 40  # FP64 refresh period of RN_PREC_MIXED (rn_opts.refresh_every = 0)
+
+
 def run_per_node(rn, gamma, iters32, iters64):
     """The per-node factor form (paper §4.4 general recursion; §5.2 streams
     per-node matrices): barcelona512, Phi_nu and K_nu streamed from HBM at
     every iteration.  Algorithmic bytes per node and iteration: the 1,491
     vector values of the shared form plus the 2 nu^2 matrix entries, in the
     iteration's precision; the mixed precision adds one FP64 evaluation
-    (the same bytes at 8 B) per refresh of its base, every 20 iterations.
+    (the same bytes at 8 B) per refresh of its base, every MIXED_REFRESH
+    iterations (the library's default period, passed explicitly).
     FP32 and mixed against FP64 of the same form at the same iteration
     count for the error; the factor step (host, FP64) timed."""
     import numpy as np
@@ -563,10 +567,11 @@ def run_per_node(rn, gamma, iters32, iters64):
     for key, prec, iters, bytes_it in (("fp32", rn.RN_PREC_FP32, iters32, per_val * 4),
                                        ("fp64", rn.RN_PREC_FP64, iters64, per_val * 8),
                                        ("mixed", rn.RN_PREC_MIXED, iters32,
-                                        per_val * 4 + per_val * 8 / 20)):
+                                        per_val * 4 + per_val * 8 / MIXED_REFRESH)):
         t0 = time.perf_counter()
         f = rn.Factor(pb.net, pb.cost, pb.tree, gamma=gamma, precision=prec,
-                      factor_form=rn.RN_FACTOR_PER_NODE)
+                      factor_form=rn.RN_FACTOR_PER_NODE,
+                      refresh_every=MIXED_REFRESH if key == "mixed" else 0)
         factor_s = time.perf_counter() - t0
         info = f.info()
         f.solve(d.x0, d.q, d.demand, d.alpha, max_iters=10)
@@ -845,6 +850,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "iters_per_step": args.iters,
                    "precision": args.precision, "l2": "flushed between steps (512 MB write)",
+                   "fp64_refresh_every": MIXED_REFRESH if args.precision == "mixed" else None,
                    "grid_ctas": info["grid_ctas"], "block_threads": info["block_threads"],
                    "gamma": info["gamma"], "parallelism": f"replicas x{world}"},
         "e2e": ({"value": e2e_val, "unit": "iters/s", "h2d_bytes_per_step": h2d,

@@ -874,7 +874,7 @@ int factor_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost,
   }
   if (f->opts.power_iters <= 0) f->opts.power_iters = 200;
   if (f->opts.check_every <= 0) f->opts.check_every = 10;
-  if (f->opts.refresh_every <= 0) f->opts.refresh_every = 20;
+  if (f->opts.refresh_every <= 0) f->opts.refresh_every = 40;
   if (f->opts.theta_rule != RN_THETA_EQUALITY && f->opts.theta_rule != RN_THETA_SIMPLE) {
     set_error("theta_rule must be RN_THETA_EQUALITY or RN_THETA_SIMPLE");
     return RN_ERR_INVAL;
@@ -1317,7 +1317,7 @@ int pernode_impl(const rn_network *net, const rn_tree *tree, const rn_cost *cost
   }
   if (f->opts.power_iters <= 0) f->opts.power_iters = 200;
   if (f->opts.check_every <= 0) f->opts.check_every = 10;
-  if (f->opts.refresh_every <= 0) f->opts.refresh_every = 20;
+  if (f->opts.refresh_every <= 0) f->opts.refresh_every = 40;
   if (f->opts.theta_rule != RN_THETA_EQUALITY && f->opts.theta_rule != RN_THETA_SIMPLE) {
     set_error("theta_rule must be RN_THETA_EQUALITY or RN_THETA_SIMPLE");
     return RN_ERR_INVAL;
