@@ -416,3 +416,59 @@ def test_mixed_precision_full_size_against_fp64():
     for k in "uy":
         assert rel_err(b[k], a[k]) <= max(1e-3, 20 * spread[k]), (k, spread)
     assert abs(b["cost"] - a["cost"]) <= max(1e-3, 20 * spread["cost"]) * abs(a["cost"])
+
+
+def test_mixed_precision_tolerance_stop():
+    """RN_PREC_MIXED on the per-node form stops at a residual check inside a
+    launch of refresh_every iterations (tol 1e-3 on tiny with A != I; the
+    oracle stops at 720 iterations): the returned residual is at or below
+    the tolerance, the primal is the FP64 evaluation at that iteration (the
+    dynamics hold to FP64 rounding), and the iteration count is within 50
+    of the oracle's (the FP32 iterates reach the tolerance at a neighbouring
+    check)."""
+    kind = "tiny_A"
+    pb = problem(kind)
+    P, F, S = oracle_for(kind, pb)
+    gamma = O.step_size(O.power_iteration(P, F, 100))
+    ref = O.apg(P, F, S, 20000, gamma, tol=1e-3, check_every=10)
+    assert ref.converged
+    fac = rn.Factor(pb.net, pb.cost, pb.tree, gamma=gamma, factor_form=PN,
+                    precision=rn.RN_PREC_MIXED)
+    out = fac.solve(pb.data.x0, pb.data.q, pb.data.demand, pb.data.alpha, max_iters=20000,
+                    tol=1e-3)
+    fac.close()
+    assert out["status"] == B.RN_OK and out["primal_res"] <= 1e-3
+    assert out["iters"] % 10 == 0 and out["iters"] < 20000
+    assert abs(out["iters"] - ref.iters) <= 50, (out["iters"], ref.iters)
+    net, d, anc = pb.net, pb.data, np.asarray(pb.tree.anc)
+    A = np.asarray(net.A).reshape(net.nx, net.nx)
+    Bm = np.asarray(net.B).reshape(net.nx, net.nu)
+    Gd = np.asarray(net.Gd).reshape(net.nx, net.nd)
+    x, u = out["x"], out["u"]
+    dyn = x[1:] - (x[anc[1:]] @ A.T + u[1:] @ Bm.T + np.asarray(d.demand)[1:] @ Gd.T)
+    assert np.abs(dyn).max() <= 1e-9 * np.abs(x).max()
+
+
+def test_mixed_precision_warm_start_simple_rule():
+    """RN_PREC_MIXED on the per-node form from a warm start (the base starts
+    at y_warm: an APG iterate, as in a receding-horizon solve) with the
+    second theta rule and the averaged primal, against the oracle at the
+    mixed bar (1e-3; measured near 3e-6).  A random dual point of the size
+    of y as the start puts FP32 iterations of either form near 5e-3 after
+    250 iterations (FP64 1e-9), so the start is an iterate."""
+    kind = "uneven1_A"
+    pb = problem(kind)
+    P, F, S = oracle_for(kind, pb)
+    gamma = O.step_size(O.power_iteration(P, F, 100))
+    y0 = O.apg(P, F, S, 60, gamma, theta_rule="simple").y
+    ref = O.apg(P, F, S, 250, gamma, y0=y0, theta_rule="simple", average=True)
+    fac = rn.Factor(pb.net, pb.cost, pb.tree, gamma=gamma, factor_form=PN,
+                    precision=rn.RN_PREC_MIXED, theta_rule=B.RN_THETA_SIMPLE)
+    out = fac.solve(pb.data.x0, pb.data.q, pb.data.demand, pb.data.alpha, max_iters=250,
+                    y_warm=y0, average=True)
+    fac.close()
+    assert out["status"] == B.RN_OK and out["iters"] == 250
+    for k in "uxy":
+        assert rel_err(out[k], getattr(ref, k)) <= 1e-3, k
+    assert rel_err(out["u_avg"], ref.u_avg) <= 1e-3
+    assert rel_err(out["x_avg"], ref.x_avg) <= 1e-3
