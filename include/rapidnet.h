@@ -65,10 +65,12 @@ typedef enum {
  *                      any A, nx and nu up to 1024, every precision
  *                      (RN_PREC_MIXED: FP32 matrices for the iterations and
  *                      an FP64 copy for the reference point, both on the
- *                      device); no batched or served solves, no duality
- *                      gap, no allocation-free entry point;
- *   RN_FACTOR_AUTO (0) the shared form, or the per-node form for A != I or
- *                      RN_PREC_FP32. */
+ *                      device); served solves (one at a time: each
+ *                      launch fills the device), no batched solves, no
+ *                      duality gap, no allocation-free entry point;
+ *   RN_FACTOR_AUTO (0) the shared form, or the per-node form for A != I,
+ *                      RN_PREC_FP32, or a layout the shared form refuses
+ *                      (RN_PREC_FP64 and RN_PREC_MIXED). */
 enum { RN_FACTOR_AUTO = 0, RN_FACTOR_SHARED = 1, RN_FACTOR_PER_NODE = 2 };
 
 /* Water network, paper §2.1 (eqs. dynamics, input-disturbance-coupling,
@@ -373,7 +375,9 @@ int rapidnet_dual_gradient_noalloc(rn_factor *f, const double *w, double *u,
  * it on that slot's stream, so requests that arrive while others run
  * overlap with them on the device.  Every result equals the same request
  * solved alone (same kernels, no shared state besides the warm start,
- * which is off unless asked for).
+ * which is off unless asked for).  A model takes its factor form as
+ * rapidnet_factor does (RN_FACTOR_AUTO: the shared form where it applies);
+ * solves of per-node models fill the device and run one at a time.
  * ------------------------------------------------------------------- */
 typedef struct rn_server rn_server;
 

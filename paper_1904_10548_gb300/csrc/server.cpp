@@ -291,9 +291,10 @@ extern "C" int rapidnet_server_add_model(rn_server *sv, const rn_network *net,
   m->tree = rn_tree{tree->N, n, m->stage_ptr.data(), m->anc.data(), ptr(m->prob)};
   m->cost = rn_cost{cost->W_alpha, ptr(m->alpha0), ptr(m->Wu), cost->Ws, cost->Wx};
   m->opts = opts ? *opts : rn_opts{};
-  // served solves run the shared-operator kernels (the per-node form
-  // occupies the whole device with one cooperative launch per solve)
-  if (m->opts.factor_form == RN_FACTOR_AUTO) m->opts.factor_form = RN_FACTOR_SHARED;
+  // RN_FACTOR_AUTO as in rapidnet_factor: the shared-operator kernels
+  // wherever they apply, else (A != I, a refused layout, RN_PREC_FP32) the
+  // per-node form, whose solves occupy the whole device with one
+  // cooperative launch each and so run one at a time
   m->nx = nx;
   m->nu = nu;
   m->nd = nd;

@@ -472,3 +472,28 @@ def test_mixed_precision_warm_start_simple_rule():
         assert rel_err(out[k], getattr(ref, k)) <= 1e-3, k
     assert rel_err(out["u_avg"], ref.u_avg) <= 1e-3
     assert rel_err(out["x_avg"], ref.x_avg) <= 1e-3
+
+
+@pytest.mark.parametrize("precision", [rn.RN_PREC_MIXED, rn.RN_PREC_FP64])
+def test_auto_form_falls_back_to_per_node(precision):
+    """RN_FACTOR_AUTO on a network the shared form cannot lay out (A = I,
+    nu = 540 above its 256): factor creation takes the per-node form, in
+    FP64 and in the mixed precision, and the solve matches the oracle (FP64
+    1e-6; mixed 1e-3)."""
+    net = make_network(300, 540, 420, 81, seed=3)
+    tree = make_tree([2, 2] + [1] * 4, seed=2)
+    pb = Problem(net=net, cost=make_cost(net, seed=3), tree=tree,
+                 data=make_data(net, tree, seed=4))
+    P, F, S = oracle_for("wide540", pb)
+    gamma = O.step_size(O.power_iteration(P, F, 100))
+    ref = O.apg(P, F, S, 300, gamma)
+    fac = rn.Factor(pb.net, pb.cost, pb.tree, gamma=gamma, precision=precision)
+    assert fac.info()["factor_form"] == PN
+    out = fac.solve(pb.data.x0, pb.data.q, pb.data.demand, pb.data.alpha, max_iters=300)
+    fac.close()
+    bar = 1e-6 if precision == rn.RN_PREC_FP64 else 1e-3
+    assert out["status"] == B.RN_OK and out["iters"] == 300
+    for k in "uy":
+        assert rel_err(out[k], getattr(ref, k)) <= bar, k
+    cost = O.primal_cost(P, S, ref.u, ref.x)
+    assert abs(out["cost"] - cost) <= bar * abs(cost)

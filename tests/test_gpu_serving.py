@@ -110,3 +110,34 @@ def test_warm_start_uses_the_slot_dual():
     f.close()
     assert np.array_equal(warm["y"], ref["y"])
     srv.close()
+
+
+@pytest.mark.parametrize("precision", [rn.RN_PREC_MIXED, rn.RN_PREC_FP64])
+def test_per_node_model_is_served(precision):
+    """A model with A != I takes the per-node form (RN_FACTOR_AUTO, as in
+    rapidnet_factor) and is served beside a shared-form model: its requests,
+    alone and in the mix, equal a direct per-node solve of the same request
+    bit for bit, and so do the shared-form model's."""
+    from tests.test_gpu_pernode import problem as pn_problem
+    pbs = [pn_problem("tiny_A"), make_problem("tiny")]
+    srv = rn.Server(workers=4, slots_per_model=2)
+    keys = [srv.add_model(pb.net, pb.cost, pb.tree, precision=precision) for pb in pbs]
+    reqs = [(i % 2, perturbed(pbs[i % 2], i)) for i in range(8)]
+    iters = 300
+    alone = [srv.wait(keys[k], srv.submit(keys[k], *data, max_iters=iters)) for k, data in reqs]
+    tickets = [srv.submit(keys[k], *data, max_iters=iters) for k, data in reqs]
+    mixed = [srv.wait(keys[k], t) for (k, _), t in zip(reqs, tickets)]
+    srv.close()
+    for a, b in zip(alone, mixed):
+        assert a["status"] == b["status"] == B.RN_OK
+        for k in ("u", "x", "y"):
+            assert np.array_equal(a[k], b[k])
+    for (k, data), a in zip(reqs[:2], alone[:2]):
+        pb = pbs[k]
+        f = rn.Factor(pb.net, pb.cost, pb.tree, precision=precision)
+        assert f.info()["factor_form"] == (rn.RN_FACTOR_PER_NODE if k == 0 else
+                                           rn.RN_FACTOR_SHARED)
+        d = f.solve(*data, max_iters=iters)
+        f.close()
+        for key in ("u", "x", "y"):
+            assert np.array_equal(d[key], a[key])
