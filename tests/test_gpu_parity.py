@@ -49,6 +49,11 @@ def problem(kind):
         net = make_network(8, 14, 10, 3, seed=5)
         tree = make_tree([1] * 20, seed=6)
         return Problem(net=net, cost=make_cost(net, seed=5), tree=tree, data=make_data(net, tree, 7))
+    if kind in ("horizon1", "horizon1s"):
+        # a one-stage horizon: the root and five leaves, or the root and one
+        net = make_network(8, 14, 10, 3, seed=5)
+        tree = make_tree([5] if kind == "horizon1" else [1], seed=3)
+        return Problem(net=net, cost=make_cost(net, seed=5), tree=tree, data=make_data(net, tree, 8))
     if kind == "ne0":
         net = make_network(6, 9, 5, 0, seed=8)
         tree = make_tree([3, 2, 1, 2, 1, 1, 1], seed=9)
@@ -96,7 +101,7 @@ def gpu_factor(pb, gamma=0.0, **kw):
 
 
 KINDS = ["tiny", "barcelona32", "uneven0", "uneven1", "uneven2", "single", "ne0",
-         "stage1_chains", "tight"]
+         "stage1_chains", "tight", "horizon1", "horizon1s"]
 
 
 # ---------------------------------------------------------------------------
@@ -142,7 +147,8 @@ def test_step_size_matches_oracle_power_iteration(kind):
 
 @pytest.mark.parametrize("kind,iters", [("tiny", 500), ("barcelona32", 300), ("uneven0", 400),
                                         ("uneven1", 400), ("uneven2", 300), ("single", 400),
-                                        ("ne0", 400), ("stage1_chains", 400), ("tight", 500)])
+                                        ("ne0", 400), ("stage1_chains", 400), ("tight", 500),
+                                        ("horizon1", 300), ("horizon1s", 300)])
 def test_apg_matches_oracle(kind, iters):
     pb = problem(kind)
     P, F, S = oracle_for(kind, pb)

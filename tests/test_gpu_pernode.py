@@ -57,6 +57,11 @@ def problem(kind):
         net = make_network(8, 14, 10, 3, seed=5)
         tree = make_tree([1] * 20, seed=6)
         pb = Problem(net=net, cost=make_cost(net, seed=5), tree=tree, data=make_data(net, tree, 7))
+    elif base in ("horizon1", "horizon1s"):
+        # a one-stage horizon: the root and five leaves, or the root and one
+        net = make_network(8, 14, 10, 3, seed=5)
+        tree = make_tree([5] if base == "horizon1" else [1], seed=3)
+        pb = Problem(net=net, cost=make_cost(net, seed=5), tree=tree, data=make_data(net, tree, 8))
     elif base == "ne0":
         net = make_network(6, 9, 5, 0, seed=8)
         tree = make_tree([3, 2, 1, 2, 1, 1, 1], seed=9)
@@ -120,7 +125,7 @@ def dual_gradient(fac, pb, w, data=True):
 
 
 DG_KINDS = ["tiny_A", "barcelona32_A", "uneven0_A", "uneven1_A", "single_A", "ne0_A", "bushy_A",
-            "dense_A", "tiny", "wide_A", "widest_A"]
+            "dense_A", "tiny", "wide_A", "widest_A", "horizon1_A", "horizon1s_A"]
 
 
 @pytest.mark.parametrize("kind", DG_KINDS)
@@ -174,7 +179,8 @@ def test_step_size_matches_oracle_power_iteration(kind):
 
 @pytest.mark.parametrize("kind,iters", [("tiny_A", 500), ("barcelona32_A", 300),
                                         ("uneven0_A", 400), ("uneven2_A", 300), ("single_A", 400),
-                                        ("ne0_A", 400), ("bushy_A", 300), ("dense_A", 300)])
+                                        ("ne0_A", 400), ("bushy_A", 300), ("dense_A", 300),
+                                        ("horizon1_A", 300), ("horizon1s_A", 300)])
 def test_apg_matches_oracle(kind, iters):
     pb = problem(kind)
     P, F, S = oracle_for(kind, pb)

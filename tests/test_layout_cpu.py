@@ -189,3 +189,16 @@ def test_batched_benchmark_set(driver):
             widths.add(pb.net.nx)
     assert refused == 42
     assert widths == {128}
+
+
+@pytest.mark.parametrize("counts", [[5], [1]])
+def test_one_stage_horizons_fit(driver, counts):
+    """A one-stage horizon (the root and its leaves): chains of one node
+    under the root, one work item per chain set, a layout in both
+    precisions."""
+    net = make_network(8, 14, 10, 3, seed=5)
+    tree = make_tree(counts, seed=3)
+    for mixed in (True, False):
+        L = layout(driver, net, tree, mixed)
+        assert L["rc"] == 0, L
+        assert L["n_items"] <= L["grid"]

@@ -86,6 +86,9 @@ TREES = {
     "ne0": lambda: make_tree([3, 2, 1, 2, 1, 1, 1], seed=9),
     "stage1_chains": lambda: _build([[4], [1, 2, 1, 3], [1, 1, 2, 1, 1, 1, 1], [1] * 8, [1] * 8,
                                      [1] * 8], 12),
+    # one-stage horizons: the root with five leaves, the root with one
+    "horizon1": lambda: make_tree([5], seed=3),
+    "horizon1_single": lambda: make_tree([1], seed=3),
     # three stage-1 subtrees: split, unsplit, split (with room for more groups)
     "mixed_split": lambda: random_branching(24, seed=2006, s_min=16, s_max=512),
 }
