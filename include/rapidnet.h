@@ -62,7 +62,11 @@ typedef enum {
  *   RN_FACTOR_PER_NODE the general recursion with one matrix pair
  *                      (Phi_nu, K_nu) per node from the factor step,
  *                      streamed from device memory at every evaluation;
- *                      any A, nx and nu up to 1024, every precision
+ *                      any A, nx and nu up to 1024 (FP64, also the FP64
+ *                      set of RN_PREC_MIXED: while one team's vectors
+ *                      and two column units fit a block's shared
+ *                      memory, nx = nu up to 800; beyond it
+ *                      RN_ERR_UNSUPPORTED), every precision
  *                      (RN_PREC_MIXED: FP32 matrices for the iterations and
  *                      an FP64 copy for the reference point, both on the
  *                      device); served solves (one at a time: each

@@ -503,3 +503,31 @@ def test_auto_form_falls_back_to_per_node(precision):
         assert rel_err(out[k], getattr(ref, k)) <= bar, k
     cost = O.primal_cost(P, S, ref.u, ref.x)
     assert abs(out["cost"] - cost) <= bar * abs(cost)
+
+
+def test_largest_dimensions():
+    """nx = nu = 1024, the largest the per-node form validates: in FP32 one
+    team per block with eight rows per thread, the dual gradient against the
+    oracle at the FP32 bar (2e-4); in FP64, and so for the FP64 set of the
+    mixed precision, one team's vectors exceed a block's shared memory (the
+    square limit is nx = nu = 800) and factor creation refuses the handle
+    with RN_ERR_UNSUPPORTED before the factor step."""
+    net = make_network(1024, 1024, 700, 120, seed=23)
+    tree = make_tree([2, 1, 1], seed=24)
+    pb = Problem(net=net, cost=make_cost(net, seed=23), tree=tree, data=make_data(net, tree, 25))
+    P, F, S = oracle_for("largest", pb)
+    rng = np.random.default_rng(1)
+    w = rng.standard_normal((P.n_nodes, P.ny))
+    w[0] = 0.0
+    u_o, x_o = O.dual_gradient(P, F, S, w)
+    fac = rn.Factor(pb.net, pb.cost, pb.tree, gamma=1.0, factor_form=PN,
+                    precision=rn.RN_PREC_FP32)
+    assert fac.info()["block_threads"] == 128
+    u, x = dual_gradient(fac, pb, w)
+    fac.close()
+    assert rel_err(u, u_o) <= 2e-4 and rel_err(x, x_o) <= 2e-4
+    for prec in (rn.RN_PREC_FP64, rn.RN_PREC_MIXED):
+        with pytest.raises(B.RapidNetError) as ei:
+            rn.Factor(pb.net, pb.cost, pb.tree, gamma=1.0, factor_form=PN, precision=prec)
+        assert ei.value.status == B.RN_ERR_UNSUPPORTED
+        assert "shared memory" in rn.rapidnet_last_error()
