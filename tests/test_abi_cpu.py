@@ -76,9 +76,9 @@ def _args(pb, **over):
     return net, cost, tree
 
 
-def _factor_status(net, cost, tree):
+def _factor_status(net, cost, tree, **kw):
     try:
-        f = rn.Factor(net, cost, tree, gamma=1.0)
+        f = rn.Factor(net, cost, tree, gamma=1.0, **kw)
         f.close()
         return B.RN_OK
     except B.RapidNetError as e:
@@ -134,6 +134,18 @@ def test_validation_errors_before_cuda(lib):
     pb7.net.B = pb7.net.B.copy()
     pb7.net.B[0, 0] = np.nan
     assert _factor_status(pb7.net, pb7.cost, pb7.tree) == B.RN_ERR_INVAL
+
+
+def test_empty_horizon_is_refused_by_both_forms(lib):
+    """A tree of the root alone (N = 0: no decision after the current one)
+    has nothing to iterate over: both factor forms refuse it with
+    RN_ERR_INVAL before any CUDA call."""
+    pb = make_problem("tiny")
+    tree = make_tree([], seed=3)
+    assert tree.N == 0 and tree.n_nodes == 1
+    for form in (rn.RN_FACTOR_SHARED, rn.RN_FACTOR_PER_NODE, rn.RN_FACTOR_AUTO):
+        assert _factor_status(pb.net, pb.cost, tree, factor_form=form) == B.RN_ERR_INVAL
+        assert "N >= 1" in rn.rapidnet_last_error()
 
 
 def test_valid_input_reaches_cuda_or_succeeds(lib):
