@@ -73,8 +73,10 @@ typedef enum {
  *                      launch fills the device), no batched solves, no
  *                      duality gap, no allocation-free entry point;
  *   RN_FACTOR_AUTO (0) the shared form, or the per-node form for A != I,
- *                      RN_PREC_FP32, or a layout the shared form refuses
- *                      (RN_PREC_FP64 and RN_PREC_MIXED). */
+ *                      RN_PREC_FP32, or (RN_PREC_FP64) a layout the
+ *                      shared form refuses; RN_PREC_MIXED keeps that
+ *                      refusal (RN_ERR_UNSUPPORTED), which tells a batched
+ *                      caller that the problem is outside solve_batch. */
 enum { RN_FACTOR_AUTO = 0, RN_FACTOR_SHARED = 1, RN_FACTOR_PER_NODE = 2 };
 
 /* Water network, paper §2.1 (eqs. dynamics, input-disturbance-coupling,

@@ -1633,7 +1633,7 @@ extern "C" int rapidnet_factor(const rn_network *net, const rn_tree *tree, const
   int rc = per_node ? pernode_impl(net, tree, cost, opts, f.get())
                     : factor_impl(net, tree, cost, opts, f.get());
   if (rc == RN_ERR_UNSUPPORTED && form == RN_FACTOR_AUTO && !per_node &&
-      prec != RN_PREC_FP32) {
+      prec == RN_PREC_FP64) {
     // outside what the shared-operator form lays out: the per-node form
     const std::string why = rapidnet_last_error();
     f.reset(new (std::nothrow) rn_factor());

@@ -292,8 +292,8 @@ extern "C" int rapidnet_server_add_model(rn_server *sv, const rn_network *net,
   m->cost = rn_cost{cost->W_alpha, ptr(m->alpha0), ptr(m->Wu), cost->Ws, cost->Wx};
   m->opts = opts ? *opts : rn_opts{};
   // RN_FACTOR_AUTO as in rapidnet_factor: the shared-operator kernels
-  // wherever they apply, else (A != I, a refused layout, RN_PREC_FP32) the
-  // per-node form, whose solves occupy the whole device with one
+  // wherever they apply, else (A != I, RN_PREC_FP32, a refused layout in
+  // FP64) the per-node form, whose solves occupy the whole device with one
   // cooperative launch each and so run one at a time
   m->nx = nx;
   m->nu = nu;

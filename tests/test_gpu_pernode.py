@@ -482,10 +482,11 @@ def test_mixed_precision_warm_start_simple_rule():
 
 @pytest.mark.parametrize("precision", [rn.RN_PREC_MIXED, rn.RN_PREC_FP64])
 def test_auto_form_falls_back_to_per_node(precision):
-    """RN_FACTOR_AUTO on a network the shared form cannot lay out (A = I,
-    nu = 540 above its 256): factor creation takes the per-node form, in
-    FP64 and in the mixed precision, and the solve matches the oracle (FP64
-    1e-6; mixed 1e-3)."""
+    """A network the shared form cannot lay out (A = I, nu = 540 above its
+    256): in FP64, RN_FACTOR_AUTO takes the per-node form; in the mixed
+    precision it keeps the shared form's refusal (RN_ERR_UNSUPPORTED: the
+    problem is outside solve_batch) and the per-node form is asked for by
+    name.  The solve matches the oracle (FP64 1e-6; mixed 1e-3)."""
     net = make_network(300, 540, 420, 81, seed=3)
     tree = make_tree([2, 2] + [1] * 4, seed=2)
     pb = Problem(net=net, cost=make_cost(net, seed=3), tree=tree,
@@ -493,7 +494,14 @@ def test_auto_form_falls_back_to_per_node(precision):
     P, F, S = oracle_for("wide540", pb)
     gamma = O.step_size(O.power_iteration(P, F, 100))
     ref = O.apg(P, F, S, 300, gamma)
-    fac = rn.Factor(pb.net, pb.cost, pb.tree, gamma=gamma, precision=precision)
+    if precision == rn.RN_PREC_MIXED:
+        with pytest.raises(B.RapidNetError) as ei:
+            rn.Factor(pb.net, pb.cost, pb.tree, gamma=gamma, precision=precision)
+        assert ei.value.status == B.RN_ERR_UNSUPPORTED
+        fac = rn.Factor(pb.net, pb.cost, pb.tree, gamma=gamma, precision=precision,
+                        factor_form=PN)
+    else:
+        fac = rn.Factor(pb.net, pb.cost, pb.tree, gamma=gamma, precision=precision)
     assert fac.info()["factor_form"] == PN
     out = fac.solve(pb.data.x0, pb.data.q, pb.data.demand, pb.data.alpha, max_iters=300)
     fac.close()
